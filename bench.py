@@ -1,0 +1,399 @@
+#!/usr/bin/env python
+"""Benchmark of the contraction path on one or more GB300 GPUs.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is one pass over the plain-method workload of the three classes, in
+FP64 with the planner's automatic mapping:
+  (i)   C[a,b,c,d] = sum_{i,j} A[a,i,j,b] B[i,j,c,d], extents 64  (Class 3.2, GEMM)
+  (ii)  C[a,b,c,d] = sum_{i,j} A[i,a,j,b] B[j,c,i,d], extents 48  (Class 3.1, fused permute)
+  (iii) C[a,b]     = sum_i     A[a,i,b]   B[i], a=b=1024, i=2048  (Class 2, GEMV)
+Inputs are seeded uniform[-1,1) values (synthetic: the paper publishes no
+data).  The L2 cache is flushed (256 MiB write) between timed steps, outside
+the timed region.  Rank 0 prints one JSON line.
+
+--impl reference times the CPU oracle (the plain FP64 loop nest) on the
+host's cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import tcsynth as ts  # noqa: E402
+
+METRIC = ("contraction TFLOP/s & % roofline vs plain FP64 path at ≤1e-6 rel err; "
+          "selector regret")
+WORKLOAD = "plain FP64, three classes: (i) direct GEMM 64^6, (ii) fused permute 48^6, (iii) GEMV 1024x2048x1024"
+N_SMS = 152
+FP64_FLOP_PER_CLK_SM = 4     # nominal 1.25 TFLOP/s = 152 SMs x 4 flop/clk x 2.07 GHz
+L2_FLUSH_BYTES = 256 << 20
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def workloads(alloc=None):
+    return [ts.direct_gemm_64(), ts.fused_permute_48(), ts.gemv_1024_full(alloc=alloc)]
+
+
+def read_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], swp=parts[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for k, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                            ("swt", "sw_thermal_slowdown"), ("swp", "sw_power_cap")):
+                if r[k].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median([r["sm"] for r in rows])),
+                "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ------------------------------------------------------------- CPU oracle
+def oracle_sample_problems(target_s: float, nthreads: int):
+    """Bounded samples of the three contractions for the CPU oracle: the last
+    free label of C is cut to s values, s chosen so each takes ~target_s."""
+    import oracle
+    full = [ts.direct_gemm_64(), ts.fused_permute_48(), None]
+    out = []
+    for j, p in enumerate(full):
+        def cut(s, p=p, j=j):
+            if j == 2:
+                q = ts.gemv_1024_full(b=s)
+                return q
+            lastc = p.C.labels[-1]
+            q = ts.Problem(p.name, p.A, p.B, p.C)
+            for name in ("A", "B", "C"):
+                t = getattr(p, name)
+                if lastc in t.labels:
+                    k = t.labels.index(lastc)
+                    ext = list(t.extents)
+                    ext[k] = s
+                    n = ts.span(ext, t.strides)
+                    setattr(q, name, ts.Tensor(t.labels, ext, t.strides, t.data[:n]))
+            return q
+        maxs = 1024 if j == 2 else p.C.extents[-1]
+        q = cut(1)
+        t0 = time.perf_counter()
+        oracle.contract_problem(q, nthreads=nthreads)
+        t1 = max(time.perf_counter() - t0, 1e-4)
+        s = int(max(1, min(maxs, round(target_s / t1))))
+        out.append(cut(s))
+    return out
+
+
+def time_oracle(problems, nthreads):
+    import oracle
+    t0 = time.perf_counter()
+    for q in problems:
+        oracle.contract_problem(q, nthreads=nthreads)
+    return time.perf_counter() - t0
+
+
+def cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def sample_desc(problems):
+    return "; ".join(f"{q.name} with last output index cut to {q.C.extents[-1]}"
+                     for q in problems)
+
+
+def run_reference(args):
+    rank, _, world = env_rank()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    nth = cores()
+    probs = oracle_sample_problems(1.5, nth)
+    flops = sum(q.flops() for q in probs)
+    for _ in range(args.warmup):
+        time_oracle(probs, nth)
+    times = [time_oracle(probs, nth) for _ in range(args.steps)]
+    total = sum(times)
+    value = flops * len(times) / total / 1e12
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "bounded CPU sample per step"},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": nth, "kind": "oracle",
+                         "sample": sample_desc(probs)},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- GPU arm
+def launches_of(info) -> int:
+    n = 2 if (info.kernel == 4 and info.M * info.N * info.batch == 1) else 1
+    return n + (1 if info.mapping == 4 else 0)
+
+
+def run_ours(args):
+    import torch
+    rank, local_rank, world = env_rank()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_1307_2100_gb300 import build as _b
+    _b.build()
+    from paper_1307_2100_gb300 import Contraction, tc
+
+    def pinned(n, dtype):
+        t = torch.empty(n, dtype=torch.float64 if dtype == np.float64 else torch.float32,
+                        pin_memory=True)
+        return t.numpy()
+
+    probs = workloads(alloc=pinned)
+    plans, dA, dB, dC = [], [], [], []
+    for p in probs:
+        pl = Contraction((p.A.labels, p.A.extents, p.A.strides),
+                         (p.B.labels, p.B.extents, p.B.strides),
+                         (p.C.labels, p.C.extents, p.C.strides), "f64", "fp64", "auto")
+        plans.append(pl)
+        dA.append(torch.from_numpy(np.ascontiguousarray(p.A.data)).to(dev))
+        dB.append(torch.from_numpy(np.ascontiguousarray(p.B.data)).to(dev))
+        dC.append(torch.empty(p.C.data.size, dtype=torch.float64, device=dev))
+    def host_pinned(a):
+        t = torch.from_numpy(a)
+        return t if t.is_pinned() else t.pin_memory()
+
+    hA = [host_pinned(p.A.data) for p in probs]
+    hB = [host_pinned(p.B.data) for p in probs]
+    hC = [torch.empty(c.numel(), dtype=c.dtype, pin_memory=True) for c in dC]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+    ws = [pl.workspace(dev) for pl in plans]
+
+    def contract(j):
+        w = ws[j]
+        tc.tc_contract(plans[j].handle, 1.0, dA[j].data_ptr(), dB[j].data_ptr(), 0.0,
+                       dC[j].data_ptr(), w.data_ptr() if w is not None else 0,
+                       w.numel() if w is not None else 0, sptr)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    nprob = len(probs)
+    for _ in range(args.warmup):
+        for j in range(nprob):
+            contract(j)
+    torch.cuda.synchronize()
+    if tc.tc_device_status(sptr) != tc.TC_OK:
+        raise RuntimeError("device status not ok after warm-up")
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(nprob)] for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()                     # L2 flush, outside the events
+        for j in range(nprob):
+            ev[k][j][0].record(stream)
+            contract(j)
+            ev[k][j][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+
+    per = np.array([[ev[k][j][0].elapsed_time(ev[k][j][1]) for j in range(nprob)]
+                    for k in range(args.steps)])        # ms
+    step_ms = per.sum(axis=1)
+    total_ms = float(step_ms.sum())
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    flops_step = sum(p.flops() for p in probs)
+    value = world * flops_step * args.steps / (total_ms / 1e3) / 1e12
+
+    # ---- e2e: host buffers, copies inside the timed region
+    h2d = sum(p.A.data.nbytes + p.B.data.nbytes for p in probs)
+    d2h = sum(c.numel() * c.element_size() for c in dC)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        for j in range(nprob):
+            dA[j].copy_(hA[j], non_blocking=True)
+            dB[j].copy_(hB[j], non_blocking=True)
+            contract(j)
+            hC[j].copy_(dC[j], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * flops_step * args.steps / (e2e_ms / 1e3) / 1e12
+    status = tc.tc_device_status(sptr)
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
+
+    peaks = read_peaks()
+    hbm = peaks.get("hbm_gbs", 6784.5)
+    sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp64_peak = N_SMS * FP64_FLOP_PER_CLK_SM * sm_mhz * 1e6 / 1e12  # TFLOP/s
+    parts = []
+    for j, p in enumerate(probs):
+        info = plans[j].info
+        kms = float(per[:, j].mean())
+        t_alu = p.flops() / (fp64_peak * 1e12)
+        t_mem = p.min_bytes() / (hbm * 1e9)
+        bound = "alu" if t_alu >= t_mem else "hbm"
+        achieved = p.flops() / (kms / 1e3) / 1e12 if bound == "alu" else \
+            p.min_bytes() / (kms / 1e3) / 1e9
+        peak = fp64_peak if bound == "alu" else hbm
+        parts.append({"name": p.name, "class": int(info.cls),
+                      "mapping": tc.MAPPING_NAME[info.mapping],
+                      "kernel": tc.KERNEL_NAME[info.kernel], "ms": kms,
+                      "tflops": p.flops() / (kms / 1e3) / 1e12,
+                      "bound": bound, "achieved": achieved, "peak": peak,
+                      "unit": "TFLOP/s" if bound == "alu" else "GB/s",
+                      "frac": achieved / peak,
+                      "roofline_ms": 1e3 * max(t_alu, t_mem)})
+    dom = max(parts, key=lambda d: d["ms"])
+    traffic = None
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded uniform[-1,1), shapes of the paper's Eq. xy and Class 2)",
+        "config": {"workload": WORKLOAD, "mapping": "auto (recipe)", "math": "fp64",
+                   "l2": "flushed between steps (256 MiB write, outside timing)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": dom["bound"], "kernel": dom["kernel"], "workload": dom["name"],
+                     "achieved": dom["achieved"], "peak": dom["peak"], "unit": dom["unit"],
+                     "frac": dom["frac"], "traffic": traffic,
+                     "peak_source": ("derived: 152 SMs x 4 FP64 flop/clk x median SM clock "
+                                     f"{sm_mhz:.0f} MHz" if dom["bound"] == "alu"
+                                     else "measured hbm_gbs (MEASURED_PEAKS.json)")},
+        "parts": parts,
+        "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms / args.steps},
+        "gpu_launches": int(args.steps * sum(launches_of(pl.info) for pl in plans)),
+        "clocks": clk,
+        "device_status": tc.tc_status_string(status),
+        "wall_s": wall,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        nth = cores()
+        sprobs = oracle_sample_problems(3.0, nth)
+        t = time_oracle(sprobs, nth)
+        line["cpu_baseline"] = {"value": sum(q.flops() for q in sprobs) / t / 1e12,
+                                "unit": "TFLOP/s", "cores": nth, "kind": "oracle",
+                                "sample": sample_desc(sprobs), "seconds": t}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

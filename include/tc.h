@@ -1,0 +1,168 @@
+/*
+ * tc.h -- binary dense tensor contraction on one GB300 GPU (sm_103a).
+ *
+ * The operation (Sec. 2.1 "c_ij = sum_h a_ih b_hj", generalised to tensors of
+ * any order in Sec. 2.3 and the Appendix): given tensors A and B whose indices
+ * carry labels, every label present in both A and B is contracted (summed over
+ * its range) and the remaining labels index the result,
+ *
+ *     C[free_A u free_B] = alpha * sum_{contracted} A * B  +  beta * C.
+ *
+ * Storage (Sec. 2.1 "stride", Sec. 2.4): each tensor is described by its
+ * labels, extents and strides counted in elements; NULL strides mean
+ * column-major (first index stride 1).  Any positive strides are accepted for
+ * A and B; C's strides must not alias (no two index tuples may share an
+ * element).
+ *
+ * The library sorts each contraction into the paper's classes by index
+ * placement and strides (Sec. 3.2: Class 1 = DOT, Class 2 = GEMV, Class 3.1 =
+ * COPY+GEMM, Class 3.2 = GEMM) and maps it onto its own CUDA kernels.  All
+ * device buffers and streams belong to the caller; plans are host objects.
+ *
+ * Errors: every function returns a tc_status; nothing aborts.  Invalid input
+ * is rejected before any launch.  Device-side waits are bounded: a wait that
+ * runs out records TC_ERR_TIMEOUT in a device flag, reported by
+ * tc_device_status().
+ */
+#ifndef TC_H
+#define TC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TC_MAX_ORDER 12   /* indices per tensor */
+
+typedef enum {
+  TC_OK = 0,
+  TC_ERR_INVALID_ARG = 1,     /* null pointer, negative extent, order out of range */
+  TC_ERR_LABEL = 2,           /* repeated label, label of C not in exactly one operand,
+                                 label of A/B in neither C nor the other operand */
+  TC_ERR_EXTENT_MISMATCH = 3, /* a label has different extents in two tensors */
+  TC_ERR_STRIDE = 4,          /* non-positive stride (extent > 1) or aliasing output */
+  TC_ERR_UNSUPPORTED = 5,     /* label in A, B and C; dtype/math/mapping combination */
+  TC_ERR_WORKSPACE = 6,       /* workspace missing or smaller than tc_plan_info.workspace */
+  TC_ERR_CUDA = 7,            /* a CUDA call failed */
+  TC_ERR_TIMEOUT = 8,         /* a bounded device wait ran out */
+  TC_ERR_NO_SELECTOR = 9      /* no selector weights loaded */
+} tc_status;
+
+/* Storage type of A, B and C. */
+typedef enum { TC_F64 = 0, TC_F32 = 1 } tc_dtype;
+
+/* Arithmetic of the contraction.
+ *   TC_MATH_FP64     FP64 inputs, FP64 multiply-add (the plain path; the paper
+ *                    computes in double precision, Sec. 4).
+ *   TC_MATH_FP32     FP32 inputs, FP32 multiply-add on the CUDA cores.
+ *   TC_MATH_BF16     FP32 inputs rounded to BF16, tensor-core products,
+ *                    FP32 accumulation.
+ *   TC_MATH_BF16X3   FP32 inputs split into 2 BF16 terms; the 3 products of
+ *                    order <= 1 on tensor cores.
+ *   TC_MATH_BF16X6   FP32 inputs split into 3 BF16 terms; the 6 products of
+ *                    order <= 2 on tensor cores (FP32-class accuracy). */
+typedef enum {
+  TC_MATH_FP64 = 0,
+  TC_MATH_FP32 = 1,
+  TC_MATH_BF16 = 2,
+  TC_MATH_BF16X3 = 3,
+  TC_MATH_BF16X6 = 4
+} tc_math;
+
+/* How the contraction is mapped onto kernels.
+ *   TC_MAP_AUTO        the selector if weights are loaded, else TC_MAP_RECIPE.
+ *   TC_MAP_RECIPE      the paper's class -> kernel family (Sec. 3.2 recipes):
+ *                      Class 3 -> GEMM (fused loader, so Class 3.1 needs no copy),
+ *                      Class 2 -> GEMV, Class 1 -> DOT.
+ *   TC_MAP_SLICE_GEMM  the Class 3 recipe's slicing literally: the two stride-1
+ *                      indices and one free index per operand stay unsliced, every
+ *                      other free index becomes a batch of GEMMs, every other
+ *                      contracted index is accumulated (Sec. 3.1 R1-R3, Sec. 3.2.3).
+ *   TC_MAP_FUSED_GEMM  one GEMM: M = all free indices of A, N = all free
+ *                      indices of B, K = all contracted indices, gathered by the
+ *                      kernel's loader (no copy pass).
+ *   TC_MAP_COPY_GEMM   explicit COPY+GEMM (Sec. 3.1 F1): the operand whose stride-1
+ *                      index is sliced is first permuted into workspace.
+ *   TC_MAP_GEMV        matrix-vector products (Sec. 3.2.2); for Class 3 one GEMV per
+ *                      value of B's free indices (slicing (c) of Sec. 2.4).
+ *   TC_MAP_DOT         one inner product per output element (Sec. 3.2.1, F3). */
+typedef enum {
+  TC_MAP_AUTO = 0,
+  TC_MAP_RECIPE = 1,
+  TC_MAP_SLICE_GEMM = 2,
+  TC_MAP_FUSED_GEMM = 3,
+  TC_MAP_COPY_GEMM = 4,
+  TC_MAP_GEMV = 5,
+  TC_MAP_DOT = 6
+} tc_mapping;
+
+/* A tensor: `order` indices with labels (distinct int32 values), extents
+ * (>= 0) and strides in elements (NULL = column-major).  The arrays are read
+ * during tc_plan only. */
+typedef struct {
+  int32_t order;
+  const int32_t* labels;
+  const int64_t* extents;
+  const int64_t* strides;
+} tc_tensor_desc;
+
+typedef struct tc_plan_s* tc_plan_t;
+
+/* What tc_plan decided.  Slicing vectors (Sec. 2.4): bit i of slice_a is 1 when
+ * index i of A is sliced (looped over) in the recipe's slicing; indices of
+ * extent 1 are reported as sliced. */
+typedef struct {
+  int32_t cls;           /* 1, 2, 31 (Class 3.1) or 32 (Class 3.2) (Sec. 3.2) */
+  int32_t p;             /* number of contracted indices of extent > 1 */
+  int32_t delta_a;       /* Delta(A) = N(A) - p, indices of extent > 1 (Sec. 3.2) */
+  int32_t delta_b;
+  int32_t stride1_a;     /* label of A's stride-1 index, -1 if none */
+  int32_t stride1_b;
+  uint32_t slice_a;      /* recipe slicing vector s(A) */
+  uint32_t slice_b;      /* recipe slicing vector s(B) */
+  int32_t mapping;       /* tc_mapping in use (never AUTO or RECIPE) */
+  int32_t kernel;        /* kernel family: 1 GEMM-SIMT, 2 GEMM-tcgen05, 3 GEMV, 4 DOT */
+  int32_t tile;          /* tile configuration index of that kernel */
+  int32_t swapped;       /* 1 when the kernel's first operand is B */
+  int64_t M, N, K, batch;   /* GEMM view after mode merging */
+  double flops;          /* 2 * product of all extents */
+  double min_bytes;      /* |A| + |B| + |C| (+|C| if beta may be non-zero) in bytes */
+  size_t workspace;      /* bytes of device workspace tc_contract needs */
+} tc_plan_info;
+
+/* Build a plan (host only; no device work).  `mapping` forces a mapping
+ * (TC_ERR_UNSUPPORTED if it cannot compute this contraction); `tile` forces a
+ * tile configuration, -1 = default.  On success *out owns a new plan. */
+tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* A, const tc_tensor_desc* B,
+                  const tc_tensor_desc* C, tc_dtype dtype, tc_math math,
+                  tc_mapping mapping, int32_t tile);
+
+/* Copy the plan's decisions into *info. */
+tc_status tc_plan_get_info(tc_plan_t plan, tc_plan_info* info);
+
+/* Free a plan (NULL is allowed). */
+tc_status tc_plan_destroy(tc_plan_t plan);
+
+/* Run the contraction asynchronously on `stream` (a cudaStream_t; NULL = the
+ * legacy default stream).  A, B, C are device pointers to elements of the
+ * plan's dtype laid out as described at tc_plan time; C is read only when
+ * beta != 0.  `workspace` is device memory of at least
+ * tc_plan_info.workspace bytes (may be NULL when that is 0).  Allocates
+ * nothing; may be captured in a CUDA graph. */
+tc_status tc_contract(tc_plan_t plan, double alpha, const void* A, const void* B, double beta,
+                      void* C, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Reads and clears the device error flag of the current device after
+ * synchronising `stream`: TC_ERR_TIMEOUT if a bounded device wait ran out
+ * since the last call, else TC_OK. */
+tc_status tc_device_status(void* stream);
+
+/* Static description of a status code. */
+const char* tc_status_string(tc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TC_H */

@@ -1,0 +1,69 @@
+// contract.cu -- tc_contract: run a plan's kernels on the caller's stream.
+#include <cuda_runtime.h>
+
+#include "tc_internal.h"
+
+namespace tc {
+
+// Set by kernels whose bounded waits ran out; read and cleared by
+// tc_device_status().
+__device__ int g_device_status = 0;
+
+}  // namespace tc
+
+using namespace tc;
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+extern "C" tc_status tc_contract(tc_plan_t plan, double alpha, const void* A, const void* B,
+                                 double beta, void* C, void* workspace, size_t ws_bytes,
+                                 void* stream) {
+  if (!plan) return TC_ERR_INVALID_ARG;
+  const Plan* P = reinterpret_cast<const Plan*>(plan);
+  if (P->empty_out) return TC_OK;
+  if (!C) return TC_ERR_INVALID_ARG;
+  if (P->workspace > 0 && (!workspace || ws_bytes < P->workspace)) return TC_ERR_WORKSPACE;
+  if (P->empty_k || alpha == 0.0)
+    return launch_scale(P->gc, C, beta, P->dtype, P->c_elems_span, stream);
+  if (!A || !B) return TC_ERR_INVALID_ARG;
+
+  GemmArgs a = P->args;
+  a.A = P->swapped ? B : A;
+  a.B = P->swapped ? A : B;
+  a.C = C;
+  a.alpha = alpha;
+  a.beta = beta;
+  char* ws = static_cast<char*>(workspace);
+  const uint64_t outs = (uint64_t)a.M * (uint64_t)a.N * (uint64_t)a.nbatch;
+  if (P->kernel == K_DOT && outs == 1) {
+    a.ws = ws;
+    ws += align256((size_t)dot_partials(a, P->tile) * 8);
+  }
+  tc_status st;
+  if (P->copy_which) {
+    PermArgs pa = P->perm;
+    pa.in = P->copy_which == 1 ? a.A : a.B;
+    pa.out = ws;
+    if ((st = launch_perm(pa, P->dtype, stream)) != TC_OK) return st;
+    if (P->copy_which == 1) a.A = ws; else a.B = ws;
+  }
+  switch (P->kernel) {
+    case K_GEMM_SIMT: return launch_gemm_simt(a, P->dtype, P->tile, stream);
+    case K_GEMV: return launch_gemv(a, P->dtype, P->tile, stream);
+    case K_DOT: return launch_dot(a, P->dtype, P->tile, stream);
+    default: return TC_ERR_UNSUPPORTED;
+  }
+}
+
+extern "C" tc_status tc_device_status(void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int h = 0;
+  const int zero = 0;
+  if (cudaMemcpyFromSymbolAsync(&h, g_device_status, sizeof(int), 0, cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaMemcpyToSymbolAsync(g_device_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return TC_ERR_CUDA;
+  return h ? TC_ERR_TIMEOUT : TC_OK;
+}

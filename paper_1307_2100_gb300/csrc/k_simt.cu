@@ -1,0 +1,558 @@
+// k_simt.cu -- CUDA-core kernels: the plain FP64 (and FP32) GEMM over gathered
+// index groups, GEMV, DOT, the permute kernel of the explicit COPY baseline,
+// and C = beta * C.
+//
+// Every kernel addresses its operands through index groups (tc_internal.h):
+// a group index is split column-major into its labels and each label adds
+// idx * stride.  This is how one kernel serves every slicing of Sec. 2.4:
+// the tile loaders gather the rows and columns of A and B wherever their
+// strides put them, so no slice is ever copied (Sec. 3.1 F1 is avoided).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+
+#include "tc_internal.h"
+
+namespace tc {
+
+// Offset of group index `idx` in tensor slot `t` (0 = first operand, 1 =
+// second operand, 2 = C).  Groups are < 2^31 elements, so 32-bit division.
+__device__ __forceinline__ int64_t goff(const Group& g, int t, uint32_t idx) {
+  if (g.n == 1) return (int64_t)idx * g.st[t][0];
+  int64_t off = 0;
+  for (int i = 0; i < g.n; ++i) {
+    uint32_t e = (uint32_t)g.ext[i];
+    uint32_t q = idx / e;
+    off += (int64_t)(idx - q * e) * g.st[t][i];
+    idx = q;
+  }
+  return off;
+}
+
+// Two offsets of one group index at once (first operand and C, etc.).
+__device__ __forceinline__ void goff2(const Group& g, int t0, int t1, uint32_t idx, int64_t& o0,
+                                      int64_t& o1) {
+  o0 = 0;
+  o1 = 0;
+  for (int i = 0; i < g.n; ++i) {
+    uint32_t e = (uint32_t)g.ext[i];
+    uint32_t q = idx / e;
+    uint32_t r = idx - q * e;
+    o0 += (int64_t)r * g.st[t0][i];
+    o1 += (int64_t)r * g.st[t1][i];
+    idx = q;
+  }
+}
+
+__device__ __forceinline__ void goff3(const Group& g, uint32_t idx, int64_t& o0, int64_t& o1,
+                                      int64_t& o2) {
+  o0 = o1 = o2 = 0;
+  for (int i = 0; i < g.n; ++i) {
+    uint32_t e = (uint32_t)g.ext[i];
+    uint32_t q = idx / e;
+    uint32_t r = idx - q * e;
+    o0 += (int64_t)r * g.st[0][i];
+    o1 += (int64_t)r * g.st[1][i];
+    o2 += (int64_t)r * g.st[2][i];
+    idx = q;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// GEMM on the CUDA cores.  CTA tile TM x TN, K step TK, each thread a 4x4
+// register tile (rows ty + i*TM/4, columns tx + j*TN/4).  Tiles are taken in
+// the order (m-tile fastest, n-tile, batch).  The next K block is fetched into
+// registers while the current one is multiplied.
+// ---------------------------------------------------------------------------
+template <typename T, int TM, int TN, int TK>
+__global__ void __launch_bounds__((TM / 4) * (TN / 4))
+    k_gemm_simt(const __grid_constant__ GemmArgs p) {
+  constexpr int NT = (TM / 4) * (TN / 4);
+  constexpr int LA = (TM * TK + NT - 1) / NT;  // A elements loaded per thread
+  constexpr int LB = (TN * TK + NT - 1) / NT;
+  __shared__ T As[TK][TM + 1];
+  __shared__ T Bs[TK][TN + 1];
+  __shared__ int64_t offAm[TM], offCm[TM], offBn[TN], offCn[TN];
+  __shared__ int64_t offAk[2][TK], offBk[2][TK];
+
+  const T* __restrict__ A = static_cast<const T*>(p.A);
+  const T* __restrict__ B = static_cast<const T*>(p.B);
+  T* __restrict__ C = static_cast<T*>(p.C);
+  const int tid = threadIdx.x;
+  const int tx = tid % (TN / 4), ty = tid / (TN / 4);
+  const uint32_t M = (uint32_t)p.M, N = (uint32_t)p.N, K = (uint32_t)p.K;
+  const uint32_t tiles_m = (M + TM - 1) / TM, tiles_n = (N + TN - 1) / TN;
+  const uint64_t total = (uint64_t)tiles_m * tiles_n * (uint64_t)p.nbatch;
+
+  for (uint64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    const uint32_t tm = (uint32_t)(tile % tiles_m);
+    const uint64_t rest = tile / tiles_m;
+    const uint32_t tn = (uint32_t)(rest % tiles_n);
+    const uint32_t b = (uint32_t)(rest / tiles_n);
+    int64_t bA, bB, bC;
+    goff3(p.gb, b, bA, bB, bC);
+
+    __syncthreads();  // previous tile's epilogue is done with the offset tables
+    for (int i = tid; i < TM; i += NT) {
+      uint32_t m = tm * TM + i;
+      int64_t oa = -1, oc = 0;
+      if (m < M) goff2(p.gm, 0, 2, m, oa, oc);
+      offAm[i] = oa;
+      offCm[i] = oc;
+    }
+    for (int i = tid; i < TN; i += NT) {
+      uint32_t n = tn * TN + i;
+      int64_t ob = -1, oc = 0;
+      if (n < N) goff2(p.gn, 1, 2, n, ob, oc);
+      offBn[i] = ob;
+      offCn[i] = oc;
+    }
+    auto k_offsets = [&](int buf, uint32_t k0) {
+      for (int i = tid; i < TK; i += NT) {
+        uint32_t k = k0 + i;
+        int64_t oa = -1, ob = -1;
+        if (k < K) goff2(p.gk, 0, 1, k, oa, ob);
+        offAk[buf][i] = oa;
+        offBk[buf][i] = ob;
+      }
+    };
+    k_offsets(0, 0);
+    __syncthreads();
+
+    T ra[LA], rb[LB];
+    auto fetch = [&](int buf) {
+#pragma unroll
+      for (int r = 0; r < LA; ++r) {
+        int e = tid + r * NT;
+        int ml, kl;
+        if (p.a_contig == CONTIG_MN) { ml = e % TM; kl = e / TM; }
+        else { kl = e % TK; ml = e / TK; }
+        T v = T(0);
+        if (kl < TK && ml < TM) {
+          int64_t om = offAm[ml], ok = offAk[buf][kl];
+          if (om >= 0 && ok >= 0) v = A[bA + om + ok];
+        }
+        ra[r] = v;
+      }
+#pragma unroll
+      for (int r = 0; r < LB; ++r) {
+        int e = tid + r * NT;
+        int nl, kl;
+        if (p.b_contig == CONTIG_MN) { nl = e % TN; kl = e / TN; }
+        else { kl = e % TK; nl = e / TK; }
+        T v = T(0);
+        if (kl < TK && nl < TN) {
+          int64_t on = offBn[nl], ok = offBk[buf][kl];
+          if (on >= 0 && ok >= 0) v = B[bB + on + ok];
+        }
+        rb[r] = v;
+      }
+    };
+    auto stash = [&]() {
+#pragma unroll
+      for (int r = 0; r < LA; ++r) {
+        int e = tid + r * NT;
+        int ml, kl;
+        if (p.a_contig == CONTIG_MN) { ml = e % TM; kl = e / TM; }
+        else { kl = e % TK; ml = e / TK; }
+        if (kl < TK && ml < TM) As[kl][ml] = ra[r];
+      }
+#pragma unroll
+      for (int r = 0; r < LB; ++r) {
+        int e = tid + r * NT;
+        int nl, kl;
+        if (p.b_contig == CONTIG_MN) { nl = e % TN; kl = e / TN; }
+        else { kl = e % TK; nl = e / TK; }
+        if (kl < TK && nl < TN) Bs[kl][nl] = rb[r];
+      }
+    };
+
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+
+    const uint32_t nk = (K + TK - 1) / TK;
+    if (nk > 0) fetch(0);
+    for (uint32_t kb = 0; kb < nk; ++kb) {
+      const int buf = kb & 1;
+      __syncthreads();  // everyone is done reading As/Bs of the previous block
+      stash();
+      if (kb + 1 < nk) k_offsets(buf ^ 1, (kb + 1) * TK);
+      __syncthreads();
+      if (kb + 1 < nk) fetch(buf ^ 1);
+#pragma unroll
+      for (int kk = 0; kk < TK; ++kk) {
+        T a[4], bv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + i * (TM / 4)];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + j * (TN / 4)];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
+      }
+    }
+
+    const T alpha = (T)p.alpha, beta = (T)p.beta;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int ml = ty + i * (TM / 4);
+      if (offAm[ml] < 0) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int nl = tx + j * (TN / 4);
+        if (offBn[nl] < 0) continue;
+        T* dst = C + bC + offCm[ml] + offCn[nl];
+        T v = alpha * acc[i][j];
+        if (p.beta != 0.0) v = fma(beta, *dst, v);
+        *dst = v;
+      }
+    }
+  }
+}
+
+struct SimtTile { int tm, tn; };
+static const SimtTile kSimtTiles[] = {{64, 64}, {32, 32}, {128, 64}};
+int num_tiles_simt(tc_dtype) { return 3; }
+
+static int grid_for(uint64_t total) {
+  return (int)std::min<uint64_t>(total, (uint64_t)1 << 30);
+}
+
+template <typename T>
+static tc_status gemm_simt_t(const GemmArgs& a, int tile, cudaStream_t s) {
+  const SimtTile t = kSimtTiles[tile];
+  const uint64_t total = (uint64_t)((a.M + t.tm - 1) / t.tm) * (uint64_t)((a.N + t.tn - 1) / t.tn) *
+                         (uint64_t)a.nbatch;
+  if (total == 0) return TC_OK;
+  const int grid = grid_for(total);
+  if (t.tm == 64 && t.tn == 64)
+    k_gemm_simt<T, 64, 64, 16><<<grid, 256, 0, s>>>(a);
+  else if (t.tm == 32 && t.tn == 32)
+    k_gemm_simt<T, 32, 32, 16><<<grid, 64, 0, s>>>(a);
+  else
+    k_gemm_simt<T, 128, 64, 16><<<grid, 512, 0, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+}
+
+tc_status launch_gemm_simt(const GemmArgs& a, tc_dtype dt, int tile, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return dt == TC_F64 ? gemm_simt_t<double>(a, tile, s) : gemm_simt_t<float>(a, tile, s);
+}
+
+// ---------------------------------------------------------------------------
+// GEMV (Sec. 3.2.2): y[m, n, b] = alpha * sum_k X[m, k, b] * Y[k, n, b] + beta*y.
+// When X is contiguous along m (non-transposed GEMV) each thread owns one m and
+// walks k, consecutive threads reading consecutive addresses; when X is
+// contiguous along k (transposed GEMV) each warp owns one output and its lanes
+// walk k, reduced with warp shuffles.  The k offsets of X and Y are staged in
+// shared memory in chunks.
+// ---------------------------------------------------------------------------
+constexpr int kGemvThreads = 256;
+constexpr int kGemvChunk = 512;
+
+template <typename T>
+__global__ void __launch_bounds__(kGemvThreads) k_gemv_m(const __grid_constant__ GemmArgs p) {
+  __shared__ int64_t oX[kGemvChunk], oY[kGemvChunk];
+  const T* __restrict__ X = static_cast<const T*>(p.A);
+  const T* __restrict__ Y = static_cast<const T*>(p.B);
+  T* __restrict__ Cp = static_cast<T*>(p.C);
+  const uint32_t M = (uint32_t)p.M, N = (uint32_t)p.N, K = (uint32_t)p.K;
+  const uint64_t mblocks = (M + kGemvThreads - 1) / kGemvThreads;
+  const uint64_t total = mblocks * (uint64_t)N * (uint64_t)p.nbatch;
+  for (uint64_t blk = blockIdx.x; blk < total; blk += gridDim.x) {
+    const uint32_t m = (uint32_t)(blk % mblocks) * kGemvThreads + threadIdx.x;
+    const uint64_t nb = blk / mblocks;  // (n, b) pair
+    const uint32_t n = (uint32_t)(nb % N), b = (uint32_t)(nb / N);
+    int64_t bX, bY, bC, oYn, oCn, oXm = 0, oCm = 0;
+    goff3(p.gb, b, bX, bY, bC);
+    goff2(p.gn, 1, 2, n, oYn, oCn);
+    if (m < M) goff2(p.gm, 0, 2, m, oXm, oCm);
+    const T* xrow = X + bX + oXm;
+    const T* yv = Y + bY + oYn;
+    T acc = T(0);
+    for (uint32_t k0 = 0; k0 < K; k0 += kGemvChunk) {
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < kGemvChunk; i += kGemvThreads) {
+        uint32_t k = k0 + i;
+        int64_t ox = 0, oy = 0;
+        if (k < K) goff2(p.gk, 0, 1, k, ox, oy);
+        oX[i] = ox;
+        oY[i] = oy;
+      }
+      __syncthreads();
+      const uint32_t kn = min((uint32_t)kGemvChunk, K - k0);
+      if (m < M) {
+        uint32_t i = 0;
+        for (; i + 8 <= kn; i += 8) {
+          T xv[8], yy[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) xv[u] = xrow[oX[i + u]];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) yy[u] = yv[oY[i + u]];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) acc = fma(xv[u], yy[u], acc);
+        }
+        for (; i < kn; ++i) acc = fma(xrow[oX[i]], yv[oY[i]], acc);
+      }
+    }
+    if (m < M) {
+      T* dst = Cp + bC + oCm + oCn;
+      T v = (T)p.alpha * acc;
+      if (p.beta != 0.0) v = fma((T)p.beta, *dst, v);
+      *dst = v;
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One warp per output (m, n, b); lanes stride over k.  Used by the transposed
+// GEMV and by the DOT mapping (Sec. 3.2.1: one inner product per output).
+template <typename T>
+__global__ void __launch_bounds__(256) k_dot_rows(const __grid_constant__ GemmArgs p) {
+  const T* __restrict__ X = static_cast<const T*>(p.A);
+  const T* __restrict__ Y = static_cast<const T*>(p.B);
+  T* __restrict__ Cp = static_cast<T*>(p.C);
+  const uint32_t M = (uint32_t)p.M, N = (uint32_t)p.N, K = (uint32_t)p.K;
+  const uint64_t total = (uint64_t)M * N * (uint64_t)p.nbatch;
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t w = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); w < total;
+       w += warps) {
+    const uint32_t m = (uint32_t)(w % M);
+    const uint64_t r = w / M;
+    const uint32_t n = (uint32_t)(r % N), b = (uint32_t)(r / N);
+    int64_t bX, bY, bC, oXm, oCm, oYn, oCn;
+    goff3(p.gb, b, bX, bY, bC);
+    goff2(p.gm, 0, 2, m, oXm, oCm);
+    goff2(p.gn, 1, 2, n, oYn, oCn);
+    const T* xr = X + bX + oXm;
+    const T* yr = Y + bY + oYn;
+    T acc = T(0);
+    for (uint32_t k = lane; k < K; k += 32) {
+      int64_t ox, oy;
+      goff2(p.gk, 0, 1, k, ox, oy);
+      acc = fma(xr[ox], yr[oy], acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      T* dst = Cp + bC + oCm + oCn;
+      T v = (T)p.alpha * acc;
+      if (p.beta != 0.0) v = fma((T)p.beta, *dst, v);
+      *dst = v;
+    }
+  }
+}
+
+int num_tiles_gemv() { return 1; }
+
+template <typename T>
+static tc_status gemv_t(const GemmArgs& a, cudaStream_t s) {
+  const uint64_t outs = (uint64_t)a.N * (uint64_t)a.nbatch;
+  if (a.M == 0 || outs == 0) return TC_OK;
+  if (a.a_contig == CONTIG_K) {
+    const uint64_t warps = (uint64_t)a.M * outs;
+    const int grid = grid_for((warps + 7) / 8);
+    k_dot_rows<T><<<grid, 256, 0, s>>>(a);
+  } else {
+    const uint64_t blocks = (uint64_t)((a.M + kGemvThreads - 1) / kGemvThreads) * outs;
+    k_gemv_m<T><<<grid_for(blocks), kGemvThreads, 0, s>>>(a);
+  }
+  return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+}
+
+tc_status launch_gemv(const GemmArgs& a, tc_dtype dt, int, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return dt == TC_F64 ? gemv_t<double>(a, s) : gemv_t<float>(a, s);
+}
+
+// ---------------------------------------------------------------------------
+// DOT.  Many outputs: one warp each (k_dot_rows).  A single output (Class 1,
+// Sec. 3.2.1: all indices contracted, a scalar result): every CTA sums a
+// grid-strided share of k into one partial in the workspace, then one CTA adds
+// the partials in index order (deterministic) and applies alpha and beta.
+// ---------------------------------------------------------------------------
+constexpr int kDotThreads = 256;
+constexpr int kDotBlocks = 152 * 4;
+
+int dot_partials(const GemmArgs&, int) { return kDotBlocks; }
+
+template <typename T>
+__global__ void __launch_bounds__(kDotThreads) k_dot_partial(const __grid_constant__ GemmArgs p) {
+  __shared__ double red[kDotThreads / 32];
+  const T* __restrict__ X = static_cast<const T*>(p.A);
+  const T* __restrict__ Y = static_cast<const T*>(p.B);
+  const uint32_t K = (uint32_t)p.K;
+  double acc = 0.0;
+  const uint32_t stride = gridDim.x * kDotThreads;
+  for (uint32_t k = blockIdx.x * kDotThreads + threadIdx.x; k < K; k += stride) {
+    int64_t ox, oy;
+    goff2(p.gk, 0, 1, k, ox, oy);
+    acc = fma((double)X[ox], (double)Y[oy], acc);
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kDotThreads / 32; ++w) s += red[w];
+    static_cast<double*>(p.ws)[blockIdx.x] = s;
+  }
+}
+
+template <typename T>
+__global__ void k_dot_final(const __grid_constant__ GemmArgs p, int nparts) {
+  __shared__ double red[32];
+  const double* part = static_cast<const double*>(p.ws);
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    T* dst = static_cast<T*>(p.C);
+    double v = p.alpha * t;
+    if (p.beta != 0.0) v += p.beta * (double)*dst;
+    *dst = (T)v;
+  }
+}
+
+template <typename T>
+static tc_status dot_t(const GemmArgs& a, cudaStream_t s) {
+  const uint64_t outs = (uint64_t)a.M * a.N * (uint64_t)a.nbatch;
+  if (outs == 0) return TC_OK;
+  if (outs == 1) {
+    if (!a.ws) return TC_ERR_WORKSPACE;
+    k_dot_partial<T><<<kDotBlocks, kDotThreads, 0, s>>>(a);
+    k_dot_final<T><<<1, 256, 0, s>>>(a, kDotBlocks);
+  } else {
+    k_dot_rows<T><<<grid_for((outs + 7) / 8), 256, 0, s>>>(a);
+  }
+  return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+}
+
+tc_status launch_dot(const GemmArgs& a, tc_dtype dt, int, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return dt == TC_F64 ? dot_t<double>(a, s) : dot_t<float>(a, s);
+}
+
+// ---------------------------------------------------------------------------
+// Permute (the COPY of Sec. 3.1 F1, kept as the explicit baseline).  The
+// output is dense in the group's label order.  When the input's fastest label
+// is not the output's first label the copy is a tiled transpose: a 32x32 tile
+// over (output-first label, input-fastest label) goes through shared memory
+// so that both the reads and the writes are coalesced.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_perm_direct(const __grid_constant__ PermArgs p) {
+  const T* __restrict__ in = static_cast<const T*>(p.in);
+  T* __restrict__ out = static_cast<T*>(p.out);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < (uint64_t)p.total;
+       q += stride) {
+    int64_t oi, oo;
+    goff2(p.g, 0, 2, (uint32_t)q, oi, oo);
+    out[oo] = in[oi];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_perm_tiled(const __grid_constant__ PermArgs p, int li,
+                                                    uint32_t rest_total) {
+  __shared__ T tile[32][33];
+  const T* __restrict__ in = static_cast<const T*>(p.in);
+  T* __restrict__ out = static_cast<T*>(p.out);
+  const uint32_t e0 = (uint32_t)p.g.ext[0], e1 = (uint32_t)p.g.ext[li];
+  const uint32_t t0n = (e0 + 31) / 32, t1n = (e1 + 31) / 32;
+  const uint64_t ntiles = (uint64_t)t0n * t1n * rest_total;
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const uint32_t t0 = (uint32_t)(t % t0n);
+    const uint64_t r1 = t / t0n;
+    const uint32_t t1 = (uint32_t)(r1 % t1n);
+    uint32_t rest = (uint32_t)(r1 / t1n);
+    int64_t bi = 0, bo = 0;
+    for (int i = 1; i < p.g.n; ++i) {  // the other labels, column-major
+      if (i == li) continue;
+      uint32_t e = (uint32_t)p.g.ext[i];
+      uint32_t q = rest / e, r = rest - q * e;
+      bi += (int64_t)r * p.g.st[0][i];
+      bo += (int64_t)r * p.g.st[2][i];
+      rest = q;
+    }
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 32; r += 8) {
+      uint32_t a1 = t1 * 32 + tx, a0 = t0 * 32 + ty + r;  // read: lanes along label li
+      if (a1 < e1 && a0 < e0)
+        tile[ty + r][tx] = in[bi + (int64_t)a1 * p.g.st[0][li] + (int64_t)a0 * p.g.st[0][0]];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 32; r += 8) {
+      uint32_t a0 = t0 * 32 + tx, a1 = t1 * 32 + ty + r;  // write: lanes along label 0
+      if (a0 < e0 && a1 < e1)
+        out[bo + (int64_t)a0 * p.g.st[2][0] + (int64_t)a1 * p.g.st[2][li]] = tile[tx][ty + r];
+    }
+  }
+}
+
+template <typename T>
+static tc_status perm_t(const PermArgs& a, cudaStream_t s) {
+  if (a.total == 0) return TC_OK;
+  int li = 0;
+  for (int i = 1; i < a.g.n; ++i)
+    if (a.g.st[0][i] < a.g.st[0][li]) li = i;
+  if (li == 0 || a.g.st[0][li] != 1) {
+    k_perm_direct<T><<<grid_for((a.total + 255) / 256), 256, 0, s>>>(a);
+  } else {
+    uint64_t rest = 1;
+    for (int i = 1; i < a.g.n; ++i)
+      if (i != li) rest *= (uint64_t)a.g.ext[i];
+    const uint64_t ntiles = ((a.g.ext[0] + 31) / 32) * ((a.g.ext[li] + 31) / 32) * rest;
+    k_perm_tiled<T><<<grid_for(std::min<uint64_t>(ntiles, 152 * 64)), 256, 0, s>>>(a, li,
+                                                                                    (uint32_t)rest);
+  }
+  return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+}
+
+tc_status launch_perm(const PermArgs& a, tc_dtype dt, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return dt == TC_F64 ? perm_t<double>(a, s) : perm_t<float>(a, s);
+}
+
+// C = beta * C over C's own labels (empty contraction or alpha == 0).
+template <typename T>
+__global__ void k_scale(const __grid_constant__ Group g, T* C, double beta, uint64_t total) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < total; q += stride) {
+    T* dst = C + goff(g, 2, (uint32_t)q);
+    *dst = beta == 0.0 ? T(0) : (T)(beta * (double)*dst);
+  }
+}
+
+tc_status launch_scale(const Group& gc, void* C, double beta, tc_dtype dt, int64_t total,
+                       void* stream) {
+  if (total <= 0) return TC_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int grid = grid_for(std::min<uint64_t>((total + 255) / 256, 152 * 32));
+  if (dt == TC_F64)
+    k_scale<double><<<grid, 256, 0, s>>>(gc, static_cast<double*>(C), beta, (uint64_t)total);
+  else
+    k_scale<float><<<grid, 256, 0, s>>>(gc, static_cast<float*>(C), beta, (uint64_t)total);
+  return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+}
+
+}  // namespace tc

@@ -1,0 +1,92 @@
+// tc_internal.h -- plan structures shared by the host planner and the kernels.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "tc.h"
+
+namespace tc {
+
+constexpr int kGroupMax = TC_MAX_ORDER;
+
+// A multi-index group: labels enumerated column-major (first label fastest).
+// st[0], st[1], st[2] are the element strides of each label in the kernel's
+// first operand ("A"), second operand ("B") and in C; 0 where a label is absent.
+struct Group {
+  int32_t n;
+  int32_t pad_;
+  int64_t ext[kGroupMax];
+  int64_t st[3][kGroupMax];
+};
+
+enum Kernel : int32_t { K_NONE = 0, K_GEMM_SIMT = 1, K_GEMM_TC = 2, K_GEMV = 3, K_DOT = 4 };
+
+// Operand contiguity (how the loader can coalesce):
+//   0 = generic gather, 1 = contiguous along the M/N group's first label,
+//   2 = contiguous along the K group's first label.
+enum Contig : int32_t { CONTIG_NONE = 0, CONTIG_MN = 1, CONTIG_K = 2 };
+
+// Kernel arguments of every GEMM-like kernel (passed by value).
+//   C[m, n, b] = alpha * sum_k A[m, k, b] * B[k, n, b] + beta * C[m, n, b]
+// with m, n, k, b multi-indices of the groups gm, gn, gk, gb.
+struct GemmArgs {
+  Group gm, gn, gk, gb;
+  int64_t M, N, K, nbatch;
+  const void* A;
+  const void* B;
+  void* C;
+  double alpha, beta;
+  int32_t a_contig, b_contig;  // Contig of A along (M | K), of B along (N | K)
+  int32_t c_contig_m;          // 1 when C's stride along the first M label is 1
+  int32_t math;                // tc_math
+  void* ws;                    // workspace (DOT partials)
+  int64_t ws_elems;
+};
+
+// Dense permutation (COPY): out[col-major over g, in g's label order] =
+// in[sum idx * st[0]].  st[2] holds the output strides.
+struct PermArgs {
+  Group g;
+  int64_t total;
+  const void* in;
+  void* out;
+};
+
+struct Plan {
+  // decisions reported through tc_plan_info
+  tc_plan_info info;
+  tc_dtype dtype;
+  tc_math math;
+  int32_t mapping;
+  int32_t kernel;
+  int32_t tile;
+  bool swapped;
+  // GEMM view (operands already swapped when `swapped`)
+  GemmArgs args;
+  // COPY+GEMM: permutation of one operand into workspace (0 none, 1 X, 2 Y)
+  int copy_which;
+  PermArgs perm;
+  int64_t copy_elems;
+  // empty output / empty contraction shortcuts
+  bool empty_out;
+  bool empty_k;
+  int64_t c_elems_span;  // C's element span (for beta-only scaling)
+  Group gc;              // C's own labels (for beta-only scaling)
+  size_t workspace;
+};
+
+size_t elem_size(tc_dtype dt);
+
+// Kernel launchers (k_simt.cu); `stream` is a cudaStream_t.
+tc_status launch_gemm_simt(const GemmArgs& a, tc_dtype dt, int tile, void* stream);
+tc_status launch_gemv(const GemmArgs& a, tc_dtype dt, int tile, void* stream);
+tc_status launch_dot(const GemmArgs& a, tc_dtype dt, int tile, void* stream);
+tc_status launch_perm(const PermArgs& a, tc_dtype dt, void* stream);
+tc_status launch_scale(const Group& gc, void* C, double beta, tc_dtype dt, int64_t total,
+                       void* stream);
+int dot_partials(const GemmArgs& a, int tile);
+int num_tiles_simt(tc_dtype dt);
+int num_tiles_gemv();
+
+}  // namespace tc

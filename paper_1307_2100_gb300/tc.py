@@ -1,0 +1,148 @@
+"""ctypes binding of libtc.so -- argument marshalling only.
+
+Functions carry the C names (tc_plan, tc_contract, ...).  Device memory and
+streams come from PyTorch; every computation runs in the library's kernels.
+If the shared library is missing this module raises at import: there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtc.so")
+
+TC_OK = 0
+STATUS = {0: "TC_OK", 1: "TC_ERR_INVALID_ARG", 2: "TC_ERR_LABEL", 3: "TC_ERR_EXTENT_MISMATCH",
+          4: "TC_ERR_STRIDE", 5: "TC_ERR_UNSUPPORTED", 6: "TC_ERR_WORKSPACE", 7: "TC_ERR_CUDA",
+          8: "TC_ERR_TIMEOUT", 9: "TC_ERR_NO_SELECTOR"}
+TC_F64, TC_F32 = 0, 1
+MATH = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16x3": 3, "bf16x6": 4}
+MAPPING = {"auto": 0, "recipe": 1, "slice_gemm": 2, "fused_gemm": 3, "copy_gemm": 4, "gemv": 5,
+           "dot": 6}
+MAPPING_NAME = {v: k for k, v in MAPPING.items()}
+KERNEL_NAME = {0: "none", 1: "gemm_simt", 2: "gemm_tc", 3: "gemv", 4: "dot"}
+MAX_ORDER = 12
+
+
+class TcError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}")
+        self.status = status
+
+
+class TensorDesc(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int32),
+                ("labels", ctypes.POINTER(ctypes.c_int32)),
+                ("extents", ctypes.POINTER(ctypes.c_int64)),
+                ("strides", ctypes.POINTER(ctypes.c_int64))]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("cls", ctypes.c_int32), ("p", ctypes.c_int32), ("delta_a", ctypes.c_int32),
+                ("delta_b", ctypes.c_int32), ("stride1_a", ctypes.c_int32),
+                ("stride1_b", ctypes.c_int32), ("slice_a", ctypes.c_uint32),
+                ("slice_b", ctypes.c_uint32), ("mapping", ctypes.c_int32),
+                ("kernel", ctypes.c_int32), ("tile", ctypes.c_int32), ("swapped", ctypes.c_int32),
+                ("M", ctypes.c_int64), ("N", ctypes.c_int64), ("K", ctypes.c_int64),
+                ("batch", ctypes.c_int64), ("flops", ctypes.c_double),
+                ("min_bytes", ctypes.c_double), ("workspace", ctypes.c_size_t)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["mapping_name"] = MAPPING_NAME.get(self.mapping, "?")
+        d["kernel_name"] = KERNEL_NAME.get(self.kernel, "?")
+        return d
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run paper_1307_2100_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    lib.tc_plan.restype = ctypes.c_int
+    lib.tc_plan.argtypes = [ctypes.POINTER(P), ctypes.POINTER(TensorDesc),
+                            ctypes.POINTER(TensorDesc), ctypes.POINTER(TensorDesc), ctypes.c_int,
+                            ctypes.c_int, ctypes.c_int, ctypes.c_int32]
+    lib.tc_plan_get_info.restype = ctypes.c_int
+    lib.tc_plan_get_info.argtypes = [P, ctypes.POINTER(PlanInfo)]
+    lib.tc_plan_destroy.restype = ctypes.c_int
+    lib.tc_plan_destroy.argtypes = [P]
+    lib.tc_contract.restype = ctypes.c_int
+    lib.tc_contract.argtypes = [P, ctypes.c_double, P, P, ctypes.c_double, P, P, ctypes.c_size_t,
+                                P]
+    lib.tc_device_status.restype = ctypes.c_int
+    lib.tc_device_status.argtypes = [P]
+    lib.tc_status_string.restype = ctypes.c_char_p
+    lib.tc_status_string.argtypes = [ctypes.c_int]
+    return lib
+
+
+lib = _load()
+
+
+def make_desc(labels: Sequence[int], extents: Sequence[int],
+              strides: Optional[Sequence[int]] = None):
+    """A TensorDesc plus the ctypes arrays that keep its pointers alive."""
+    n = len(labels)
+    la = (ctypes.c_int32 * max(n, 1))(*[int(x) for x in labels])
+    ex = (ctypes.c_int64 * max(n, 1))(*[int(x) for x in extents])
+    st = (ctypes.c_int64 * max(n, 1))(*[int(x) for x in strides]) if strides is not None else None
+    d = TensorDesc(n, la, ex, st if st is not None else ctypes.POINTER(ctypes.c_int64)())
+    return d, (la, ex, st)
+
+
+def tc_status_string(status: int) -> str:
+    return lib.tc_status_string(int(status)).decode()
+
+
+def tc_plan(A, B, C, dtype: int, math: int, mapping: int = 0, tile: int = -1) -> int:
+    """A, B, C: (labels, extents, strides-or-None).  Returns the plan handle."""
+    dA, kA = make_desc(*A)
+    dB, kB = make_desc(*B)
+    dC, kC = make_desc(*C)
+    out = ctypes.c_void_p()
+    st = lib.tc_plan(ctypes.byref(out), ctypes.byref(dA), ctypes.byref(dB), ctypes.byref(dC),
+                     int(dtype), int(math), int(mapping), int(tile))
+    if st != TC_OK:
+        raise TcError(st, "tc_plan")
+    return out.value
+
+
+def tc_plan_status(A, B, C, dtype: int, math: int, mapping: int = 0, tile: int = -1) -> int:
+    """tc_plan's status code only (the plan, if any, is destroyed)."""
+    try:
+        h = tc_plan(A, B, C, dtype, math, mapping, tile)
+    except TcError as e:
+        return e.status
+    tc_plan_destroy(h)
+    return TC_OK
+
+
+def tc_plan_get_info(plan: int) -> PlanInfo:
+    info = PlanInfo()
+    st = lib.tc_plan_get_info(ctypes.c_void_p(plan), ctypes.byref(info))
+    if st != TC_OK:
+        raise TcError(st, "tc_plan_get_info")
+    return info
+
+
+def tc_plan_destroy(plan: int) -> None:
+    lib.tc_plan_destroy(ctypes.c_void_p(plan))
+
+
+def tc_contract(plan: int, alpha: float, A: int, B: int, beta: float, C: int, workspace: int = 0,
+                workspace_bytes: int = 0, stream: int = 0) -> None:
+    """Pointers are integer device addresses; stream is a cudaStream_t as int."""
+    st = lib.tc_contract(ctypes.c_void_p(plan), float(alpha), ctypes.c_void_p(A),
+                         ctypes.c_void_p(B), float(beta), ctypes.c_void_p(C),
+                         ctypes.c_void_p(workspace), int(workspace_bytes),
+                         ctypes.c_void_p(stream))
+    if st != TC_OK:
+        raise TcError(st, "tc_contract")
+
+
+def tc_device_status(stream: int = 0) -> int:
+    return lib.tc_device_status(ctypes.c_void_p(stream))

@@ -285,3 +285,59 @@ def batching_items(n=512, seed=BASE_SEED + 3, max_elems=1 << 22, max_flops=float
             lc, [ext[l] for l in lc], col_major([ext[l] for l in lc]), np.zeros(0, dtype))
         items.append(Problem(f"batch{len(items)}", A, B, C))
     return items
+
+
+_CHUNK = 1 << 24  # elements per independent stream; fixed so results do not depend on threads
+
+
+def fill_uniform_parallel(seed: int, n: int, dtype=np.float64, lo=-1.0, hi=1.0,
+                          nthreads: int = 0, out: Optional[np.ndarray] = None) -> np.ndarray:
+    """n uniform[lo, hi) values; chunk c (of 2^24 elements) comes from
+    PCG64(seed) jumped c+1 times, so element q depends only on (seed, q): a
+    shorter fill is a prefix of a longer one."""
+    import concurrent.futures as cf
+    import os
+    if out is None:
+        out = np.empty(n, dtype=dtype)
+    nchunks = (n + _CHUNK - 1) // _CHUNK
+    base = np.random.PCG64(seed)
+
+    def work(c):
+        g = np.random.Generator(base.jumped(c + 1))
+        view = out[c * _CHUNK:min(n, (c + 1) * _CHUNK)]
+        if dtype == np.float64:
+            g.random(out=view)
+        else:
+            view[:] = g.random(view.size)
+        view *= (hi - lo)
+        view += lo
+        return c
+
+    nt = nthreads or min(32, os.cpu_count() or 1)
+    with cf.ThreadPoolExecutor(max_workers=nt) as ex:
+        list(ex.map(work, range(nchunks)))
+    return out
+
+
+def big_problem(name, la, lb, lc, extents, seed, dtype=np.float64, alloc=None) -> Problem:
+    """Like `problem` with uniform[-1, 1) entries, filled by fill_uniform_parallel
+    (for operands of many gigabytes).  `alloc(n, dtype)` may supply the buffers
+    (e.g. pinned host memory)."""
+    ext = {lab(k)[0]: int(v) for k, v in extents.items()}
+    tens = []
+    for t, ls in enumerate((la, lb)):
+        ls = lab(ls)
+        e = [ext[l] for l in ls]
+        st = col_major(e)
+        n = span(e, st)
+        buf = alloc(n, dtype) if alloc is not None else None
+        tens.append(Tensor(ls, e, st, fill_uniform_parallel(seed * 16 + t, n, dtype, out=buf)))
+    C = empty_output(lc, ext, dtype)
+    return Problem(name, tens[0], tens[1], C, meta={"seed": seed, "dist": "uniform"})
+
+
+def gemv_1024_full(seed=BASE_SEED + 1, b=1024, alloc=None) -> Problem:
+    """The Class 2 workload at full size: A is 2^31 FP64 values (17.2 GB).
+    A smaller b gives the leading slab of the same tensor."""
+    return big_problem("gemv_1024", "aib", "i", "ab", dict(a=1024, b=b, i=2048), seed + 200,
+                       alloc=alloc)

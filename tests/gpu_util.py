@@ -1,0 +1,100 @@
+"""Helpers of the GPU parity tests: run a tcsynth.Problem through the C ABI and
+compute sampled oracle outputs for problems too large for the full oracle."""
+from __future__ import annotations
+
+import copy
+import itertools
+
+import numpy as np
+
+import oracle
+import tcsynth as ts
+
+TOL_FP64 = 1e-12        # relative Frobenius, FP64 path
+
+
+def addressed_index(t) -> np.ndarray:
+    """Flat buffer positions of every element of tensor t, column-major order."""
+    if t.order == 0:
+        return np.zeros(1, dtype=np.int64)
+    grids = np.meshgrid(*[np.arange(e, dtype=np.int64) * s for e, s in zip(t.extents, t.strides)],
+                        indexing="ij")
+    tot = sum(grids)
+    return np.asarray(tot).reshape(-1, order="F")
+
+
+def run(p, math="fp64", mapping="auto", tile=-1, alpha=None, beta=None, stream=None,
+        plan_out=None):
+    """Run problem p on cuda:0; returns the full C buffer (float64 copy)."""
+    import torch
+    from paper_1307_2100_gb300 import Contraction
+    dt = "f64" if p.A.data.dtype == np.float64 else "f32"
+    alpha = p.alpha if alpha is None else alpha
+    beta = p.beta if beta is None else beta
+    plan = Contraction((p.A.labels, p.A.extents, p.A.strides),
+                       (p.B.labels, p.B.extents, p.B.strides),
+                       (p.C.labels, p.C.extents, p.C.strides), dt, math, mapping, tile)
+    if plan_out is not None:
+        plan_out.append(plan.info.as_dict())
+    dev = torch.device("cuda:0")
+    A = torch.from_numpy(np.ascontiguousarray(p.A.data)).to(dev)
+    B = torch.from_numpy(np.ascontiguousarray(p.B.data)).to(dev)
+    C = torch.from_numpy(np.ascontiguousarray(p.C.data)).to(dev)
+    if A.numel() == 0:
+        A = torch.zeros(1, dtype=C.dtype, device=dev)
+    if B.numel() == 0:
+        B = torch.zeros(1, dtype=C.dtype, device=dev)
+    if C.numel() == 0:
+        C = torch.zeros(1, dtype=A.dtype, device=dev)
+    plan(A, B, C, alpha, beta, stream)
+    torch.cuda.synchronize()
+    out = C.cpu().numpy().astype(np.float64)
+    return out[: p.C.data.size] if p.C.data.size else out[:0]
+
+
+def oracle_full(p, **kw):
+    return oracle.contract_problem(p, **kw)
+
+
+def compare(got, ref, C):
+    """Relative Frobenius error over the addressed elements of C."""
+    idx = addressed_index(C) if C.numel else np.zeros(0, dtype=np.int64)
+    return oracle.rel_fro(got[idx], ref[idx])
+
+
+def sample_outputs(p, samples):
+    """Oracle values of selected output elements: for each output multi-index
+    the free labels are fixed by offsetting A and B and the oracle contracts
+    what remains (the contracted labels) into a scalar."""
+    con = [l for l in p.A.labels if l in p.B.labels]
+    vals = []
+    for cidx in samples:
+        fix = dict(zip(p.C.labels, cidx))
+        parts = []
+        for t in (p.A, p.B):
+            off = sum(fix[l] * s for l, s in zip(t.labels, t.strides) if l in fix)
+            keep = [k for k, l in enumerate(t.labels) if l in con]
+            labels = [t.labels[k] for k in keep]
+            ext = [t.extents[k] for k in keep]
+            st = [t.strides[k] for k in keep]
+            end = off + ts.span(ext, st)
+            parts.append((labels, ext, st, np.asarray(t.data[off:end], np.float64)))
+        c = np.zeros(1)
+        c0 = 0.0
+        if p.beta != 0:
+            coff = sum(i * s for i, s in zip(cidx, p.C.strides))
+            c0 = float(p.C.data[coff])
+        c[0] = c0
+        (la, ea, sa, a), (lb, eb, sb, b) = parts
+        oracle.contract_raw(la, ea, sa, a, lb, eb, sb, b, [], [], [], c, p.alpha, p.beta)
+        vals.append(c[0])
+    return np.array(vals)
+
+
+def random_output_indices(p, n, seed=0):
+    rng = np.random.default_rng(seed)
+    return [tuple(int(rng.integers(0, e)) for e in p.C.extents) for _ in range(n)]
+
+
+def gather(buf, C, samples):
+    return np.array([buf[sum(i * s for i, s in zip(cidx, C.strides))] for cidx in samples])

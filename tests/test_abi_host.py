@@ -1,0 +1,169 @@
+"""Host-side tests of libtc.so (no GPU needed): exported symbols, the planner's
+classification against the classification oracle, error statuses and the
+GEMM views built for the workloads."""
+import glob
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+
+import tcsynth as ts
+from oracle import classify as oc
+
+tc = pytest.importorskip("paper_1307_2100_gb300.tc")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        src = re.sub(r"#[^\n]*", "", src)
+        names |= set(re.findall(r"\b(tc_[A-Za-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_function():
+    names = declared_functions()
+    assert "tc_plan" in names and "tc_contract" in names
+    missing = [n for n in names if not hasattr(tc.lib, n)]
+    assert not missing, missing
+
+
+def _t(t):
+    return (t.labels, t.extents, t.strides)
+
+
+def plan_info(p, math=0, mapping=0, tile=-1, dtype=None):
+    dt = tc.TC_F64 if dtype is None else dtype
+    h = tc.tc_plan(_t(p.A), _t(p.B), _t(p.C), dt, math, mapping, tile)
+    try:
+        return tc.tc_plan_get_info(h)
+    finally:
+        tc.tc_plan_destroy(h)
+
+
+def bits(v):
+    return sum(1 << i for i, x in enumerate(v) if x)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_planner_classification_matches_oracle(seed):
+    rng = np.random.Generator(np.random.PCG64(1000 + seed))
+    for _ in range(300):
+        p = ts.random_problem(rng, max_order=5, max_ext=4, min_ext=1, max_p=3)
+        info = plan_info(p)
+        r = oc.classify(p.A, p.B, p.C)
+        assert info.cls == r.cls
+        assert (info.p, info.delta_a, info.delta_b) == (r.p, r.delta_a, r.delta_b)
+        assert info.stride1_a == (r.stride1_a if r.stride1_a is not None else -1)
+        assert info.stride1_b == (r.stride1_b if r.stride1_b is not None else -1)
+        assert info.slice_a == bits(r.slice_a), (p.A.labels, p.B.labels, p.C.labels)
+        assert info.slice_b == bits(r.slice_b)
+
+
+def test_planner_on_paper_cases():
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "classification_cases.json")))
+    names = {}
+    for case in gold["cases"]:
+        def mk(ls, out=False):
+            labels = [names.setdefault(x, len(names) + 1) for x in ls]
+            ext = [5] * len(labels)
+            data = np.zeros(ts.span(ext, ts.col_major(ext)))
+            return ts.Tensor(labels, ext, ts.col_major(ext), data)
+        A, B, C = mk(case["A"]), mk(case["B"]), mk(case["C"])
+        info = plan_info(ts.Problem(case["name"], A, B, C))
+        assert info.cls == case["cls"], case["cite"]
+        r = oc.classify(A, B, C)
+        assert info.slice_a == bits(r.slice_a) and info.slice_b == bits(r.slice_b)
+
+
+def test_gemm_views_of_the_workloads():
+    i1 = plan_info(ts.slice_gemm_48())
+    assert (i1.cls, i1.M, i1.N, i1.K, i1.batch) == (32, 48 * 48, 48, 48, 1)
+    s1 = plan_info(ts.slice_gemm_48(), mapping=tc.MAPPING["slice_gemm"])
+    assert (s1.M, s1.N, s1.K, s1.batch) == (48, 48, 48, 48)
+    d = plan_info(ts.direct_gemm_64())
+    assert (d.cls, d.M, d.N, d.K) == (32, 64 * 64, 64 * 64, 64 * 64)
+    f = plan_info(ts.fused_permute_48())
+    assert (f.cls, f.M, f.N, f.K) == (31, 48 * 48, 48 * 48, 48 * 48)
+    c = plan_info(ts.fused_permute_48(), mapping=tc.MAPPING["copy_gemm"])
+    assert c.workspace >= 48 ** 4 * 8
+    g = plan_info(ts.gemv_1024())
+    assert (g.cls, g.kernel, g.M, g.N, g.K) == (2, 3, 1024 * 1024, 1, 2048)
+    assert g.flops == 2.0 * 1024 * 1024 * 2048
+
+
+def test_class1_dot_needs_workspace():
+    p = ts.problem("dot", "ij", "ji", "", dict(i=50, j=40), 1)
+    info = plan_info(p)
+    assert info.cls == 1 and info.kernel == 4 and info.workspace > 0
+
+
+E = dict(a=3, b=4, i=5, j=6)
+
+
+def _desc(ls, strides=None):
+    labels = ts.lab(ls)
+    ext = [E[c] for c in ls]
+    return (labels, ext, strides)
+
+
+@pytest.mark.parametrize("A,B,C,code", [
+    (_desc("ai"), _desc("ib"), _desc("abi"), 5),          # label in A, B and C
+    (_desc("ai"), _desc("jb"), _desc("ab"), 2),           # label in neither C nor B
+    (_desc("ai"), _desc("ib"), _desc("a"), 2),            # free label of B not in C
+    (_desc("aa"), _desc("ab"), _desc("b"), 2),            # repeated label
+    (_desc("ai", [1, -3]), _desc("ib"), _desc("ab"), 4),  # negative stride
+    (_desc("ai", [0, 3]), _desc("ib"), _desc("ab"), 4),   # zero stride, extent > 1
+    (_desc("ai"), _desc("ib"), _desc("ab", [1, 1]), 4),   # aliasing output
+])
+def test_plan_rejects_invalid_descriptors(A, B, C, code):
+    assert tc.tc_plan_status(A, B, C, tc.TC_F64, 0) == code
+
+
+def test_plan_rejects_extent_mismatch_and_bad_enums():
+    A = (ts.lab("ai"), [3, 5], None)
+    B = (ts.lab("ib"), [6, 4], None)
+    C = (ts.lab("ab"), [3, 4], None)
+    assert tc.tc_plan_status(A, B, C, tc.TC_F64, 0) == 3
+    B = (ts.lab("ib"), [5, 4], None)
+    assert tc.tc_plan_status(A, B, C, tc.TC_F64, 0) == 0
+    assert tc.tc_plan_status(A, B, C, 7, 0) == 1             # bad dtype
+    assert tc.tc_plan_status(A, B, C, tc.TC_F64, 9) == 1     # bad math
+    assert tc.tc_plan_status(A, B, C, tc.TC_F64, 2) == 5     # FP64 storage, BF16 math
+    assert tc.tc_plan_status(A, B, C, tc.TC_F32, 0) == 5     # FP32 storage, FP64 math
+    assert tc.tc_plan_status(A, B, C, tc.TC_F64, 0, 42) == 1  # bad mapping
+    assert tc.tc_plan_status(A, B, C, tc.TC_F64, 0, 0, 99) == 5  # bad tile
+    x = (ts.lab("i"), [5], None)
+    # SLICE_GEMM and COPY_GEMM exist only for Class 3
+    assert tc.tc_plan_status(A, x, (ts.lab("a"), [3], None), tc.TC_F64, 0,
+                             tc.MAPPING["slice_gemm"]) == 5
+
+
+def test_order_limit():
+    n = tc.MAX_ORDER + 1
+    A = (list(range(1, n + 1)), [1] * n, None)
+    assert tc.tc_plan_status(A, A, ([], [], None), tc.TC_F64, 0) == 1
+
+
+def test_contract_host_checks_before_any_launch():
+    h = tc.tc_plan(_desc("ij"), (ts.lab("ji"), [6, 5], None), ([], [], None), tc.TC_F64, 0)
+    try:
+        with pytest.raises(tc.TcError) as e:
+            tc.tc_contract(h, 1.0, 16, 16, 0.0, 16, 0, 0, 0)   # no workspace given
+        assert e.value.status == 6
+        with pytest.raises(tc.TcError) as e:
+            tc.tc_contract(0, 1.0, 16, 16, 0.0, 16)
+        assert e.value.status == 1
+    finally:
+        tc.tc_plan_destroy(h)
+
+
+def test_status_strings():
+    assert tc.tc_status_string(0) == "ok"
+    assert "timed out" in tc.tc_status_string(8)
