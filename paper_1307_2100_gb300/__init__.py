@@ -2,51 +2,19 @@
 
 The compute path is libtc.so (hand-written sm_103a kernels behind a C ABI,
 declared in include/tc.h).  :mod:`.tc` is the ctypes binding with the C
-names; :class:`Contraction` is a thin convenience layer over it that takes
-PyTorch tensors (device memory and streams only).
+names (importing it fails loudly when the library is not built: there is no
+fallback); :class:`Contraction` (in :mod:`.api`) takes PyTorch tensors.
+:mod:`.build` compiles the library and does not need it to exist.
 """
 from __future__ import annotations
-
-from typing import Optional, Sequence
-
-from . import tc  # noqa: F401  (fails loudly when the library is not built)
 
 __all__ = ["tc", "Contraction"]
 
 
-class Contraction:
-    """A planned contraction C = alpha * A.B + beta * C over labelled indices.
-
-    Each operand is (labels, extents, strides-or-None); strides count
-    elements.  `math` is one of tc.MATH, `mapping` one of tc.MAPPING.
-    """
-
-    def __init__(self, A, B, C, dtype: str = "f64", math: str = "fp64",
-                 mapping: str = "auto", tile: int = -1):
-        self.dtype = tc.TC_F64 if dtype == "f64" else tc.TC_F32
-        self.handle = tc.tc_plan(A, B, C, self.dtype, tc.MATH[math], tc.MAPPING[mapping], tile)
-        self.info = tc.tc_plan_get_info(self.handle)
-        self._ws = None
-
-    def workspace(self, device):
-        import torch
-        n = int(self.info.workspace)
-        if n and (self._ws is None or self._ws.numel() < n or self._ws.device != device):
-            self._ws = torch.empty(n, dtype=torch.uint8, device=device)
-        return self._ws
-
-    def __call__(self, A, B, C, alpha: float = 1.0, beta: float = 0.0, stream=None):
-        """A, B, C: CUDA tensors whose storage holds the described layouts."""
-        import torch
-        ws = self.workspace(C.device)
-        s = stream if stream is not None else torch.cuda.current_stream(C.device)
-        tc.tc_contract(self.handle, alpha, A.data_ptr(), B.data_ptr(), beta, C.data_ptr(),
-                       ws.data_ptr() if ws is not None else 0,
-                       ws.numel() if ws is not None else 0, s.cuda_stream)
-        return C
-
-    def __del__(self):
-        h = getattr(self, "handle", None)
-        if h:
-            tc.tc_plan_destroy(h)
-            self.handle = None
+def __getattr__(name):
+    import importlib
+    if name == "Contraction":
+        return importlib.import_module(".api", __name__).Contraction
+    if name == "tc":
+        return importlib.import_module(".tc", __name__)
+    raise AttributeError(name)
