@@ -49,6 +49,7 @@ extern "C" tc_status tc_contract(tc_plan_t plan, double alpha, const void* A, co
   }
   switch (P->kernel) {
     case K_GEMM_SIMT: return launch_gemm_simt(a, P->dtype, P->tile, stream);
+    case K_GEMM_TC: return launch_gemm_tc(a, P->math, stream);
     case K_GEMV: return launch_gemv(a, P->dtype, P->tile, stream);
     case K_DOT: return launch_dot(a, P->dtype, P->tile, stream);
     default: return TC_ERR_UNSUPPORTED;

@@ -12,52 +12,10 @@
 #include <algorithm>
 #include <cstdio>
 
+#include "groups.cuh"
 #include "tc_internal.h"
 
 namespace tc {
-
-// Offset of group index `idx` in tensor slot `t` (0 = first operand, 1 =
-// second operand, 2 = C).  Groups are < 2^31 elements, so 32-bit division.
-__device__ __forceinline__ int64_t goff(const Group& g, int t, uint32_t idx) {
-  if (g.n == 1) return (int64_t)idx * g.st[t][0];
-  int64_t off = 0;
-  for (int i = 0; i < g.n; ++i) {
-    uint32_t e = (uint32_t)g.ext[i];
-    uint32_t q = idx / e;
-    off += (int64_t)(idx - q * e) * g.st[t][i];
-    idx = q;
-  }
-  return off;
-}
-
-// Two offsets of one group index at once (first operand and C, etc.).
-__device__ __forceinline__ void goff2(const Group& g, int t0, int t1, uint32_t idx, int64_t& o0,
-                                      int64_t& o1) {
-  o0 = 0;
-  o1 = 0;
-  for (int i = 0; i < g.n; ++i) {
-    uint32_t e = (uint32_t)g.ext[i];
-    uint32_t q = idx / e;
-    uint32_t r = idx - q * e;
-    o0 += (int64_t)r * g.st[t0][i];
-    o1 += (int64_t)r * g.st[t1][i];
-    idx = q;
-  }
-}
-
-__device__ __forceinline__ void goff3(const Group& g, uint32_t idx, int64_t& o0, int64_t& o1,
-                                      int64_t& o2) {
-  o0 = o1 = o2 = 0;
-  for (int i = 0; i < g.n; ++i) {
-    uint32_t e = (uint32_t)g.ext[i];
-    uint32_t q = idx / e;
-    uint32_t r = idx - q * e;
-    o0 += (int64_t)r * g.st[0][i];
-    o1 += (int64_t)r * g.st[1][i];
-    o2 += (int64_t)r * g.st[2][i];
-    idx = q;
-  }
-}
 
 // ---------------------------------------------------------------------------
 // GEMM on the CUDA cores.  CTA tile TM x TN, K step TK, each thread a 4x4

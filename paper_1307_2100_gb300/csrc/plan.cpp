@@ -358,10 +358,6 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   const bool tensor_core = math == TC_MATH_BF16 || math == TC_MATH_BF16X3 || math == TC_MATH_BF16X6;
   int32_t kernel = gemm_family ? (tensor_core ? K_GEMM_TC : K_GEMM_SIMT)
                                : (map == TC_MAP_GEMV ? K_GEMV : K_DOT);
-  if (kernel == K_GEMM_TC) {  // tensor-core kernels are not part of this build
-    delete P;
-    return TC_ERR_UNSUPPORTED;
-  }
 
   // ---- operand roles: the kernel's first operand X provides M
   bool swap = false;
@@ -476,7 +472,10 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   }
 
   // ---- tiles and workspace
-  int ntiles = kernel == K_GEMM_SIMT ? num_tiles_simt(dtype) : kernel == K_GEMV ? num_tiles_gemv() : 1;
+  int ntiles = kernel == K_GEMM_SIMT ? num_tiles_simt(dtype)
+               : kernel == K_GEMM_TC ? num_tiles_tc()
+               : kernel == K_GEMV    ? num_tiles_gemv()
+                                     : 1;
   if (tile >= ntiles) {
     delete P;
     return TC_ERR_UNSUPPORTED;
@@ -491,6 +490,12 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
     }
   }
   P->tile = tile;
+  if (kernel == K_GEMM_TC) {
+    g.chunk_kb = tc_chunk_kb(math, tile);
+    // n-tiles fastest when there are few of them: the CTAs that share a panel
+    // of the first operand then run at the same time and read it once from HBM
+    g.raster = ((N + 127) / 128) <= 16 ? 1 : 0;
+  }
   size_t ws = 0;
   if (kernel == K_DOT && M * N * Bt == 1) ws += (size_t)dot_partials(g, tile) * 8;
   ws = (ws + 255) & ~(size_t)255;

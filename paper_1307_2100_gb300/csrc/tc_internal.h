@@ -40,6 +40,8 @@ struct GemmArgs {
   int32_t a_contig, b_contig;  // Contig of A along (M | K), of B along (N | K)
   int32_t c_contig_m;          // 1 when C's stride along the first M label is 1
   int32_t math;                // tc_math
+  int32_t raster;              // tensor-core GEMM: 1 = n-tiles fastest in launch order
+  int32_t chunk_kb;            // tensor-core GEMM: K blocks per FP32 accumulation chunk
   void* ws;                    // workspace (DOT partials)
   int64_t ws_elems;
 };
@@ -85,7 +87,10 @@ tc_status launch_dot(const GemmArgs& a, tc_dtype dt, int tile, void* stream);
 tc_status launch_perm(const PermArgs& a, tc_dtype dt, void* stream);
 tc_status launch_scale(const Group& gc, void* C, double beta, tc_dtype dt, int64_t total,
                        void* stream);
+tc_status launch_gemm_tc(const GemmArgs& a, int math, void* stream);
 int dot_partials(const GemmArgs& a, int tile);
+int num_tiles_tc();
+int tc_chunk_kb(int math, int tile);
 int num_tiles_simt(tc_dtype dt);
 int num_tiles_gemv();
 

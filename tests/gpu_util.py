@@ -98,3 +98,36 @@ def random_output_indices(p, n, seed=0):
 
 def gather(buf, C, samples):
     return np.array([buf[sum(i * s for i, s in zip(cidx, C.strides))] for cidx in samples])
+
+
+def sample_outputs_form(p, samples, form):
+    """Oracle values of selected outputs for a split-product form: the operand
+    slices of each sample are split into BF16 terms (oracle.precision) and the
+    form's term products are contracted in FP64 and summed."""
+    from oracle import precision as op
+    con = [l for l in p.A.labels if l in p.B.labels]
+    nt = op.TERMS[form]
+    vals = []
+    for cidx in samples:
+        fix = dict(zip(p.C.labels, cidx))
+        parts = []
+        for t in (p.A, p.B):
+            off = sum(fix[l] * s for l, s in zip(t.labels, t.strides) if l in fix)
+            keep = [k for k, l in enumerate(t.labels) if l in con]
+            labels = [t.labels[k] for k in keep]
+            ext = [t.extents[k] for k in keep]
+            st = [t.strides[k] for k in keep]
+            end = off + ts.span(ext, st)
+            terms = op.split_bf16(np.asarray(t.data[off:end], np.float32), nt)
+            parts.append((labels, ext, st, terms))
+        (la, ea, sa, ta), (lb, eb, sb, tb) = parts
+        acc = 0.0
+        for i, j in op.FORMS[form]:
+            c = np.zeros(1)
+            oracle.contract_raw(la, ea, sa, ta[i], lb, eb, sb, tb[j], [], [], [], c, 1.0, 0.0)
+            acc += c[0]
+        v = p.alpha * acc
+        if p.beta != 0:
+            v += p.beta * float(p.C.data[sum(i * s for i, s in zip(cidx, p.C.strides))])
+        vals.append(v)
+    return np.array(vals)

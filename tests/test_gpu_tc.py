@@ -1,0 +1,98 @@
+"""GPU parity of the tensor-core path (FP32 storage; BF16, BF16x3, BF16x6 math).
+
+Two references:
+  * the split-form oracle (oracle.precision.contract_form): the same BF16 term
+    products summed exactly in FP64.  The kernel differs from it only by FP32
+    accumulation inside one K-chunk (chunks are summed in FP64), so the bound
+    is a few FP32 ulps of the result norm: relative Frobenius <= 2e-6;
+  * the FP64 oracle on the FP32 inputs, within each form's stated error:
+    BF16 <= 1e-2, BF16x3 <= 2e-5, BF16x6 <= 1e-6 (FP32-class).
+Integer inputs in [-4, 4] are BF16 values and all partial sums are exact in
+FP32, so every form must then match the FP64 oracle bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import precision as op
+import tcsynth as ts
+from gpu_util import (compare, gather, random_output_indices, run, sample_outputs,
+                      sample_outputs_form)
+
+pytestmark = pytest.mark.gpu
+
+FORMS = ["bf16", "bf16x3", "bf16x6"]
+TOL_METHOD = 2e-6
+TOL_FP64 = {"bf16": 1e-2, "bf16x3": 2e-5, "bf16x6": 1e-6}
+
+
+def f32(p):
+    for t in (p.A, p.B, p.C):
+        t.data = t.data.astype(np.float32)
+    return p
+
+
+def shapes():
+    return [
+        f32(ts.direct_gemm_64(n=23)),                                  # Class 3.2, ragged tiles
+        f32(ts.fused_permute_48(n=17)),                                # Class 3.1, fused permute
+        f32(ts.problem("m1", "ai", "ib", "ab", dict(a=300, i=200, b=130), 51)),
+        f32(ts.problem("cfromb", "ai", "ib", "ba", dict(a=140, i=77, b=260), 52)),
+        f32(ts.slice_gemm_48()),
+    ]
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_integer_inputs_exact(form):
+    p = ts.problem("int", "iajb", "jcid", "abcd", dict(i=9, a=70, j=11, b=3, c=65, d=2), 61,
+                   dist="int", dtype=np.float32, lo=-4, hi=4)
+    got = run(p, form, "auto")
+    np.testing.assert_array_equal(got, oracle.contract_problem(p))
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_forms_against_method_and_fp64_oracles(form):
+    for p in shapes():
+        got = run(p, form, "auto")
+        ref_m = op.contract_form(p, form)
+        ref_64 = oracle.contract_problem(p)
+        em = compare(got, ref_m, p.C)
+        e64 = compare(got, ref_64, p.C)
+        assert em <= TOL_METHOD, (p.name, form, em)
+        assert e64 <= TOL_FP64[form], (p.name, form, e64)
+
+
+@pytest.mark.parametrize("mapping", ["fused_gemm", "slice_gemm", "copy_gemm"])
+def test_bf16x6_mappings(mapping):
+    p = f32(ts.fused_permute_48(n=19))
+    got = run(p, "bf16x6", mapping)
+    assert compare(got, op.contract_form(p, "bf16x6"), p.C) <= TOL_METHOD
+
+
+@pytest.mark.parametrize("tile", [0, 1, 2])
+def test_chunk_configurations(tile):
+    p = f32(ts.problem("longk", "aijb", "ijc", "abc", dict(a=130, i=40, j=60, b=2, c=129), 53))
+    for form in ("bf16x3", "bf16x6"):
+        got = run(p, form, "fused_gemm", tile)
+        assert compare(got, op.contract_form(p, form), p.C) <= TOL_METHOD, (tile, form)
+
+
+def test_alpha_beta_tc():
+    p = f32(ts.direct_gemm_64(n=21))
+    p.C.data = np.linspace(-2, 2, p.C.data.size).astype(np.float32)
+    p.alpha, p.beta = -1.5, 0.25
+    got = run(p, "bf16x6", "auto")
+    assert compare(got, op.contract_form(p, "bf16x6"), p.C) <= TOL_METHOD
+
+
+def test_precision_workload_full_size_sampled():
+    """C[a,b,i,j] = sum_{e,f} A[a,b,e,f] B[e,f,i,j], a=b=e=f=128, i=j=32 (FP32
+    storage) at full size, sampled outputs against both oracles."""
+    p = ts.precision_ccd()
+    s = random_output_indices(p, 96, seed=3)
+    ref64 = sample_outputs(p, s)
+    for form in FORMS:
+        got = run(p, form, "auto")
+        g = gather(got, p.C, s)
+        assert oracle.rel_fro(g, sample_outputs_form(p, s, form)) <= TOL_METHOD, form
+        assert oracle.rel_fro(g, ref64) <= TOL_FP64[form], form
+        assert np.all(np.isfinite(got))
