@@ -46,11 +46,41 @@ def env_rank():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
-def workloads(alloc=None, only=None):
+def workloads(alloc=None, only=None, kind="class3_fp64"):
+    if kind == "precision":
+        return [ts.precision_ccd()]
     makers = {"direct_gemm_64": ts.direct_gemm_64, "fused_permute_48": ts.fused_permute_48,
               "gemv_1024": lambda: ts.gemv_1024_full(alloc=alloc)}
     names = list(makers) if not only else [n for n in only.split(",") if n]
     return [makers[n]() for n in names]
+
+
+NPROD = {"bf16": 1, "bf16x3": 3, "bf16x6": 6}
+
+
+def sampled_error(p, got, nsamp=64):
+    """Relative Frobenius error of sampled outputs against the FP64 oracle."""
+    import oracle
+    rng = np.random.default_rng(7)
+    con = [l for l in p.A.labels if l in p.B.labels]
+    ref, val = [], []
+    for _ in range(nsamp):
+        cidx = tuple(int(rng.integers(0, e)) for e in p.C.extents)
+        fix = dict(zip(p.C.labels, cidx))
+        parts = []
+        for t in (p.A, p.B):
+            off = sum(fix[l] * st for l, st in zip(t.labels, t.strides) if l in fix)
+            keep = [k for k, l in enumerate(t.labels) if l in con]
+            ext = [t.extents[k] for k in keep]
+            stv = [t.strides[k] for k in keep]
+            parts.append(([t.labels[k] for k in keep], ext, stv,
+                          np.asarray(t.data[off:off + ts.span(ext, stv)], np.float64)))
+        c = np.zeros(1)
+        (la, ea, sa, a), (lb, eb, sb, b) = parts
+        oracle.contract_raw(la, ea, sa, a, lb, eb, sb, b, [], [], [], c, 1.0, 0.0)
+        ref.append(c[0])
+        val.append(float(got[sum(i * st for i, st in zip(cidx, p.C.strides))]))
+    return oracle.rel_fro(np.array(val), np.array(ref))
 
 
 def read_peaks():
@@ -222,16 +252,20 @@ def run_ours(args):
                         pin_memory=True)
         return t.numpy()
 
-    probs = workloads(alloc=pinned, only=args.only)
+    probs = workloads(alloc=pinned, only=args.only, kind=args.workload)
+    fp64 = args.workload == "class3_fp64"
+    math = "fp64" if fp64 else args.math
+    tdt = torch.float64 if fp64 else torch.float32
     plans, dA, dB, dC = [], [], [], []
     for p in probs:
         pl = Contraction((p.A.labels, p.A.extents, p.A.strides),
                          (p.B.labels, p.B.extents, p.B.strides),
-                         (p.C.labels, p.C.extents, p.C.strides), "f64", "fp64", "auto")
+                         (p.C.labels, p.C.extents, p.C.strides), "f64" if fp64 else "f32",
+                         math, "auto", args.tile)
         plans.append(pl)
         dA.append(torch.from_numpy(np.ascontiguousarray(p.A.data)).to(dev))
         dB.append(torch.from_numpy(np.ascontiguousarray(p.B.data)).to(dev))
-        dC.append(torch.empty(p.C.data.size, dtype=torch.float64, device=dev))
+        dC.append(torch.empty(p.C.data.size, dtype=tdt, device=dev))
     def host_pinned(a):
         t = torch.from_numpy(a)
         return t if t.is_pinned() else t.pin_memory()
@@ -327,39 +361,53 @@ def run_ours(args):
     hbm = peaks.get("hbm_gbs", 6784.5)
     sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     fp64_peak = N_SMS * FP64_FLOP_PER_CLK_SM * sm_mhz * 1e6 / 1e12  # TFLOP/s
+    bf16_peak = peaks.get("bf16_tflops", 1884.0)
     parts = []
     for j, p in enumerate(probs):
         info = plans[j].info
         kms = float(per[:, j].mean())
-        t_alu = p.flops() / (fp64_peak * 1e12)
+        if fp64 or info.kernel != 2:
+            cpeak, work, cbound = fp64_peak if fp64 else 77.7, p.flops(), "alu"
+        else:  # tensor-core forms: NPROD BF16 products per logical multiply-add
+            cpeak, work, cbound = bf16_peak, p.flops() * NPROD[math], "tensor"
+        t_alu = work / (cpeak * 1e12)
         t_mem = p.min_bytes() / (hbm * 1e9)
-        bound = "alu" if t_alu >= t_mem else "hbm"
-        achieved = p.flops() / (kms / 1e3) / 1e12 if bound == "alu" else \
+        bound = cbound if t_alu >= t_mem else "hbm"
+        achieved = work / (kms / 1e3) / 1e12 if bound != "hbm" else \
             p.min_bytes() / (kms / 1e3) / 1e9
-        peak = fp64_peak if bound == "alu" else hbm
+        peak = cpeak if bound != "hbm" else hbm
         parts.append({"name": p.name, "class": int(info.cls),
                       "mapping": tc.MAPPING_NAME[info.mapping],
                       "kernel": tc.KERNEL_NAME[info.kernel], "ms": kms,
                       "tflops": p.flops() / (kms / 1e3) / 1e12,
                       "bound": bound, "achieved": achieved, "peak": peak,
-                      "unit": "TFLOP/s" if bound == "alu" else "GB/s",
+                      "unit": "TFLOP/s" if bound != "hbm" else "GB/s",
                       "frac": achieved / peak,
                       "roofline_ms": 1e3 * max(t_alu, t_mem)})
+    if not fp64:
+        for j, p in enumerate(probs):
+            parts[j]["rel_err_vs_fp64_oracle_sampled"] = sampled_error(
+                p, dC[j].cpu().numpy().astype(np.float64))
     dom = max(parts, key=lambda d: d["ms"])
     traffic = None
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if fp64 else "f32 storage, " + math,
         "data": "synthetic (seeded uniform[-1,1), shapes of the paper's Eq. xy and Class 2)",
-        "config": {"workload": WORKLOAD, "mapping": "auto (recipe)", "math": "fp64",
+        "config": {"workload": WORKLOAD if fp64 else "precision: CCD-like 128^4 x 128^2*32^2",
+                   "mapping": "auto (recipe)", "math": math,
                    "l2": "flushed between steps (256 MiB write, outside timing)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": dom["bound"], "kernel": dom["kernel"], "workload": dom["name"],
                      "achieved": dom["achieved"], "peak": dom["peak"], "unit": dom["unit"],
                      "frac": dom["frac"], "traffic": traffic,
-                     "peak_source": ("derived: 152 SMs x 4 FP64 flop/clk x median SM clock "
-                                     f"{sm_mhz:.0f} MHz" if dom["bound"] == "alu"
+                     "peak_source": (("derived: 152 SMs x 4 FP64 flop/clk x median SM clock "
+                                      f"{sm_mhz:.0f} MHz") if dom["bound"] == "alu"
+                                     else "measured bf16_tflops burst (MEASURED_PEAKS.json); "
+                                     "achieved counts every BF16 product"
+                                     if dom["bound"] == "tensor"
                                      else "measured hbm_gbs (MEASURED_PEAKS.json)")},
         "parts": parts,
         "e2e": None if args.no_e2e else {
@@ -370,7 +418,7 @@ def run_ours(args):
         "device_status": tc.tc_status_string(status),
         "wall_s": wall,
     }
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and fp64:
         import oracle
         oracle.build()
         nth = cores()
@@ -394,6 +442,10 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
+    ap.add_argument("--workload", default="class3_fp64", choices=["class3_fp64", "precision"])
+    ap.add_argument("--math", default="bf16x6", choices=["bf16", "bf16x3", "bf16x6", "fp32"],
+                    help="math of the precision workload")
+    ap.add_argument("--tile", type=int, default=-1)
     ap.add_argument("--only", default="", help="comma-separated subset of the workload "
                     "(direct_gemm_64, fused_permute_48, gemv_1024), for profiling")
     args = ap.parse_args(argv)

@@ -154,10 +154,53 @@ tc_status tc_plan_destroy(tc_plan_t plan);
 tc_status tc_contract(tc_plan_t plan, double alpha, const void* A, const void* B, double beta,
                       void* C, void* workspace, size_t workspace_bytes, void* stream);
 
+/* ---- Batched contractions in one persistent launch ------------------------
+ * Many independent contractions (e.g. the products of a coupled-cluster
+ * iteration, Sec. 4.2) run as one launch of the tensor-core GEMM: one CTA per
+ * SM works through a list of (contraction, 128x128 output tile) entries,
+ * longest tiles first.  A batch is built once from plans (FP32 storage, one
+ * tensor-core math form shared by all plans, any mapping but COPY_GEMM); it
+ * owns a small device table of the plans' index groups and work list, so the
+ * plans may be destroyed afterwards. */
+typedef struct tc_batch_s* tc_batch_t;
+
+typedef struct {
+  int32_t n_items;
+  int32_t math;          /* tc_math shared by every item */
+  int64_t n_tiles;       /* work-list entries */
+  double flops;          /* sum over items of 2 * product of all extents */
+  double min_bytes;      /* sum over items of |A| + |B| + |C| bytes */
+} tc_batch_info;
+
+/* Build a batch from n plans (host and device allocation; synchronous).
+ * TC_ERR_UNSUPPORTED if a plan is not FP32 tensor-core math, if the plans use
+ * different math forms, or if a plan needs a workspace (COPY_GEMM). */
+tc_status tc_batch_plan(tc_batch_t* out, const tc_plan_t* plans, int32_t n);
+
+tc_status tc_batch_get_info(tc_batch_t batch, tc_batch_info* info);
+
+/* Run every contraction of the batch asynchronously on `stream` in one kernel
+ * launch.  A, B, C, alpha, beta are DEVICE arrays of n entries (item i uses
+ * A[i], B[i], C[i], alpha[i], beta[i], with the layouts of plan i).  Nothing
+ * is allocated or copied by the call, so it may be captured in a CUDA graph;
+ * a replay reads the pointer and scalar arrays at replay time. */
+tc_status tc_contract_batched(tc_batch_t batch, const void* const* A, const void* const* B,
+                              void* const* C, const double* alpha, const double* beta,
+                              void* stream);
+
+/* Free a batch (NULL is allowed).  The batch must not be in use on the GPU. */
+tc_status tc_batch_destroy(tc_batch_t batch);
+
 /* Reads and clears the device error flag of the current device after
  * synchronising `stream`: TC_ERR_TIMEOUT if a bounded device wait ran out
  * since the last call, else TC_OK. */
 tc_status tc_device_status(void* stream);
+
+/* Self-test of the bounded device waits: launches one warp that waits on an
+ * mbarrier nothing ever arrives on.  The wait gives up after `timeout_ns`
+ * nanoseconds, records the timeout in the device flag and returns, so a
+ * following tc_device_status() reports TC_ERR_TIMEOUT.  No fault, no hang. */
+tc_status tc_selftest_wait_timeout(int64_t timeout_ns, void* stream);
 
 /* Static description of a status code. */
 const char* tc_status_string(tc_status s);

@@ -1,15 +1,8 @@
 // contract.cu -- tc_contract: run a plan's kernels on the caller's stream.
 #include <cuda_runtime.h>
 
+#include "sm100.cuh"
 #include "tc_internal.h"
-
-namespace tc {
-
-// Set by kernels whose bounded waits ran out; read and cleared by
-// tc_device_status().
-__device__ int g_device_status = 0;
-
-}  // namespace tc
 
 using namespace tc;
 
@@ -56,15 +49,32 @@ extern "C" tc_status tc_contract(tc_plan_t plan, double alpha, const void* A, co
   }
 }
 
+namespace tc {
+// One warp waits (bounded) on a barrier that never completes.
+__global__ void k_selftest_wait(uint64_t timeout_ns) {
+  __shared__ uint64_t bar;
+  __shared__ int abort;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait(&bar, 0, &abort, timeout_ns);
+}
+}  // namespace tc
+
+extern "C" tc_status tc_selftest_wait_timeout(int64_t timeout_ns, void* stream) {
+  if (timeout_ns <= 0 || timeout_ns > 10000000000ll) return TC_ERR_INVALID_ARG;
+  k_selftest_wait<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>((uint64_t)timeout_ns);
+  return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+}
+
 extern "C" tc_status tc_device_status(void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  int h = 0;
-  const int zero = 0;
-  if (cudaMemcpyFromSymbolAsync(&h, g_device_status, sizeof(int), 0, cudaMemcpyDeviceToHost, s) !=
-          cudaSuccess ||
-      cudaMemcpyToSymbolAsync(g_device_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s) !=
-          cudaSuccess ||
+  int h0 = 0, h1 = 0;
+  if (read_clear_status(&h0, s) != cudaSuccess || tc_gemm_read_status(&h1, s) != TC_OK ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return TC_ERR_CUDA;
-  return h ? TC_ERR_TIMEOUT : TC_OK;
+  return (h0 || h1) ? TC_ERR_TIMEOUT : TC_OK;
 }

@@ -1,4 +1,5 @@
-// k_tc.cu -- the tensor-core GEMM over gathered index groups (sm_103a, tcgen05).
+// k_tc.cu -- the tensor-core GEMM over gathered index groups (sm_103a, tcgen05),
+// for one contraction or a batch of contractions in one persistent launch.
 //
 // C[m, n, b] = alpha * sum_k A[m, k, b] * B[k, n, b] + beta * C[m, n, b] for
 // FP32 tensors of any layout, computed as a sum of BF16 products:
@@ -8,28 +9,34 @@
 // with x = x0 + x1 + x2 the split of an FP32 value into BF16 terms, each the
 // round-to-nearest-even BF16 value of the remaining residual.
 //
-// One CTA computes a 128 x 128 tile of C.  Warp roles (288 threads):
-//   warps 0-3  producers: read FP32 elements of A and B through the index
-//              groups (any strides; the permutation of a Class 3.1 operand is
-//              absorbed here, so no copy pass touches HBM), split them into
-//              BF16 terms in registers and store the terms to shared memory in
-//              the canonical K-major layout of the tensor cores;
-//   warps 4-7  epilogue: drain each finished K-chunk accumulator from tensor
-//              memory and add it to an FP64 running sum kept in tensor memory;
-//              the last chunk is combined with alpha/beta and stored to C;
-//   warp 8     tensor-memory allocation and the single thread issuing
-//              tcgen05.mma for every product of every K-step.
-// The K range is cut into chunks (a few hundred to a thousand K): each chunk
-// is accumulated in FP32 in one of two tensor-memory accumulators (double
-// buffered so the tensor cores keep running while the other is drained), and
-// the chunks are summed in FP64, so FP32 rounding grows only over one chunk.
+// Accuracy.  The tensor cores add each 16-product block into the FP32
+// accumulator without rounding to nearest (the error grows with the number of
+// additions, not with its square root), so the main product a0 b0 and the
+// small correction products go to separate accumulators, and the main
+// accumulator is emptied every K-chunk (256 K by default): the chunks are
+// summed in compensated FP32 (TwoSum; the high word in tensor memory, the low
+// word in registers) and the final sum hi + lo + corrections is formed in FP64.
 //
-// Tensor memory (512 columns x 128 lanes): columns [0,128) and [128,256) are
-// the two accumulators, [256,512) holds the FP64 running sums (two 32-bit
-// columns per output column).
+// One CTA per SM, persistent over a work list of 128 x 128 output tiles.
+// Warp roles (416 threads):
+//   warps 0-3   producers: read FP32 elements of A and B through the index
+//               groups (any strides: the permutation of a Class 3.1 operand is
+//               absorbed here, so no copy pass touches HBM), split them into
+//               BF16 terms in registers, store the terms to shared memory in the
+//               canonical K-major layout of the tensor cores;
+//   warps 4-11  epilogue: two warps per tensor-memory lane quadrant, 64 columns
+//               each; drain K-chunks, finish with alpha/beta and a strided store;
+//   warp 12     tensor-memory allocation and the single thread issuing
+//               tcgen05.mma.
+// Tensor memory (512 columns x 128 lanes): [0,128) and [128,256) the double
+// buffered main accumulator, [256,384) the correction accumulator, [384,512)
+// the high word of the compensated chunk sum.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
 
 #include "groups.cuh"
 #include "sm100.cuh"
@@ -40,12 +47,29 @@ namespace tc {
 namespace tcg {
 
 constexpr int BM = 128, BN = 128, BK = 64;
-constexpr int kThreads = 288;
 constexpr int kProducers = 128;
-constexpr int kEpiWarp0 = 4;
-constexpr int kMmaWarp = 8;
+constexpr int kEpiWarps = 8;
+constexpr int kMmaWarp = 4 + kEpiWarps;
+constexpr int kThreads = (kMmaWarp + 1) * 32;
 constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t COL_MAIN = 0, COL_CORR = 256, COL_HI = 384;
 constexpr uint64_t kTimeoutNs = 2000000000ull;  // 2 s per wait
+
+struct Work {
+  int32_t item, tile;
+};
+
+struct Launch {
+  GemmArgs single;             // one contraction (items == nullptr)
+  const GemmArgs* items;       // batch: per-item arguments (device)
+  const Work* work;            // batch: (item, tile) entries (device)
+  int64_t nwork;
+  const void* const* Ap;       // batch: device arrays of per-item pointers and scalars
+  const void* const* Bp;
+  void* const* Cp;
+  const double* alpha;
+  const double* beta;
+};
 
 template <int NT>
 struct Cfg {
@@ -55,13 +79,14 @@ struct Cfg {
   static constexpr uint32_t STAGE = NT * (A_TERM + B_TERM);
   static constexpr uint32_t OFF_KOFF = S * STAGE;                   // int64 koffA[S][BK], koffB[S][BK]
   static constexpr uint32_t OFF_ROWS = OFF_KOFF + S * BK * 2 * 8;  // rowA[BM], rowB[BN], rowC[BM], colC[BN]
-  static constexpr uint32_t OFF_BAR = OFF_ROWS + (2 * BM + 2 * BN) * 8;
+  static constexpr uint32_t OFF_ARGS = OFF_ROWS + (2 * BM + 2 * BN) * 8;
+  static constexpr uint32_t OFF_BAR = OFF_ARGS + ((sizeof(GemmArgs) + 15) / 16) * 16;
   static constexpr uint32_t NBAR = 2 * S + 5;
   static constexpr uint32_t OFF_MISC = OFF_BAR + NBAR * 8;
   static constexpr uint32_t BYTES = OFF_MISC + 16 + 1024;          // + alignment slack
 };
 
-// Products (term of A, term of B) of each form, largest first.
+// Products (term of A, term of B) of each form; product 0 is the main one.
 __constant__ int8_t kProdA[6] = {0, 0, 1, 0, 1, 2};
 __constant__ int8_t kProdB[6] = {0, 1, 0, 2, 1, 0};
 __host__ __device__ constexpr int nprod(int nt) { return nt == 1 ? 1 : nt == 2 ? 3 : 6; }
@@ -98,8 +123,8 @@ __device__ __forceinline__ void produce(const float* __restrict__ X, const int64
       for (int q = 0; q < 4; ++q) {
         w[q] = pack_bf16x2(v[2 * q], v[2 * q + 1]);
         if (t + 1 < NT) {  // exact FP32 residuals
-          v[2 * q] -= bf16_lo(w[q]);
-          v[2 * q + 1] -= bf16_hi(w[q]);
+          v[2 * q] = __fsub_rn(v[2 * q], bf16_lo(w[q]));
+          v[2 * q + 1] = __fsub_rn(v[2 * q + 1], bf16_hi(w[q]));
         }
       }
       st_shared_v4(dst + t * TERM, w[0], w[1], w[2], w[3]);
@@ -112,8 +137,17 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volati
   return __all_sync(0xffffffffu, ok);
 }
 
+// s + e == a + b exactly (Knuth's TwoSum).
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+  const float s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  const float ap = __fsub_rn(s, bp);
+  e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+  return s;
+}
+
 template <int NT>
-__global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__ GemmArgs p) {
+__global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__ Launch L) {
   using G = Cfg<NT>;
   constexpr int S = G::S;
   extern __shared__ uint8_t smem_raw[];
@@ -125,6 +159,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
   int64_t* rowB = rowA + BM;
   int64_t* rowC = rowB + BN;
   int64_t* colC = rowC + BM;
+  GemmArgs* sargs = reinterpret_cast<GemmArgs*>(smem + G::OFF_ARGS);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + G::OFF_BAR);
   uint64_t* full = bars;
   uint64_t* empty = bars + S;
@@ -135,39 +170,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
   volatile int* abort = reinterpret_cast<volatile int*>(smem + G::OFF_MISC + 4);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t M = (uint32_t)p.M, N = (uint32_t)p.N, K = (uint32_t)p.K;
-  const uint32_t tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
-  uint32_t tm, tn, b;
-  {
-    const uint64_t t = blockIdx.x;
-    if (p.raster) {  // n-tiles fastest: the CTAs sharing an A panel run together
-      tn = (uint32_t)(t % tiles_n);
-      tm = (uint32_t)((t / tiles_n) % tiles_m);
-      b = (uint32_t)(t / ((uint64_t)tiles_n * tiles_m));
-    } else {
-      tm = (uint32_t)(t % tiles_m);
-      tn = (uint32_t)((t / tiles_m) % tiles_n);
-      b = (uint32_t)(t / ((uint64_t)tiles_n * tiles_m));
-    }
-  }
-  int64_t bA, bB, bC;
-  goff3(p.gb, b, bA, bB, bC);
 
-  // ---- set-up: offsets, barriers, tensor memory
-  for (int i = tid; i < BM; i += kThreads) {
-    const uint32_t m = tm * BM + i;
-    int64_t oa = -1, oc = -1;
-    if (m < M) goff2(p.gm, 0, 2, m, oa, oc);
-    rowA[i] = oa;
-    rowC[i] = oc;
-  }
-  for (int i = tid; i < BN; i += kThreads) {
-    const uint32_t n = tn * BN + i;
-    int64_t ob = -1, oc = -1;
-    if (n < N) goff2(p.gn, 1, 2, n, ob, oc);
-    rowB[i] = ob;
-    colC[i] = oc;
-  }
+  // ---- once per CTA: barriers, tensor memory
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], kProducers);
@@ -175,7 +179,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&accf[i], 1);
-      mbar_init(&acce[i], 128);
+      mbar_init(&acce[i], kEpiWarps * 32);
     }
     mbar_init(done, 1);
     *abort = 0;
@@ -186,117 +190,184 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-
-  const uint32_t nkb = (K + BK - 1) / BK;
-  const uint32_t ckb = (uint32_t)max(p.chunk_kb, 1);  // K blocks per chunk
-  const uint32_t nchunks = (nkb + ckb - 1) / ckb;
   const uint32_t sbase = smem_u32(smem);
 
-  if (warp < 4) {
-    // ------------------------------------------------------------ producers
-    const float* __restrict__ Xa = static_cast<const float*>(p.A) + bA;
-    const float* __restrict__ Xb = static_cast<const float*>(p.B) + bB;
-    const bool amn = p.a_contig == CONTIG_MN, bmn = p.b_contig == CONTIG_MN;
-    for (uint32_t kb = 0; kb < nkb; ++kb) {
-      const int s = kb % S;
-      const uint32_t ph = (kb / S) & 1;
-      bool ok = true;
-      if (kb >= S) ok = warp_wait(&empty[s], ph ^ 1, abort);
-      if (tid < BK) {
-        const uint32_t k = kb * BK + tid;
-        int64_t oa = -1, ob = -1;
-        if (k < K) goff2(p.gk, 0, 1, k, oa, ob);
-        koffA[s * BK + tid] = oa;
-        koffB[s * BK + tid] = ob;
-      }
-      named_bar_sync(1, kProducers);
-      if (ok && !*abort) {
-        const uint32_t st = sbase + s * G::STAGE;
-        produce<NT, BM>(Xa, rowA, koffA + s * BK, amn, st, tid);
-        produce<NT, BN>(Xb, rowB, koffB + s * BK, bmn, st + NT * G::A_TERM, tid);
-        fence_async_smem();
-        mbar_arrive(&full[s]);
-      }
+  uint32_t g_kb = 0;     // K blocks processed by this CTA (stage ring position)
+  uint32_t g_chunk = 0;  // K chunks processed by this CTA (accumulator ring position)
+  int cur_item = -2;
+
+  for (int64_t w = blockIdx.x; w < L.nwork; w += gridDim.x) {
+    // ---- the tile's arguments
+    int item = -1;
+    uint32_t tile = (uint32_t)w;
+    if (L.items) {
+      const Work wk = L.work[w];
+      item = wk.item;
+      tile = (uint32_t)wk.tile;
     }
-  } else if (warp < kMmaWarp) {
-    // ------------------------------------------------------------- epilogue
-    const int q = warp & 3;  // tensor-memory lane quadrant of this warp
-    const int row = q * 32 + lane;
-    const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
-    const bool rvalid = rowC[row] >= 0;
-    float* __restrict__ Cp = static_cast<float*>(p.C) + bC;
-    for (uint32_t j = 0; j < nchunks; ++j) {
-      const uint32_t buf = j & 1;
-      if (!warp_wait(&accf[buf], (j >> 1) & 1, abort)) break;
-      tc_fence_after();
-      const bool last = j + 1 == nchunks;
-#pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 16) {
-        uint32_t c[16], wl[16], wh[16];
-        tmem_ld16(tl + buf * BN + c0, c);
-        if (j > 0) {
-          tmem_ld16(tl + 2 * BN + 2 * c0, wl);
-          tmem_ld16(tl + 2 * BN + 2 * c0 + 16, wh);
+    if (item != cur_item) {
+      const uint32_t* src = item >= 0 ? reinterpret_cast<const uint32_t*>(L.items + item)
+                                      : reinterpret_cast<const uint32_t*>(&L.single);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(sargs);
+      for (int i = tid; i < (int)(sizeof(GemmArgs) / 4); i += kThreads) dst[i] = src[i];
+      __syncthreads();
+      if (item >= 0 && tid == 0) {
+        const bool sw = sargs->swapped != 0;
+        sargs->A = sw ? L.Bp[item] : L.Ap[item];
+        sargs->B = sw ? L.Ap[item] : L.Bp[item];
+        sargs->C = L.Cp[item];
+        sargs->alpha = L.alpha[item];
+        sargs->beta = L.beta[item];
+      }
+      cur_item = item;
+    }
+    __syncthreads();
+    const GemmArgs& p = *sargs;
+    const uint32_t M = (uint32_t)p.M, N = (uint32_t)p.N, K = (uint32_t)p.K;
+    const uint32_t tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
+    uint32_t tm, tn, b;
+    if (p.raster) {  // n-tiles fastest: the CTAs sharing an A panel run together
+      tn = tile % tiles_n;
+      tm = (tile / tiles_n) % tiles_m;
+    } else {
+      tm = tile % tiles_m;
+      tn = (tile / tiles_m) % tiles_n;
+    }
+    b = tile / (tiles_n * tiles_m);
+    int64_t bA, bB, bC;
+    goff3(p.gb, b, bA, bB, bC);
+    for (int i = tid; i < BM; i += kThreads) {
+      const uint32_t m = tm * BM + i;
+      int64_t oa = -1, oc = -1;
+      if (m < M) goff2(p.gm, 0, 2, m, oa, oc);
+      rowA[i] = oa;
+      rowC[i] = oc;
+    }
+    for (int i = tid; i < BN; i += kThreads) {
+      const uint32_t n = tn * BN + i;
+      int64_t ob = -1, oc = -1;
+      if (n < N) goff2(p.gn, 1, 2, n, ob, oc);
+      rowB[i] = ob;
+      colC[i] = oc;
+    }
+    __syncthreads();
+
+    const uint32_t nkb = (K + BK - 1) / BK;
+    const uint32_t ckb = (uint32_t)max(p.chunk_kb, 1);  // K blocks per chunk
+    const uint32_t nchunks = (nkb + ckb - 1) / ckb;
+
+    if (warp < 4) {
+      // ---------------------------------------------------------- producers
+      const float* __restrict__ Xa = static_cast<const float*>(p.A) + bA;
+      const float* __restrict__ Xb = static_cast<const float*>(p.B) + bB;
+      const bool amn = p.a_contig == CONTIG_MN, bmn = p.b_contig == CONTIG_MN;
+      for (uint32_t kb = 0; kb < nkb; ++kb, ++g_kb) {
+        const int s = g_kb % S;
+        const uint32_t ph = (g_kb / S) & 1;
+        bool ok = true;
+        if (g_kb >= (uint32_t)S) ok = warp_wait(&empty[s], ph ^ 1, abort);
+        if (tid < BK) {
+          const uint32_t k = kb * BK + tid;
+          int64_t oa = -1, ob = -1;
+          if (k < K) goff2(p.gk, 0, 1, k, oa, ob);
+          koffA[s * BK + tid] = oa;
+          koffB[s * BK + tid] = ob;
         }
-        tmem_wait_ld();
-        double s[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          double prev = 0.0;
-          if (j > 0) {
-            const uint32_t lo = i < 8 ? wl[2 * i] : wh[2 * (i - 8)];
-            const uint32_t hi = i < 8 ? wl[2 * i + 1] : wh[2 * (i - 8) + 1];
-            prev = __hiloint2double((int)hi, (int)lo);
-          }
-          s[i] = prev + (double)__uint_as_float(c[i]);
-        }
-        if (!last) {
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            wl[2 * i] = (uint32_t)__double2loint(s[i]);
-            wl[2 * i + 1] = (uint32_t)__double2hiint(s[i]);
-            wh[2 * i] = (uint32_t)__double2loint(s[8 + i]);
-            wh[2 * i + 1] = (uint32_t)__double2hiint(s[8 + i]);
-          }
-          tmem_st16(tl + 2 * BN + 2 * c0, wl);
-          tmem_st16(tl + 2 * BN + 2 * c0 + 16, wh);
-        } else if (rvalid) {
-          const int64_t rc = rowC[row];
-#pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int64_t cc = colC[c0 + i];
-            if (cc < 0) continue;
-            float* dst = Cp + rc + cc;
-            double v = p.alpha * s[i];
-            if (p.beta != 0.0) v += p.beta * (double)*dst;
-            *dst = (float)v;
-          }
+        named_bar_sync(1, kProducers);
+        if (ok && !*abort) {
+          const uint32_t st = sbase + s * G::STAGE;
+          produce<NT, BM>(Xa, rowA, koffA + s * BK, amn, st, tid);
+          produce<NT, BN>(Xb, rowB, koffB + s * BK, bmn, st + NT * G::A_TERM, tid);
+          fence_async_smem();
+          mbar_arrive(&full[s]);
         }
       }
-      if (!last) tmem_wait_st();
-      tc_fence_before();
-      mbar_arrive(&acce[buf]);
-    }
-  } else {
-    // -------------------------------------------------------------- MMA issue
-    if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16(BM, BN);
-      constexpr uint32_t LBO_A = (BM / 8) * 128, LBO_B = (BN / 8) * 128;
-      uint32_t kb = 0;
-      bool ok = true;
-      for (uint32_t j = 0; j < nchunks && ok; ++j) {
-        const uint32_t buf = j & 1;
-        if (j >= 2 && !mbar_wait(&acce[buf], ((j >> 1) - 1) & 1, abort, kTimeoutNs)) {
-          ok = false;
+    } else if (warp < kMmaWarp) {
+      // ----------------------------------------------------------- epilogue
+      const int q = warp & 3;            // tensor-memory lane quadrant
+      const int h = (warp - 4) >> 2;     // column half
+      const int row = q * 32 + lane;
+      const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + h * 64;
+      const int64_t rc = rowC[row];
+      float* __restrict__ Cp = static_cast<float*>(p.C) + bC;
+      float lo[64];
+#pragma unroll
+      for (int i = 0; i < 64; ++i) lo[i] = 0.0f;
+      for (uint32_t j = 0; j < nchunks; ++j, ++g_chunk) {
+        const uint32_t buf = g_chunk & 1;
+        if (!warp_wait(&accf[buf], (g_chunk >> 1) & 1, abort)) {
+          g_chunk += nchunks - j;
           break;
         }
         tc_fence_after();
-        const uint32_t d = tmem + buf * BN;
-        uint32_t acc = 0;
+        const uint32_t tmain = tl + COL_MAIN + buf * 128;
+        if (j + 1 < nchunks) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            uint32_t mv[16], hv[16];
+            tmem_ld16(tmain + c * 16, mv);
+            if (j > 0) tmem_ld16(tl + COL_HI + c * 16, hv);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const float hi0 = j > 0 ? __uint_as_float(hv[i]) : 0.0f;
+              float e;
+              const float s = two_sum(hi0, __uint_as_float(mv[i]), e);
+              lo[c * 16 + i] = __fadd_rn(lo[c * 16 + i], e);
+              hv[i] = __float_as_uint(s);
+            }
+            tmem_st16(tl + COL_HI + c * 16, hv);
+          }
+          tmem_wait_st();
+        } else {
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            uint32_t mv[8], hv[8], cv[8];
+            tmem_ld8(tmain + c * 8, mv);
+            if (j > 0) tmem_ld8(tl + COL_HI + c * 8, hv);
+            if (NT > 1) tmem_ld8(tl + COL_CORR + c * 8, cv);
+            tmem_wait_ld();
+            if (rc >= 0) {
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                const int64_t cc = colC[h * 64 + c * 8 + i];
+                if (cc < 0) continue;
+                double t = (double)__uint_as_float(mv[i]);
+                if (j > 0) t += (double)__uint_as_float(hv[i]) + (double)lo[c * 8 + i];
+                if (NT > 1) t += (double)__uint_as_float(cv[i]);
+                float* dst = Cp + rc + cc;
+                double v = p.alpha * t;
+                if (p.beta != 0.0) v += p.beta * (double)*dst;
+                *dst = (float)v;
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&acce[buf]);
+      }
+    } else if (lane == 0) {
+      // ------------------------------------------------------ MMA issue
+      constexpr uint32_t idesc = idesc_bf16(BM, BN);
+      constexpr uint32_t LBO_A = (BM / 8) * 128, LBO_B = (BN / 8) * 128;
+      uint32_t kb = 0;
+      bool ok = !*abort;
+      for (uint32_t j = 0; j < nchunks; ++j, ++g_chunk) {
+        const uint32_t buf = g_chunk & 1;
+        if (ok && g_chunk >= 2 && !mbar_wait(&acce[buf], ((g_chunk >> 1) - 1) & 1, abort, kTimeoutNs))
+          ok = false;
+        if (!ok) {
+          g_kb += nkb - kb;
+          g_chunk += nchunks - j;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dmain = tmem + COL_MAIN + buf * 128;
         const uint32_t kend = min(nkb, (j + 1) * ckb);
-        for (; kb < kend; ++kb) {
-          const int s = kb % S;
-          if (!mbar_wait(&full[s], (kb / S) & 1, abort, kTimeoutNs)) {
+        const uint32_t kstart = kb;
+        for (; kb < kend; ++kb, ++g_kb) {
+          const int s = g_kb % S;
+          if (!mbar_wait(&full[s], (g_kb / S) & 1, abort, kTimeoutNs)) {
             ok = false;
             break;
           }
@@ -305,28 +376,40 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
           const uint32_t sb = sa + NT * G::A_TERM;
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
+            mma_bf16(dmain, smem_desc(sa + kk * 2 * LBO_A, LBO_A, 128),
+                     smem_desc(sb + kk * 2 * LBO_B, LBO_B, 128), idesc,
+                     (kb > kstart || kk > 0) ? 1u : 0u);
 #pragma unroll
-            for (int pi = 0; pi < nprod(NT); ++pi) {
-              const uint64_t ad =
-                  smem_desc(sa + kProdA[pi] * G::A_TERM + kk * 2 * LBO_A, LBO_A, 128);
-              const uint64_t bd =
-                  smem_desc(sb + kProdB[pi] * G::B_TERM + kk * 2 * LBO_B, LBO_B, 128);
-              mma_bf16(d, ad, bd, idesc, acc);
-              acc = 1;
+            for (int pi = 1; pi < nprod(NT); ++pi) {
+              mma_bf16(tmem + COL_CORR,
+                       smem_desc(sa + kProdA[pi] * G::A_TERM + kk * 2 * LBO_A, LBO_A, 128),
+                       smem_desc(sb + kProdB[pi] * G::B_TERM + kk * 2 * LBO_B, LBO_B, 128),
+                       idesc, (kb > 0 || kk > 0 || pi > 1) ? 1u : 0u);
             }
           }
           mma_commit(&empty[s]);
         }
-        if (!ok) break;
+        if (!ok) {
+          g_kb += nkb - kb;
+          g_chunk += nchunks - j;
+          break;
+        }
         mma_commit(&accf[buf]);
       }
-      mma_commit(done);  // every MMA issued above has completed when this arrives
-      volatile int keep_waiting = 0;  // wait for in-flight MMAs even after an abort
-      mbar_wait(done, 0, &keep_waiting, kTimeoutNs);
+    } else {
+      g_kb += nkb;  // other lanes of the MMA warp keep the counters in step
+      g_chunk += nchunks;
     }
     __syncwarp();
+    __syncthreads();  // the tile is finished (its last accumulator was drained)
   }
 
+  if (warp == kMmaWarp && lane == 0) {
+    mma_commit(done);  // arrives once every MMA issued by this thread has completed
+    volatile int keep_waiting = 0;
+    mbar_wait(done, 0, &keep_waiting, kTimeoutNs);
+  }
+  __syncwarp();
   tc_fence_before();
   __syncthreads();
   if (warp == kMmaWarp) {
@@ -335,51 +418,197 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
   }
 }
 
-}  // namespace tcg
-
-// Tile configurations of the tensor-core GEMM: K blocks (of 64) per FP32
-// accumulation chunk.  Tile 0 keeps one chunk for plain BF16 (its error is set
-// by the BF16 rounding of the inputs) and 1024-K chunks for the split forms.
-int num_tiles_tc() { return 3; }
-int tc_chunk_kb(int math, int tile) {
-  if (tile == 1) return 4;
-  if (tile == 2) return 64;
-  return math == TC_MATH_BF16 ? (1 << 30) : 16;
-}
-
 template <int NT>
-static tc_status launch_tc_t(const GemmArgs& a, cudaStream_t s) {
-  using G = tcg::Cfg<NT>;
-  // The whole opt-in shared memory is requested: one CTA per SM (it owns all
-  // 512 tensor-memory columns) and room beyond the last operand tile.
-  static int smem_bytes = 0;
-  if (smem_bytes == 0) {
+int smem_bytes() {
+  static int bytes = 0;
+  if (bytes == 0) {
     int dev = 0, optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
-      return TC_ERR_CUDA;
-    if (optin < (int)G::BYTES) return TC_ERR_UNSUPPORTED;
-    if (cudaFuncSetAttribute(tcg::k_gemm_tc<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             optin) != cudaSuccess)
-      return TC_ERR_CUDA;
-    smem_bytes = optin;
+      return -1;
+    if (optin < (int)Cfg<NT>::BYTES) return -2;
+    // The whole opt-in shared memory is requested: one CTA per SM (it owns all
+    // 512 tensor-memory columns) and room beyond the last operand tile.
+    if (cudaFuncSetAttribute(k_gemm_tc<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) !=
+        cudaSuccess)
+      return -1;
+    bytes = optin;
   }
-  const uint64_t tiles = (uint64_t)((a.M + tcg::BM - 1) / tcg::BM) *
-                         (uint64_t)((a.N + tcg::BN - 1) / tcg::BN) * (uint64_t)a.nbatch;
-  if (tiles == 0) return TC_OK;
-  if (tiles > 0x7fffffffull) return TC_ERR_UNSUPPORTED;
-  tcg::k_gemm_tc<NT><<<(unsigned)tiles, tcg::kThreads, smem_bytes, s>>>(a);
+  return bytes;
+}
+
+int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      n = 0;
+  }
+  return n;
+}
+
+template <int NT>
+tc_status launch(const Launch& L, cudaStream_t s) {
+  if (L.nwork == 0) return TC_OK;
+  const int bytes = smem_bytes<NT>();
+  if (bytes == -2) return TC_ERR_UNSUPPORTED;
+  const int sms = num_sms();
+  if (bytes < 0 || sms <= 0) return TC_ERR_CUDA;
+  const int grid = (int)std::min<int64_t>(L.nwork, sms);
+  k_gemm_tc<NT><<<grid, kThreads, bytes, s>>>(L);
   return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
 }
 
-tc_status launch_gemm_tc(const GemmArgs& a, int math, void* stream) {
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+tc_status launch_math(const Launch& L, int math, cudaStream_t s) {
   switch (math) {
-    case TC_MATH_BF16: return launch_tc_t<1>(a, s);
-    case TC_MATH_BF16X3: return launch_tc_t<2>(a, s);
-    case TC_MATH_BF16X6: return launch_tc_t<3>(a, s);
+    case TC_MATH_BF16: return launch<1>(L, s);
+    case TC_MATH_BF16X3: return launch<2>(L, s);
+    case TC_MATH_BF16X6: return launch<3>(L, s);
     default: return TC_ERR_UNSUPPORTED;
   }
 }
 
+uint64_t tiles_of(const GemmArgs& a) {
+  return (uint64_t)((a.M + BM - 1) / BM) * (uint64_t)((a.N + BN - 1) / BN) * (uint64_t)a.nbatch;
+}
+
+}  // namespace tcg
+
+// Tile configurations of the tensor-core GEMM: K blocks (of 64) per chunk of
+// the main accumulator.  Tile 0: one chunk for plain BF16 (its error is that of
+// the BF16 inputs), 256-K chunks for the split forms; tile 1: 64-K chunks;
+// tile 2: 1024-K chunks.
+int num_tiles_tc() { return 3; }
+int tc_chunk_kb(int math, int tile) {
+  if (tile == 1) return 1;
+  if (tile == 2) return 16;
+  return math == TC_MATH_BF16 ? (1 << 30) : 4;
+}
+
+tc_status tc_gemm_read_status(int* h, void* stream) {
+  return read_clear_status(h, static_cast<cudaStream_t>(stream)) == cudaSuccess ? TC_OK
+                                                                                : TC_ERR_CUDA;
+}
+
+tc_status launch_gemm_tc(const GemmArgs& a, int math, void* stream) {
+  tcg::Launch L;
+  std::memset(&L, 0, sizeof(L));
+  L.single = a;
+  L.nwork = (int64_t)tcg::tiles_of(a);
+  if ((uint64_t)L.nwork > 0x7fffffffull) return TC_ERR_UNSUPPORTED;
+  return tcg::launch_math(L, math, static_cast<cudaStream_t>(stream));
+}
+
+// ------------------------------------------------------------ batched launch
+struct Batch {
+  int32_t n;
+  int32_t math;
+  int64_t nwork;
+  double flops, min_bytes;
+  GemmArgs* d_items;
+  tcg::Work* d_work;
+};
+
 }  // namespace tc
+
+using namespace tc;
+
+extern "C" tc_status tc_batch_plan(tc_batch_t* out, const tc_plan_t* plans, int32_t n) {
+  if (!out || (!plans && n > 0) || n < 0) return TC_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::vector<GemmArgs> items((size_t)n);
+  std::vector<std::pair<uint64_t, tcg::Work>> work;  // (cost, entry)
+  int32_t math = -1;
+  double flops = 0, bytes = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    const Plan* P = reinterpret_cast<const Plan*>(plans[i]);
+    if (!P) return TC_ERR_INVALID_ARG;
+    if (P->dtype != TC_F32 || P->math < TC_MATH_BF16 || P->math > TC_MATH_BF16X6)
+      return TC_ERR_UNSUPPORTED;
+    if (math >= 0 && P->math != math) return TC_ERR_UNSUPPORTED;
+    if (P->copy_which || P->empty_out || P->empty_k) return TC_ERR_UNSUPPORTED;
+    math = P->math;
+    GemmArgs a = P->args;
+    a.swapped = P->swapped ? 1 : 0;
+    a.chunk_kb = tc_chunk_kb(math, 0);
+    a.raster = 0;
+    items[i] = a;
+    flops += P->info.flops;
+    bytes += P->info.min_bytes;
+    const uint64_t t = tcg::tiles_of(a);
+    const uint64_t cost = (uint64_t)((a.K + tcg::BK - 1) / tcg::BK) + 2;  // per tile
+    for (uint64_t k = 0; k < t; ++k) work.push_back({cost, tcg::Work{i, (int32_t)k}});
+  }
+  // longest tiles first: the persistent CTAs take entries round-robin
+  std::stable_sort(work.begin(), work.end(),
+                   [](const auto& x, const auto& y) { return x.first > y.first; });
+  Batch* B = new (std::nothrow) Batch();
+  if (!B) return TC_ERR_INVALID_ARG;
+  B->n = n;
+  B->math = math;
+  B->nwork = (int64_t)work.size();
+  B->flops = flops;
+  B->min_bytes = bytes;
+  B->d_items = nullptr;
+  B->d_work = nullptr;
+  std::vector<tcg::Work> w(work.size());
+  for (size_t k = 0; k < work.size(); ++k) w[k] = work[k].second;
+  if (n > 0 && (cudaMalloc(&B->d_items, sizeof(GemmArgs) * (size_t)n) != cudaSuccess ||
+                cudaMemcpy(B->d_items, items.data(), sizeof(GemmArgs) * (size_t)n,
+                           cudaMemcpyHostToDevice) != cudaSuccess)) {
+    cudaFree(B->d_items);
+    delete B;
+    return TC_ERR_CUDA;
+  }
+  if (!w.empty() && (cudaMalloc(&B->d_work, sizeof(tcg::Work) * w.size()) != cudaSuccess ||
+                     cudaMemcpy(B->d_work, w.data(), sizeof(tcg::Work) * w.size(),
+                                cudaMemcpyHostToDevice) != cudaSuccess)) {
+    cudaFree(B->d_items);
+    cudaFree(B->d_work);
+    delete B;
+    return TC_ERR_CUDA;
+  }
+  *out = reinterpret_cast<tc_batch_t>(B);
+  return TC_OK;
+}
+
+extern "C" tc_status tc_batch_get_info(tc_batch_t batch, tc_batch_info* info) {
+  if (!batch || !info) return TC_ERR_INVALID_ARG;
+  const Batch* B = reinterpret_cast<const Batch*>(batch);
+  info->n_items = B->n;
+  info->math = B->math;
+  info->n_tiles = B->nwork;
+  info->flops = B->flops;
+  info->min_bytes = B->min_bytes;
+  return TC_OK;
+}
+
+extern "C" tc_status tc_contract_batched(tc_batch_t batch, const void* const* A,
+                                         const void* const* B, void* const* C,
+                                         const double* alpha, const double* beta, void* stream) {
+  if (!batch) return TC_ERR_INVALID_ARG;
+  const Batch* Bt = reinterpret_cast<const Batch*>(batch);
+  if (Bt->nwork == 0) return TC_OK;
+  if (!A || !B || !C || !alpha || !beta) return TC_ERR_INVALID_ARG;
+  tcg::Launch L;
+  std::memset(&L, 0, sizeof(L));
+  L.items = Bt->d_items;
+  L.work = Bt->d_work;
+  L.nwork = Bt->nwork;
+  L.Ap = A;
+  L.Bp = B;
+  L.Cp = C;
+  L.alpha = alpha;
+  L.beta = beta;
+  return tcg::launch_math(L, Bt->math, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" tc_status tc_batch_destroy(tc_batch_t batch) {
+  if (!batch) return TC_OK;
+  Batch* B = reinterpret_cast<Batch*>(batch);
+  cudaFree(B->d_items);
+  cudaFree(B->d_work);
+  delete B;
+  return TC_OK;
+}

@@ -2,11 +2,27 @@
 // sm_103a: mbarriers with bounded waits, tensor memory (TMEM) allocation,
 // tcgen05.mma / commit / ld / st, and shared-memory matrix descriptors.
 #pragma once
+#include <cuda_runtime.h>
+
 #include <cstdint>
 
 namespace tc {
 
-extern __device__ int g_device_status;  // contract.cu
+// Set to 1 by a bounded wait that ran out.  Each translation unit that
+// includes this header has its own flag (the library is compiled without
+// relocatable device code); read_clear_status() reads and clears this unit's
+// flag and tc_device_status() combines the units.
+static __device__ int g_device_status = 0;
+
+static inline cudaError_t read_clear_status(int* h, cudaStream_t s) {
+  static const int zero = 0;
+  cudaError_t e =
+      cudaMemcpyFromSymbolAsync(h, g_device_status, sizeof(int), 0, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyToSymbolAsync(g_device_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice,
+                                s);
+  return e;
+}
 
 // ----------------------------------------------------------------- mbarrier
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -117,6 +133,13 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
         "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                 "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
 }
 
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {

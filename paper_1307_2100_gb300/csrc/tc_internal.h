@@ -42,6 +42,8 @@ struct GemmArgs {
   int32_t math;                // tc_math
   int32_t raster;              // tensor-core GEMM: 1 = n-tiles fastest in launch order
   int32_t chunk_kb;            // tensor-core GEMM: K blocks per FP32 accumulation chunk
+  int32_t swapped;             // batched items: the kernel's first operand is B
+  int32_t pad_;
   void* ws;                    // workspace (DOT partials)
   int64_t ws_elems;
 };
@@ -90,6 +92,8 @@ tc_status launch_scale(const Group& gc, void* C, double beta, tc_dtype dt, int64
 tc_status launch_gemm_tc(const GemmArgs& a, int math, void* stream);
 int dot_partials(const GemmArgs& a, int tile);
 int num_tiles_tc();
+// Enqueue a read-and-clear of the tensor-core kernels' timeout flag into *h.
+tc_status tc_gemm_read_status(int* h, void* stream);
 int tc_chunk_kb(int math, int tile);
 int num_tiles_simt(tc_dtype dt);
 int num_tiles_gemv();

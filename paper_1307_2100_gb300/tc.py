@@ -15,6 +15,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libtc.so")
 
 TC_OK = 0
+TC_ERR_TIMEOUT = 8
 STATUS = {0: "TC_OK", 1: "TC_ERR_INVALID_ARG", 2: "TC_ERR_LABEL", 3: "TC_ERR_EXTENT_MISMATCH",
           4: "TC_ERR_STRIDE", 5: "TC_ERR_UNSUPPORTED", 6: "TC_ERR_WORKSPACE", 7: "TC_ERR_CUDA",
           8: "TC_ERR_TIMEOUT", 9: "TC_ERR_NO_SELECTOR"}
@@ -57,6 +58,12 @@ class PlanInfo(ctypes.Structure):
         return d
 
 
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("n_items", ctypes.c_int32), ("math", ctypes.c_int32),
+                ("n_tiles", ctypes.c_int64), ("flops", ctypes.c_double),
+                ("min_bytes", ctypes.c_double)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is not built; run paper_1307_2100_gb300.build.build()")
@@ -73,6 +80,16 @@ def _load():
     lib.tc_contract.restype = ctypes.c_int
     lib.tc_contract.argtypes = [P, ctypes.c_double, P, P, ctypes.c_double, P, P, ctypes.c_size_t,
                                 P]
+    lib.tc_batch_plan.restype = ctypes.c_int
+    lib.tc_batch_plan.argtypes = [ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_int32]
+    lib.tc_batch_get_info.restype = ctypes.c_int
+    lib.tc_batch_get_info.argtypes = [P, ctypes.POINTER(BatchInfo)]
+    lib.tc_contract_batched.restype = ctypes.c_int
+    lib.tc_contract_batched.argtypes = [P, P, P, P, P, P, P]
+    lib.tc_batch_destroy.restype = ctypes.c_int
+    lib.tc_batch_destroy.argtypes = [P]
+    lib.tc_selftest_wait_timeout.restype = ctypes.c_int
+    lib.tc_selftest_wait_timeout.argtypes = [ctypes.c_int64, P]
     lib.tc_device_status.restype = ctypes.c_int
     lib.tc_device_status.argtypes = [P]
     lib.tc_status_string.restype = ctypes.c_char_p
@@ -146,3 +163,40 @@ def tc_contract(plan: int, alpha: float, A: int, B: int, beta: float, C: int, wo
 
 def tc_device_status(stream: int = 0) -> int:
     return lib.tc_device_status(ctypes.c_void_p(stream))
+
+
+def tc_batch_plan(plans) -> int:
+    arr = (ctypes.c_void_p * max(len(plans), 1))(*plans)
+    out = ctypes.c_void_p()
+    st = lib.tc_batch_plan(ctypes.byref(out), arr, len(plans))
+    if st != TC_OK:
+        raise TcError(st, "tc_batch_plan")
+    return out.value
+
+
+def tc_batch_get_info(batch: int) -> BatchInfo:
+    info = BatchInfo()
+    st = lib.tc_batch_get_info(ctypes.c_void_p(batch), ctypes.byref(info))
+    if st != TC_OK:
+        raise TcError(st, "tc_batch_get_info")
+    return info
+
+
+def tc_contract_batched(batch: int, A: int, B: int, C: int, alpha: int, beta: int,
+                        stream: int = 0) -> None:
+    """A, B, C, alpha, beta: device addresses of arrays of n pointers / doubles."""
+    st = lib.tc_contract_batched(ctypes.c_void_p(batch), ctypes.c_void_p(A), ctypes.c_void_p(B),
+                                 ctypes.c_void_p(C), ctypes.c_void_p(alpha),
+                                 ctypes.c_void_p(beta), ctypes.c_void_p(stream))
+    if st != TC_OK:
+        raise TcError(st, "tc_contract_batched")
+
+
+def tc_batch_destroy(batch: int) -> None:
+    lib.tc_batch_destroy(ctypes.c_void_p(batch))
+
+
+def tc_selftest_wait_timeout(timeout_ns: int, stream: int = 0) -> None:
+    st = lib.tc_selftest_wait_timeout(int(timeout_ns), ctypes.c_void_p(stream))
+    if st != TC_OK:
+        raise TcError(st, "tc_selftest_wait_timeout")

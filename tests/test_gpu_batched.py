@@ -1,0 +1,135 @@
+"""GPU parity of the batched persistent launch (tc_contract_batched): every
+item against the split-form oracle and the FP64 oracle, against the same
+contraction run alone, and replayed from a captured CUDA graph."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import precision as op
+import tcsynth as ts
+from gpu_util import compare
+
+pytestmark = pytest.mark.gpu
+TOL_METHOD = 2e-6
+TOL_FP64 = {"bf16": 1e-2, "bf16x3": 2e-5, "bf16x6": 1e-6}
+
+
+def _plans_and_buffers(items, form, mapping="auto"):
+    import torch
+    from paper_1307_2100_gb300 import Contraction
+    dev = torch.device("cuda:0")
+    plans, bufs = [], []
+    for p in items:
+        pl = Contraction((p.A.labels, p.A.extents, p.A.strides),
+                         (p.B.labels, p.B.extents, p.B.strides),
+                         (p.C.labels, p.C.extents, p.C.strides), "f32", form, mapping)
+        plans.append(pl)
+        A = torch.from_numpy(np.ascontiguousarray(p.A.data, np.float32)).to(dev)
+        B = torch.from_numpy(np.ascontiguousarray(p.B.data, np.float32)).to(dev)
+        C = torch.from_numpy(np.ascontiguousarray(p.C.data, np.float32)).to(dev)
+        bufs.append((A, B, C))
+    return plans, bufs
+
+
+def _pointer_arrays(bufs, items):
+    import torch
+    dev = torch.device("cuda:0")
+    ptr = lambda k: torch.tensor([b[k].data_ptr() for b in bufs], dtype=torch.int64, device=dev)
+    alpha = torch.tensor([p.alpha for p in items], dtype=torch.float64, device=dev)
+    beta = torch.tensor([p.beta for p in items], dtype=torch.float64, device=dev)
+    return ptr(0), ptr(1), ptr(2), alpha, beta
+
+
+def _run_batch(items, form):
+    import torch
+    from paper_1307_2100_gb300 import tc
+    plans, bufs = _plans_and_buffers(items, form)
+    batch = tc.tc_batch_plan([pl.handle for pl in plans])
+    try:
+        pa, pb, pc, al, be = _pointer_arrays(bufs, items)
+        s = torch.cuda.current_stream().cuda_stream
+        tc.tc_contract_batched(batch, pa.data_ptr(), pb.data_ptr(), pc.data_ptr(),
+                               al.data_ptr(), be.data_ptr(), s)
+        torch.cuda.synchronize()
+        assert tc.tc_device_status(s) == tc.TC_OK
+        info = tc.tc_batch_get_info(batch)
+    finally:
+        tc.tc_batch_destroy(batch)
+    return [b[2].cpu().numpy().astype(np.float64) for b in bufs], info
+
+
+def small_items(n=48, seed=ts.BASE_SEED + 30):
+    return ts.batching_items(n, seed=seed, max_elems=1 << 16, max_flops=float(1 << 26), lo=4,
+                             hi=40)
+
+
+@pytest.mark.parametrize("form", ["bf16x3", "bf16x6"])
+def test_batched_items_against_oracles(form):
+    items = small_items()
+    outs, info = _run_batch(items, form)
+    assert info.n_items == len(items)
+    for p, got in zip(items, outs):
+        em = compare(got, op.contract_form(p, form), p.C)
+        e64 = compare(got, oracle.contract_problem(p), p.C)
+        assert em <= TOL_METHOD, (p.A.labels, p.B.labels, em)
+        assert e64 <= TOL_FP64[form], (p.A.labels, p.B.labels, e64)
+
+
+def test_batched_alpha_beta():
+    items = small_items(16, seed=ts.BASE_SEED + 31)
+    rng = np.random.default_rng(5)
+    for p in items:
+        p.alpha = float(rng.uniform(-2, 2))
+        p.beta = float(rng.uniform(-1, 1))
+        p.C.data = rng.uniform(-1, 1, p.C.data.size).astype(np.float32)
+    outs, _ = _run_batch(items, "bf16x6")
+    for p, got in zip(items, outs):
+        assert compare(got, op.contract_form(p, "bf16x6"), p.C) <= TOL_METHOD
+
+
+def test_batched_graph_capture_and_replay():
+    import torch
+    from paper_1307_2100_gb300 import tc
+    items = small_items(24, seed=ts.BASE_SEED + 32)
+    plans, bufs = _plans_and_buffers(items, "bf16x6")
+    batch = tc.tc_batch_plan([pl.handle for pl in plans])
+    try:
+        pa, pb, pc, al, be = _pointer_arrays(bufs, items)
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            tc.tc_contract_batched(batch, pa.data_ptr(), pb.data_ptr(), pc.data_ptr(),
+                                   al.data_ptr(), be.data_ptr(), s.cuda_stream)
+        for rep in range(2):
+            rng = np.random.default_rng(100 + rep)
+            for p, (A, B, C) in zip(items, bufs):
+                p.A.data = rng.uniform(-1, 1, p.A.data.size).astype(np.float32)
+                p.B.data = rng.uniform(-1, 1, p.B.data.size).astype(np.float32)
+                A.copy_(torch.from_numpy(p.A.data))
+                B.copy_(torch.from_numpy(p.B.data))
+                C.fill_(float("nan"))
+            torch.cuda.synchronize()
+            g.replay()
+            torch.cuda.synchronize()
+            for p, (A, B, C) in zip(items, bufs):
+                got = C.cpu().numpy().astype(np.float64)
+                assert compare(got, op.contract_form(p, "bf16x6"), p.C) <= TOL_METHOD
+    finally:
+        tc.tc_batch_destroy(batch)
+
+
+def test_batched_equals_single_launches_bitwise():
+    """The batched launch runs the same tiles with the same chunking as a lone
+    tc_contract of a tensor-core plan, so those results agree bit for bit."""
+    from gpu_util import run
+    items = small_items(20, seed=ts.BASE_SEED + 33)
+    outs, _ = _run_batch(items, "bf16x6")
+    checked = 0
+    for p, got in zip(items, outs):
+        info = []
+        single = run(p, "bf16x6", "auto", plan_out=info)
+        if info[0]["kernel_name"] != "gemm_tc":
+            continue
+        np.testing.assert_array_equal(got, single)
+        checked += 1
+    assert checked >= 5
