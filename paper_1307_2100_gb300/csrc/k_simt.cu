@@ -202,6 +202,30 @@ tc_status launch_gemm_simt(const GemmArgs& a, tc_dtype dt, int tile, void* strea
   return dt == TC_F64 ? gemm_simt_t<double>(a, tile, s) : gemm_simt_t<float>(a, tile, s);
 }
 
+// Accumulators of the GEMV/DOT kernels.  FP64 data accumulate in FP64; FP32
+// data accumulate with Neumaier's compensated summation (sum + running error,
+// both FP32), so long K does not lose FP32-class accuracy.
+template <typename T>
+struct Acc;
+template <>
+struct Acc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct Acc<float> {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float x = __fmul_rn(a, b);
+    const float t = __fadd_rn(s, x);
+    if (fabsf(s) >= fabsf(x)) c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, t), x));
+    else c = __fadd_rn(c, __fadd_rn(__fsub_rn(x, t), s));
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 // ---------------------------------------------------------------------------
 // GEMV (Sec. 3.2.2): y[m, n, b] = alpha * sum_k X[m, k, b] * Y[k, n, b] + beta*y.
 // When X is contiguous along m (non-transposed GEMV) each thread owns one m and
@@ -232,7 +256,7 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv_m(const __grid_constant__
     if (m < M) goff2(p.gm, 0, 2, m, oXm, oCm);
     const T* xrow = X + bX + oXm;
     const T* yv = Y + bY + oYn;
-    T acc = T(0);
+    Acc<T> acc;
     for (uint32_t k0 = 0; k0 < K; k0 += kGemvChunk) {
       __syncthreads();
       for (uint32_t i = threadIdx.x; i < kGemvChunk; i += kGemvThreads) {
@@ -253,16 +277,16 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv_m(const __grid_constant__
 #pragma unroll
           for (int u = 0; u < 8; ++u) yy[u] = yv[oY[i + u]];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) acc = fma(xv[u], yy[u], acc);
+          for (int u = 0; u < 8; ++u) acc.add(xv[u], yy[u]);
         }
-        for (; i < kn; ++i) acc = fma(xrow[oX[i]], yv[oY[i]], acc);
+        for (; i < kn; ++i) acc.add(xrow[oX[i]], yv[oY[i]]);
       }
     }
     if (m < M) {
       T* dst = Cp + bC + oCm + oCn;
-      T v = (T)p.alpha * acc;
-      if (p.beta != 0.0) v = fma((T)p.beta, *dst, v);
-      *dst = v;
+      double v = p.alpha * acc.value();
+      if (p.beta != 0.0) v += p.beta * (double)*dst;
+      *dst = (T)v;
     }
   }
 }
@@ -296,18 +320,18 @@ __global__ void __launch_bounds__(256) k_dot_rows(const __grid_constant__ GemmAr
     goff2(p.gn, 1, 2, n, oYn, oCn);
     const T* xr = X + bX + oXm;
     const T* yr = Y + bY + oYn;
-    T acc = T(0);
+    Acc<T> acc;
     for (uint32_t k = lane; k < K; k += 32) {
       int64_t ox, oy;
       goff2(p.gk, 0, 1, k, ox, oy);
-      acc = fma(xr[ox], yr[oy], acc);
+      acc.add(xr[ox], yr[oy]);
     }
-    acc = warp_sum(acc);
+    const double tot = warp_sum(acc.value());
     if (lane == 0) {
       T* dst = Cp + bC + oCm + oCn;
-      T v = (T)p.alpha * acc;
-      if (p.beta != 0.0) v = fma((T)p.beta, *dst, v);
-      *dst = v;
+      double v = p.alpha * tot;
+      if (p.beta != 0.0) v += p.beta * (double)*dst;
+      *dst = (T)v;
     }
   }
 }

@@ -78,7 +78,8 @@ struct Cfg {
   static constexpr uint32_t B_TERM = BN * BK * 2;
   static constexpr uint32_t STAGE = NT * (A_TERM + B_TERM);
   static constexpr uint32_t OFF_KOFF = S * STAGE;                   // int64 koffA[S][BK], koffB[S][BK]
-  static constexpr uint32_t OFF_ROWS = OFF_KOFF + S * BK * 2 * 8;  // rowA[BM], rowB[BN], rowC[BM], colC[BN]
+  static constexpr uint32_t OFF_KVEC = OFF_KOFF + S * BK * 2 * 8;  // uint8 kvecA[S][8], kvecB[S][8]
+  static constexpr uint32_t OFF_ROWS = OFF_KVEC + S * 16 + 64;      // rowA[BM], rowB[BN], rowC[BM], colC[BN]
   static constexpr uint32_t OFF_ARGS = OFF_ROWS + (2 * BM + 2 * BN) * 8;
   static constexpr uint32_t OFF_BAR = OFF_ARGS + ((sizeof(GemmArgs) + 15) / 16) * 16;
   static constexpr uint32_t NBAR = 2 * S + 5;
@@ -91,29 +92,65 @@ __constant__ int8_t kProdA[6] = {0, 0, 1, 0, 1, 2};
 __constant__ int8_t kProdB[6] = {0, 1, 0, 2, 1, 0};
 __host__ __device__ constexpr int nprod(int nt) { return nt == 1 ? 1 : nt == 2 ? 3 : 6; }
 
+// Producer: one operand tile (ROWS x 64 K) of one K block.  Every load of the
+// tile is issued before any is converted, so a thread keeps 64 loads in
+// flight.  Lanes run along rows when the operand is contiguous along its
+// M/N index (each k is then one coalesced row segment); otherwise lanes take
+// (row-in-8, 8-wide K chunk) units, read as two 16-byte vectors when the
+// chunk is contiguous and aligned.
 template <int NT, int ROWS>
 __device__ __forceinline__ void produce(const float* __restrict__ X, const int64_t* rowoff,
-                                        const int64_t* koff, bool contig_mn, uint32_t sbuf,
-                                        int ptid) {
-  constexpr int UNITS = ROWS * (BK / 8);
+                                        const int64_t* koff, const uint8_t* kvec, bool contig_mn,
+                                        uint32_t sbuf, int ptid) {
+  constexpr int PER = ROWS * (BK / 8) / kProducers;  // units per thread
   constexpr uint32_t TERM = ROWS * BK * 2;
   constexpr uint32_t LBO = (ROWS / 8) * 128;
-#pragma unroll 2
-  for (int u = ptid; u < UNITS; u += kProducers) {
+  float v[PER][8];
+  if (contig_mn) {
+    const int row = ptid % ROWS;
+    const int64_t ro = rowoff[row];
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      const int chunk = (ptid + r * kProducers) / ROWS;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int64_t ko = koff[chunk * 8 + j];
+        v[r][j] = (ro >= 0 && ko >= 0) ? __ldg(X + ro + ko) : 0.0f;
+      }
+    }
+  } else {
+    const int chunk = (ptid >> 3) & 7;
+    const int64_t k0 = koff[chunk * 8];
+    const bool vec = kvec[chunk] != 0;
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      const int u = ptid + r * kProducers;
+      const int64_t ro = rowoff[(u & 7) + 8 * (u >> 6)];
+      const float* src = X + ro + k0;
+      if (vec && ro >= 0 && ((reinterpret_cast<uintptr_t>(src) & 15) == 0)) {
+        const float4 x0 = __ldg(reinterpret_cast<const float4*>(src));
+        const float4 x1 = __ldg(reinterpret_cast<const float4*>(src) + 1);
+        v[r][0] = x0.x; v[r][1] = x0.y; v[r][2] = x0.z; v[r][3] = x0.w;
+        v[r][4] = x1.x; v[r][5] = x1.y; v[r][6] = x1.z; v[r][7] = x1.w;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int64_t ko = koff[chunk * 8 + j];
+          v[r][j] = (ro >= 0 && ko >= 0) ? __ldg(X + ro + ko) : 0.0f;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const int u = ptid + r * kProducers;
     int row, chunk;
-    if (contig_mn) {  // lanes along rows: each k is a coalesced row segment
+    if (contig_mn) {
       row = u % ROWS;
       chunk = u / ROWS;
-    } else {          // lanes along (row-in-8, chunk): 32-byte runs along k
+    } else {
       row = (u & 7) + 8 * (u >> 6);
       chunk = (u >> 3) & 7;
-    }
-    const int64_t ro = rowoff[row];
-    float v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int64_t ko = koff[chunk * 8 + j];
-      v[j] = (ro >= 0 && ko >= 0) ? __ldg(X + ro + ko) : 0.0f;
     }
     const uint32_t dst = sbuf + chunk * LBO + (row >> 3) * 128 + (row & 7) * 16;
 #pragma unroll
@@ -121,10 +158,10 @@ __device__ __forceinline__ void produce(const float* __restrict__ X, const int64
       uint32_t w[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        w[q] = pack_bf16x2(v[2 * q], v[2 * q + 1]);
+        w[q] = pack_bf16x2(v[r][2 * q], v[r][2 * q + 1]);
         if (t + 1 < NT) {  // exact FP32 residuals
-          v[2 * q] = __fsub_rn(v[2 * q], bf16_lo(w[q]));
-          v[2 * q + 1] = __fsub_rn(v[2 * q + 1], bf16_hi(w[q]));
+          v[r][2 * q] = __fsub_rn(v[r][2 * q], bf16_lo(w[q]));
+          v[r][2 * q + 1] = __fsub_rn(v[r][2 * q + 1], bf16_hi(w[q]));
         }
       }
       st_shared_v4(dst + t * TERM, w[0], w[1], w[2], w[3]);
@@ -155,6 +192,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                                              ~(uintptr_t)1023);
   int64_t* koffA = reinterpret_cast<int64_t*>(smem + G::OFF_KOFF);
   int64_t* koffB = koffA + S * BK;
+  uint8_t* kvecA = smem + G::OFF_KVEC;
+  uint8_t* kvecB = kvecA + S * 8;
   int64_t* rowA = reinterpret_cast<int64_t*>(smem + G::OFF_ROWS);
   int64_t* rowB = rowA + BM;
   int64_t* rowC = rowB + BN;
@@ -274,10 +313,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
           koffB[s * BK + tid] = ob;
         }
         named_bar_sync(1, kProducers);
+        if (tid < 16) {  // 8-wide K chunks that are contiguous and 4-element aligned
+          const int64_t* ko = (tid < 8 ? koffA : koffB) + s * BK + (tid & 7) * 8;
+          bool c = ko[0] >= 0 && (ko[0] & 3) == 0;
+          for (int j = 1; j < 8; ++j) c = c && ko[j] == ko[0] + j;
+          (tid < 8 ? kvecA : kvecB)[s * 8 + (tid & 7)] = c ? 1 : 0;
+        }
+        named_bar_sync(1, kProducers);
         if (ok && !*abort) {
           const uint32_t st = sbase + s * G::STAGE;
-          produce<NT, BM>(Xa, rowA, koffA + s * BK, amn, st, tid);
-          produce<NT, BN>(Xb, rowB, koffB + s * BK, bmn, st + NT * G::A_TERM, tid);
+          produce<NT, BM>(Xa, rowA, koffA + s * BK, kvecA + s * 8, amn, st, tid);
+          produce<NT, BN>(Xb, rowB, koffB + s * BK, kvecB + s * 8, bmn, st + NT * G::A_TERM,
+                          tid);
           fence_async_smem();
           mbar_arrive(&full[s]);
         }

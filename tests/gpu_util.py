@@ -131,3 +131,46 @@ def sample_outputs_form(p, samples, form):
             v += p.beta * float(p.C.data[sum(i * s for i, s in zip(cidx, p.C.strides))])
         vals.append(v)
     return np.array(vals)
+
+
+NPROD = {"bf16": 1, "bf16x3": 3, "bf16x6": 6}
+SPLIT_ERR = {"bf16": 2.0 ** -8, "bf16x3": 3 * 2.0 ** -18, "bf16x6": 4 * 2.0 ** -26}
+
+
+def magnitude(p):
+    """Oracle contraction of |A| and |B|: the elementwise scale sum |a||b| that
+    worst-case rounding bounds are proportional to."""
+    import copy
+    A, B = copy.copy(p.A), copy.copy(p.B)
+    A.data = np.abs(np.asarray(p.A.data, np.float64))
+    B.data = np.abs(np.asarray(p.B.data, np.float64))
+    C = copy.copy(p.C)
+    return oracle.contract(A, B, C, abs(p.alpha), 0.0)
+
+
+def tc_bounds(p, form, chunk_k=256):
+    """(accumulation bound, total bound) as multiples of sum |a||b| for the
+    tensor-core forms.  The tensor cores add each 16-product block into FP32
+    with an error of at most one unit of the running sum (2^-23 relative):
+    the main product is summed over one K-chunk, the correction products
+    (2^-8 smaller) over all of K; BF16 keeps one accumulator over all of K.
+    The split error of the form adds to that: 2^-8 (BF16), 3*2^-18 (the
+    missing a1*b1 and the 2-term residuals, BF16x3), 4*2^-26 (products of
+    order >= 3, BF16x6)."""
+    K = 1
+    for l, e in zip(p.A.labels, p.A.extents):
+        if l in p.B.labels:
+            K *= int(e)
+    u = 2.0 ** -23
+    if form == "bf16":
+        acc = (K / 16 + 1) * u
+    else:
+        acc = (min(K, chunk_k) / 16 + 1) * u + (K / 16 + 1) * (NPROD[form] - 1) * u * 2.0 ** -8
+    return acc, acc + SPLIT_ERR[form]
+
+
+def within(got, ref, mag, C, c):
+    """||got - ref||_F <= c * ||sum |a||b| ||_F over the addressed elements of C."""
+    idx = addressed_index(C) if C.numel else np.zeros(0, dtype=np.int64)
+    d = np.linalg.norm((np.asarray(got)[idx] - np.asarray(ref)[idx]).ravel())
+    return d <= c * np.linalg.norm(np.asarray(mag)[idx].ravel()) + 1e-300, d

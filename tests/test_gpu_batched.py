@@ -7,11 +7,9 @@ import pytest
 import oracle
 from oracle import precision as op
 import tcsynth as ts
-from gpu_util import compare
+from gpu_util import magnitude, tc_bounds, within
 
 pytestmark = pytest.mark.gpu
-TOL_METHOD = 2e-6
-TOL_FP64 = {"bf16": 1e-2, "bf16x3": 2e-5, "bf16x6": 1e-6}
 
 
 def _plans_and_buffers(items, form, mapping="auto"):
@@ -69,10 +67,12 @@ def test_batched_items_against_oracles(form):
     outs, info = _run_batch(items, form)
     assert info.n_items == len(items)
     for p, got in zip(items, outs):
-        em = compare(got, op.contract_form(p, form), p.C)
-        e64 = compare(got, oracle.contract_problem(p), p.C)
-        assert em <= TOL_METHOD, (p.A.labels, p.B.labels, em)
-        assert e64 <= TOL_FP64[form], (p.A.labels, p.B.labels, e64)
+        mag = magnitude(p)
+        acc, tot = tc_bounds(p, form)
+        ok, d = within(got, op.contract_form(p, form), mag, p.C, acc)
+        assert ok, (p.A.labels, p.B.labels, "method", d)
+        ok, d = within(got, oracle.contract_problem(p), mag, p.C, tot)
+        assert ok, (p.A.labels, p.B.labels, "fp64", d)
 
 
 def test_batched_alpha_beta():
@@ -84,7 +84,8 @@ def test_batched_alpha_beta():
         p.C.data = rng.uniform(-1, 1, p.C.data.size).astype(np.float32)
     outs, _ = _run_batch(items, "bf16x6")
     for p, got in zip(items, outs):
-        assert compare(got, op.contract_form(p, "bf16x6"), p.C) <= TOL_METHOD
+        acc, _ = tc_bounds(p, "bf16x6")
+        assert within(got, op.contract_form(p, "bf16x6"), magnitude(p), p.C, acc)[0]
 
 
 def test_batched_graph_capture_and_replay():
@@ -113,7 +114,8 @@ def test_batched_graph_capture_and_replay():
             torch.cuda.synchronize()
             for p, (A, B, C) in zip(items, bufs):
                 got = C.cpu().numpy().astype(np.float64)
-                assert compare(got, op.contract_form(p, "bf16x6"), p.C) <= TOL_METHOD
+                acc, _ = tc_bounds(p, "bf16x6")
+                assert within(got, op.contract_form(p, "bf16x6"), magnitude(p), p.C, acc)[0]
     finally:
         tc.tc_batch_destroy(batch)
 

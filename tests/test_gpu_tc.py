@@ -1,12 +1,13 @@
 """GPU parity of the tensor-core path (FP32 storage; BF16, BF16x3, BF16x6 math).
 
-Two references:
+Two references, each with a worst-case bound proportional to sum |a||b|
+(gpu_util.tc_bounds derives them from the arithmetic):
   * the split-form oracle (oracle.precision.contract_form): the same BF16 term
-    products summed exactly in FP64.  The kernel differs from it only by FP32
-    accumulation inside one K-chunk (chunks are summed in FP64), so the bound
-    is a few FP32 ulps of the result norm: relative Frobenius <= 2e-6;
-  * the FP64 oracle on the FP32 inputs, within each form's stated error:
-    BF16 <= 1e-2, BF16x3 <= 2e-5, BF16x6 <= 1e-6 (FP32-class).
+    products summed exactly in FP64; the kernel differs only by its FP32
+    accumulation;
+  * the FP64 oracle on the FP32 inputs: the form's split error on top.
+The FP32-class claim is checked as stated: BF16x6 on the precision workload
+is within 1e-6 relative Frobenius of the FP64 oracle.
 Integer inputs in [-4, 4] are BF16 values and all partial sums are exact in
 FP32, so every form must then match the FP64 oracle bit for bit."""
 import numpy as np
@@ -15,14 +16,13 @@ import pytest
 import oracle
 from oracle import precision as op
 import tcsynth as ts
-from gpu_util import (compare, gather, random_output_indices, run, sample_outputs,
-                      sample_outputs_form)
+from gpu_util import (compare, gather, magnitude, random_output_indices, run, sample_outputs,
+                      sample_outputs_form, tc_bounds, within)
 
 pytestmark = pytest.mark.gpu
 
 FORMS = ["bf16", "bf16x3", "bf16x6"]
-TOL_METHOD = 2e-6
-TOL_FP64 = {"bf16": 1e-2, "bf16x3": 2e-5, "bf16x6": 1e-6}
+FP32_CLASS = 1e-6
 
 
 def f32(p):
@@ -53,27 +53,30 @@ def test_integer_inputs_exact(form):
 def test_forms_against_method_and_fp64_oracles(form):
     for p in shapes():
         got = run(p, form, "auto")
-        ref_m = op.contract_form(p, form)
-        ref_64 = oracle.contract_problem(p)
-        em = compare(got, ref_m, p.C)
-        e64 = compare(got, ref_64, p.C)
-        assert em <= TOL_METHOD, (p.name, form, em)
-        assert e64 <= TOL_FP64[form], (p.name, form, e64)
+        mag = magnitude(p)
+        acc, tot = tc_bounds(p, form)
+        ok, d = within(got, op.contract_form(p, form), mag, p.C, acc)
+        assert ok, (p.name, form, "method", d)
+        ok, d = within(got, oracle.contract_problem(p), mag, p.C, tot)
+        assert ok, (p.name, form, "fp64", d)
 
 
 @pytest.mark.parametrize("mapping", ["fused_gemm", "slice_gemm", "copy_gemm"])
 def test_bf16x6_mappings(mapping):
     p = f32(ts.fused_permute_48(n=19))
     got = run(p, "bf16x6", mapping)
-    assert compare(got, op.contract_form(p, "bf16x6"), p.C) <= TOL_METHOD
+    acc, _ = tc_bounds(p, "bf16x6")
+    assert within(got, op.contract_form(p, "bf16x6"), magnitude(p), p.C, acc)[0]
 
 
 @pytest.mark.parametrize("tile", [0, 1, 2])
 def test_chunk_configurations(tile):
     p = f32(ts.problem("longk", "aijb", "ijc", "abc", dict(a=130, i=40, j=60, b=2, c=129), 53))
+    mag = magnitude(p)
     for form in ("bf16x3", "bf16x6"):
         got = run(p, form, "fused_gemm", tile)
-        assert compare(got, op.contract_form(p, form), p.C) <= TOL_METHOD, (tile, form)
+        acc, _ = tc_bounds(p, form, chunk_k={0: 256, 1: 64, 2: 1024}[tile])
+        assert within(got, op.contract_form(p, form), mag, p.C, acc)[0], (tile, form)
 
 
 def test_alpha_beta_tc():
@@ -81,7 +84,8 @@ def test_alpha_beta_tc():
     p.C.data = np.linspace(-2, 2, p.C.data.size).astype(np.float32)
     p.alpha, p.beta = -1.5, 0.25
     got = run(p, "bf16x6", "auto")
-    assert compare(got, op.contract_form(p, "bf16x6"), p.C) <= TOL_METHOD
+    acc, _ = tc_bounds(p, "bf16x6")
+    assert within(got, op.contract_form(p, "bf16x6"), magnitude(p), p.C, acc)[0]
 
 
 def test_precision_workload_full_size_sampled():
@@ -90,9 +94,19 @@ def test_precision_workload_full_size_sampled():
     p = ts.precision_ccd()
     s = random_output_indices(p, 96, seed=3)
     ref64 = sample_outputs(p, s)
+    import copy
+    pm = copy.copy(p)
+    pm.A = copy.copy(p.A)
+    pm.B = copy.copy(p.B)
+    pm.A.data = np.abs(p.A.data)
+    pm.B.data = np.abs(p.B.data)
+    mag = sample_outputs(pm, s)
     for form in FORMS:
         got = run(p, form, "auto")
         g = gather(got, p.C, s)
-        assert oracle.rel_fro(g, sample_outputs_form(p, s, form)) <= TOL_METHOD, form
-        assert oracle.rel_fro(g, ref64) <= TOL_FP64[form], form
+        acc, tot = tc_bounds(p, form)
+        assert np.linalg.norm(g - sample_outputs_form(p, s, form)) <= acc * np.linalg.norm(mag), form
+        assert np.linalg.norm(g - ref64) <= tot * np.linalg.norm(mag), form
         assert np.all(np.isfinite(got))
+        if form == "bf16x6":   # the FP32-class claim
+            assert oracle.rel_fro(g, ref64) <= FP32_CLASS
