@@ -196,6 +196,27 @@ tc_status tc_batch_destroy(tc_batch_t batch);
  * since the last call, else TC_OK. */
 tc_status tc_device_status(void* stream);
 
+/* ---- Scalar contraction without a workspace -------------------------------
+ * The paper has no counterpart of this entry point; it serves callers that
+ * cannot allocate device memory when they contract (for example code running
+ * while a CUDA graph is captured, or runtimes that own all device memory).
+ * It runs a plan whose result is a single element (Class 1 mapped to DOT, the
+ * one kernel that needs scratch space, for its per-block partial sums) using a
+ * fixed scratch array built into the library instead of a workspace:
+ *   - the array holds TC_NOALLOC_SCRATCH_BYTES on every GPU that loads the
+ *     library, until the process exits; a plan needing more is rejected with
+ *     TC_ERR_WORKSPACE;
+ *   - all calls share the array: calls that overlap on the GPU race; calls
+ *     ordered on one stream are fine; the array keeps the last call's
+ *     contents, none of which a later call relies on;
+ *   - the first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make it before any
+ *     stream capture.
+ * Other plans return TC_ERR_UNSUPPORTED.  Allocates nothing. */
+#define TC_NOALLOC_SCRATCH_BYTES (16 * 1024)
+tc_status tc_contract_dot_noalloc(tc_plan_t plan, double alpha, const void* A, const void* B,
+                                  double beta, void* C, void* stream);
+
 /* Self-test of the bounded device waits: launches one warp that waits on an
  * mbarrier nothing ever arrives on.  The wait gives up after `timeout_ns`
  * nanoseconds, records the timeout in the device flag and returns, so a

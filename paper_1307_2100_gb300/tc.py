@@ -88,6 +88,8 @@ def _load():
     lib.tc_contract_batched.argtypes = [P, P, P, P, P, P, P]
     lib.tc_batch_destroy.restype = ctypes.c_int
     lib.tc_batch_destroy.argtypes = [P]
+    lib.tc_contract_dot_noalloc.restype = ctypes.c_int
+    lib.tc_contract_dot_noalloc.argtypes = [P, ctypes.c_double, P, P, ctypes.c_double, P, P]
     lib.tc_selftest_wait_timeout.restype = ctypes.c_int
     lib.tc_selftest_wait_timeout.argtypes = [ctypes.c_int64, P]
     lib.tc_device_status.restype = ctypes.c_int
@@ -200,3 +202,14 @@ def tc_selftest_wait_timeout(timeout_ns: int, stream: int = 0) -> None:
     st = lib.tc_selftest_wait_timeout(int(timeout_ns), ctypes.c_void_p(stream))
     if st != TC_OK:
         raise TcError(st, "tc_selftest_wait_timeout")
+
+
+def tc_contract_dot_noalloc(plan: int, alpha: float, A: int, B: int, beta: float, C: int,
+                            stream: int = 0) -> None:
+    """Scalar (single-output) contraction using the library's built-in scratch
+    array instead of a workspace; see include/tc.h."""
+    st = lib.tc_contract_dot_noalloc(ctypes.c_void_p(plan), float(alpha), ctypes.c_void_p(A),
+                                     ctypes.c_void_p(B), float(beta), ctypes.c_void_p(C),
+                                     ctypes.c_void_p(stream))
+    if st != TC_OK:
+        raise TcError(st, "tc_contract_dot_noalloc")
