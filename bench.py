@@ -434,6 +434,115 @@ def run_ours(args):
     return 0
 
 
+def run_batching(args):
+    """512 independent contractions (orders 2-5, extents log-uniform in
+    [8, 192], 1-3 contracted indices, random storage orders, FP32) in one
+    graph-captured tc_contract_batched, against 512 tc_contract calls."""
+    import torch
+    import oracle
+    from paper_1307_2100_gb300 import build as _b
+    _b.build()
+    from paper_1307_2100_gb300 import Contraction, tc
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    items = ts.batching_items(args.items)
+    math = args.math
+    plans, bufs = [], []
+    for p in items:
+        plans.append(Contraction((p.A.labels, p.A.extents, p.A.strides),
+                                 (p.B.labels, p.B.extents, p.B.strides),
+                                 (p.C.labels, p.C.extents, p.C.strides), "f32", math, "auto"))
+        bufs.append((torch.from_numpy(p.A.data).to(dev), torch.from_numpy(p.B.data).to(dev),
+                     torch.empty(max(p.C.data.size, 1), dtype=torch.float32, device=dev)))
+    batch = tc.tc_batch_plan([pl.handle for pl in plans])
+    info = tc.tc_batch_get_info(batch)
+    ptr = lambda k: torch.tensor([b[k].data_ptr() for b in bufs], dtype=torch.int64, device=dev)
+    pa, pb, pc = ptr(0), ptr(1), ptr(2)
+    al = torch.ones(len(items), dtype=torch.float64, device=dev)
+    be = torch.zeros(len(items), dtype=torch.float64, device=dev)
+    s = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ws = [pl.workspace(dev) for pl in plans]
+
+    def batched():
+        tc.tc_contract_batched(batch, pa.data_ptr(), pb.data_ptr(), pc.data_ptr(), al.data_ptr(),
+                               be.data_ptr(), s.cuda_stream)
+
+    def separate():
+        for j, pl in enumerate(plans):
+            w = ws[j]
+            tc.tc_contract(pl.handle, 1.0, bufs[j][0].data_ptr(), bufs[j][1].data_ptr(), 0.0,
+                           bufs[j][2].data_ptr(), w.data_ptr() if w is not None else 0,
+                           w.numel() if w is not None else 0, s.cuda_stream)
+
+    with torch.cuda.stream(s):
+        for _ in range(args.warmup):
+            batched()
+            separate()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        batched()
+
+    def timed(fn):
+        ts_ = []
+        for _ in range(args.steps):
+            with torch.cuda.stream(s):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                fn()
+                e1.record(s)
+            torch.cuda.synchronize()
+            ts_.append(e0.elapsed_time(e1))
+        return float(np.median(ts_)), ts_
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    t_graph, all_graph = timed(g.replay)
+    t_sep, _ = timed(separate)
+    clk = clocks.stop()
+    status = tc.tc_device_status(s.cuda_stream)
+    # accuracy of every item against the FP64 oracle
+    g.replay()
+    torch.cuda.synchronize()
+    errs = []
+    for p, b in zip(items, bufs):
+        got = b[2].cpu().numpy().astype(np.float64)[: p.C.data.size]
+        errs.append(oracle.rel_fro(got, oracle.contract_problem(p, nthreads=cores())))
+    tc.tc_batch_destroy(batch)
+    peaks = read_peaks()
+    hbm = peaks.get("hbm_gbs", 6784.5)
+    bf16_peak = peaks.get("bf16_tflops", 1884.0)
+    flops = info.flops
+    roof_ms = 1e3 * max(flops * NPROD[math] / (bf16_peak * 1e12), info.min_bytes / (hbm * 1e9))
+    value = flops / (t_graph / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_graph, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 storage, " + math,
+        "data": "synthetic (seeded uniform[-1,1); shapes of the batched workload)",
+        "config": {"workload": f"batching: {len(items)} contractions, orders 2-5, extents "
+                               "log-uniform [8,192], 1-3 contracted, random storage orders",
+                   "l2": "flushed between steps (256 MiB write, outside timing)",
+                   "launch": "one CUDA graph of tc_contract_batched"},
+        "roofline": {"bound": "hbm" if info.min_bytes / (hbm * 1e9) >
+                     flops * NPROD[math] / (bf16_peak * 1e12) else "tensor",
+                     "achieved_ms": t_graph, "roofline_ms": roof_ms, "frac": roof_ms / t_graph,
+                     "traffic": None},
+        "batched_vs_separate": {"batched_ms": t_graph, "separate_ms": t_sep,
+                                "speedup": t_sep / t_graph},
+        "routes": {"tensor_core_items": info.n_tc_items, "cuda_core_items": info.n_simt_items,
+                   "tc_tiles": info.n_tiles, "simt_work": info.n_simt_work},
+        "rel_err_vs_fp64_oracle": {"max": float(np.max(errs)), "median": float(np.median(errs))},
+        "sum_flops": flops, "sum_bytes": info.min_bytes, "clocks": clk,
+        "device_status": tc.tc_status_string(status),
+        "gpu_launches": args.steps * (int(info.n_tiles > 0) + 2 * int(info.n_simt_work > 0)),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -442,7 +551,9 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
-    ap.add_argument("--workload", default="class3_fp64", choices=["class3_fp64", "precision"])
+    ap.add_argument("--workload", default="class3_fp64",
+                    choices=["class3_fp64", "precision", "batching"])
+    ap.add_argument("--items", type=int, default=512, help="batching: number of contractions")
     ap.add_argument("--math", default="bf16x6", choices=["bf16", "bf16x3", "bf16x6", "fp32"],
                     help="math of the precision workload")
     ap.add_argument("--tile", type=int, default=-1)
@@ -451,6 +562,10 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batching":
+        if args.math == "bf16x6" and "--math" not in (argv or sys.argv):
+            args.math = "bf16x3"
+        return run_batching(args)
     return run_ours(args)
 
 

@@ -154,23 +154,35 @@ tc_status tc_plan_destroy(tc_plan_t plan);
 tc_status tc_contract(tc_plan_t plan, double alpha, const void* A, const void* B, double beta,
                       void* C, void* workspace, size_t workspace_bytes, void* stream);
 
-/* ---- Batched contractions in one persistent launch ------------------------
+/* ---- Batched contractions in one submission ------------------------------
  * Many independent contractions (e.g. the products of a coupled-cluster
- * iteration, Sec. 4.2) run as one launch of the tensor-core GEMM: one CTA per
- * SM works through a list of (contraction, 128x128 output tile) entries,
- * longest tiles first.  A batch is built once from plans (FP32 storage, one
- * tensor-core math form shared by all plans, any mapping but COPY_GEMM); it
- * owns a small device table of the plans' index groups and work list, so the
- * plans may be destroyed afterwards. */
+ * iteration, Sec. 4.2) run as one submission.  A batch is built once from
+ * plans (FP32 storage, one tensor-core math form shared by all plans, any
+ * mapping but COPY_GEMM); it owns device tables of the plans' index groups,
+ * its work lists and a workspace for partial sums, so the plans may be
+ * destroyed afterwards.  Each contraction is routed by its GEMM view:
+ *   - M and N both >= the route threshold (64 by default): its 128x128 output
+ *     tiles join the work list of one persistent tensor-core launch (one CTA
+ *     per SM, longest K first);
+ *   - otherwise (the BLAS-1/2 cases of Sec. 3.2.1-3.2.2 and skinny GEMMs): a
+ *     batched CUDA-core kernel sums K segments in compensated FP32 and a
+ *     second kernel adds each output's segments in order. */
 typedef struct tc_batch_s* tc_batch_t;
 
 typedef struct {
   int32_t n_items;
   int32_t math;          /* tc_math shared by every item */
-  int64_t n_tiles;       /* work-list entries */
+  int64_t n_tiles;       /* tensor-core work-list entries */
   double flops;          /* sum over items of 2 * product of all extents */
   double min_bytes;      /* sum over items of |A| + |B| + |C| bytes */
+  int32_t n_tc_items;    /* items on the tensor-core route */
+  int32_t n_simt_items;  /* items on the CUDA-core route */
+  int64_t n_simt_work;   /* CUDA-core partial-sum work entries */
 } tc_batch_info;
+
+/* Route threshold used by later tc_batch_plan calls (process-wide): a
+ * contraction goes to the tensor cores when its M and N are both >= tc_min_mn. */
+tc_status tc_batch_set_route(int32_t tc_min_mn);
 
 /* Build a batch from n plans (host and device allocation; synchronous).
  * TC_ERR_UNSUPPORTED if a plan is not FP32 tensor-core math, if the plans use
@@ -179,8 +191,8 @@ tc_status tc_batch_plan(tc_batch_t* out, const tc_plan_t* plans, int32_t n);
 
 tc_status tc_batch_get_info(tc_batch_t batch, tc_batch_info* info);
 
-/* Run every contraction of the batch asynchronously on `stream` in one kernel
- * launch.  A, B, C, alpha, beta are DEVICE arrays of n entries (item i uses
+/* Run every contraction of the batch asynchronously on `stream` (at most three
+ * kernel launches).  A, B, C, alpha, beta are DEVICE arrays of n entries (item i uses
  * A[i], B[i], C[i], alpha[i], beta[i], with the layouts of plan i).  Nothing
  * is allocated or copied by the call, so it may be captured in a CUDA graph;
  * a replay reads the pointer and scalar arrays at replay time. */
@@ -195,6 +207,38 @@ tc_status tc_batch_destroy(tc_batch_t batch);
  * synchronising `stream`: TC_ERR_TIMEOUT if a bounded device wait ran out
  * since the last call, else TC_OK. */
 tc_status tc_device_status(void* stream);
+
+/* ---- The mapping selector's network ---------------------------------------
+ * A 3-layer perceptron (in -> hidden -> hidden -> out, ReLU) that predicts the
+ * log2 runtime of every candidate mapping from a descriptor's features
+ * (tc_plan_features), trained and run by the library's own kernels: the
+ * forward pass, the masked mean-squared-error backward pass and Adam.
+ * Parameters are one flat FP32 vector W1[h][in], b1, W2[h][h], b2, W3[out][h],
+ * b3 (the master copy); forward and backward use its FP16 rounding (the
+ * working copy).  All pointers below are device pointers unless stated; X is
+ * [batch][in], T and mask are [batch][out] row-major FP32.  The paper's recipe
+ * (Sec. 3.2) is the fallback whenever no trained network is loaded. */
+typedef struct tc_mlp_s* tc_mlp_t;
+
+/* Allocates the network (parameters zero) for batches up to max_batch. */
+tc_status tc_mlp_create(tc_mlp_t* out, int32_t n_in, int32_t n_hidden, int32_t n_out,
+                        int32_t max_batch);
+tc_status tc_mlp_destroy(tc_mlp_t net);
+tc_status tc_mlp_num_params(tc_mlp_t net, int64_t* n);
+/* Host array of n FP32 parameters -> master copy (and its FP16 working copy);
+ * resets the Adam moments.  Synchronous. */
+tc_status tc_mlp_set_params(tc_mlp_t net, const float* host, int64_t n);
+/* Master copy (working == 0) or FP16 working copy (working != 0) -> host. */
+tc_status tc_mlp_get_params(tc_mlp_t net, float* host, int64_t n, int32_t working);
+/* Y[batch][out] = network(X) with the working copy. */
+tc_status tc_mlp_forward(tc_mlp_t net, const float* X, float* Y, int32_t batch, void* stream);
+/* loss (device scalar) = sum(mask * (Y - T)^2) / sum(mask) and its gradient
+ * with respect to the working parameters (device array of n_params). */
+tc_status tc_mlp_loss_grad(tc_mlp_t net, const float* X, const float* T, const float* mask,
+                           int32_t batch, float* loss, float* grad, void* stream);
+/* One bias-corrected Adam step (step number t >= 1) on the master copy. */
+tc_status tc_mlp_adam_step(tc_mlp_t net, const float* grad, float lr, float beta1, float beta2,
+                           float eps, int32_t t, void* stream);
 
 /* ---- Scalar contraction without a workspace -------------------------------
  * The paper has no counterpart of this entry point; it serves callers that

@@ -1,0 +1,355 @@
+// batch.cu -- many contractions in one submission (tc_batch_plan /
+// tc_contract_batched).
+//
+// Each contraction of a batch is routed by its GEMM view:
+//   * tensor-core route: M and N both at least `tc_min_mn` (64 by default):
+//     its 128x128 tiles join one work list, longest K first, processed by the
+//     persistent tcgen05 kernel (one CTA per SM);
+//   * SIMT route: the low-arithmetic-intensity contractions (Class 1 and 2 and
+//     skinny Class 3 ones; the paper's BLAS-1/2 cases of Sec. 3.2.1-3.2.2),
+//     where a 128x128 tile would waste most of its work: a batched CUDA-core
+//     kernel computes partial sums over K segments into the batch's own
+//     workspace and a second kernel adds the segments of each output in order
+//     (deterministic) and applies alpha and beta.  Long K is split so that even
+//     a single-output contraction spreads over many SMs.
+// The three kernels are launched back to back on the caller's stream; nothing
+// is allocated or copied per call, so tc_contract_batched may be captured in a
+// CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "groups.cuh"
+#include "tc_internal.h"
+
+namespace tc {
+namespace bat {
+
+constexpr int kThreads = 256;
+constexpr int kChunk = 512;     // K offsets staged in shared memory at a time
+
+struct TcWork {
+  int32_t item, tile;
+};
+
+// One entry of the SIMT partial-sum kernel.
+struct SimtWork {
+  int32_t item;    // index into the batch's items
+  int32_t mode;    // 0: a thread per output (256 consecutive outputs), 1: a block per output
+  int64_t out0;    // first output of the entry
+  int64_t k0, k1;  // K segment [k0, k1)
+  int64_t slot;    // partial-sum slot of the first output (thread mode: + thread index)
+  int32_t nseg;    // segments of this item (slots of one output are nseg apart)
+  int32_t pad_;
+};
+
+// One entry of the SIMT final kernel: 256 consecutive outputs of an item.
+struct SimtFinal {
+  int32_t item, nseg;
+  int64_t out0, slot0;  // slot of output out0, segment 0
+};
+
+struct Batch {
+  int32_t n;
+  int32_t math;
+  double flops, min_bytes;
+  int32_t n_tc_items, n_simt_items;
+  int64_t n_tc_work, n_simt_work, n_simt_final;
+  GemmArgs* d_items;
+  TcWork* d_tc_work;
+  SimtWork* d_simt_work;
+  SimtFinal* d_simt_final;
+  double* d_partials;
+};
+
+template <typename T>
+struct Acc;
+template <>
+struct Acc<float> {  // Neumaier's compensated summation
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float x = __fmul_rn(a, b);
+    const float t = __fadd_rn(s, x);
+    if (fabsf(s) >= fabsf(x)) c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, t), x));
+    else c = __fadd_rn(c, __fadd_rn(__fsub_rn(x, t), s));
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Partial sums of one K segment.  Operand pointers come from the device
+// pointer arrays (exchanged for items whose plan swapped the operands).
+__global__ void __launch_bounds__(kThreads) k_simt_partial(
+    const GemmArgs* __restrict__ items, const SimtWork* __restrict__ work, int64_t nwork,
+    const void* const* Ap, const void* const* Bp, double* __restrict__ partials) {
+  __shared__ GemmArgs sa;
+  __shared__ int64_t oX[kChunk], oY[kChunk];
+  __shared__ double red[kThreads / 32];
+  const int tid = threadIdx.x;
+  int cur = -1;
+  for (int64_t w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const SimtWork wk = work[w];
+    __syncthreads();
+    if (wk.item != cur) {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(items + wk.item);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&sa);
+      for (int i = tid; i < (int)(sizeof(GemmArgs) / 4); i += kThreads) dst[i] = src[i];
+      cur = wk.item;
+      __syncthreads();
+    }
+    const GemmArgs& p = sa;
+    const float* X = static_cast<const float*>(p.swapped ? Bp[wk.item] : Ap[wk.item]);
+    const float* Y = static_cast<const float*>(p.swapped ? Ap[wk.item] : Bp[wk.item]);
+    const uint64_t M = (uint64_t)p.M, N = (uint64_t)p.N;
+    const uint64_t outs = M * N * (uint64_t)p.nbatch;
+    // output of this thread (thread mode) or of the block (block mode)
+    const uint64_t o = wk.mode == 0 ? (uint64_t)wk.out0 + tid : (uint64_t)wk.out0;
+    int64_t xo = 0, yo = 0;
+    const bool valid = o < outs;
+    if (valid) {
+      const uint32_t m = (uint32_t)(o % M);
+      const uint64_t r = o / M;
+      const uint32_t n = (uint32_t)(r % N), b = (uint32_t)(r / N);
+      int64_t bX, bY, bC, oXm, oCm, oYn, oCn;
+      goff3(p.gb, b, bX, bY, bC);
+      goff2(p.gm, 0, 2, m, oXm, oCm);
+      goff2(p.gn, 1, 2, n, oYn, oCn);
+      xo = bX + oXm;
+      yo = bY + oYn;
+    }
+    Acc<float> acc;
+    for (int64_t c0 = wk.k0; c0 < wk.k1; c0 += kChunk) {
+      const int kn = (int)min((int64_t)kChunk, wk.k1 - c0);
+      __syncthreads();
+      for (int i = tid; i < kn; i += kThreads) {
+        int64_t ox, oy;
+        goff2(p.gk, 0, 1, (uint32_t)(c0 + i), ox, oy);
+        oX[i] = ox;
+        oY[i] = oy;
+      }
+      __syncthreads();
+      if (wk.mode == 0) {
+        if (valid)
+          for (int i = 0; i < kn; ++i) acc.add(X[xo + oX[i]], Y[yo + oY[i]]);
+      } else {
+        for (int i = tid; i < kn; i += kThreads) acc.add(X[xo + oX[i]], Y[yo + oY[i]]);
+      }
+    }
+    if (wk.mode == 0) {
+      if (valid) partials[wk.slot + (int64_t)tid * wk.nseg] = acc.value();
+    } else {
+      const double v = warp_sum(acc.value());
+      if ((tid & 31) == 0) red[tid >> 5] = v;
+      __syncthreads();
+      if (tid == 0) {
+        double t = 0.0;
+        for (int i = 0; i < kThreads / 32; ++i) t += red[i];
+        partials[wk.slot] = t;
+      }
+    }
+  }
+}
+
+// C = alpha * (sum of an output's segments, in order) + beta * C.
+__global__ void __launch_bounds__(kThreads) k_simt_final(
+    const GemmArgs* __restrict__ items, const SimtFinal* __restrict__ fin, int64_t nfin,
+    void* const* Cp, const double* alpha, const double* beta,
+    const double* __restrict__ partials) {
+  for (int64_t w = blockIdx.x; w < nfin; w += gridDim.x) {
+    const SimtFinal f = fin[w];
+    const GemmArgs& p = items[f.item];
+    const uint64_t M = (uint64_t)p.M, N = (uint64_t)p.N;
+    const uint64_t outs = M * N * (uint64_t)p.nbatch;
+    const uint64_t o = (uint64_t)f.out0 + threadIdx.x;
+    if (o >= outs) continue;
+    const double* ps = partials + f.slot0 + (int64_t)threadIdx.x * f.nseg;
+    double s = 0.0;
+    for (int i = 0; i < f.nseg; ++i) s += ps[i];
+    const uint32_t m = (uint32_t)(o % M);
+    const uint64_t r = o / M;
+    const uint32_t n = (uint32_t)(r % N), b = (uint32_t)(r / N);
+    int64_t bX, bY, bC, oXm, oCm, oYn, oCn;
+    goff3(p.gb, b, bX, bY, bC);
+    goff2(p.gm, 0, 2, m, oXm, oCm);
+    goff2(p.gn, 1, 2, n, oYn, oCn);
+    float* dst = static_cast<float*>(Cp[f.item]) + bC + oCm + oCn;
+    double v = alpha[f.item] * s;
+    if (beta[f.item] != 0.0) v += beta[f.item] * (double)*dst;
+    *dst = (float)v;
+  }
+}
+
+template <typename T>
+cudaError_t upload(T** dst, const std::vector<T>& v) {
+  *dst = nullptr;
+  if (v.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), sizeof(T) * v.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+  return e;
+}
+
+void free_batch(Batch* B) {
+  if (!B) return;
+  cudaFree(B->d_items);
+  cudaFree(B->d_tc_work);
+  cudaFree(B->d_simt_work);
+  cudaFree(B->d_simt_final);
+  cudaFree(B->d_partials);
+  delete B;
+}
+
+int g_tc_min_mn = 64;
+
+}  // namespace bat
+}  // namespace tc
+
+using namespace tc;
+using namespace tc::bat;
+
+extern "C" tc_status tc_batch_set_route(int32_t tc_min_mn) {
+  if (tc_min_mn < 1) return TC_ERR_INVALID_ARG;
+  g_tc_min_mn = tc_min_mn;
+  return TC_OK;
+}
+
+extern "C" tc_status tc_batch_plan(tc_batch_t* out, const tc_plan_t* plans, int32_t n) {
+  if (!out || (!plans && n > 0) || n < 0) return TC_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::vector<GemmArgs> items((size_t)n);
+  std::vector<std::pair<uint64_t, TcWork>> tcw;  // (cost, entry)
+  std::vector<SimtWork> sw;
+  std::vector<SimtFinal> sf;
+  int64_t slots = 0;
+  int32_t math = -1;
+  double flops = 0, bytes = 0;
+  int32_t ntc = 0, nsimt = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    const Plan* P = reinterpret_cast<const Plan*>(plans[i]);
+    if (!P) return TC_ERR_INVALID_ARG;
+    if (P->dtype != TC_F32 || P->math < TC_MATH_BF16 || P->math > TC_MATH_BF16X6)
+      return TC_ERR_UNSUPPORTED;
+    if (math >= 0 && P->math != math) return TC_ERR_UNSUPPORTED;
+    if (P->copy_which || P->empty_out || P->empty_k) return TC_ERR_UNSUPPORTED;
+    math = P->math;
+    GemmArgs a = P->args;
+    a.swapped = P->swapped ? 1 : 0;
+    a.chunk_kb = tc_chunk_kb(math, 0);
+    a.raster = 0;
+    items[i] = a;
+    flops += P->info.flops;
+    bytes += P->info.min_bytes;
+    if (a.M >= g_tc_min_mn && a.N >= g_tc_min_mn) {
+      ++ntc;
+      const uint64_t t = tc_gemm_tiles(a);
+      const uint64_t cost = (uint64_t)((a.K + 63) / 64) + 2;  // per tile
+      for (uint64_t k = 0; k < t; ++k) tcw.push_back({cost, TcWork{i, (int32_t)k}});
+    } else {
+      ++nsimt;
+      const int64_t outs = a.M * a.N * a.nbatch;
+      const int64_t K = a.K;
+      if (outs < kThreads) {  // a block per output and K segment
+        const int64_t KS = std::max<int64_t>(4096, (K + 255) / 256);
+        const int32_t nseg = (int32_t)((K + KS - 1) / KS);
+        for (int64_t o = 0; o < outs; ++o)
+          for (int32_t s = 0; s < nseg; ++s)
+            sw.push_back(SimtWork{i, 1, o, s * KS, std::min(K, (s + 1) * KS),
+                                  slots + o * nseg + s, nseg, 0});
+        for (int64_t o0 = 0; o0 < outs; o0 += kThreads)
+          sf.push_back(SimtFinal{i, nseg, o0, slots + o0 * nseg});
+        slots += outs * nseg;
+      } else {  // a thread per output; split K when there are few output blocks
+        const int64_t blocks = (outs + kThreads - 1) / kThreads;
+        int64_t nseg = std::max<int64_t>(1, std::min<int64_t>((K + 255) / 256, 1216 / blocks));
+        const int64_t KS = (K + nseg - 1) / nseg;
+        nseg = (K + KS - 1) / KS;
+        for (int64_t bl = 0; bl < blocks; ++bl) {
+          for (int64_t s = 0; s < nseg; ++s)
+            sw.push_back(SimtWork{i, 0, bl * kThreads, s * KS, std::min(K, (s + 1) * KS),
+                                  slots + bl * kThreads * nseg + s, (int32_t)nseg, 0});
+          sf.push_back(SimtFinal{i, (int32_t)nseg, bl * kThreads, slots + bl * kThreads * nseg});
+        }
+        slots += blocks * kThreads * nseg;
+      }
+    }
+  }
+  std::stable_sort(tcw.begin(), tcw.end(),
+                   [](const auto& x, const auto& y) { return x.first > y.first; });
+  std::vector<TcWork> tw(tcw.size());
+  for (size_t k = 0; k < tcw.size(); ++k) tw[k] = tcw[k].second;
+
+  Batch* B = new (std::nothrow) Batch();
+  if (!B) return TC_ERR_INVALID_ARG;
+  std::memset(B, 0, sizeof(*B));
+  B->n = n;
+  B->math = math;
+  B->flops = flops;
+  B->min_bytes = bytes;
+  B->n_tc_items = ntc;
+  B->n_simt_items = nsimt;
+  B->n_tc_work = (int64_t)tw.size();
+  B->n_simt_work = (int64_t)sw.size();
+  B->n_simt_final = (int64_t)sf.size();
+  if (upload(&B->d_items, items) != cudaSuccess || upload(&B->d_tc_work, tw) != cudaSuccess ||
+      upload(&B->d_simt_work, sw) != cudaSuccess || upload(&B->d_simt_final, sf) != cudaSuccess ||
+      (slots > 0 && cudaMalloc(reinterpret_cast<void**>(&B->d_partials),
+                               sizeof(double) * (size_t)slots) != cudaSuccess)) {
+    free_batch(B);
+    return TC_ERR_CUDA;
+  }
+  *out = reinterpret_cast<tc_batch_t>(B);
+  return TC_OK;
+}
+
+extern "C" tc_status tc_batch_get_info(tc_batch_t batch, tc_batch_info* info) {
+  if (!batch || !info) return TC_ERR_INVALID_ARG;
+  const Batch* B = reinterpret_cast<const Batch*>(batch);
+  info->n_items = B->n;
+  info->math = B->math;
+  info->n_tiles = B->n_tc_work;
+  info->flops = B->flops;
+  info->min_bytes = B->min_bytes;
+  info->n_tc_items = B->n_tc_items;
+  info->n_simt_items = B->n_simt_items;
+  info->n_simt_work = B->n_simt_work;
+  return TC_OK;
+}
+
+extern "C" tc_status tc_contract_batched(tc_batch_t batch, const void* const* A,
+                                         const void* const* B, void* const* C,
+                                         const double* alpha, const double* beta, void* stream) {
+  if (!batch) return TC_ERR_INVALID_ARG;
+  const Batch* Bt = reinterpret_cast<const Batch*>(batch);
+  if (Bt->n == 0) return TC_OK;
+  if (!A || !B || !C || !alpha || !beta) return TC_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (Bt->n_tc_work > 0) {
+    tc_status st = launch_gemm_tc_batch(Bt->d_items, Bt->d_tc_work, Bt->n_tc_work, A, B, C,
+                                        alpha, beta, Bt->math, stream);
+    if (st != TC_OK) return st;
+  }
+  if (Bt->n_simt_work > 0) {
+    const int g1 = (int)std::min<int64_t>(Bt->n_simt_work, 152 * 8);
+    k_simt_partial<<<g1, kThreads, 0, s>>>(Bt->d_items, Bt->d_simt_work, Bt->n_simt_work, A, B,
+                                           Bt->d_partials);
+    const int g2 = (int)std::min<int64_t>(Bt->n_simt_final, 152 * 8);
+    k_simt_final<<<g2, kThreads, 0, s>>>(Bt->d_items, Bt->d_simt_final, Bt->n_simt_final, C,
+                                         alpha, beta, Bt->d_partials);
+    if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;
+  }
+  return TC_OK;
+}
+
+extern "C" tc_status tc_batch_destroy(tc_batch_t batch) {
+  free_batch(reinterpret_cast<Batch*>(batch));
+  return TC_OK;
+}

@@ -547,115 +547,22 @@ tc_status launch_gemm_tc(const GemmArgs& a, int math, void* stream) {
   return tcg::launch_math(L, math, static_cast<cudaStream_t>(stream));
 }
 
-// ------------------------------------------------------------ batched launch
-struct Batch {
-  int32_t n;
-  int32_t math;
-  int64_t nwork;
-  double flops, min_bytes;
-  GemmArgs* d_items;
-  tcg::Work* d_work;
-};
-
-}  // namespace tc
-
-using namespace tc;
-
-extern "C" tc_status tc_batch_plan(tc_batch_t* out, const tc_plan_t* plans, int32_t n) {
-  if (!out || (!plans && n > 0) || n < 0) return TC_ERR_INVALID_ARG;
-  *out = nullptr;
-  std::vector<GemmArgs> items((size_t)n);
-  std::vector<std::pair<uint64_t, tcg::Work>> work;  // (cost, entry)
-  int32_t math = -1;
-  double flops = 0, bytes = 0;
-  for (int32_t i = 0; i < n; ++i) {
-    const Plan* P = reinterpret_cast<const Plan*>(plans[i]);
-    if (!P) return TC_ERR_INVALID_ARG;
-    if (P->dtype != TC_F32 || P->math < TC_MATH_BF16 || P->math > TC_MATH_BF16X6)
-      return TC_ERR_UNSUPPORTED;
-    if (math >= 0 && P->math != math) return TC_ERR_UNSUPPORTED;
-    if (P->copy_which || P->empty_out || P->empty_k) return TC_ERR_UNSUPPORTED;
-    math = P->math;
-    GemmArgs a = P->args;
-    a.swapped = P->swapped ? 1 : 0;
-    a.chunk_kb = tc_chunk_kb(math, 0);
-    a.raster = 0;
-    items[i] = a;
-    flops += P->info.flops;
-    bytes += P->info.min_bytes;
-    const uint64_t t = tcg::tiles_of(a);
-    const uint64_t cost = (uint64_t)((a.K + tcg::BK - 1) / tcg::BK) + 2;  // per tile
-    for (uint64_t k = 0; k < t; ++k) work.push_back({cost, tcg::Work{i, (int32_t)k}});
-  }
-  // longest tiles first: the persistent CTAs take entries round-robin
-  std::stable_sort(work.begin(), work.end(),
-                   [](const auto& x, const auto& y) { return x.first > y.first; });
-  Batch* B = new (std::nothrow) Batch();
-  if (!B) return TC_ERR_INVALID_ARG;
-  B->n = n;
-  B->math = math;
-  B->nwork = (int64_t)work.size();
-  B->flops = flops;
-  B->min_bytes = bytes;
-  B->d_items = nullptr;
-  B->d_work = nullptr;
-  std::vector<tcg::Work> w(work.size());
-  for (size_t k = 0; k < work.size(); ++k) w[k] = work[k].second;
-  if (n > 0 && (cudaMalloc(&B->d_items, sizeof(GemmArgs) * (size_t)n) != cudaSuccess ||
-                cudaMemcpy(B->d_items, items.data(), sizeof(GemmArgs) * (size_t)n,
-                           cudaMemcpyHostToDevice) != cudaSuccess)) {
-    cudaFree(B->d_items);
-    delete B;
-    return TC_ERR_CUDA;
-  }
-  if (!w.empty() && (cudaMalloc(&B->d_work, sizeof(tcg::Work) * w.size()) != cudaSuccess ||
-                     cudaMemcpy(B->d_work, w.data(), sizeof(tcg::Work) * w.size(),
-                                cudaMemcpyHostToDevice) != cudaSuccess)) {
-    cudaFree(B->d_items);
-    cudaFree(B->d_work);
-    delete B;
-    return TC_ERR_CUDA;
-  }
-  *out = reinterpret_cast<tc_batch_t>(B);
-  return TC_OK;
-}
-
-extern "C" tc_status tc_batch_get_info(tc_batch_t batch, tc_batch_info* info) {
-  if (!batch || !info) return TC_ERR_INVALID_ARG;
-  const Batch* B = reinterpret_cast<const Batch*>(batch);
-  info->n_items = B->n;
-  info->math = B->math;
-  info->n_tiles = B->nwork;
-  info->flops = B->flops;
-  info->min_bytes = B->min_bytes;
-  return TC_OK;
-}
-
-extern "C" tc_status tc_contract_batched(tc_batch_t batch, const void* const* A,
-                                         const void* const* B, void* const* C,
-                                         const double* alpha, const double* beta, void* stream) {
-  if (!batch) return TC_ERR_INVALID_ARG;
-  const Batch* Bt = reinterpret_cast<const Batch*>(batch);
-  if (Bt->nwork == 0) return TC_OK;
-  if (!A || !B || !C || !alpha || !beta) return TC_ERR_INVALID_ARG;
+tc_status launch_gemm_tc_batch(const GemmArgs* d_items, const void* d_work, int64_t nwork,
+                               const void* const* A, const void* const* B, void* const* C,
+                               const double* alpha, const double* beta, int math, void* stream) {
   tcg::Launch L;
   std::memset(&L, 0, sizeof(L));
-  L.items = Bt->d_items;
-  L.work = Bt->d_work;
-  L.nwork = Bt->nwork;
+  L.items = d_items;
+  L.work = static_cast<const tcg::Work*>(d_work);
+  L.nwork = nwork;
   L.Ap = A;
   L.Bp = B;
   L.Cp = C;
   L.alpha = alpha;
   L.beta = beta;
-  return tcg::launch_math(L, Bt->math, static_cast<cudaStream_t>(stream));
+  return tcg::launch_math(L, math, static_cast<cudaStream_t>(stream));
 }
 
-extern "C" tc_status tc_batch_destroy(tc_batch_t batch) {
-  if (!batch) return TC_OK;
-  Batch* B = reinterpret_cast<Batch*>(batch);
-  cudaFree(B->d_items);
-  cudaFree(B->d_work);
-  delete B;
-  return TC_OK;
-}
+uint64_t tc_gemm_tiles(const GemmArgs& a) { return tcg::tiles_of(a); }
+
+}  // namespace tc

@@ -92,6 +92,11 @@ tc_status launch_scale(const Group& gc, void* C, double beta, tc_dtype dt, int64
 tc_status launch_gemm_tc(const GemmArgs& a, int math, void* stream);
 int dot_partials(const GemmArgs& a, int tile);
 int num_tiles_tc();
+// Tensor-core GEMM over a device work list of (item, tile) pairs, int32 each.
+tc_status launch_gemm_tc_batch(const GemmArgs* d_items, const void* d_work, int64_t nwork,
+                               const void* const* A, const void* const* B, void* const* C,
+                               const double* alpha, const double* beta, int math, void* stream);
+uint64_t tc_gemm_tiles(const GemmArgs& a);  // 128x128 output tiles of a GEMM view
 // Enqueue a read-and-clear of the tensor-core kernels' timeout flag into *h.
 tc_status tc_gemm_read_status(int* h, void* stream);
 int tc_chunk_kb(int math, int tile);

@@ -61,7 +61,8 @@ class PlanInfo(ctypes.Structure):
 class BatchInfo(ctypes.Structure):
     _fields_ = [("n_items", ctypes.c_int32), ("math", ctypes.c_int32),
                 ("n_tiles", ctypes.c_int64), ("flops", ctypes.c_double),
-                ("min_bytes", ctypes.c_double)]
+                ("min_bytes", ctypes.c_double), ("n_tc_items", ctypes.c_int32),
+                ("n_simt_items", ctypes.c_int32), ("n_simt_work", ctypes.c_int64)]
 
 
 def _load():
@@ -80,6 +81,8 @@ def _load():
     lib.tc_contract.restype = ctypes.c_int
     lib.tc_contract.argtypes = [P, ctypes.c_double, P, P, ctypes.c_double, P, P, ctypes.c_size_t,
                                 P]
+    lib.tc_batch_set_route.restype = ctypes.c_int
+    lib.tc_batch_set_route.argtypes = [ctypes.c_int32]
     lib.tc_batch_plan.restype = ctypes.c_int
     lib.tc_batch_plan.argtypes = [ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_int32]
     lib.tc_batch_get_info.restype = ctypes.c_int
@@ -90,6 +93,24 @@ def _load():
     lib.tc_batch_destroy.argtypes = [P]
     lib.tc_contract_dot_noalloc.restype = ctypes.c_int
     lib.tc_contract_dot_noalloc.argtypes = [P, ctypes.c_double, P, P, ctypes.c_double, P, P]
+    lib.tc_mlp_create.restype = ctypes.c_int
+    lib.tc_mlp_create.argtypes = [ctypes.POINTER(P), ctypes.c_int32, ctypes.c_int32,
+                                  ctypes.c_int32, ctypes.c_int32]
+    lib.tc_mlp_destroy.restype = ctypes.c_int
+    lib.tc_mlp_destroy.argtypes = [P]
+    lib.tc_mlp_num_params.restype = ctypes.c_int
+    lib.tc_mlp_num_params.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+    lib.tc_mlp_set_params.restype = ctypes.c_int
+    lib.tc_mlp_set_params.argtypes = [P, P, ctypes.c_int64]
+    lib.tc_mlp_get_params.restype = ctypes.c_int
+    lib.tc_mlp_get_params.argtypes = [P, P, ctypes.c_int64, ctypes.c_int32]
+    lib.tc_mlp_forward.restype = ctypes.c_int
+    lib.tc_mlp_forward.argtypes = [P, P, P, ctypes.c_int32, P]
+    lib.tc_mlp_loss_grad.restype = ctypes.c_int
+    lib.tc_mlp_loss_grad.argtypes = [P, P, P, P, ctypes.c_int32, P, P, P]
+    lib.tc_mlp_adam_step.restype = ctypes.c_int
+    lib.tc_mlp_adam_step.argtypes = [P, P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                     ctypes.c_float, ctypes.c_int32, P]
     lib.tc_selftest_wait_timeout.restype = ctypes.c_int
     lib.tc_selftest_wait_timeout.argtypes = [ctypes.c_int64, P]
     lib.tc_device_status.restype = ctypes.c_int
@@ -213,3 +234,58 @@ def tc_contract_dot_noalloc(plan: int, alpha: float, A: int, B: int, beta: float
                                      ctypes.c_void_p(stream))
     if st != TC_OK:
         raise TcError(st, "tc_contract_dot_noalloc")
+
+
+def tc_batch_set_route(tc_min_mn: int) -> None:
+    st = lib.tc_batch_set_route(int(tc_min_mn))
+    if st != TC_OK:
+        raise TcError(st, "tc_batch_set_route")
+
+
+def _check(st, where):
+    if st != TC_OK:
+        raise TcError(st, where)
+
+
+def tc_mlp_create(n_in: int, n_hidden: int, n_out: int, max_batch: int) -> int:
+    out = ctypes.c_void_p()
+    _check(lib.tc_mlp_create(ctypes.byref(out), n_in, n_hidden, n_out, max_batch), "tc_mlp_create")
+    return out.value
+
+
+def tc_mlp_destroy(net: int) -> None:
+    lib.tc_mlp_destroy(ctypes.c_void_p(net))
+
+
+def tc_mlp_num_params(net: int) -> int:
+    n = ctypes.c_int64()
+    _check(lib.tc_mlp_num_params(ctypes.c_void_p(net), ctypes.byref(n)), "tc_mlp_num_params")
+    return n.value
+
+
+def tc_mlp_set_params(net: int, host_ptr: int, n: int) -> None:
+    _check(lib.tc_mlp_set_params(ctypes.c_void_p(net), ctypes.c_void_p(host_ptr), n),
+           "tc_mlp_set_params")
+
+
+def tc_mlp_get_params(net: int, host_ptr: int, n: int, working: bool = False) -> None:
+    _check(lib.tc_mlp_get_params(ctypes.c_void_p(net), ctypes.c_void_p(host_ptr), n,
+                                 1 if working else 0), "tc_mlp_get_params")
+
+
+def tc_mlp_forward(net: int, X: int, Y: int, batch: int, stream: int = 0) -> None:
+    _check(lib.tc_mlp_forward(ctypes.c_void_p(net), ctypes.c_void_p(X), ctypes.c_void_p(Y),
+                              batch, ctypes.c_void_p(stream)), "tc_mlp_forward")
+
+
+def tc_mlp_loss_grad(net: int, X: int, T: int, mask: int, batch: int, loss: int, grad: int,
+                     stream: int = 0) -> None:
+    _check(lib.tc_mlp_loss_grad(ctypes.c_void_p(net), ctypes.c_void_p(X), ctypes.c_void_p(T),
+                                ctypes.c_void_p(mask), batch, ctypes.c_void_p(loss),
+                                ctypes.c_void_p(grad), ctypes.c_void_p(stream)), "tc_mlp_loss_grad")
+
+
+def tc_mlp_adam_step(net: int, grad: int, lr: float, beta1: float, beta2: float, eps: float,
+                     t: int, stream: int = 0) -> None:
+    _check(lib.tc_mlp_adam_step(ctypes.c_void_p(net), ctypes.c_void_p(grad), lr, beta1, beta2,
+                                eps, t, ctypes.c_void_p(stream)), "tc_mlp_adam_step")

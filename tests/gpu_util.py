@@ -52,6 +52,23 @@ def run(p, math="fp64", mapping="auto", tile=-1, alpha=None, beta=None, stream=N
     return out[: p.C.data.size] if p.C.data.size else out[:0]
 
 
+def _sub_operand(t, fix, con):
+    """The contracted sub-tensor of operand t at fixed free-label values,
+    gathered into a compact column-major array (labels, extents, strides, data)."""
+    off = sum(fix[l] * s for l, s in zip(t.labels, t.strides) if l in fix)
+    keep = [k for k, l in enumerate(t.labels) if l in con]
+    labels = [t.labels[k] for k in keep]
+    ext = [int(t.extents[k]) for k in keep]
+    st = [int(t.strides[k]) for k in keep]
+    if ext:
+        grids = np.meshgrid(*[np.arange(e, dtype=np.int64) * s for e, s in zip(ext, st)],
+                            indexing="ij")
+        idx = (off + sum(grids)).reshape(-1, order="F")
+    else:
+        idx = np.array([off], dtype=np.int64)
+    return labels, ext, ts.col_major(ext), np.asarray(t.data[idx], np.float64)
+
+
 def oracle_full(p, **kw):
     return oracle.contract_problem(p, **kw)
 
@@ -64,28 +81,17 @@ def compare(got, ref, C):
 
 def sample_outputs(p, samples):
     """Oracle values of selected output elements: for each output multi-index
-    the free labels are fixed by offsetting A and B and the oracle contracts
-    what remains (the contracted labels) into a scalar."""
+    the free labels are fixed, the operands' contracted sub-tensors gathered,
+    and the oracle contracts them into a scalar."""
     con = [l for l in p.A.labels if l in p.B.labels]
     vals = []
     for cidx in samples:
         fix = dict(zip(p.C.labels, cidx))
-        parts = []
-        for t in (p.A, p.B):
-            off = sum(fix[l] * s for l, s in zip(t.labels, t.strides) if l in fix)
-            keep = [k for k, l in enumerate(t.labels) if l in con]
-            labels = [t.labels[k] for k in keep]
-            ext = [t.extents[k] for k in keep]
-            st = [t.strides[k] for k in keep]
-            end = off + ts.span(ext, st)
-            parts.append((labels, ext, st, np.asarray(t.data[off:end], np.float64)))
+        (la, ea, sa, a) = _sub_operand(p.A, fix, con)
+        (lb, eb, sb, b) = _sub_operand(p.B, fix, con)
         c = np.zeros(1)
-        c0 = 0.0
         if p.beta != 0:
-            coff = sum(i * s for i, s in zip(cidx, p.C.strides))
-            c0 = float(p.C.data[coff])
-        c[0] = c0
-        (la, ea, sa, a), (lb, eb, sb, b) = parts
+            c[0] = float(p.C.data[sum(i * s for i, s in zip(cidx, p.C.strides))])
         oracle.contract_raw(la, ea, sa, a, lb, eb, sb, b, [], [], [], c, p.alpha, p.beta)
         vals.append(c[0])
     return np.array(vals)
@@ -101,26 +107,20 @@ def gather(buf, C, samples):
 
 
 def sample_outputs_form(p, samples, form):
-    """Oracle values of selected outputs for a split-product form: the operand
-    slices of each sample are split into BF16 terms (oracle.precision) and the
-    form's term products are contracted in FP64 and summed."""
+    """Oracle values of selected outputs for a split-product form: each
+    sample's gathered operand sub-tensors are split into BF16 terms
+    (oracle.precision) and the form's term products are contracted in FP64
+    and summed."""
     from oracle import precision as op
     con = [l for l in p.A.labels if l in p.B.labels]
     nt = op.TERMS[form]
     vals = []
     for cidx in samples:
         fix = dict(zip(p.C.labels, cidx))
-        parts = []
-        for t in (p.A, p.B):
-            off = sum(fix[l] * s for l, s in zip(t.labels, t.strides) if l in fix)
-            keep = [k for k, l in enumerate(t.labels) if l in con]
-            labels = [t.labels[k] for k in keep]
-            ext = [t.extents[k] for k in keep]
-            st = [t.strides[k] for k in keep]
-            end = off + ts.span(ext, st)
-            terms = op.split_bf16(np.asarray(t.data[off:end], np.float32), nt)
-            parts.append((labels, ext, st, terms))
-        (la, ea, sa, ta), (lb, eb, sb, tb) = parts
+        la, ea, sa, a = _sub_operand(p.A, fix, con)
+        lb, eb, sb, b = _sub_operand(p.B, fix, con)
+        ta = op.split_bf16(a.astype(np.float32), nt)
+        tb = op.split_bf16(b.astype(np.float32), nt)
         acc = 0.0
         for i, j in op.FORMS[form]:
             c = np.zeros(1)

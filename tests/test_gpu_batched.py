@@ -61,6 +61,25 @@ def small_items(n=48, seed=ts.BASE_SEED + 30):
                              hi=40)
 
 
+def test_batched_routes_and_long_k_items():
+    """Items of every class, including scalar results with long K, through both
+    routes (tensor cores and the split-K CUDA-core kernels)."""
+    from paper_1307_2100_gb300 import tc
+    items = small_items(40, seed=ts.BASE_SEED + 34)
+    items.append(ts.problem("dotlong", "ijk", "kji", "", dict(i=60, j=50, k=70), 35,
+                            dtype=np.float32))
+    items.append(ts.problem("gemvlong", "aib", "ib", "a", dict(a=300, i=200, b=90), 36,
+                            dtype=np.float32))
+    for p in items[-2:]:
+        p.C.data = p.C.data.astype(np.float32)
+    outs, info = _run_batch(items, "bf16x6")
+    assert info.n_tc_items > 0 and info.n_simt_items > 0
+    for p, got in zip(items, outs):
+        acc, tot = tc_bounds(p, "bf16x6")
+        ok, d = within(got, oracle.contract_problem(p), magnitude(p), p.C, tot)
+        assert ok, (p.name, p.A.labels, p.B.labels, d)
+
+
 @pytest.mark.parametrize("form", ["bf16x3", "bf16x6"])
 def test_batched_items_against_oracles(form):
     items = small_items()
@@ -130,8 +149,8 @@ def test_batched_equals_single_launches_bitwise():
     for p, got in zip(items, outs):
         info = []
         single = run(p, "bf16x6", "auto", plan_out=info)
-        if info[0]["kernel_name"] != "gemm_tc":
-            continue
+        if info[0]["kernel_name"] != "gemm_tc" or min(info[0]["M"], info[0]["N"]) < 64:
+            continue   # only contractions the batch routes to the tensor cores
         np.testing.assert_array_equal(got, single)
         checked += 1
     assert checked >= 5
