@@ -84,7 +84,7 @@ struct Cfg {
   static constexpr uint32_t OFF_BAR = OFF_ARGS + ((sizeof(GemmArgs) + 15) / 16) * 16;
   static constexpr uint32_t NBAR = 2 * S + 5;
   static constexpr uint32_t OFF_MISC = OFF_BAR + NBAR * 8;
-  static constexpr uint32_t BYTES = OFF_MISC + 16 + 1024;          // + alignment slack
+  static constexpr uint32_t BYTES = OFF_MISC + 32 + 1024;          // + alignment slack
 };
 
 // Products (term of A, term of B) of each form; product 0 is the main one.
@@ -101,11 +101,56 @@ __host__ __device__ constexpr int nprod(int nt) { return nt == 1 ? 1 : nt == 2 ?
 template <int NT, int ROWS>
 __device__ __forceinline__ void produce(const float* __restrict__ X, const int64_t* rowoff,
                                         const int64_t* koff, const uint8_t* kvec, bool contig_mn,
-                                        uint32_t sbuf, int ptid) {
+                                        bool rowvec, uint32_t sbuf, int ptid) {
   constexpr int PER = ROWS * (BK / 8) / kProducers;  // units per thread
   constexpr uint32_t TERM = ROWS * BK * 2;
   constexpr uint32_t LBO = (ROWS / 8) * 128;
   float v[PER][8];
+  if (contig_mn && rowvec) {
+    // four consecutive rows per 16-byte load: thread -> (row quad, chunk pair)
+    const int quad = ptid & (ROWS / 4 - 1);
+    const int cp = ptid / (ROWS / 4);          // 0 .. 128 / (ROWS / 4) - 1
+    constexpr int NCP = kProducers / (ROWS / 4);
+    const int64_t ro = rowoff[quad * 4];
+#pragma unroll
+    for (int h = 0; h < PER / 4; ++h) {
+      const int chunk = cp + h * NCP;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int64_t ko = koff[chunk * 8 + j];
+        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (ko >= 0) x = __ldg(reinterpret_cast<const float4*>(X + ro + ko));
+        v[h * 4 + 0][j] = x.x;
+        v[h * 4 + 1][j] = x.y;
+        v[h * 4 + 2][j] = x.z;
+        v[h * 4 + 3][j] = x.w;
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < PER / 4; ++h) {
+      const int chunk = cp + h * NCP;
+#pragma unroll
+      for (int q4 = 0; q4 < 4; ++q4) {
+        const int row = quad * 4 + q4;
+        const uint32_t dst = sbuf + chunk * LBO + (row >> 3) * 128 + (row & 7) * 16;
+        float* vv = v[h * 4 + q4];
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+          uint32_t w[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            w[q] = pack_bf16x2(vv[2 * q], vv[2 * q + 1]);
+            if (t + 1 < NT) {
+              vv[2 * q] = __fsub_rn(vv[2 * q], bf16_lo(w[q]));
+              vv[2 * q + 1] = __fsub_rn(vv[2 * q + 1], bf16_hi(w[q]));
+            }
+          }
+          st_shared_v4(dst + t * TERM, w[0], w[1], w[2], w[3]);
+        }
+      }
+    }
+    return;
+  }
   if (contig_mn) {
     const int row = ptid % ROWS;
     const int64_t ro = rowoff[row];
@@ -121,7 +166,7 @@ __device__ __forceinline__ void produce(const float* __restrict__ X, const int64
   } else {
     const int chunk = (ptid >> 3) & 7;
     const int64_t k0 = koff[chunk * 8];
-    const bool vec = kvec[chunk] != 0;
+    const bool vec = (kvec[chunk] & 1) != 0;
 #pragma unroll
     for (int r = 0; r < PER; ++r) {
       const int u = ptid + r * kProducers;
@@ -198,6 +243,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
   int64_t* rowB = rowA + BM;
   int64_t* rowC = rowB + BN;
   int64_t* colC = rowC + BM;
+  int* rowvec = reinterpret_cast<int*>(smem + G::OFF_MISC + 8);  // [A, B]
   GemmArgs* sargs = reinterpret_cast<GemmArgs*>(smem + G::OFF_ARGS);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + G::OFF_BAR);
   uint64_t* full = bars;
@@ -290,6 +336,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
       colC[i] = oc;
     }
     __syncthreads();
+    if (warp == 0) {  // may rows be read four at a time (16-byte vectors)?
+      for (int which = 0; which < 2; ++which) {
+        const int64_t* ro = which ? rowB : rowA;
+        const bool mn = (which ? p.b_contig : p.a_contig) == CONTIG_MN;
+        const uintptr_t base = reinterpret_cast<uintptr_t>(which ? p.B : p.A) +
+                               (uintptr_t)((which ? bB : bA) * 4);
+        bool ok = mn && (base & 15) == 0;
+        for (int r = lane; r < 128 && ok; r += 32)
+          ok = ro[r] >= 0 && (r % 4 == 0 ? (ro[r] & 3) == 0 : ro[r] == ro[r - 1] + 1);
+        ok = __all_sync(0xffffffffu, ok);
+        if (lane == 0) rowvec[which] = ok ? 1 : 0;
+      }
+    }
+    __syncthreads();
 
     const uint32_t nkb = (K + BK - 1) / BK;
     const uint32_t ckb = (uint32_t)max(p.chunk_kb, 1);  // K blocks per chunk
@@ -316,15 +376,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
         if (tid < 16) {  // 8-wide K chunks that are contiguous and 4-element aligned
           const int64_t* ko = (tid < 8 ? koffA : koffB) + s * BK + (tid & 7) * 8;
           bool c = ko[0] >= 0 && (ko[0] & 3) == 0;
+          bool al = true;  // every k offset a multiple of 4 (or beyond K)
           for (int j = 1; j < 8; ++j) c = c && ko[j] == ko[0] + j;
-          (tid < 8 ? kvecA : kvecB)[s * 8 + (tid & 7)] = c ? 1 : 0;
+          for (int j = 0; j < 8; ++j) al = al && (ko[j] < 0 || (ko[j] & 3) == 0);
+          (tid < 8 ? kvecA : kvecB)[s * 8 + (tid & 7)] = (c ? 1 : 0) | (al ? 2 : 0);
         }
         named_bar_sync(1, kProducers);
+        bool kal[2] = {true, true};
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          kal[0] = kal[0] && (kvecA[s * 8 + c] & 2);
+          kal[1] = kal[1] && (kvecB[s * 8 + c] & 2);
+        }
         if (ok && !*abort) {
           const uint32_t st = sbase + s * G::STAGE;
-          produce<NT, BM>(Xa, rowA, koffA + s * BK, kvecA + s * 8, amn, st, tid);
-          produce<NT, BN>(Xb, rowB, koffB + s * BK, kvecB + s * 8, bmn, st + NT * G::A_TERM,
+          produce<NT, BM>(Xa, rowA, koffA + s * BK, kvecA + s * 8, amn, rowvec[0] && kal[0], st,
                           tid);
+          produce<NT, BN>(Xb, rowB, koffB + s * BK, kvecB + s * 8, bmn, rowvec[1] && kal[1],
+                          st + NT * G::A_TERM, tid);
           fence_async_smem();
           mbar_arrive(&full[s]);
         }

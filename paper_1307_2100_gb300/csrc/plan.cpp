@@ -16,6 +16,7 @@
 // stride-1 index is larger keeps it (ties: A).
 #include <algorithm>
 #include <climits>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <new>
@@ -344,8 +345,76 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   info.min_bytes = (double)(A.numel() + B.numel() + C.numel()) * (double)es;
 
   // ---- mapping
+  // ---- descriptor features (the selector's input; computed for every plan)
+  {
+    float* f = P->features;
+    for (int i = 0; i < TC_SELECTOR_FEATURES; ++i) f[i] = 0.0f;
+    auto lg = [](double x) { return (float)(std::log2(std::max(x, 1.0))); };
+    auto prod = [&](const std::vector<int32_t>& v) {
+      double t = 1.0;
+      for (auto l : v) t *= (double)an.ext[l];
+      return t;
+    };
+    auto nbig = [&](const std::vector<int32_t>& v) {
+      int c = 0;
+      for (auto l : v) c += an.ext[l] > 1;
+      return (float)c;
+    };
+    f[0] = lg(prod(an.fa)) / 16;
+    f[1] = lg(prod(an.fb)) / 16;
+    f[2] = lg(prod(an.con)) / 16;
+    f[3] = nbig(an.fa) / 8;
+    f[4] = nbig(an.fb) / 8;
+    f[5] = nbig(an.con) / 8;
+    f[6] = an.cls == 1;
+    f[7] = an.cls == 2;
+    f[8] = an.cls == 31;
+    f[9] = an.cls == 32;
+    f[10] = an.s1a >= 0 && contains(an.con, an.s1a);
+    f[11] = an.s1a >= 0 && contains(an.fa, an.s1a);
+    f[12] = an.s1b >= 0 && contains(an.con, an.s1b);
+    f[13] = an.s1b >= 0 && contains(an.fb, an.s1b);
+    const int32_t s1c = C.stride1();
+    f[14] = s1c >= 0 && contains(an.fa, s1c);
+    f[15] = s1c >= 0 && contains(an.fb, s1c);
+    int32_t kf = -1, kc = -1, kb = -1;
+    for (auto l : an.keep_a) (contains(an.con, l) ? kc : kf) = l;
+    for (auto l : an.keep_b)
+      if (!contains(an.con, l)) kb = l;
+    f[16] = kf >= 0 ? lg((double)an.ext[kf]) / 16 : 0.0f;
+    f[17] = kb >= 0 ? lg((double)an.ext[kb]) / 16 : 0.0f;
+    f[18] = kc >= 0 ? lg((double)an.ext[kc]) / 16 : 0.0f;
+    f[19] = lg(info.flops) / 48;
+    f[20] = lg(info.min_bytes) / 40;
+    // fragmentation of the fused view: labels left after mode merging
+    Group ga, gb, gk;
+    int64_t t0, t1, t2;
+    int merged = 0;
+    if (make_group(sorted_by(an.fa, A), an.ext, &A, nullptr, &C, ga, t0)) merged += ga.n;
+    if (make_group(sorted_by(an.fb, B), an.ext, nullptr, &B, &C, gb, t1)) merged += gb.n;
+    if (make_group(sorted_by(an.con, A), an.ext, &A, &B, nullptr, gk, t2)) merged += gk.n;
+    f[21] = (float)merged / 12;
+    f[22] = (float)(A.lab.size() + B.lab.size()) / 12;
+  }
+
   int32_t map = mapping;
-  if (map == TC_MAP_AUTO) map = TC_MAP_RECIPE;  // selector hook (weights not loaded)
+  if (map == TC_MAP_AUTO) {
+    int32_t cand[16], nc = 0;
+    float pred[16];
+    map = TC_MAP_RECIPE;
+    if (selector_predict(P->features, dtype, math, cand, pred, &nc)) {
+      const bool class3 = an.cls == 31 || an.cls == 32;
+      float best = 0;
+      for (int i = 0; i < nc; ++i) {
+        const bool feasible =
+            class3 || (cand[i] != TC_MAP_SLICE_GEMM && cand[i] != TC_MAP_COPY_GEMM);
+        if (feasible && (map == TC_MAP_RECIPE || pred[i] < best)) {
+          map = cand[i];
+          best = pred[i];
+        }
+      }
+    }
+  }
   if (map == TC_MAP_RECIPE)
     map = (an.cls == 1) ? TC_MAP_DOT : (an.cls == 2) ? TC_MAP_GEMV : TC_MAP_FUSED_GEMM;
   const bool is3 = an.cls == 31 || an.cls == 32;
@@ -512,6 +581,13 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   info.batch = Bt;
   info.workspace = ws;
   *out = reinterpret_cast<tc_plan_t>(P);
+  return TC_OK;
+}
+
+extern "C" tc_status tc_plan_features(tc_plan_t plan, float* out, int32_t n) {
+  if (!plan || !out || n < 0) return TC_ERR_INVALID_ARG;
+  const Plan* P = reinterpret_cast<const Plan*>(plan);
+  for (int32_t i = 0; i < n && i < TC_SELECTOR_FEATURES; ++i) out[i] = P->features[i];
   return TC_OK;
 }
 

@@ -78,9 +78,16 @@ struct Plan {
   int64_t c_elems_span;  // C's element span (for beta-only scaling)
   Group gc;              // C's own labels (for beta-only scaling)
   size_t workspace;
+  float features[TC_SELECTOR_FEATURES];  // descriptor features (selector input)
 };
 
 size_t elem_size(tc_dtype dt);
+
+// Host forward pass of a loaded selector: predicted log2 runtime of each of
+// its candidates (returns false when no selector applies to dtype/math or a
+// feature lies outside the training range).
+bool selector_predict(const float* features, tc_dtype dtype, tc_math math, int32_t* cand,
+                      float* pred, int32_t* n_cand);
 
 // Kernel launchers (k_simt.cu); `stream` is a cudaStream_t.
 tc_status launch_gemm_simt(const GemmArgs& a, tc_dtype dt, int tile, void* stream);

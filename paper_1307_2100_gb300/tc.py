@@ -26,6 +26,7 @@ MAPPING = {"auto": 0, "recipe": 1, "slice_gemm": 2, "fused_gemm": 3, "copy_gemm"
 MAPPING_NAME = {v: k for k, v in MAPPING.items()}
 KERNEL_NAME = {0: "none", 1: "gemm_simt", 2: "gemm_tc", 3: "gemv", 4: "dot"}
 MAX_ORDER = 12
+N_FEATURES = 23
 
 
 class TcError(RuntimeError):
@@ -111,6 +112,14 @@ def _load():
     lib.tc_mlp_adam_step.restype = ctypes.c_int
     lib.tc_mlp_adam_step.argtypes = [P, P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                      ctypes.c_float, ctypes.c_int32, P]
+    lib.tc_plan_features.restype = ctypes.c_int
+    lib.tc_plan_features.argtypes = [P, P, ctypes.c_int32]
+    lib.tc_selector_load.restype = ctypes.c_int
+    lib.tc_selector_load.argtypes = [ctypes.c_char_p]
+    lib.tc_selector_unload.restype = ctypes.c_int
+    lib.tc_selector_unload.argtypes = []
+    lib.tc_selector_predict.restype = ctypes.c_int
+    lib.tc_selector_predict.argtypes = [P, ctypes.c_int32, P, P, P]
     lib.tc_selftest_wait_timeout.restype = ctypes.c_int
     lib.tc_selftest_wait_timeout.argtypes = [ctypes.c_int64, P]
     lib.tc_device_status.restype = ctypes.c_int
@@ -289,3 +298,34 @@ def tc_mlp_adam_step(net: int, grad: int, lr: float, beta1: float, beta2: float,
                      t: int, stream: int = 0) -> None:
     _check(lib.tc_mlp_adam_step(ctypes.c_void_p(net), ctypes.c_void_p(grad), lr, beta1, beta2,
                                 eps, t, ctypes.c_void_p(stream)), "tc_mlp_adam_step")
+
+
+def tc_plan_features(plan: int):
+    import numpy as np
+    out = np.zeros(N_FEATURES, np.float32)
+    _check(lib.tc_plan_features(ctypes.c_void_p(plan), ctypes.c_void_p(out.ctypes.data),
+                                N_FEATURES), "tc_plan_features")
+    return out
+
+
+def tc_selector_load(path: str) -> None:
+    _check(lib.tc_selector_load(str(path).encode()), "tc_selector_load")
+
+
+def tc_selector_unload() -> None:
+    lib.tc_selector_unload()
+
+
+def tc_selector_predict(features):
+    """features: float32 array [n, N_FEATURES] -> (pred [n, n_cand], candidate mappings)."""
+    import numpy as np
+    X = np.ascontiguousarray(features, np.float32).reshape(-1, N_FEATURES)
+    out = np.zeros((X.shape[0], 16), np.float32)
+    cand = np.zeros(16, np.int32)
+    nc = ctypes.c_int32()
+    _check(lib.tc_selector_predict(ctypes.c_void_p(X.ctypes.data), X.shape[0],
+                                   ctypes.c_void_p(out.ctypes.data),
+                                   ctypes.c_void_p(cand.ctypes.data), ctypes.byref(nc)),
+           "tc_selector_predict")
+    n = nc.value
+    return out.reshape(-1)[: X.shape[0] * n].reshape(X.shape[0], n), cand[:n]
