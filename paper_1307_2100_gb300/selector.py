@@ -1,0 +1,314 @@
+"""The learned mapping selector: timing dataset, training and evaluation.
+
+    python -m paper_1307_2100_gb300.selector generate --n 20000 --out sel_data.npz
+    python -m paper_1307_2100_gb300.selector train --data sel_data.npz --out selector.bin
+    python -m paper_1307_2100_gb300.selector evaluate --data sel_data.npz --weights selector.bin
+
+Every descriptor is planned under each candidate mapping (FP32 storage,
+BF16x6 math, the FP32-class form) and timed by CUDA events (median of a few
+runs after a warm-up).  The network (libtc's tc_mlp_* kernels: forward,
+masked-MSE backward, Adam; FP16 working weights) learns the log2 runtime of
+every candidate from the plan's features (tc_plan_features).  Regret of a
+choice is t(choice) / t(best) - 1 against the same exhaustive timing table;
+the paper's class recipe (Sec. 3.2) is the method the network is compared
+with and falls back to.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import struct
+import sys
+import time
+
+import numpy as np
+
+from . import tc
+
+CANDIDATES = ["fused_gemm", "slice_gemm", "copy_gemm", "gemv", "dot"]
+CAND_IDS = [tc.MAPPING[c] for c in CANDIDATES]
+MATH = "bf16x6"
+HIDDEN = 128
+
+
+def _desc(t):
+    return (t.labels, t.extents, t.strides)
+
+
+def _span(t):
+    if any(e == 0 for e in t.extents):
+        return 0
+    return 1 + sum((e - 1) * s for e, s in zip(t.extents, t.strides))
+
+
+def generate(n, seed, out, reps=5, checkpoint=500, log=sys.stderr):
+    """Time every candidate on n descriptors; save features, times (ms; NaN if
+    the candidate cannot compute it), class and the recipe's choice."""
+    import torch
+    import tcsynth as ts
+    dev = torch.device("cuda", 0)
+    descs = ts.selector_descriptors(n, seed=seed)
+    big = max(max(_span(a), _span(b), _span(c)) for a, b, c in descs)
+    arena = [torch.rand(big, device=dev) * 2 - 1 for _ in range(2)]
+    cbuf = torch.zeros(big, device=dev)
+    ws = torch.empty(1 << 28, dtype=torch.uint8, device=dev)
+    s = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    F = np.zeros((n, tc.N_FEATURES), np.float32)
+    T = np.full((n, len(CANDIDATES)), np.nan, np.float64)
+    cls = np.zeros(n, np.int32)
+    recipe = np.zeros(n, np.int32)
+    start = 0
+    if os.path.exists(out + ".partial.npz"):
+        z = np.load(out + ".partial.npz")
+        start = int(z["done"])
+        F[:start], T[:start], cls[:start], recipe[:start] = z["F"][:start], z["T"][:start], \
+            z["cls"][:start], z["recipe"][:start]
+    t0 = time.time()
+    for i in range(start, n):
+        A, B, C = descs[i]
+        h = tc.tc_plan(_desc(A), _desc(B), _desc(C), tc.TC_F32, tc.MATH[MATH], tc.MAPPING["recipe"])
+        info = tc.tc_plan_get_info(h)
+        F[i] = tc.tc_plan_features(h)
+        cls[i] = info.cls
+        recipe[i] = info.mapping
+        tc.tc_plan_destroy(h)
+        for j, cname in enumerate(CANDIDATES):
+            try:
+                h = tc.tc_plan(_desc(A), _desc(B), _desc(C), tc.TC_F32, tc.MATH[MATH],
+                               tc.MAPPING[cname])
+            except tc.TcError:
+                continue
+            try:
+                w = tc.tc_plan_get_info(h).workspace
+                if w > ws.numel():
+                    continue
+                args = (h, 1.0, arena[0].data_ptr(), arena[1].data_ptr(), 0.0, cbuf.data_ptr(),
+                        ws.data_ptr(), ws.numel(), s.cuda_stream)
+                tc.tc_contract(*args)                        # warm-up
+                times = []
+                for r in range(reps):
+                    e0.record(s)
+                    tc.tc_contract(*args)
+                    e1.record(s)
+                    e1.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                    if times[0] > 50.0:                       # long runs: one sample
+                        break
+                T[i, j] = float(np.median(times))
+            finally:
+                tc.tc_plan_destroy(h)
+        if (i + 1) % checkpoint == 0 or i + 1 == n:
+            np.savez(out + ".partial.npz", F=F, T=T, cls=cls, recipe=recipe, done=i + 1)
+            print(f"[selector] {i + 1}/{n} descriptors, {time.time() - t0:.0f} s", file=log,
+                  flush=True)
+    if tc.tc_device_status(s.cuda_stream) != tc.TC_OK:
+        raise RuntimeError("device status not ok after timing")
+    np.savez(out, F=F, T=T, cls=cls, recipe=recipe, candidates=np.array(CAND_IDS, np.int32),
+             seed=seed)
+    if os.path.exists(out + ".partial.npz"):
+        os.remove(out + ".partial.npz")
+    return out
+
+
+def split(n, holdout, seed=1):
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(n)
+    return perm[holdout:], perm[:holdout]
+
+
+def _targets(T):
+    """log2 of the runtime in microseconds; mask of candidates that ran."""
+    mask = np.isfinite(T)
+    Y = np.where(mask, np.log2(np.maximum(np.nan_to_num(T, nan=1.0), 1e-6) * 1e3), 0.0)
+    return Y.astype(np.float32), mask.astype(np.float32)
+
+
+def train(data, out, holdout=2000, epochs=400, batch=256, lr=2e-3, seed=0, log=sys.stderr):
+    """Train the network on the GPU with libtc's kernels and write the
+    selector file read by tc_selector_load."""
+    import torch
+    z = np.load(data)
+    F, T = z["F"].astype(np.float32), z["T"]
+    tr, _ = split(len(F), holdout)
+    Y, M = _targets(T)
+    lo, hi = F[tr].min(axis=0), F[tr].max(axis=0)
+    mean = F[tr].mean(axis=0)
+    std = F[tr].std(axis=0)
+    scale = np.where(std > 1e-6, 1.0 / np.maximum(std, 1e-6), 0.0).astype(np.float32)
+    ym = float((Y[tr] * M[tr]).sum() / M[tr].sum())
+    ys = float(np.sqrt(((Y[tr] - ym) ** 2 * M[tr]).sum() / M[tr].sum()))
+    Xn = ((F - mean) * scale).astype(np.float32)
+    Yn = ((Y - ym) / ys).astype(np.float32)
+    dev = torch.device("cuda", 0)
+    n_in, n_out = F.shape[1], T.shape[1]
+    net = tc.tc_mlp_create(n_in, HIDDEN, n_out, batch)
+    try:
+        n_par = tc.tc_mlp_num_params(net)
+        rng = np.random.default_rng(seed)
+        theta = []
+        for shape in ((HIDDEN, n_in), (HIDDEN,), (HIDDEN, HIDDEN), (HIDDEN,), (n_out, HIDDEN),
+                      (n_out,)):
+            if len(shape) == 2:   # He-uniform initialisation
+                lim = np.sqrt(6.0 / shape[1])
+                theta.append(rng.uniform(-lim, lim, shape).ravel())
+            else:
+                theta.append(np.zeros(shape))
+        theta = np.concatenate(theta).astype(np.float32)
+        assert theta.size == n_par
+        tc.tc_mlp_set_params(net, theta.ctypes.data, n_par)
+        dX = torch.from_numpy(Xn[tr]).to(dev)
+        dY = torch.from_numpy(Yn[tr]).to(dev)
+        dM = torch.from_numpy(M[tr]).to(dev)
+        loss = torch.zeros(1, device=dev)
+        grad = torch.zeros(n_par, device=dev)
+        ntr = len(tr)
+        step = 0
+        hist = []
+        for ep in range(epochs):
+            perm = torch.from_numpy(np.random.default_rng(seed + ep).permutation(ntr)).to(dev)
+            tot = 0.0
+            nb = 0
+            for b0 in range(0, ntr - batch + 1, batch):
+                idx = perm[b0:b0 + batch]
+                xb, yb, mb = dX[idx].contiguous(), dY[idx].contiguous(), dM[idx].contiguous()
+                tc.tc_mlp_loss_grad(net, xb.data_ptr(), yb.data_ptr(), mb.data_ptr(), batch,
+                                    loss.data_ptr(), grad.data_ptr())
+                step += 1
+                cur = lr * 0.5 * (1 + np.cos(np.pi * ep / epochs))   # cosine schedule
+                tc.tc_mlp_adam_step(net, grad.data_ptr(), float(cur), 0.9, 0.999, 1e-8, step)
+                tot += float(loss.item()) if b0 == 0 else 0.0
+                nb += 1
+            hist.append(tot)
+            if ep % 50 == 0 or ep == epochs - 1:
+                print(f"[selector] epoch {ep} loss {tot:.4f}", file=log, flush=True)
+        work = np.empty(n_par, np.float32)
+        tc.tc_mlp_get_params(net, work.ctypes.data, n_par, working=True)
+    finally:
+        tc.tc_mlp_destroy(net)
+    write_weights(out, n_in, HIDDEN, n_out, CAND_IDS, lo, hi, mean, scale, ym, ys, work)
+    return out
+
+
+def write_weights(path, n_in, n_hidden, n_out, cand, lo, hi, mean, scale, ym, ys, params):
+    with open(path, "wb") as f:
+        f.write(b"TCSEL01\0")
+        f.write(struct.pack("<5i", n_in, n_hidden, n_out, tc.TC_F32, tc.MATH[MATH]))
+        f.write(np.asarray(cand, "<i4").tobytes())
+        for a in (lo, hi, mean, scale):
+            f.write(np.asarray(a, "<f4").tobytes())
+        f.write(struct.pack("<2f", ym, ys))
+        f.write(np.asarray(params, np.float32).astype("<f2").tobytes())
+
+
+def feasible(cls):
+    """Candidates able to compute a contraction of the given class: slicing and
+    COPY+GEMM need a free index in each operand (Class 3)."""
+    ok = np.ones((len(cls), len(CANDIDATES)), bool)
+    c3 = np.isin(cls, [31, 32])
+    ok[~c3, CANDIDATES.index("slice_gemm")] = False
+    ok[~c3, CANDIDATES.index("copy_gemm")] = False
+    return ok
+
+
+def regret_stats(choice_t, best_t):
+    r = choice_t / best_t - 1.0
+    return {"mean": float(np.mean(r)), "median": float(np.median(r)),
+            "p90": float(np.percentile(r, 90)), "max": float(np.max(r))}
+
+
+def evaluate(data, weights, holdout=2000, use_gpu=True):
+    """Regret of the network, of the recipe, and of each fixed candidate on the
+    held-out descriptors (timings from the dataset)."""
+    z = np.load(data)
+    F, T, cls, recipe = z["F"].astype(np.float32), z["T"], z["cls"], z["recipe"]
+    _, te = split(len(F), holdout)
+    F, T, cls, recipe = F[te], T[te], cls[te], recipe[te]
+    ran = np.isfinite(T)
+    keep = ran.any(axis=1)
+    F, T, cls, recipe, ran = F[keep], T[keep], cls[keep], recipe[keep], ran[keep]
+    ok = feasible(cls) & ran
+    best = np.where(ok, T, np.inf).min(axis=1)
+    tc.tc_selector_load(weights)
+    try:
+        pred, cand = tc.tc_selector_predict(F)
+    finally:
+        tc.tc_selector_unload()
+    gpu_pred = None
+    if use_gpu:
+        gpu_pred = gpu_forward(weights, F)
+    choice = np.argmin(np.where(ok, pred, np.inf), axis=1)
+    t_choice = T[np.arange(len(T)), choice]
+    rec_idx = np.array([CAND_IDS.index(m) if m in CAND_IDS else 0 for m in recipe])
+    t_recipe = np.where(ok[np.arange(len(T)), rec_idx], T[np.arange(len(T)), rec_idx], np.inf)
+    res = {"n": int(len(T)), "network": regret_stats(t_choice, best),
+           "recipe": regret_stats(t_recipe, best),
+           "total_time_ms": {"network": float(t_choice.sum()), "recipe": float(t_recipe.sum()),
+                             "best": float(best.sum())}}
+    for j, c in enumerate(CANDIDATES):
+        tj = np.where(ok[:, j], T[:, j], np.inf)
+        fin = np.isfinite(tj)
+        res["always_" + c] = {"coverage": float(fin.mean()),
+                              "mean_regret_where_feasible": float(np.mean(tj[fin] / best[fin] - 1))}
+    if gpu_pred is not None:
+        res["gpu_host_max_abs_diff"] = float(np.max(np.abs(gpu_pred - pred)))
+    return res
+
+
+def gpu_forward(weights, F):
+    """The trained network on the GPU (libtc's forward kernel) for rows of F;
+    returns de-normalised log2 runtimes like tc_selector_predict."""
+    import torch
+    with open(weights, "rb") as f:
+        raw = f.read()
+    n_in, n_hidden, n_out, _, _ = struct.unpack("<5i", raw[8:28])
+    off = 28 + 4 * n_out
+    vec = []
+    for _ in range(4):          # lo, hi, mean, scale
+        vec.append(np.frombuffer(raw, "<f4", n_in, off))
+        off += 4 * n_in
+    mean, scale = vec[2], vec[3]
+    ym, ys = struct.unpack("<2f", raw[off:off + 8])
+    params = np.frombuffer(raw, "<f2", -1, off + 8).astype(np.float32)
+    dev = torch.device("cuda", 0)
+    X = torch.from_numpy(((F - mean) * scale).astype(np.float32)).to(dev)
+    Y = torch.empty(len(F), n_out, device=dev)
+    net = tc.tc_mlp_create(n_in, n_hidden, n_out, max(len(F), 1))
+    try:
+        tc.tc_mlp_set_params(net, np.ascontiguousarray(params).ctypes.data, params.size)
+        tc.tc_mlp_forward(net, X.data_ptr(), Y.data_ptr(), len(F))
+        torch.cuda.synchronize()
+    finally:
+        tc.tc_mlp_destroy(net)
+    return Y.cpu().numpy() * ys + ym
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    g = sub.add_parser("generate")
+    g.add_argument("--n", type=int, default=20000)
+    g.add_argument("--seed", type=int, default=20130712)
+    g.add_argument("--out", required=True)
+    g.add_argument("--reps", type=int, default=5)
+    t = sub.add_parser("train")
+    t.add_argument("--data", required=True)
+    t.add_argument("--out", required=True)
+    t.add_argument("--epochs", type=int, default=400)
+    t.add_argument("--holdout", type=int, default=2000)
+    e = sub.add_parser("evaluate")
+    e.add_argument("--data", required=True)
+    e.add_argument("--weights", required=True)
+    e.add_argument("--holdout", type=int, default=2000)
+    a = ap.parse_args(argv)
+    if a.cmd == "generate":
+        generate(a.n, a.seed, a.out, a.reps)
+    elif a.cmd == "train":
+        train(a.data, a.out, a.holdout, a.epochs)
+    else:
+        print(json.dumps(evaluate(a.data, a.weights, a.holdout)))
+
+
+if __name__ == "__main__":
+    main()

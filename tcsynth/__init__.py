@@ -341,3 +341,40 @@ def gemv_1024_full(seed=BASE_SEED + 1, b=1024, alloc=None) -> Problem:
     A smaller b gives the leading slab of the same tensor."""
     return big_problem("gemv_1024", "aib", "i", "ab", dict(a=1024, b=b, i=2048), seed + 200,
                        alloc=alloc)
+
+
+def selector_descriptors(n: int, seed: int = BASE_SEED + 4, lo: int = 4, hi: int = 256,
+                         max_elems: int = 1 << 24, max_out: int = 1 << 24,
+                         max_flops: float = float(1 << 35)):
+    """Random contraction descriptors of the selector workload: orders 2-6,
+    1-3 contracted labels, extents log-uniform in [lo, hi], random storage
+    orders of A, B and C.  A draw is repeated until every tensor has at most
+    max_elems elements, C at most max_out, and 2 * prod(extents) <= max_flops.
+    Returns (A, B, C) descriptor triples of Tensor objects without data."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    while len(out) < n:
+        na = int(rng.integers(2, 7))
+        nb = int(rng.integers(2, 7))
+        p = int(rng.integers(1, min(3, na, nb) + 1))
+        names = list(range(1, 1 + na + nb - p))
+        con, fa, fb = names[:p], names[p:na], names[na:]
+        ext = {l: log_uniform_int(rng, lo, hi) for l in names}
+
+        def numel(ls):
+            v = 1
+            for l in ls:
+                v *= ext[l]
+            return v
+
+        if (max(numel(con + fa), numel(con + fb)) > max_elems or numel(fa + fb) > max_out
+                or 2.0 * numel(names) > max_flops):
+            continue
+        tens = []
+        for ls in (con + fa, con + fb, fa + fb):
+            ls = [ls[k] for k in rng.permutation(len(ls))]
+            e = [ext[l] for l in ls]
+            order = list(rng.permutation(len(ls)))
+            tens.append(Tensor(ls, e, storage_strides(e, order), np.zeros(0, np.float32)))
+        out.append(tuple(tens))
+    return out
