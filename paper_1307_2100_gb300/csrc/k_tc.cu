@@ -19,11 +19,13 @@
 //
 // One CTA per SM, persistent over a work list of 128 x 128 output tiles.
 // Warp roles (416 threads):
-//   warps 0-3   producers: read FP32 elements of A and B through the index
-//               groups (any strides: the permutation of a Class 3.1 operand is
-//               absorbed here, so no copy pass touches HBM), split them into
-//               BF16 terms in registers, store the terms to shared memory in the
-//               canonical K-major layout of the tensor cores;
+//   warps 0-3   producers: copy FP32 elements of A and B, gathered through the
+//               index groups (any strides: the permutation of a Class 3.1
+//               operand is absorbed here, so no copy pass touches HBM), into a
+//               shared-memory staging ring with cp.async (16-byte copies where
+//               four elements are contiguous), several K blocks ahead; then
+//               split each staged block into BF16 terms and store the terms in
+//               the canonical K-major layout of the tensor cores;
 //   warps 4-11  epilogue: two warps per tensor-memory lane quadrant, 64 columns
 //               each; drain K-chunks, finish with alpha/beta and a strided store;
 //   warp 12     tensor-memory allocation and the single thread issuing
@@ -46,7 +48,7 @@ namespace tc {
 
 namespace tcg {
 
-constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int BM = 128, BN = 128, BK = 32;
 constexpr int kProducers = 128;
 constexpr int kEpiWarps = 8;
 constexpr int kMmaWarp = 4 + kEpiWarps;
@@ -73,13 +75,19 @@ struct Launch {
 
 template <int NT>
 struct Cfg {
-  static constexpr int S = NT == 1 ? 6 : NT == 2 ? 3 : 2;         // pipeline stages
+  static constexpr int S = NT == 1 ? 4 : NT == 2 ? 3 : 2;         // BF16 term stages
+  static constexpr int D = NT == 1 ? 4 : 3;                       // FP32 staging depth
   static constexpr uint32_t A_TERM = BM * BK * 2;                  // bytes per A term
   static constexpr uint32_t B_TERM = BN * BK * 2;
   static constexpr uint32_t STAGE = NT * (A_TERM + B_TERM);
-  static constexpr uint32_t OFF_KOFF = S * STAGE;                   // int64 koffA[S][BK], koffB[S][BK]
-  static constexpr uint32_t OFF_KVEC = OFF_KOFF + S * BK * 2 * 8;  // uint8 kvecA[S][8], kvecB[S][8]
-  static constexpr uint32_t OFF_ROWS = OFF_KVEC + S * 16 + 64;      // rowA[BM], rowB[BN], rowC[BM], colC[BN]
+  // FP32 staging of one operand: [row][BK + 4] (K-contiguous or gathered
+  // operands) or [k][128 + 4] (operands contiguous along rows).
+  static constexpr uint32_t SOP = 128 * (BK + 4) * 4;
+  static constexpr uint32_t OFF_STG = S * STAGE;
+  static constexpr uint32_t OFF_KOFF = OFF_STG + D * 2 * SOP;       // int64 koffA[BK], koffB[BK]
+  static constexpr uint32_t OFF_KFLAG = OFF_KOFF + 2 * BK * 8;      // uint8 kflag[2][BK / 4]
+  static constexpr uint32_t OFF_ROWQ = OFF_KFLAG + 16;              // uint8 rowq[2][32]
+  static constexpr uint32_t OFF_ROWS = OFF_ROWQ + 64;               // rowA, rowB, rowC, colC
   static constexpr uint32_t OFF_ARGS = OFF_ROWS + (2 * BM + 2 * BN) * 8;
   static constexpr uint32_t OFF_BAR = OFF_ARGS + ((sizeof(GemmArgs) + 15) / 16) * 16;
   static constexpr uint32_t NBAR = 2 * S + 5;
@@ -92,110 +100,83 @@ __constant__ int8_t kProdA[6] = {0, 0, 1, 0, 1, 2};
 __constant__ int8_t kProdB[6] = {0, 1, 0, 2, 1, 0};
 __host__ __device__ constexpr int nprod(int nt) { return nt == 1 ? 1 : nt == 2 ? 3 : 6; }
 
-// Producer: one operand tile (ROWS x 64 K) of one K block.  Every load of the
-// tile is issued before any is converted, so a thread keeps 64 loads in
-// flight.  Lanes run along rows when the operand is contiguous along its
-// M/N index (each k is then one coalesced row segment); otherwise lanes take
-// (row-in-8, 8-wide K chunk) units, read as two 16-byte vectors when the
-// chunk is contiguous and aligned.
-template <int NT, int ROWS>
-__device__ __forceinline__ void produce(const float* __restrict__ X, const int64_t* rowoff,
-                                        const int64_t* koff, const uint8_t* kvec, bool contig_mn,
-                                        bool rowvec, uint32_t sbuf, int ptid) {
-  constexpr int PER = ROWS * (BK / 8) / kProducers;  // units per thread
-  constexpr uint32_t TERM = ROWS * BK * 2;
-  constexpr uint32_t LBO = (ROWS / 8) * 128;
-  float v[PER][8];
-  if (contig_mn && rowvec) {
-    // four consecutive rows per 16-byte load: thread -> (row quad, chunk pair)
-    const int quad = ptid & (ROWS / 4 - 1);
-    const int cp = ptid / (ROWS / 4);          // 0 .. 128 / (ROWS / 4) - 1
-    constexpr int NCP = kProducers / (ROWS / 4);
-    const int64_t ro = rowoff[quad * 4];
-#pragma unroll
-    for (int h = 0; h < PER / 4; ++h) {
-      const int chunk = cp + h * NCP;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int64_t ko = koff[chunk * 8 + j];
-        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (ko >= 0) x = __ldg(reinterpret_cast<const float4*>(X + ro + ko));
-        v[h * 4 + 0][j] = x.x;
-        v[h * 4 + 1][j] = x.y;
-        v[h * 4 + 2][j] = x.z;
-        v[h * 4 + 3][j] = x.w;
-      }
-    }
-#pragma unroll
-    for (int h = 0; h < PER / 4; ++h) {
-      const int chunk = cp + h * NCP;
-#pragma unroll
-      for (int q4 = 0; q4 < 4; ++q4) {
-        const int row = quad * 4 + q4;
-        const uint32_t dst = sbuf + chunk * LBO + (row >> 3) * 128 + (row & 7) * 16;
-        float* vv = v[h * 4 + q4];
-#pragma unroll
-        for (int t = 0; t < NT; ++t) {
-          uint32_t w[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            w[q] = pack_bf16x2(vv[2 * q], vv[2 * q + 1]);
-            if (t + 1 < NT) {
-              vv[2 * q] = __fsub_rn(vv[2 * q], bf16_lo(w[q]));
-              vv[2 * q + 1] = __fsub_rn(vv[2 * q + 1], bf16_hi(w[q]));
-            }
-          }
-          st_shared_v4(dst + t * TERM, w[0], w[1], w[2], w[3]);
-        }
-      }
-    }
-    return;
-  }
+// Copy one operand's FP32 block (ROWS x BK) into a staging slot.  Operands
+// contiguous along their rows are staged [k][row]: lanes take row quads, one
+// 16-byte copy per (quad, k) when the four rows are contiguous and aligned.
+// Other operands are staged [row][k]: lanes take (row, 4-wide K group), one
+// 16-byte copy when the four k are contiguous and aligned.  Elements outside
+// the tensor are zero-filled.
+template <int ROWS>
+__device__ __forceinline__ void issue_copies(const float* __restrict__ X,
+                                             const int64_t* rowoff, const uint8_t* rowq,
+                                             const int64_t* koff, const uint8_t* kflag,
+                                             bool contig_mn, uint32_t slot, int ptid) {
   if (contig_mn) {
-    const int row = ptid % ROWS;
-    const int64_t ro = rowoff[row];
+    const int quad = ptid & (ROWS / 4 - 1);
+    const int kg = ptid / (ROWS / 4);
+    constexpr int NK = kProducers / (ROWS / 4);
+    const bool q4 = rowq[quad] != 0;
 #pragma unroll
-    for (int r = 0; r < PER; ++r) {
-      const int chunk = (ptid + r * kProducers) / ROWS;
+    for (int r = 0; r < BK / NK; ++r) {
+      const int k = kg + r * NK;
+      const int64_t ko = koff[k];
+      const uint32_t dst = slot + (uint32_t)(k * (ROWS + 4) + quad * 4) * 4;
+      const float* src = X + rowoff[quad * 4] + ko;
+      if (q4 && ko >= 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        cp_async16(dst, src);
+      } else {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int64_t ko = koff[chunk * 8 + j];
-        v[r][j] = (ro >= 0 && ko >= 0) ? __ldg(X + ro + ko) : 0.0f;
+        for (int i = 0; i < 4; ++i) {
+          const int64_t ro = rowoff[quad * 4 + i];
+          const bool ok = ro >= 0 && ko >= 0;
+          cp_async4(dst + 4 * i, ok ? (const void*)(X + ro + ko) : (const void*)X, ok ? 4u : 0u);
+        }
       }
     }
   } else {
-    const int chunk = (ptid >> 3) & 7;
-    const int64_t k0 = koff[chunk * 8];
-    const bool vec = (kvec[chunk] & 1) != 0;
+    const int kg = ptid & (BK / 4 - 1);
+    constexpr int RSTEP = kProducers / (BK / 4);
+    const bool k4 = kflag[kg] != 0;
+    const int64_t ko0 = koff[kg * 4];
 #pragma unroll
-    for (int r = 0; r < PER; ++r) {
-      const int u = ptid + r * kProducers;
-      const int64_t ro = rowoff[(u & 7) + 8 * (u >> 6)];
-      const float* src = X + ro + k0;
-      if (vec && ro >= 0 && ((reinterpret_cast<uintptr_t>(src) & 15) == 0)) {
-        const float4 x0 = __ldg(reinterpret_cast<const float4*>(src));
-        const float4 x1 = __ldg(reinterpret_cast<const float4*>(src) + 1);
-        v[r][0] = x0.x; v[r][1] = x0.y; v[r][2] = x0.z; v[r][3] = x0.w;
-        v[r][4] = x1.x; v[r][5] = x1.y; v[r][6] = x1.z; v[r][7] = x1.w;
+    for (int r = 0; r < ROWS / RSTEP; ++r) {
+      const int row = ptid / (BK / 4) + r * RSTEP;
+      const int64_t ro = rowoff[row];
+      const uint32_t dst = slot + (uint32_t)(row * (BK + 4) + kg * 4) * 4;
+      const float* src = X + ro + ko0;
+      if (k4 && ro >= 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        cp_async16(dst, src);
       } else {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int64_t ko = koff[chunk * 8 + j];
-          v[r][j] = (ro >= 0 && ko >= 0) ? __ldg(X + ro + ko) : 0.0f;
+        for (int i = 0; i < 4; ++i) {
+          const int64_t ko = koff[kg * 4 + i];
+          const bool ok = ro >= 0 && ko >= 0;
+          cp_async4(dst + 4 * i, ok ? (const void*)(X + ro + ko) : (const void*)X, ok ? 4u : 0u);
         }
       }
     }
   }
+}
+
+// Split a staged FP32 block into NT BF16 terms in the canonical K-major layout
+// (8-row x 16-byte core matrices; 8-wide K chunks LBO bytes apart).
+template <int NT, int ROWS>
+__device__ __forceinline__ void convert(const float* stg, bool contig_mn, uint32_t sbuf,
+                                        int ptid) {
+  constexpr uint32_t TERM = ROWS * BK * 2;
+  constexpr uint32_t LBO = (ROWS / 8) * 128;
+  const int row = ptid;  // ROWS == kProducers
 #pragma unroll
-  for (int r = 0; r < PER; ++r) {
-    const int u = ptid + r * kProducers;
-    int row, chunk;
+  for (int chunk = 0; chunk < BK / 8; ++chunk) {
+    float v[8];
     if (contig_mn) {
-      row = u % ROWS;
-      chunk = u / ROWS;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = stg[(chunk * 8 + j) * (ROWS + 4) + row];
     } else {
-      row = (u & 7) + 8 * (u >> 6);
-      chunk = (u >> 3) & 7;
+      const float4 x0 = *reinterpret_cast<const float4*>(stg + row * (BK + 4) + chunk * 8);
+      const float4 x1 = *reinterpret_cast<const float4*>(stg + row * (BK + 4) + chunk * 8 + 4);
+      v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
+      v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
     }
     const uint32_t dst = sbuf + chunk * LBO + (row >> 3) * 128 + (row & 7) * 16;
 #pragma unroll
@@ -203,10 +184,10 @@ __device__ __forceinline__ void produce(const float* __restrict__ X, const int64
       uint32_t w[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        w[q] = pack_bf16x2(v[r][2 * q], v[r][2 * q + 1]);
+        w[q] = pack_bf16x2(v[2 * q], v[2 * q + 1]);
         if (t + 1 < NT) {  // exact FP32 residuals
-          v[r][2 * q] = __fsub_rn(v[r][2 * q], bf16_lo(w[q]));
-          v[r][2 * q + 1] = __fsub_rn(v[r][2 * q + 1], bf16_hi(w[q]));
+          v[2 * q] = __fsub_rn(v[2 * q], bf16_lo(w[q]));
+          v[2 * q + 1] = __fsub_rn(v[2 * q + 1], bf16_hi(w[q]));
         }
       }
       st_shared_v4(dst + t * TERM, w[0], w[1], w[2], w[3]);
@@ -236,14 +217,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~(uintptr_t)1023);
   int64_t* koffA = reinterpret_cast<int64_t*>(smem + G::OFF_KOFF);
-  int64_t* koffB = koffA + S * BK;
-  uint8_t* kvecA = smem + G::OFF_KVEC;
-  uint8_t* kvecB = kvecA + S * 8;
+  int64_t* koffB = koffA + BK;
+  uint8_t* kflagA = smem + G::OFF_KFLAG;
+  uint8_t* kflagB = kflagA + BK / 4;
+  uint8_t* rowqA = smem + G::OFF_ROWQ;
+  uint8_t* rowqB = rowqA + 32;
   int64_t* rowA = reinterpret_cast<int64_t*>(smem + G::OFF_ROWS);
   int64_t* rowB = rowA + BM;
   int64_t* rowC = rowB + BN;
   int64_t* colC = rowC + BM;
-  int* rowvec = reinterpret_cast<int*>(smem + G::OFF_MISC + 8);  // [A, B]
   GemmArgs* sargs = reinterpret_cast<GemmArgs*>(smem + G::OFF_ARGS);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + G::OFF_BAR);
   uint64_t* full = bars;
@@ -336,18 +318,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
       colC[i] = oc;
     }
     __syncthreads();
-    if (warp == 0) {  // may rows be read four at a time (16-byte vectors)?
-      for (int which = 0; which < 2; ++which) {
-        const int64_t* ro = which ? rowB : rowA;
-        const bool mn = (which ? p.b_contig : p.a_contig) == CONTIG_MN;
-        const uintptr_t base = reinterpret_cast<uintptr_t>(which ? p.B : p.A) +
-                               (uintptr_t)((which ? bB : bA) * 4);
-        bool ok = mn && (base & 15) == 0;
-        for (int r = lane; r < 128 && ok; r += 32)
-          ok = ro[r] >= 0 && (r % 4 == 0 ? (ro[r] & 3) == 0 : ro[r] == ro[r - 1] + 1);
-        ok = __all_sync(0xffffffffu, ok);
-        if (lane == 0) rowvec[which] = ok ? 1 : 0;
-      }
+    if (tid < 64) {  // row quads that are valid and contiguous (16-byte copies)
+      const int which = tid >> 5, q = tid & 31;
+      const int64_t* ro = which ? rowB : rowA;
+      bool ok = true;
+      for (int i = 0; i < 4; ++i) ok = ok && ro[q * 4 + i] >= 0 && ro[q * 4 + i] == ro[q * 4] + i;
+      (which ? rowqB : rowqA)[q] = ok ? 1 : 0;
     }
     __syncthreads();
 
@@ -360,44 +336,55 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
       const float* __restrict__ Xa = static_cast<const float*>(p.A) + bA;
       const float* __restrict__ Xb = static_cast<const float*>(p.B) + bB;
       const bool amn = p.a_contig == CONTIG_MN, bmn = p.b_contig == CONTIG_MN;
+      const uint32_t stg0 = sbase + G::OFF_STG;
+      const float* stgp = reinterpret_cast<const float*>(smem + G::OFF_STG);
+      // K offsets (and 4-wide contiguity flags) of block kk, then its copies
+      auto load_block = [&](uint32_t kk, int slot) {
+        if (tid < BK) {
+          const uint32_t k = kk * BK + tid;
+          int64_t oa = -1, ob = -1;
+          if (k < K) goff2(p.gk, 0, 1, k, oa, ob);
+          koffA[tid] = oa;
+          koffB[tid] = ob;
+        }
+        named_bar_sync(1, kProducers);
+        if (tid < BK / 2) {
+          const int which = tid / (BK / 4), g = tid % (BK / 4);
+          const int64_t* ko = (which ? koffB : koffA) + g * 4;
+          bool c = ko[0] >= 0;
+          for (int i = 1; i < 4; ++i) c = c && ko[i] == ko[0] + i;
+          (which ? kflagB : kflagA)[g] = c ? 1 : 0;
+        }
+        named_bar_sync(1, kProducers);
+        const uint32_t sl = stg0 + (uint32_t)slot * 2 * G::SOP;
+        issue_copies<BM>(Xa, rowA, rowqA, koffA, kflagA, amn, sl, tid);
+        issue_copies<BN>(Xb, rowB, rowqB, koffB, kflagB, bmn, sl + G::SOP, tid);
+      };
+      constexpr int D = G::D;
+      for (int d = 0; d < D - 1; ++d) {
+        if ((uint32_t)d < nkb) load_block((uint32_t)d, d);
+        cp_async_commit();
+      }
       for (uint32_t kb = 0; kb < nkb; ++kb, ++g_kb) {
+        if (kb + D - 1 < nkb) load_block(kb + D - 1, (int)((kb + D - 1) % D));
+        cp_async_commit();
+        cp_async_wait<D - 1>();              // this thread's copies of block kb landed
+        named_bar_sync(1, kProducers);       // ... and every producer's
         const int s = g_kb % S;
         const uint32_t ph = (g_kb / S) & 1;
         bool ok = true;
         if (g_kb >= (uint32_t)S) ok = warp_wait(&empty[s], ph ^ 1, abort);
-        if (tid < BK) {
-          const uint32_t k = kb * BK + tid;
-          int64_t oa = -1, ob = -1;
-          if (k < K) goff2(p.gk, 0, 1, k, oa, ob);
-          koffA[s * BK + tid] = oa;
-          koffB[s * BK + tid] = ob;
-        }
-        named_bar_sync(1, kProducers);
-        if (tid < 16) {  // 8-wide K chunks that are contiguous and 4-element aligned
-          const int64_t* ko = (tid < 8 ? koffA : koffB) + s * BK + (tid & 7) * 8;
-          bool c = ko[0] >= 0 && (ko[0] & 3) == 0;
-          bool al = true;  // every k offset a multiple of 4 (or beyond K)
-          for (int j = 1; j < 8; ++j) c = c && ko[j] == ko[0] + j;
-          for (int j = 0; j < 8; ++j) al = al && (ko[j] < 0 || (ko[j] & 3) == 0);
-          (tid < 8 ? kvecA : kvecB)[s * 8 + (tid & 7)] = (c ? 1 : 0) | (al ? 2 : 0);
-        }
-        named_bar_sync(1, kProducers);
-        bool kal[2] = {true, true};
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          kal[0] = kal[0] && (kvecA[s * 8 + c] & 2);
-          kal[1] = kal[1] && (kvecB[s * 8 + c] & 2);
-        }
         if (ok && !*abort) {
           const uint32_t st = sbase + s * G::STAGE;
-          produce<NT, BM>(Xa, rowA, koffA + s * BK, kvecA + s * 8, amn, rowvec[0] && kal[0], st,
-                          tid);
-          produce<NT, BN>(Xb, rowB, koffB + s * BK, kvecB + s * 8, bmn, rowvec[1] && kal[1],
-                          st + NT * G::A_TERM, tid);
+          const float* sl = stgp + (size_t)(kb % D) * 2 * (G::SOP / 4);
+          convert<NT, BM>(sl, amn, st, tid);
+          convert<NT, BN>(sl + G::SOP / 4, bmn, st + NT * G::A_TERM, tid);
           fence_async_smem();
           mbar_arrive(&full[s]);
         }
+        named_bar_sync(1, kProducers);       // staging slot kb % D may be refilled
       }
+      cp_async_wait<0>();
     } else if (warp < kMmaWarp) {
       // ----------------------------------------------------------- epilogue
       const int q = warp & 3;            // tensor-memory lane quadrant
@@ -591,15 +578,15 @@ uint64_t tiles_of(const GemmArgs& a) {
 
 }  // namespace tcg
 
-// Tile configurations of the tensor-core GEMM: K blocks (of 64) per chunk of
+// Tile configurations of the tensor-core GEMM: K blocks (of 32) per chunk of
 // the main accumulator.  Tile 0: one chunk for plain BF16 (its error is that of
 // the BF16 inputs), 256-K chunks for the split forms; tile 1: 64-K chunks;
 // tile 2: 1024-K chunks.
 int num_tiles_tc() { return 3; }
 int tc_chunk_kb(int math, int tile) {
-  if (tile == 1) return 1;
-  if (tile == 2) return 16;
-  return math == TC_MATH_BF16 ? (1 << 30) : 4;
+  if (tile == 1) return 2;
+  if (tile == 2) return 32;
+  return math == TC_MATH_BF16 ? (1 << 30) : 8;
 }
 
 tc_status tc_gemm_read_status(int* h, void* stream) {
