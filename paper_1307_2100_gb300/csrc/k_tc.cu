@@ -106,11 +106,28 @@ __host__ __device__ constexpr int nprod(int nt) { return nt == 1 ? 1 : nt == 2 ?
 // Other operands are staged [row][k]: lanes take (row, 4-wide K group), one
 // 16-byte copy when the four k are contiguous and aligned.  Elements outside
 // the tensor are zero-filled.
+// K offsets of a block: a shared table (K groups of several labels) or
+// base + k * stride (one label); -1 marks k beyond K.
+struct KOff {
+  const int64_t* table;
+  const uint8_t* flag;   // per 4-wide K group: contiguous (table mode)
+  int64_t base, stride;
+  int kvalid;
+  __device__ __forceinline__ int64_t operator()(int k) const {
+    if (table) return table[k];
+    return k < kvalid ? base + (int64_t)k * stride : -1;
+  }
+  __device__ __forceinline__ bool contiguous4(int g) const {
+    if (table) return flag[g] != 0;
+    return stride == 1 && g * 4 + 3 < kvalid;
+  }
+};
+
 template <int ROWS>
 __device__ __forceinline__ void issue_copies(const float* __restrict__ X,
                                              const int64_t* rowoff, const uint8_t* rowq,
-                                             const int64_t* koff, const uint8_t* kflag,
-                                             bool contig_mn, uint32_t slot, int ptid) {
+                                             const KOff& koff, bool contig_mn, uint32_t slot,
+                                             int ptid) {
   if (contig_mn) {
     const int quad = ptid & (ROWS / 4 - 1);
     const int kg = ptid / (ROWS / 4);
@@ -119,7 +136,7 @@ __device__ __forceinline__ void issue_copies(const float* __restrict__ X,
 #pragma unroll
     for (int r = 0; r < BK / NK; ++r) {
       const int k = kg + r * NK;
-      const int64_t ko = koff[k];
+      const int64_t ko = koff(k);
       const uint32_t dst = slot + (uint32_t)(k * (ROWS + 4) + quad * 4) * 4;
       const float* src = X + rowoff[quad * 4] + ko;
       if (q4 && ko >= 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
@@ -136,8 +153,8 @@ __device__ __forceinline__ void issue_copies(const float* __restrict__ X,
   } else {
     const int kg = ptid & (BK / 4 - 1);
     constexpr int RSTEP = kProducers / (BK / 4);
-    const bool k4 = kflag[kg] != 0;
-    const int64_t ko0 = koff[kg * 4];
+    const bool k4 = koff.contiguous4(kg);
+    const int64_t ko0 = koff(kg * 4);
 #pragma unroll
     for (int r = 0; r < ROWS / RSTEP; ++r) {
       const int row = ptid / (BK / 4) + r * RSTEP;
@@ -149,7 +166,7 @@ __device__ __forceinline__ void issue_copies(const float* __restrict__ X,
       } else {
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          const int64_t ko = koff[kg * 4 + i];
+          const int64_t ko = koff(kg * 4 + i);
           const bool ok = ro >= 0 && ko >= 0;
           cp_async4(dst + 4 * i, ok ? (const void*)(X + ro + ko) : (const void*)X, ok ? 4u : 0u);
         }
@@ -339,26 +356,39 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
       const uint32_t stg0 = sbase + G::OFF_STG;
       const float* stgp = reinterpret_cast<const float*>(smem + G::OFF_STG);
       // K offsets (and 4-wide contiguity flags) of block kk, then its copies
+      // A K group of one (merged) label has offsets k * stride: the offsets
+      // are computed where they are used and no barrier is needed; otherwise
+      // one thread per k splits k into its labels and the producers
+      // synchronise on the shared tables.
+      const bool klin = p.gk.n <= 1;
+      const int64_t ksa = p.gk.n ? p.gk.st[0][0] : 0, ksb = p.gk.n ? p.gk.st[1][0] : 0;
       auto load_block = [&](uint32_t kk, int slot) {
-        if (tid < BK) {
-          const uint32_t k = kk * BK + tid;
-          int64_t oa = -1, ob = -1;
-          if (k < K) goff2(p.gk, 0, 1, k, oa, ob);
-          koffA[tid] = oa;
-          koffB[tid] = ob;
+        const int kvalid = (int)min((uint32_t)BK, K - kk * BK);
+        KOff ka{nullptr, nullptr, (int64_t)kk * BK * ksa, ksa, kvalid};
+        KOff kb_{nullptr, nullptr, (int64_t)kk * BK * ksb, ksb, kvalid};
+        if (!klin) {
+          if (tid < BK) {
+            const uint32_t k = kk * BK + tid;
+            int64_t oa = -1, ob = -1;
+            if (k < K) goff2(p.gk, 0, 1, k, oa, ob);
+            koffA[tid] = oa;
+            koffB[tid] = ob;
+          }
+          named_bar_sync(1, kProducers);
+          if (tid < BK / 2) {
+            const int which = tid / (BK / 4), g = tid % (BK / 4);
+            const int64_t* ko = (which ? koffB : koffA) + g * 4;
+            bool c = ko[0] >= 0;
+            for (int i = 1; i < 4; ++i) c = c && ko[i] == ko[0] + i;
+            (which ? kflagB : kflagA)[g] = c ? 1 : 0;
+          }
+          named_bar_sync(1, kProducers);
+          ka = KOff{koffA, kflagA, 0, 0, kvalid};
+          kb_ = KOff{koffB, kflagB, 0, 0, kvalid};
         }
-        named_bar_sync(1, kProducers);
-        if (tid < BK / 2) {
-          const int which = tid / (BK / 4), g = tid % (BK / 4);
-          const int64_t* ko = (which ? koffB : koffA) + g * 4;
-          bool c = ko[0] >= 0;
-          for (int i = 1; i < 4; ++i) c = c && ko[i] == ko[0] + i;
-          (which ? kflagB : kflagA)[g] = c ? 1 : 0;
-        }
-        named_bar_sync(1, kProducers);
         const uint32_t sl = stg0 + (uint32_t)slot * 2 * G::SOP;
-        issue_copies<BM>(Xa, rowA, rowqA, koffA, kflagA, amn, sl, tid);
-        issue_copies<BN>(Xb, rowB, rowqB, koffB, kflagB, bmn, sl + G::SOP, tid);
+        issue_copies<BM>(Xa, rowA, rowqA, ka, amn, sl, tid);
+        issue_copies<BN>(Xb, rowB, rowqB, kb_, bmn, sl + G::SOP, tid);
       };
       constexpr int D = G::D;
       for (int d = 0; d < D - 1; ++d) {
