@@ -1,7 +1,9 @@
 """Reduced-precision forms of the contraction -- TEST INFRASTRUCTURE ONLY.
 
 Parity: pinned (tests/test_oracle_precision.py: exact reconstruction of FP32
-values by three BF16 terms, hand-made rounding ties, the E4M3 value table).
+values by three BF16 terms, hand-made rounding ties, the E4M3 value table; the
+FP8 form exact on small integers, equivariant under power-of-two scaling, and
+its GEMM view reproducing the FP64 contraction).
 
 The paper computes in FP64 only (Sec. 4); these forms come from the project's
 goal of running the bulk of the multiply on BF16/FP8 tensor cores:
@@ -149,3 +151,65 @@ def quantize_rows_e4m3(mat: np.ndarray, block: int = 128):
         out[:, bi * block:(bi + 1) * block] = e4m3_rne(blk / s) * s
         exps[:, bi] = e
     return out, exps
+
+
+# ------------------------------------------------ FP8 form of a contraction
+
+def gemm_view(p):
+    """Dense matrices of the contraction's GEMM view: A_mat [M, K], B_mat [K, N]
+    with rows m enumerated column-major over A's free labels (A's order), rows
+    n over B's free labels (B's order), and K column-major over the contracted
+    labels sorted by ascending stride in A (ties: position in A).  Returns
+    (A_mat, B_mat, m_labels, n_labels, k_labels)."""
+    A, B = p.A, p.B
+    con = [l for l in A.labels if l in B.labels]
+    fa = [l for l in A.labels if l not in B.labels]
+    fb = [l for l in B.labels if l not in A.labels]
+    sa = dict(zip(A.labels, A.strides))
+    pos = {l: k for k, l in enumerate(A.labels)}
+    kl = sorted(con, key=lambda l: (sa[l], pos[l]))
+    ext = dict(zip(A.labels, A.extents))
+    ext.update(zip(B.labels, B.extents))
+
+    def offsets(t, labels):
+        st = dict(zip(t.labels, t.strides))
+        if not labels:
+            return np.zeros(1, dtype=np.int64)
+        grids = np.meshgrid(*[np.arange(ext[l], dtype=np.int64) * st[l] for l in labels],
+                            indexing="ij")
+        return np.asarray(sum(grids)).reshape(-1, order="F")
+
+    am = offsets(A, fa)[:, None] + offsets(A, kl)[None, :]
+    bm = offsets(B, kl)[:, None] + offsets(B, fb)[None, :]
+    return (np.asarray(A.data, np.float64)[am], np.asarray(B.data, np.float64)[bm], fa, fb, kl)
+
+
+def contract_fp8(p, block: int = 128):
+    """FP64 result of the FP8 form: each operand row (a free multi-index) is
+    cut into blocks of `block` consecutive K (in the gemm_view order), scaled by
+    the block's power of two 2^e (smallest e with amax / 2^e <= 448) and
+    rounded to E4M3; the dequantised products are summed exactly (FP64).
+    Returns a buffer laid out like p.C."""
+    Am, Bm, fa, fb, kl = gemm_view(p)
+    qa, _ = quantize_rows_e4m3(Am, block)
+    qb, _ = quantize_rows_e4m3(Bm.T.copy(), block)
+    Cm = qa @ qb.T                                    # [M, N], FP64
+    C = p.C
+    ext = dict(zip(p.A.labels, p.A.extents))
+    ext.update(zip(p.B.labels, p.B.extents))
+    st = dict(zip(C.labels, C.strides))
+
+    def offs(labels):
+        if not labels:
+            return np.zeros(1, dtype=np.int64)
+        grids = np.meshgrid(*[np.arange(ext[l], dtype=np.int64) * st[l] for l in labels],
+                            indexing="ij")
+        return np.asarray(sum(grids)).reshape(-1, order="F")
+
+    idx = offs(fa)[:, None] + offs(fb)[None, :]
+    out = np.array(np.asarray(C.data, np.float64), copy=True)
+    val = p.alpha * Cm
+    if p.beta != 0:
+        val = val + p.beta * out[idx]
+    out[idx] = val
+    return out

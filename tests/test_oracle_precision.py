@@ -1,4 +1,6 @@
 """Pins of the reduced-precision oracle (BF16 rounding and split terms, E4M3)."""
+import copy
+
 import numpy as np
 import pytest
 
@@ -109,3 +111,30 @@ def test_block_quantisation_error():
     dq, e = op.quantize_rows_e4m3(m)
     assert e.shape == (8, 3)
     assert np.max(np.abs(dq - m) / np.maximum(np.abs(m), 2.0 ** -6 * np.exp2(e.max()))) < 0.07
+
+
+def test_gemm_view_reproduces_the_contraction():
+    p = ts.problem("v", "iajb", "jcid", "abcd", dict(i=5, a=3, j=4, b=2, c=3, d=2), 9)
+    Am, Bm, fa, fb, kl = op.gemm_view(p)
+    assert kl == ts.lab("ij")                      # ascending stride in A
+    ref = oracle.contract_problem(p)
+    Cm = Am @ Bm
+    # C is column-major over (a,b,c,d) = (free A, free B): same flattening
+    np.testing.assert_allclose(Cm.reshape(-1, order="F"), ref, rtol=1e-13)
+
+
+def test_fp8_form_is_exact_on_small_integers():
+    # |x| <= 4 integers: the block scale is 2^-6 and 64 * x is an E4M3 value
+    p = ts.problem("i8", "aijb", "ijc", "abc", dict(a=7, i=40, j=9, b=3, c=11), 10,
+                   dist="int", dtype=np.float32, lo=-4, hi=4)
+    np.testing.assert_array_equal(op.contract_fp8(p), oracle.contract_problem(p))
+
+
+def test_fp8_form_scale_equivariance_and_error():
+    p = ts.precision_ccd(v=16, o=8)
+    base = op.contract_fp8(p)
+    q = copy.deepcopy(p)
+    q.A.data = (p.A.data * np.float32(2.0 ** 5)).astype(np.float32)
+    np.testing.assert_array_equal(op.contract_fp8(q), base * 2.0 ** 5)
+    err = oracle.rel_fro(base, oracle.contract_problem(p))
+    assert 1e-4 < err < 6e-2
