@@ -56,6 +56,7 @@ def workloads(alloc=None, only=None, kind="class3_fp64"):
 
 
 NPROD = {"bf16": 1, "bf16x3": 3, "bf16x6": 6}
+FP8_PER_BF16 = 2.0   # nominal dense tensor rate of E4M3 over BF16 (4.5 / 2.25 PFLOP/s)
 
 
 def sampled_error(p, got, nsamp=64):
@@ -231,7 +232,7 @@ def run_reference(args):
 
 # --------------------------------------------------------------- GPU arm
 def launches_of(info) -> int:
-    n = 2 if (info.kernel == 4 and info.M * info.N * info.batch == 1) else 1
+    n = 2 if ((info.kernel == 4 and info.M * info.N * info.batch == 1) or info.kernel == 5) else 1
     return n + (1 if info.mapping == 4 else 0)
 
 
@@ -366,7 +367,9 @@ def run_ours(args):
     for j, p in enumerate(probs):
         info = plans[j].info
         kms = float(per[:, j].mean())
-        if fp64 or info.kernel != 2:
+        if info.kernel == 5:  # FP8 form: one E4M3 product per multiply-add
+            cpeak, work, cbound = bf16_peak * FP8_PER_BF16, p.flops(), "tensor"
+        elif fp64 or info.kernel != 2:
             cpeak, work, cbound = fp64_peak if fp64 else 77.7, p.flops(), "alu"
         else:  # tensor-core forms: NPROD BF16 products per logical multiply-add
             cpeak, work, cbound = bf16_peak, p.flops() * NPROD[math], "tensor"
@@ -405,6 +408,10 @@ def run_ours(args):
                      "frac": dom["frac"], "traffic": traffic,
                      "peak_source": (("derived: 152 SMs x 4 FP64 flop/clk x median SM clock "
                                       f"{sm_mhz:.0f} MHz") if dom["bound"] == "alu"
+                                     else "measured bf16_tflops burst (MEASURED_PEAKS.json) x 2 "
+                                     "(nominal FP8/BF16 dense ratio); achieved = FLOPs over the "
+                                     "pack pass and the GEMM"
+                                     if dom["bound"] == "tensor" and math == "fp8"
                                      else "measured bf16_tflops burst (MEASURED_PEAKS.json); "
                                      "achieved counts every BF16 product"
                                      if dom["bound"] == "tensor"
@@ -554,7 +561,8 @@ def main(argv=None):
     ap.add_argument("--workload", default="class3_fp64",
                     choices=["class3_fp64", "precision", "batching"])
     ap.add_argument("--items", type=int, default=512, help="batching: number of contractions")
-    ap.add_argument("--math", default="bf16x6", choices=["bf16", "bf16x3", "bf16x6", "fp32"],
+    ap.add_argument("--math", default="bf16x6",
+                    choices=["bf16", "bf16x3", "bf16x6", "fp8", "fp32"],
                     help="math of the precision workload")
     ap.add_argument("--tile", type=int, default=-1)
     ap.add_argument("--only", default="", help="comma-separated subset of the workload "

@@ -62,13 +62,26 @@ typedef enum { TC_F64 = 0, TC_F32 = 1 } tc_dtype;
  *   TC_MATH_BF16X3   FP32 inputs split into 2 BF16 terms; the 3 products of
  *                    order <= 1 on tensor cores.
  *   TC_MATH_BF16X6   FP32 inputs split into 3 BF16 terms; the 6 products of
- *                    order <= 2 on tensor cores (FP32-class accuracy). */
+ *                    order <= 2 on tensor cores (FP32-class accuracy).
+ *   TC_MATH_FP8      FP32 inputs rounded to FP8-E4M3 with one power-of-two
+ *                    scale per operand row and block of 128 consecutive
+ *                    contracted elements (contracted indices enumerated in
+ *                    ascending order of their strides in A, the first one
+ *                    fastest; a row is one value of the operand's free
+ *                    indices); the scale 2^e of a block is the smallest with
+ *                    max |x| / 2^e <= 448, e >= -126.  Products on tensor
+ *                    cores, each block summed in FP32 and scaled, blocks
+ *                    added in FP32.  Class 3 contractions only, mapping AUTO,
+ *                    RECIPE or FUSED_GEMM (one GEMM).  The paper has no
+ *                    reduced-precision form; this one trades accuracy (about
+ *                    2^-5 relative per product) for tensor-core throughput. */
 typedef enum {
   TC_MATH_FP64 = 0,
   TC_MATH_FP32 = 1,
   TC_MATH_BF16 = 2,
   TC_MATH_BF16X3 = 3,
-  TC_MATH_BF16X6 = 4
+  TC_MATH_BF16X6 = 4,
+  TC_MATH_FP8 = 5
 } tc_math;
 
 /* How the contraction is mapped onto kernels.
@@ -123,7 +136,8 @@ typedef struct {
   uint32_t slice_a;      /* recipe slicing vector s(A) */
   uint32_t slice_b;      /* recipe slicing vector s(B) */
   int32_t mapping;       /* tc_mapping in use (never AUTO or RECIPE) */
-  int32_t kernel;        /* kernel family: 1 GEMM-SIMT, 2 GEMM-tcgen05, 3 GEMV, 4 DOT */
+  int32_t kernel;        /* kernel family: 1 GEMM-SIMT, 2 GEMM-tcgen05, 3 GEMV, 4 DOT,
+                            5 GEMM-tcgen05 FP8 (pack pass + GEMM) */
   int32_t tile;          /* tile configuration index of that kernel */
   int32_t swapped;       /* 1 when the kernel's first operand is B */
   int64_t M, N, K, batch;   /* GEMM view after mode merging */
@@ -149,8 +163,10 @@ tc_status tc_plan_destroy(tc_plan_t plan);
  * legacy default stream).  A, B, C are device pointers to elements of the
  * plan's dtype laid out as described at tc_plan time; C is read only when
  * beta != 0.  `workspace` is device memory of at least
- * tc_plan_info.workspace bytes (may be NULL when that is 0).  Allocates
- * nothing; may be captured in a CUDA graph. */
+ * tc_plan_info.workspace bytes (may be NULL when that is 0); with
+ * TC_MATH_FP8 it must be 16-byte aligned (else TC_ERR_INVALID_ARG) and holds
+ * the packed E4M3 operands and their scales.  Allocates nothing; may be
+ * captured in a CUDA graph. */
 tc_status tc_contract(tc_plan_t plan, double alpha, const void* A, const void* B, double beta,
                       void* C, void* workspace, size_t workspace_bytes, void* stream);
 

@@ -20,7 +20,9 @@ goal of running the bulk of the multiply on BF16/FP8 tensor cores:
 * FP8-E4M3 (1 sign, 4 exponent bits with bias 7, 3 significand bits, no
   infinities, largest finite 448): round to nearest, ties to even code,
   saturating to +-448.  Block scales are powers of two 2^e, e the smallest
-  integer with amax / 2^e <= 448.
+  integer with amax / 2^e <= 448, but not below -126 (so that 2^e and 2^-e
+  are normal FP32 numbers; blocks whose largest value is below about 2^-135
+  then round to zero).
 """
 from __future__ import annotations
 
@@ -127,14 +129,17 @@ def e4m3_rne(x) -> np.ndarray:
     return np.copysign(q, x)
 
 
+E_MIN = -126   # scales stay normal FP32 numbers (2^-126 .. 2^120)
+
+
 def pow2_scale_exponent(amax) -> np.ndarray:
-    """Smallest integer e with amax / 2^e <= 448 (e = -127 for amax == 0)."""
+    """Smallest integer e >= -126 with amax / 2^e <= 448 (-126 for amax == 0)."""
     amax = np.asarray(amax, dtype=np.float64)
     e = np.ceil(np.log2(np.where(amax > 0, amax, 1.0) / E4M3_MAX)).astype(np.int64)
     # correct possible off-by-one of log2 at exact powers of two
     e = np.where(amax / np.exp2(e - 1) <= E4M3_MAX, e - 1, e)
     e = np.where(amax / np.exp2(e) > E4M3_MAX, e + 1, e)
-    return np.where(amax > 0, e, -127)
+    return np.maximum(np.where(amax > 0, e, E_MIN), E_MIN)
 
 
 def quantize_rows_e4m3(mat: np.ndarray, block: int = 128):
@@ -155,6 +160,16 @@ def quantize_rows_e4m3(mat: np.ndarray, block: int = 128):
 
 # ------------------------------------------------ FP8 form of a contraction
 
+def k_order(p):
+    """Contracted labels in the order that defines the FP8 form's K blocks:
+    ascending stride in A, ties kept in A's label order."""
+    A, B = p.A, p.B
+    con = [l for l in A.labels if l in B.labels]
+    sa = dict(zip(A.labels, A.strides))
+    pos = {l: k for k, l in enumerate(A.labels)}
+    return sorted(con, key=lambda l: (sa[l], pos[l]))
+
+
 def gemm_view(p):
     """Dense matrices of the contraction's GEMM view: A_mat [M, K], B_mat [K, N]
     with rows m enumerated column-major over A's free labels (A's order), rows
@@ -162,12 +177,9 @@ def gemm_view(p):
     labels sorted by ascending stride in A (ties: position in A).  Returns
     (A_mat, B_mat, m_labels, n_labels, k_labels)."""
     A, B = p.A, p.B
-    con = [l for l in A.labels if l in B.labels]
     fa = [l for l in A.labels if l not in B.labels]
     fb = [l for l in B.labels if l not in A.labels]
-    sa = dict(zip(A.labels, A.strides))
-    pos = {l: k for k, l in enumerate(A.labels)}
-    kl = sorted(con, key=lambda l: (sa[l], pos[l]))
+    kl = k_order(p)
     ext = dict(zip(A.labels, A.extents))
     ext.update(zip(B.labels, B.extents))
 

@@ -1,0 +1,494 @@
+// k_fp8.cu -- the FP8-E4M3 form of a Class 3 contraction on the tensor cores
+// (sm_103a, tcgen05 kind::f8f6f4), with one power-of-two scale per operand
+// row and block of 128 consecutive K.
+//
+// The GEMM view is that of the fused mapping (M = free indices of the first
+// operand, N = those of the second, K = the contracted indices in ascending
+// order of their strides in A).  Row m of the first operand is cut into
+// blocks k in [128 j, 128 j + 128); its block j is stored as E4M3 codes of
+// x / 2^e with e = e_A(m, j) the smallest integer for which the block's
+// largest |x| / 2^e <= 448 (never below -126); the same for the columns of
+// the second operand.  Then
+//   C[m, n] = alpha * sum_j 2^(e_A(m, j) + e_B(n, j)) * sum_{k in block j} qa qb
+//           + beta * C[m, n].
+//
+// Two kernels:
+//   k_fp8_pack   one CTA per (128-row tile, K block) of each operand: gathers
+//                the FP32 block through the index groups (coalesced along the
+//                operand's contiguous index), finds each row's exponent,
+//                rounds to E4M3 and writes the 16 KB block in the tensor
+//                cores' canonical K-major layout (8-row x 16-byte core
+//                matrices: byte (k / 16) * 2048 + row * 16 + k % 16), plus the
+//                scale 2^e of every (row, block) as FP32.  The operand is read
+//                from HBM once; the GEMM never touches the FP32 data.
+//   k_gemm_fp8   persistent, one CTA per SM over 128 x 128 output tiles.
+//                warp 0   one thread moves each (tile, block) pair of packed
+//                         blocks into a 6-stage shared-memory ring with two
+//                         bulk copies (cp.async.bulk, mbarrier transaction
+//                         count);
+//                warp 1   tensor-memory allocation; one thread issues the four
+//                         K = 32 MMAs of each block into a fresh accumulator of
+//                         a 4-deep ring in tensor memory (4 x 128 columns);
+//                warps 2-9  epilogue: two warps per lane quadrant, 64 columns
+//                         each; for every block, read the accumulator, release
+//                         it, and add it times 2^(e_A + e_B) into FP32
+//                         registers; finish with alpha, beta and a strided store.
+// The products of E4M3 values are exact in FP32; each block sum is an FP32
+// tensor-core accumulation of 128 products, and the block sums are added with
+// one FP32 fused multiply-add each.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "groups.cuh"
+#include "sm100.cuh"
+#include "tc_internal.h"
+
+namespace tc {
+
+namespace fp8 {
+
+constexpr int TILE = 128;                 // rows of a tile (M and N)
+constexpr int KB = 128;                   // K block: one scale, one pipeline stage
+constexpr uint32_t CHUNK = TILE * KB;     // bytes of one packed (tile, block)
+constexpr int kPackThreads = 256;
+constexpr int kLd = KB + 1;               // shared-memory row pitch of the pack tile (floats)
+constexpr uint32_t kPackSmem = TILE * kLd * 4 + 2 * TILE * 8 + TILE * 4;
+
+constexpr int S = 6;                      // stages of the operand ring
+constexpr int NACC = 4;                   // accumulators in tensor memory
+constexpr int kEpiThreads = 256;
+constexpr int kThreads = 64 + kEpiThreads;
+constexpr uint32_t kTmemCols = 512;
+constexpr uint64_t kTimeoutNs = 2000000000ull;
+constexpr uint32_t OFF_COLC = S * 2 * CHUNK;                    // int64 colC[2][128]
+constexpr uint32_t OFF_BAR = OFF_COLC + 2 * TILE * 8;
+constexpr uint32_t NBAR = 2 * S + 2 * NACC + 1;
+constexpr uint32_t OFF_MISC = OFF_BAR + NBAR * 8;
+constexpr uint32_t kGemmSmem = OFF_MISC + 16 + 1024;            // + alignment slack
+
+struct PackArgs {
+  Group gr[2];          // rows of operand o (the M and N groups); strides in slot o
+  Group gk;             // K group; operand o's strides in slot o
+  const float* in[2];
+  uint8_t* q[2];        // packed blocks [tile][block][CHUNK]
+  float* scale[2];      // 2^e, [block][tiles * 128]
+  int64_t rows[2];
+  int64_t K;
+  int64_t nblocks0;     // CTAs of operand 0 (tiles[0] * nkb)
+  int32_t tiles[2];
+  int32_t nkb;
+  int32_t rows_fast[2]; // operand contiguous along its rows: load row-fastest
+};
+
+__global__ void __launch_bounds__(kPackThreads) k_fp8_pack(const __grid_constant__ PackArgs P) {
+  extern __shared__ float4 pack_smem[];
+  float* tile = reinterpret_cast<float*>(pack_smem);
+  int64_t* roff = reinterpret_cast<int64_t*>(tile + TILE * kLd);
+  int64_t* koff = roff + TILE;
+  float* qmul = reinterpret_cast<float*>(koff + KB);
+
+  int64_t bid = blockIdx.x;
+  const int o = bid < P.nblocks0 ? 0 : 1;
+  if (o) bid -= P.nblocks0;
+  const int t = (int)(bid / P.nkb), kb = (int)(bid % P.nkb);
+  const int tid = threadIdx.x;
+  if (tid < TILE) {
+    const int64_t r = (int64_t)t * TILE + tid;
+    roff[tid] = r < P.rows[o] ? goff(P.gr[o], o, (uint32_t)r) : -1;
+  } else {
+    const int64_t k = (int64_t)kb * KB + (tid - TILE);
+    koff[tid - TILE] = k < P.K ? goff(P.gk, o, (uint32_t)k) : -1;
+  }
+  __syncthreads();
+
+  // gather the FP32 block; consecutive threads take consecutive elements of
+  // the operand's contiguous index
+  const float* __restrict__ X = P.in[o];
+  if (P.rows_fast[o]) {
+    const int r = tid & (TILE - 1);
+    const int64_t ro = roff[r];
+#pragma unroll 16
+    for (int j = 0; j < TILE * KB / kPackThreads; ++j) {
+      const int k = (tid >> 7) + 2 * j;
+      const int64_t ko = koff[k];
+      tile[r * kLd + k] = (ro >= 0 && ko >= 0) ? __ldg(X + ro + ko) : 0.0f;
+    }
+  } else {
+    const int k = tid & (KB - 1);
+    const int64_t ko = koff[k];
+#pragma unroll 16
+    for (int j = 0; j < TILE * KB / kPackThreads; ++j) {
+      const int r = (tid >> 7) + 2 * j;
+      const int64_t ro = roff[r];
+      tile[r * kLd + k] = (ro >= 0 && ko >= 0) ? __ldg(X + ro + ko) : 0.0f;
+    }
+  }
+  __syncthreads();
+
+  // exponent of each row: two threads per row
+  {
+    const int r = tid >> 1, h = tid & 1;
+    float m = 0.0f;
+#pragma unroll 8
+    for (int j = 0; j < KB / 2; ++j) m = fmaxf(m, fabsf(tile[r * kLd + h * (KB / 2) + j]));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+    if (h == 0) {
+      // m = f * 2^E with f in [1, 2): m <= 448 * 2^e  <=>  e >= E - 8 (f <= 1.75)
+      // or e >= E - 7 (f > 1.75); zero and FP32-subnormal maxima give -126.
+      const uint32_t b = __float_as_uint(m);
+      const int be = (int)(b >> 23);
+      int e = be == 0 ? -126 : be - 135 + ((b & 0x7FFFFFu) > 0x600000u ? 1 : 0);
+      e = max(e, -126);
+      qmul[r] = __uint_as_float((uint32_t)(127 - e) << 23);                 // 2^-e
+      P.scale[o][(int64_t)kb * P.tiles[o] * TILE + (int64_t)t * TILE + r] =
+          __uint_as_float((uint32_t)(127 + e) << 23);                        // 2^e
+    }
+  }
+  __syncthreads();
+
+  // round to E4M3 and store: unit u = (k / 16) * 128 + row is the 16-byte row
+  // of a core matrix, at byte u * 16 of the block
+  uint8_t* __restrict__ Q = P.q[o] + ((int64_t)t * P.nkb + kb) * CHUNK;
+#pragma unroll
+  for (int j = 0; j < (int)(CHUNK / 16) / kPackThreads; ++j) {
+    const int u = tid + j * kPackThreads;
+    const int kc = u >> 7, r = u & (TILE - 1);
+    const float* src = tile + r * kLd + kc * 16;
+    const float mul = qmul[r];
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t lo = pack_e4m3x2(src[4 * i] * mul, src[4 * i + 1] * mul);
+      const uint32_t hi = pack_e4m3x2(src[4 * i + 2] * mul, src[4 * i + 3] * mul);
+      w[i] = lo | (hi << 16);
+    }
+    *reinterpret_cast<uint4*>(Q + (size_t)u * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+struct GemmFp8 {
+  Group gm, gn;          // C offsets in slot 2
+  const uint8_t* qa;
+  const uint8_t* qb;
+  const float* sa;       // [block][tiles_m * 128]
+  const float* sb;       // [block][tiles_n * 128]
+  float* C;
+  int64_t M, N, ntiles;
+  float alpha, beta;
+  int32_t tiles_m, tiles_n, nkb, raster;
+};
+
+__device__ __forceinline__ void tile_coords(const GemmFp8& P, int64_t w, int& tm, int& tn) {
+  if (P.raster) {
+    tn = (int)(w % P.tiles_n);
+    tm = (int)(w / P.tiles_n);
+  } else {
+    tm = (int)(w % P.tiles_m);
+    tn = (int)(w / P.tiles_m);
+  }
+}
+
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  bool ok = (*abort == 0) && mbar_wait(bar, parity, abort, kTimeoutNs);
+  return __all_sync(0xffffffffu, ok);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_gemm_fp8(const __grid_constant__ GemmFp8 P) {
+  extern __shared__ uint8_t fp8_smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(fp8_smem_raw) + 1023) & ~(uintptr_t)1023);
+  int64_t* colC = reinterpret_cast<int64_t*>(smem + OFF_COLC);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OFF_BAR);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + S;
+  uint64_t* accf = bars + 2 * S;
+  uint64_t* acce = bars + 2 * S + NACC;
+  uint64_t* done = bars + 2 * S + 2 * NACC;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + OFF_MISC);
+  volatile int* abort = reinterpret_cast<volatile int*>(smem + OFF_MISC + 4);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int i = 0; i < NACC; ++i) {
+      mbar_init(&accf[i], 1);
+      mbar_init(&acce[i], kEpiThreads);
+    }
+    mbar_init(done, 1);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t sbase = smem_u32(smem);
+  const int nkb = P.nkb;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------------------ producer
+      uint32_t g = 0;
+      bool ok = true;
+      for (int64_t w = blockIdx.x; ok && w < P.ntiles; w += gridDim.x) {
+        int tm, tn;
+        tile_coords(P, w, tm, tn);
+        const uint8_t* a = P.qa + (size_t)tm * nkb * CHUNK;
+        const uint8_t* b = P.qb + (size_t)tn * nkb * CHUNK;
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int s = (int)(g % S);
+          if (g >= (uint32_t)S && !mbar_wait(&empty[s], ((g / S) - 1) & 1, abort, kTimeoutNs)) {
+            ok = false;
+            break;
+          }
+          const uint32_t dst = sbase + (uint32_t)s * 2 * CHUNK;
+          mbar_arrive_expect_tx(&full[s], 2 * CHUNK);
+          bulk_g2s(dst, a + (size_t)kb * CHUNK, CHUNK, &full[s]);
+          bulk_g2s(dst + CHUNK, b + (size_t)kb * CHUNK, CHUNK, &full[s]);
+        }
+      }
+      // the copies still in flight (at most the last S blocks) land before exit
+      volatile int never = 0;
+      for (uint32_t i = g > (uint32_t)S ? g - S : 0; i < g; ++i)
+        mbar_wait(&full[i % S], (i / S) & 1, &never, kTimeoutNs);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ----------------------------------------------------------- MMA issue
+      constexpr uint32_t idesc = idesc_e4m3(TILE, TILE);
+      constexpr uint32_t LBO = (TILE / 8) * 128;   // next 16-byte K chunk
+      uint32_t g = 0;
+      bool ok = true;
+      for (int64_t w = blockIdx.x; ok && w < P.ntiles; w += gridDim.x) {
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const uint32_t buf = g % NACC;
+          if (g >= (uint32_t)NACC &&
+              !mbar_wait(&acce[buf], ((g / NACC) - 1) & 1, abort, kTimeoutNs)) {
+            ok = false;
+            break;
+          }
+          const int s = (int)(g % S);
+          if (!mbar_wait(&full[s], (g / S) & 1, abort, kTimeoutNs)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = sbase + (uint32_t)s * 2 * CHUNK, sb = sa + CHUNK;
+          const uint32_t d = tmem + buf * TILE;
+#pragma unroll
+          for (int kk = 0; kk < KB / 32; ++kk)
+            mma_e4m3(d, smem_desc(sa + kk * 2 * LBO, LBO, 128),
+                     smem_desc(sb + kk * 2 * LBO, LBO, 128), idesc, kk > 0 ? 1u : 0u);
+          mma_commit(&empty[s]);
+          mma_commit(&accf[buf]);
+        }
+      }
+      mma_commit(done);  // arrives once every MMA issued above has completed
+      volatile int never = 0;
+      mbar_wait(done, 0, &never, kTimeoutNs);
+    }
+  } else {
+    // ------------------------------------------------------------- epilogue
+    const int ew = warp - 2;
+    const int q = warp & 3;                 // tensor-memory lane quadrant of this warp
+    const int h = ew >> 2;                  // column half
+    const int row = q * 32 + lane;
+    const int etid = ew * 32 + lane;
+    const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)h * 64;
+    const size_t sta = (size_t)P.tiles_m * TILE, stb = (size_t)P.tiles_n * TILE;
+    uint32_t g = 0;
+    int64_t it = 0;
+    bool live = true;  // after a wait gave up, tiles are walked without work so
+                       // that every epilogue warp still meets each named barrier
+    for (int64_t w = blockIdx.x; w < P.ntiles; w += gridDim.x, ++it) {
+      int tm, tn;
+      tile_coords(P, w, tm, tn);
+      int64_t* cc = colC + (it & 1) * TILE;
+      if (etid < TILE) {
+        const int64_t n = (int64_t)tn * TILE + etid;
+        cc[etid] = n < P.N ? goff(P.gn, 2, (uint32_t)n) : -1;
+      }
+      named_bar_sync(1, kEpiThreads);
+      if (!live) continue;
+      const int64_t m = (int64_t)tm * TILE + row;
+      const int64_t rc = m < P.M ? goff(P.gm, 2, (uint32_t)m) : -1;
+      const float* sap = P.sa + (size_t)tm * TILE + row;
+      const float* sbp = P.sb + (size_t)tn * TILE + h * 64;
+      float acc[64];
+#pragma unroll
+      for (int i = 0; i < 64; ++i) acc[i] = 0.0f;
+      float sav = __ldg(sap);
+      float4 sbv[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) sbv[i] = __ldg(reinterpret_cast<const float4*>(sbp) + i);
+      for (int kb = 0; kb < nkb; ++kb, ++g) {
+        const uint32_t buf = g % NACC;
+        if (!warp_wait(&accf[buf], (g / NACC) & 1, abort)) {
+          live = false;
+          break;
+        }
+        tc_fence_after();
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          uint32_t v[16];
+          tmem_ld16(tl + buf * TILE + c * 16, v);
+          tmem_wait_ld();
+#pragma unroll
+          for (int i = 0; i < 16; i += 4) {
+            const float4 sbq = sbv[(c * 16 + i) / 4];
+            acc[c * 16 + i] = fmaf(__uint_as_float(v[i]) * sav, sbq.x, acc[c * 16 + i]);
+            acc[c * 16 + i + 1] = fmaf(__uint_as_float(v[i + 1]) * sav, sbq.y, acc[c * 16 + i + 1]);
+            acc[c * 16 + i + 2] = fmaf(__uint_as_float(v[i + 2]) * sav, sbq.z, acc[c * 16 + i + 2]);
+            acc[c * 16 + i + 3] = fmaf(__uint_as_float(v[i + 3]) * sav, sbq.w, acc[c * 16 + i + 3]);
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&acce[buf]);
+        if (kb + 1 < nkb) {  // scales of the next block, loaded before its wait
+          sav = __ldg(sap + (size_t)(kb + 1) * sta);
+          const float4* sbn = reinterpret_cast<const float4*>(sbp + (size_t)(kb + 1) * stb);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) sbv[i] = __ldg(sbn + i);
+        }
+      }
+      if (!live || rc < 0) continue;
+      float* Cr = P.C + rc;
+#pragma unroll
+      for (int i = 0; i < 64; ++i) {
+        const int64_t ci = cc[h * 64 + i];
+        if (ci < 0) continue;
+        float x = P.alpha * acc[i];
+        if (P.beta != 0.0f) x = fmaf(P.beta, Cr[ci], x);
+        Cr[ci] = x;
+      }
+    }
+  }
+
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      n = 0;
+  }
+  return n;
+}
+
+// Shared memory of both kernels, set once per process (first call).
+int set_smem() {
+  static int bytes = 0;
+  if (bytes == 0) {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess)
+      return -1;
+    if (optin < (int)kGemmSmem) return -2;
+    if (cudaFuncSetAttribute(k_fp8_pack, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kPackSmem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_gemm_fp8, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kGemmSmem) != cudaSuccess)
+      return -1;
+    bytes = (int)kGemmSmem;
+  }
+  return bytes;
+}
+
+}  // namespace fp8
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+Fp8Layout fp8_layout(const GemmArgs& a) {
+  Fp8Layout L;
+  std::memset(&L, 0, sizeof(L));
+  L.tiles_m = (a.M + fp8::TILE - 1) / fp8::TILE;
+  L.tiles_n = (a.N + fp8::TILE - 1) / fp8::TILE;
+  L.nkb = (a.K + fp8::KB - 1) / fp8::KB;
+  L.off_qa = 0;
+  L.off_qb = align256((size_t)L.tiles_m * L.nkb * fp8::CHUNK);
+  L.off_sa = L.off_qb + align256((size_t)L.tiles_n * L.nkb * fp8::CHUNK);
+  L.off_sb = L.off_sa + align256((size_t)L.nkb * L.tiles_m * fp8::TILE * 4);
+  L.bytes = L.off_sb + align256((size_t)L.nkb * L.tiles_n * fp8::TILE * 4);
+  return L;
+}
+
+tc_status launch_gemm_fp8(const GemmArgs& a, void* ws, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Fp8Layout L = fp8_layout(a);
+  if (L.tiles_m == 0 || L.tiles_n == 0 || L.nkb == 0) return TC_OK;
+  const int sm = fp8::set_smem();
+  if (sm == -2) return TC_ERR_UNSUPPORTED;
+  const int sms = fp8::num_sms();
+  if (sm < 0 || sms <= 0) return TC_ERR_CUDA;
+  uint8_t* w = static_cast<uint8_t*>(ws);
+
+  fp8::PackArgs pk;
+  std::memset(&pk, 0, sizeof(pk));
+  pk.gr[0] = a.gm;
+  pk.gr[1] = a.gn;
+  pk.gk = a.gk;
+  pk.in[0] = static_cast<const float*>(a.A);
+  pk.in[1] = static_cast<const float*>(a.B);
+  pk.q[0] = w + L.off_qa;
+  pk.q[1] = w + L.off_qb;
+  pk.scale[0] = reinterpret_cast<float*>(w + L.off_sa);
+  pk.scale[1] = reinterpret_cast<float*>(w + L.off_sb);
+  pk.rows[0] = a.M;
+  pk.rows[1] = a.N;
+  pk.K = a.K;
+  pk.tiles[0] = (int32_t)L.tiles_m;
+  pk.tiles[1] = (int32_t)L.tiles_n;
+  pk.nkb = (int32_t)L.nkb;
+  pk.nblocks0 = L.tiles_m * L.nkb;
+  pk.rows_fast[0] = a.a_contig == CONTIG_MN;
+  pk.rows_fast[1] = a.b_contig == CONTIG_MN;
+  const int64_t nblocks = (L.tiles_m + L.tiles_n) * L.nkb;
+  if (nblocks > 0x7fffffffll) return TC_ERR_UNSUPPORTED;
+  fp8::k_fp8_pack<<<(unsigned)nblocks, fp8::kPackThreads, fp8::kPackSmem, s>>>(pk);
+  if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;
+
+  fp8::GemmFp8 g;
+  std::memset(&g, 0, sizeof(g));
+  g.gm = a.gm;
+  g.gn = a.gn;
+  g.qa = pk.q[0];
+  g.qb = pk.q[1];
+  g.sa = pk.scale[0];
+  g.sb = pk.scale[1];
+  g.C = static_cast<float*>(a.C);
+  g.M = a.M;
+  g.N = a.N;
+  g.ntiles = L.tiles_m * L.tiles_n;
+  g.alpha = (float)a.alpha;
+  g.beta = (float)a.beta;
+  g.tiles_m = (int32_t)L.tiles_m;
+  g.tiles_n = (int32_t)L.tiles_n;
+  g.nkb = (int32_t)L.nkb;
+  g.raster = a.raster;
+  const int grid = (int)std::min<int64_t>(g.ntiles, sms);
+  fp8::k_gemm_fp8<<<grid, fp8::kThreads, sm, s>>>(g);
+  return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+}
+
+tc_status tc_fp8_read_status(int* h, void* stream) {
+  return read_clear_status(h, static_cast<cudaStream_t>(stream)) == cudaSuccess ? TC_OK
+                                                                                : TC_ERR_CUDA;
+}
+
+}  // namespace tc

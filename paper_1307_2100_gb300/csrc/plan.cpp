@@ -280,7 +280,7 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   if (!out) return TC_ERR_INVALID_ARG;
   *out = nullptr;
   if (dtype != TC_F64 && dtype != TC_F32) return TC_ERR_INVALID_ARG;
-  if (math < TC_MATH_FP64 || math > TC_MATH_BF16X6) return TC_ERR_INVALID_ARG;
+  if (math < TC_MATH_FP64 || math > TC_MATH_FP8) return TC_ERR_INVALID_ARG;
   if (mapping < TC_MAP_AUTO || mapping > TC_MAP_DOT) return TC_ERR_INVALID_ARG;
   if ((math == TC_MATH_FP64) != (dtype == TC_F64)) return TC_ERR_UNSUPPORTED;
 
@@ -418,6 +418,12 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   if (map == TC_MAP_RECIPE)
     map = (an.cls == 1) ? TC_MAP_DOT : (an.cls == 2) ? TC_MAP_GEMV : TC_MAP_FUSED_GEMM;
   const bool is3 = an.cls == 31 || an.cls == 32;
+  const bool fp8 = math == TC_MATH_FP8;
+  if (fp8 && (!is3 || map != TC_MAP_FUSED_GEMM)) {
+    // the FP8 form is one block-scaled GEMM: Class 3, fused mapping only
+    delete P;
+    return TC_ERR_UNSUPPORTED;
+  }
   if ((map == TC_MAP_SLICE_GEMM || map == TC_MAP_COPY_GEMM) && !is3) {
     delete P;
     return TC_ERR_UNSUPPORTED;
@@ -425,7 +431,8 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   const bool gemm_family =
       map == TC_MAP_SLICE_GEMM || map == TC_MAP_FUSED_GEMM || map == TC_MAP_COPY_GEMM;
   const bool tensor_core = math == TC_MATH_BF16 || math == TC_MATH_BF16X3 || math == TC_MATH_BF16X6;
-  int32_t kernel = gemm_family ? (tensor_core ? K_GEMM_TC : K_GEMM_SIMT)
+  int32_t kernel = fp8 ? K_GEMM_FP8
+                 : gemm_family ? (tensor_core ? K_GEMM_TC : K_GEMM_SIMT)
                                : (map == TC_MAP_GEMV ? K_GEMV : K_DOT);
 
   // ---- operand roles: the kernel's first operand X provides M
@@ -464,7 +471,8 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   } else {
     lm = sorted_by(fx, X);
     ln = sorted_by(fy, Y);
-    lk = sorted_by(an.con, X);
+    // the FP8 form's scale blocks follow A's strides, whichever operand is first
+    lk = sorted_by(an.con, fp8 ? A : X);
   }
 
   // COPY+GEMM: permute the copied operand (the one whose stride-1 index the
@@ -543,6 +551,7 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   // ---- tiles and workspace
   int ntiles = kernel == K_GEMM_SIMT ? num_tiles_simt(dtype)
                : kernel == K_GEMM_TC ? num_tiles_tc()
+               : kernel == K_GEMM_FP8 ? 1
                : kernel == K_GEMV    ? num_tiles_gemv()
                                      : 1;
   if (tile >= ntiles) {
@@ -559,8 +568,8 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
     }
   }
   P->tile = tile;
-  if (kernel == K_GEMM_TC) {
-    g.chunk_kb = tc_chunk_kb(math, tile);
+  if (kernel == K_GEMM_TC || kernel == K_GEMM_FP8) {
+    if (kernel == K_GEMM_TC) g.chunk_kb = tc_chunk_kb(math, tile);
     // n-tiles fastest when there are few of them: the CTAs that share a panel
     // of the first operand then run at the same time and read it once from HBM
     g.raster = ((N + 127) / 128) <= 16 ? 1 : 0;
@@ -569,6 +578,7 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   if (kernel == K_DOT && M * N * Bt == 1) ws += (size_t)dot_partials(g, tile) * 8;
   ws = (ws + 255) & ~(size_t)255;
   if (P->copy_which) ws += ((size_t)P->copy_elems * es + 255) & ~(size_t)255;
+  if (kernel == K_GEMM_FP8) ws += fp8_layout(g).bytes;
   P->workspace = ws;
 
   info.mapping = map;

@@ -20,7 +20,14 @@ struct Group {
   int64_t st[3][kGroupMax];
 };
 
-enum Kernel : int32_t { K_NONE = 0, K_GEMM_SIMT = 1, K_GEMM_TC = 2, K_GEMV = 3, K_DOT = 4 };
+enum Kernel : int32_t {
+  K_NONE = 0,
+  K_GEMM_SIMT = 1,
+  K_GEMM_TC = 2,
+  K_GEMV = 3,
+  K_DOT = 4,
+  K_GEMM_FP8 = 5
+};
 
 // Operand contiguity (how the loader can coalesce):
 //   0 = generic gather, 1 = contiguous along the M/N group's first label,
@@ -107,6 +114,16 @@ uint64_t tc_gemm_tiles(const GemmArgs& a);  // 128x128 output tiles of a GEMM vi
 // Enqueue a read-and-clear of the tensor-core kernels' timeout flag into *h.
 tc_status tc_gemm_read_status(int* h, void* stream);
 int tc_chunk_kb(int math, int tile);
+
+// FP8 form: workspace layout of the packed operands (byte offsets).
+struct Fp8Layout {
+  int64_t tiles_m, tiles_n, nkb;
+  size_t off_qa, off_qb, off_sa, off_sb, bytes;
+};
+Fp8Layout fp8_layout(const GemmArgs& a);
+// Pack both operands into `ws` (16-byte aligned) and run the FP8 GEMM.
+tc_status launch_gemm_fp8(const GemmArgs& a, void* ws, void* stream);
+tc_status tc_fp8_read_status(int* h, void* stream);
 int num_tiles_simt(tc_dtype dt);
 int num_tiles_gemv();
 

@@ -20,11 +20,11 @@ STATUS = {0: "TC_OK", 1: "TC_ERR_INVALID_ARG", 2: "TC_ERR_LABEL", 3: "TC_ERR_EXT
           4: "TC_ERR_STRIDE", 5: "TC_ERR_UNSUPPORTED", 6: "TC_ERR_WORKSPACE", 7: "TC_ERR_CUDA",
           8: "TC_ERR_TIMEOUT", 9: "TC_ERR_NO_SELECTOR"}
 TC_F64, TC_F32 = 0, 1
-MATH = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16x3": 3, "bf16x6": 4}
+MATH = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16x3": 3, "bf16x6": 4, "fp8": 5}
 MAPPING = {"auto": 0, "recipe": 1, "slice_gemm": 2, "fused_gemm": 3, "copy_gemm": 4, "gemv": 5,
            "dot": 6}
 MAPPING_NAME = {v: k for k, v in MAPPING.items()}
-KERNEL_NAME = {0: "none", 1: "gemm_simt", 2: "gemm_tc", 3: "gemv", 4: "dot"}
+KERNEL_NAME = {0: "none", 1: "gemm_simt", 2: "gemm_tc", 3: "gemv", 4: "dot", 5: "gemm_fp8"}
 MAX_ORDER = 12
 N_FEATURES = 23
 

@@ -174,3 +174,53 @@ def within(got, ref, mag, C, c):
     idx = addressed_index(C) if C.numel else np.zeros(0, dtype=np.int64)
     d = np.linalg.norm((np.asarray(got)[idx] - np.asarray(ref)[idx]).ravel())
     return d <= c * np.linalg.norm(np.asarray(mag)[idx].ravel()) + 1e-300, d
+
+
+def _k_row(t, fix, kl, ext):
+    """Operand t's values along the contracted labels kl (first fastest) at
+    fixed free-label values."""
+    st = dict(zip(t.labels, t.strides))
+    off = sum(fix[l] * st[l] for l in t.labels if l in fix)
+    if not kl:
+        return np.asarray([t.data[off]], np.float64)
+    grids = np.meshgrid(*[np.arange(ext[l], dtype=np.int64) * st[l] for l in kl], indexing="ij")
+    idx = (off + sum(grids)).reshape(-1, order="F")
+    return np.asarray(t.data[idx], np.float64)
+
+
+def sample_outputs_fp8(p, samples, block=128):
+    """Oracle values of selected outputs of the FP8 form: the sample's row of A
+    and column of B along the K order are quantised per block
+    (oracle.precision) and their dequantised products summed in FP64."""
+    from oracle import precision as op
+    kl = op.k_order(p)
+    ext = dict(zip(p.A.labels, p.A.extents))
+    ext.update(zip(p.B.labels, p.B.extents))
+    vals = []
+    for cidx in samples:
+        fix = dict(zip(p.C.labels, cidx))
+        a = _k_row(p.A, fix, kl, ext)
+        b = _k_row(p.B, fix, kl, ext)
+        qa, _ = op.quantize_rows_e4m3(a[None, :], block)
+        qb, _ = op.quantize_rows_e4m3(b[None, :], block)
+        v = p.alpha * float(qa[0] @ qb[0])
+        if p.beta != 0:
+            v += p.beta * float(p.C.data[sum(i * s for i, s in zip(cidx, p.C.strides))])
+        vals.append(v)
+    return np.array(vals)
+
+
+def fp8_bound(p, block=128):
+    """Accumulation bound of the FP8 kernel against the FP8 oracle, as a
+    multiple of sum |qa||qb| (<= 1.13 sum |a||b|, E4M3 rounding being <= 2^-4
+    relative): each block of `block` exact products is summed by the tensor
+    cores in FP32 (at most one unit of the running sum, 2^-23, per 16-product
+    step) and the scaled block sums are added with one rounding (2^-24) each,
+    plus the final alpha/beta rounding."""
+    K = 1
+    for l, e in zip(p.A.labels, p.A.extents):
+        if l in p.B.labels:
+            K *= int(e)
+    nblk = -(-K // block)
+    u = 2.0 ** -23
+    return 1.13 * ((min(K, block) / 16 + 1) * u + (nblk + 2) * u / 2)

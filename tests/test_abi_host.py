@@ -167,3 +167,43 @@ def test_contract_host_checks_before_any_launch():
 def test_status_strings():
     assert tc.tc_status_string(0) == "ok"
     assert "timed out" in tc.tc_status_string(8)
+
+
+def test_fp8_plans():
+    p = ts.fused_permute_48(n=40)                       # Class 3.1: M=N=K=1600
+    info = plan_info(p, tc.MATH["fp8"], dtype=tc.TC_F32)
+    assert tc.KERNEL_NAME[info.kernel] == "gemm_fp8"
+    assert tc.MAPPING_NAME[info.mapping] == "fused_gemm"
+    tm, tn, nkb = -(-info.M // 128), -(-info.N // 128), -(-info.K // 128)
+    r = lambda x: -(-x // 256) * 256
+    want = r(tm * nkb * 16384) + r(tn * nkb * 16384) + r(nkb * tm * 512) + r(nkb * tn * 512)
+    assert info.workspace == want
+    f8 = tc.MATH["fp8"]
+    x = (ts.lab("i"), [5], None)
+    A = (ts.lab("ai"), [3, 5], None)
+    # one block-scaled GEMM: Class 3 and the fused mapping only; FP32 storage only
+    assert tc.tc_plan_status(A, x, (ts.lab("a"), [3], None), tc.TC_F32, f8) == 5
+    assert tc.tc_plan_status(x, x, ([], [], None), tc.TC_F32, f8) == 5
+    B = (ts.lab("ib"), [5, 4], None)
+    C = (ts.lab("ab"), [3, 4], None)
+    assert tc.tc_plan_status(A, B, C, tc.TC_F32, f8) == 0
+    assert tc.tc_plan_status(A, B, C, tc.TC_F64, f8) == 5
+    for m in ("slice_gemm", "copy_gemm", "gemv", "dot"):
+        assert tc.tc_plan_status(A, B, C, tc.TC_F32, f8, tc.MAPPING[m]) == 5
+    # a workspace that is not 16-byte aligned is refused before any launch
+    h = tc.tc_plan(A, B, C, tc.TC_F32, f8)
+    try:
+        ws = tc.tc_plan_get_info(h).workspace
+        with pytest.raises(tc.TcError) as e:
+            tc.tc_contract(h, 1.0, 256, 256, 0.0, 256, 4104, ws)
+        assert e.value.status == 1
+    finally:
+        tc.tc_plan_destroy(h)
+
+
+def test_fp8_k_order_follows_a_whichever_operand_is_first():
+    # C's stride-1 index b is B's: the kernel's first operand is B, yet the
+    # contracted indices keep A's stride order (i before j) for the scale blocks
+    p = ts.problem("kord", "aij", "jib", "ba", dict(a=150, i=20, j=30, b=140), 71)
+    info = plan_info(p, tc.MATH["fp8"], dtype=tc.TC_F32)
+    assert info.swapped == 1 and info.K == 600

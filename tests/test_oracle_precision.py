@@ -100,9 +100,14 @@ def test_e4m3_rounding_hand_values():
 
 
 def test_pow2_scale_exponent():
-    for amax in (448.0, 449.0, 1.0, 0.001, 1e5, 896.0):
+    for amax in (448.0, 449.0, 1.0, 0.001, 1e5, 896.0, 2.0 ** -100, 3.4e38):
         e = int(op.pow2_scale_exponent(amax))
         assert amax / 2.0 ** e <= 448.0 < amax / 2.0 ** (e - 1)
+    # the floor: zero and tiny maxima
+    assert int(op.pow2_scale_exponent(0.0)) == -126
+    assert int(op.pow2_scale_exponent(2.0 ** -140)) == -126
+    assert int(op.pow2_scale_exponent(448 * 2.0 ** -126)) == -126
+    assert int(op.pow2_scale_exponent(449 * 2.0 ** -126)) == -125
 
 
 def test_block_quantisation_error():
