@@ -1,5 +1,5 @@
 // k_fp8.cu -- the FP8-E4M3 form of a Class 3 contraction on the tensor cores
-// (sm_103a, tcgen05 kind::f8f6f4), with one power-of-two scale per operand
+// (sm_103a, tcgen05 kind::mxf8f6f4), with one power-of-two scale per operand
 // row and block of 128 consecutive K.
 //
 // The GEMM view is that of the fused mapping (M = free indices of the first
@@ -18,24 +18,35 @@
 //                operand's contiguous index), finds each row's exponent,
 //                rounds to E4M3 and writes the 16 KB block in the tensor
 //                cores' canonical K-major layout (8-row x 16-byte core
-//                matrices: byte (k / 16) * 2048 + row * 16 + k % 16), plus the
-//                scale 2^e of every (row, block) as FP32.  The operand is read
-//                from HBM once; the GEMM never touches the FP32 data.
-//   k_gemm_fp8   persistent, one CTA per SM over 128 x 128 output tiles.
-//                warp 0   one thread moves each (tile, block) pair of packed
-//                         blocks into a 6-stage shared-memory ring with two
-//                         bulk copies (cp.async.bulk, mbarrier transaction
-//                         count);
-//                warp 1   tensor-memory allocation; one thread issues the four
-//                         K = 32 MMAs of each block into a fresh accumulator of
-//                         a 4-deep ring in tensor memory (4 x 128 columns);
-//                warps 2-9  epilogue: two warps per lane quadrant, 64 columns
-//                         each; for every block, read the accumulator, release
-//                         it, and add it times 2^(e_A + e_B) into FP32
-//                         registers; finish with alpha, beta and a strided store.
-// The products of E4M3 values are exact in FP32; each block sum is an FP32
-// tensor-core accumulation of 128 products, and the block sums are added with
-// one FP32 fused multiply-add each.
+//                matrices: byte (k / 16) * 2048 + row * 16 + k % 16), plus each
+//                row's scale as an exponent byte e + 127 (UE8M0).  The operand
+//                is read from HBM once; the GEMM never touches the FP32 data.
+//   k_gemm_fp8   persistent, one CTA per SM over 128 x 128 output tiles, on
+//                the block-scaled MMA (kind::mxf8f6f4): the tensor cores
+//                multiply each K = 32 step by 2^(e_A + e_B) of its rows and
+//                columns and accumulate all of K in FP32 in tensor memory.
+//                warp 0     one thread moves each (tile, block) pair of packed
+//                           blocks into a 6-stage shared-memory ring with two
+//                           bulk copies (cp.async.bulk, mbarrier transaction
+//                           count);
+//                warp 1     tensor-memory allocation; one thread issues the
+//                           four K = 32 MMAs of each block;
+//                warps 2-5  one per lane quadrant: write the scale bytes of
+//                           four consecutive blocks into tensor memory (a ring
+//                           of 4 x 8 columns) ahead of the MMAs;
+//                warps 6-13 epilogue, once per tile: two warps per lane
+//                           quadrant read 64 accumulator columns each (double
+//                           buffered, 2 x 128 columns), apply alpha and beta
+//                           and store through C's strides.
+// Scale bytes in tensor memory (one layout for A and B, in all four lane
+// quadrants): lane 32 q + l, column c of a group, byte j holds the exponent of
+// row (A) or column (B) 32 c + l for the group's block j.  The MMA takes row
+// m's from lane m, column m / 32, and column n's (for the rows of quadrant q)
+// from lane 32 q + n % 32, column n / 32; the instruction descriptor selects
+// the byte.
+// The products of E4M3 values and their power-of-two scaling are exact; the
+// error against the exact sum of the dequantised products is that of the
+// tensor cores' FP32 accumulation over K.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -57,28 +68,37 @@ constexpr int kLd = KB + 1;               // shared-memory row pitch of the pack
 constexpr uint32_t kPackSmem = TILE * kLd * 4 + 2 * TILE * 8 + TILE * 4;
 
 constexpr int S = 6;                      // stages of the operand ring
-constexpr int NACC = 4;                   // accumulators in tensor memory
+constexpr int NACC = 2;                   // accumulators in tensor memory (128 columns each)
+constexpr int NG = 4;                     // groups of scale columns in tensor memory
+constexpr uint32_t COL_SF = NACC * TILE;  // first scale column; 8 per group (A 0-3, B 4-7)
 constexpr int kEpiThreads = 256;
-constexpr int kThreads = 64 + kEpiThreads;
+constexpr int kThreads = 64 + 128 + kEpiThreads;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 constexpr uint32_t OFF_COLC = S * 2 * CHUNK;                    // int64 colC[2][128]
 constexpr uint32_t OFF_BAR = OFF_COLC + 2 * TILE * 8;
-constexpr uint32_t NBAR = 2 * S + 2 * NACC + 1;
+constexpr uint32_t NBAR = 2 * S + 2 * NACC + 2 * NG + 1;
 constexpr uint32_t OFF_MISC = OFF_BAR + NBAR * 8;
 constexpr uint32_t kGemmSmem = OFF_MISC + 16 + 1024;            // + alignment slack
+
+// Scale bytes of one operand: per (tile, group of 4 blocks) 512 bytes laid
+// out as the tensor-memory cells of one lane quadrant: [l][c][j] = row
+// 32 c + l, block 4 g + j.
+__host__ __device__ constexpr int64_t sf_index(int64_t tile, int64_t ngroups, int kb, int r) {
+  return ((tile * ngroups + kb / 4) * 32 + (r & 31)) * 16 + (r >> 5) * 4 + (kb & 3);
+}
 
 struct PackArgs {
   Group gr[2];          // rows of operand o (the M and N groups); strides in slot o
   Group gk;             // K group; operand o's strides in slot o
   const float* in[2];
   uint8_t* q[2];        // packed blocks [tile][block][CHUNK]
-  float* scale[2];      // 2^e, [block][tiles * 128]
+  uint8_t* sf[2];       // scale bytes e + 127, sf_index layout
   int64_t rows[2];
   int64_t K;
   int64_t nblocks0;     // CTAs of operand 0 (tiles[0] * nkb)
   int32_t tiles[2];
-  int32_t nkb;
+  int32_t nkb, ngroups;
   int32_t rows_fast[2]; // operand contiguous along its rows: load row-fastest
 };
 
@@ -104,25 +124,37 @@ __global__ void __launch_bounds__(kPackThreads) k_fp8_pack(const __grid_constant
   __syncthreads();
 
   // gather the FP32 block; consecutive threads take consecutive elements of
-  // the operand's contiguous index
+  // the operand's contiguous index.  Sixteen loads are issued before their
+  // sixteen shared-memory stores, so that each thread has them in flight at once.
   const float* __restrict__ X = P.in[o];
+  constexpr int NJ = TILE * KB / kPackThreads, U = 16;
   if (P.rows_fast[o]) {
-    const int r = tid & (TILE - 1);
+    const int r = tid & (TILE - 1), k0 = tid >> 7;
     const int64_t ro = roff[r];
-#pragma unroll 16
-    for (int j = 0; j < TILE * KB / kPackThreads; ++j) {
-      const int k = (tid >> 7) + 2 * j;
-      const int64_t ko = koff[k];
-      tile[r * kLd + k] = (ro >= 0 && ko >= 0) ? __ldg(X + ro + ko) : 0.0f;
+#pragma unroll
+    for (int j0 = 0; j0 < NJ; j0 += U) {
+      float v[U];
+#pragma unroll
+      for (int j = 0; j < U; ++j) {
+        const int64_t ko = koff[k0 + 2 * (j0 + j)];
+        v[j] = (ro >= 0 && ko >= 0) ? __ldg(X + ro + ko) : 0.0f;
+      }
+#pragma unroll
+      for (int j = 0; j < U; ++j) tile[r * kLd + k0 + 2 * (j0 + j)] = v[j];
     }
   } else {
-    const int k = tid & (KB - 1);
+    const int k = tid & (KB - 1), r0 = tid >> 7;
     const int64_t ko = koff[k];
-#pragma unroll 16
-    for (int j = 0; j < TILE * KB / kPackThreads; ++j) {
-      const int r = (tid >> 7) + 2 * j;
-      const int64_t ro = roff[r];
-      tile[r * kLd + k] = (ro >= 0 && ko >= 0) ? __ldg(X + ro + ko) : 0.0f;
+#pragma unroll
+    for (int j0 = 0; j0 < NJ; j0 += U) {
+      float v[U];
+#pragma unroll
+      for (int j = 0; j < U; ++j) {
+        const int64_t ro = roff[r0 + 2 * (j0 + j)];
+        v[j] = (ro >= 0 && ko >= 0) ? __ldg(X + ro + ko) : 0.0f;
+      }
+#pragma unroll
+      for (int j = 0; j < U; ++j) tile[(r0 + 2 * (j0 + j)) * kLd + k] = v[j];
     }
   }
   __syncthreads();
@@ -142,8 +174,7 @@ __global__ void __launch_bounds__(kPackThreads) k_fp8_pack(const __grid_constant
       int e = be == 0 ? -126 : be - 135 + ((b & 0x7FFFFFu) > 0x600000u ? 1 : 0);
       e = max(e, -126);
       qmul[r] = __uint_as_float((uint32_t)(127 - e) << 23);                 // 2^-e
-      P.scale[o][(int64_t)kb * P.tiles[o] * TILE + (int64_t)t * TILE + r] =
-          __uint_as_float((uint32_t)(127 + e) << 23);                        // 2^e
+      P.sf[o][sf_index(t, P.ngroups, kb, r)] = (uint8_t)(127 + e);
     }
   }
   __syncthreads();
@@ -172,12 +203,12 @@ struct GemmFp8 {
   Group gm, gn;          // C offsets in slot 2
   const uint8_t* qa;
   const uint8_t* qb;
-  const float* sa;       // [block][tiles_m * 128]
-  const float* sb;       // [block][tiles_n * 128]
+  const uint8_t* sfa;    // scale bytes, sf_index layout
+  const uint8_t* sfb;
   float* C;
   int64_t M, N, ntiles;
   float alpha, beta;
-  int32_t tiles_m, tiles_n, nkb, raster;
+  int32_t tiles_m, tiles_n, nkb, ngroups, raster, pad_;
 };
 
 __device__ __forceinline__ void tile_coords(const GemmFp8& P, int64_t w, int& tm, int& tn) {
@@ -204,8 +235,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_fp8(const __grid_constant_
   uint64_t* full = bars;
   uint64_t* empty = bars + S;
   uint64_t* accf = bars + 2 * S;
-  uint64_t* acce = bars + 2 * S + NACC;
-  uint64_t* done = bars + 2 * S + 2 * NACC;
+  uint64_t* acce = accf + NACC;
+  uint64_t* sff = acce + NACC;
+  uint64_t* sfe = sff + NG;
+  uint64_t* done = sfe + NG;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + OFF_MISC);
   volatile int* abort = reinterpret_cast<volatile int*>(smem + OFF_MISC + 4);
 
@@ -219,6 +252,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_fp8(const __grid_constant_
       mbar_init(&accf[i], 1);
       mbar_init(&acce[i], kEpiThreads);
     }
+    for (int i = 0; i < NG; ++i) {
+      mbar_init(&sff[i], 128);
+      mbar_init(&sfe[i], 1);
+    }
     mbar_init(done, 1);
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -229,7 +266,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_fp8(const __grid_constant_
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const uint32_t sbase = smem_u32(smem);
-  const int nkb = P.nkb;
+  const int nkb = P.nkb, ngroups = P.ngroups;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -261,17 +298,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_fp8(const __grid_constant_
   } else if (warp == 1) {
     if (lane == 0) {
       // ----------------------------------------------------------- MMA issue
-      constexpr uint32_t idesc = idesc_e4m3(TILE, TILE);
       constexpr uint32_t LBO = (TILE / 8) * 128;   // next 16-byte K chunk
-      uint32_t g = 0;
+      uint32_t g = 0, G = 0, t = 0;
       bool ok = true;
-      for (int64_t w = blockIdx.x; ok && w < P.ntiles; w += gridDim.x) {
+      for (int64_t w = blockIdx.x; ok && w < P.ntiles; w += gridDim.x, ++t) {
+        const uint32_t buf = t % NACC;
+        if (t >= (uint32_t)NACC &&
+            !mbar_wait(&acce[buf], ((t / NACC) - 1) & 1, abort, kTimeoutNs)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + buf * TILE;
         for (int kb = 0; kb < nkb; ++kb, ++g) {
-          const uint32_t buf = g % NACC;
-          if (g >= (uint32_t)NACC &&
-              !mbar_wait(&acce[buf], ((g / NACC) - 1) & 1, abort, kTimeoutNs)) {
-            ok = false;
-            break;
+          const uint32_t slot = G % NG;
+          if ((kb & 3) == 0) {  // the group's scale columns are written
+            if (!mbar_wait(&sff[slot], (G / NG) & 1, abort, kTimeoutNs)) {
+              ok = false;
+              break;
+            }
           }
           const int s = (int)(g % S);
           if (!mbar_wait(&full[s], (g / S) & 1, abort, kTimeoutNs)) {
@@ -280,36 +325,68 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_fp8(const __grid_constant_
           }
           tc_fence_after();
           const uint32_t sa = sbase + (uint32_t)s * 2 * CHUNK, sb = sa + CHUNK;
-          const uint32_t d = tmem + buf * TILE;
+          const uint32_t id = (uint32_t)(kb & 3);
+          const uint32_t idesc = idesc_mx_e4m3(TILE, TILE, id, id);
+          const uint32_t tsf = tmem + COL_SF + slot * 8;
 #pragma unroll
           for (int kk = 0; kk < KB / 32; ++kk)
-            mma_e4m3(d, smem_desc(sa + kk * 2 * LBO, LBO, 128),
-                     smem_desc(sb + kk * 2 * LBO, LBO, 128), idesc, kk > 0 ? 1u : 0u);
+            mma_mx_e4m3(d, smem_desc(sa + kk * 2 * LBO, LBO, 128),
+                        smem_desc(sb + kk * 2 * LBO, LBO, 128), idesc, tsf, tsf + 4,
+                        (kb > 0 || kk > 0) ? 1u : 0u);
           mma_commit(&empty[s]);
-          mma_commit(&accf[buf]);
+          if ((kb & 3) == 3 || kb == nkb - 1) {
+            mma_commit(&sfe[slot]);  // the group's scale columns may be rewritten
+            ++G;
+          }
         }
+        if (!ok) break;
+        mma_commit(&accf[buf]);
       }
       mma_commit(done);  // arrives once every MMA issued above has completed
       volatile int never = 0;
       mbar_wait(done, 0, &never, kTimeoutNs);
     }
+  } else if (warp < 6) {
+    // --------------------------------------------------- scale-byte writers
+    const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    uint32_t G = 0;
+    bool ok = true;
+    for (int64_t w = blockIdx.x; ok && w < P.ntiles; w += gridDim.x) {
+      int tm, tn;
+      tile_coords(P, w, tm, tn);
+      const uint4* pa = reinterpret_cast<const uint4*>(P.sfa + sf_index(tm, ngroups, 0, 0)) + lane;
+      const uint4* pb = reinterpret_cast<const uint4*>(P.sfb + sf_index(tn, ngroups, 0, 0)) + lane;
+      for (int gi = 0; gi < ngroups; ++gi, ++G) {
+        const uint4 va = __ldg(pa + gi * 32), vb = __ldg(pb + gi * 32);
+        const uint32_t slot = G % NG;
+        if (G >= (uint32_t)NG && !warp_wait(&sfe[slot], ((G / NG) - 1) & 1, abort)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t ra[4] = {va.x, va.y, va.z, va.w}, rb[4] = {vb.x, vb.y, vb.z, vb.w};
+        tmem_st4(tl + COL_SF + slot * 8, ra);
+        tmem_st4(tl + COL_SF + slot * 8 + 4, rb);
+        tmem_wait_st();
+        tc_fence_before();
+        mbar_arrive(&sff[slot]);
+      }
+    }
   } else {
     // ------------------------------------------------------------- epilogue
-    const int ew = warp - 2;
+    const int ew = warp - 6;
     const int q = warp & 3;                 // tensor-memory lane quadrant of this warp
     const int h = ew >> 2;                  // column half
     const int row = q * 32 + lane;
     const int etid = ew * 32 + lane;
     const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)h * 64;
-    const size_t sta = (size_t)P.tiles_m * TILE, stb = (size_t)P.tiles_n * TILE;
-    uint32_t g = 0;
-    int64_t it = 0;
+    uint32_t t = 0;
     bool live = true;  // after a wait gave up, tiles are walked without work so
                        // that every epilogue warp still meets each named barrier
-    for (int64_t w = blockIdx.x; w < P.ntiles; w += gridDim.x, ++it) {
+    for (int64_t w = blockIdx.x; w < P.ntiles; w += gridDim.x, ++t) {
       int tm, tn;
       tile_coords(P, w, tm, tn);
-      int64_t* cc = colC + (it & 1) * TILE;
+      int64_t* cc = colC + (t & 1) * TILE;
       if (etid < TILE) {
         const int64_t n = (int64_t)tn * TILE + etid;
         cc[etid] = n < P.N ? goff(P.gn, 2, (uint32_t)n) : -1;
@@ -318,52 +395,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_fp8(const __grid_constant_
       if (!live) continue;
       const int64_t m = (int64_t)tm * TILE + row;
       const int64_t rc = m < P.M ? goff(P.gm, 2, (uint32_t)m) : -1;
-      const float* sap = P.sa + (size_t)tm * TILE + row;
-      const float* sbp = P.sb + (size_t)tn * TILE + h * 64;
-      float acc[64];
-#pragma unroll
-      for (int i = 0; i < 64; ++i) acc[i] = 0.0f;
-      float sav = __ldg(sap);
-      float4 sbv[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) sbv[i] = __ldg(reinterpret_cast<const float4*>(sbp) + i);
-      for (int kb = 0; kb < nkb; ++kb, ++g) {
-        const uint32_t buf = g % NACC;
-        if (!warp_wait(&accf[buf], (g / NACC) & 1, abort)) {
-          live = false;
-          break;
-        }
-        tc_fence_after();
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          uint32_t v[16];
-          tmem_ld16(tl + buf * TILE + c * 16, v);
-          tmem_wait_ld();
-#pragma unroll
-          for (int i = 0; i < 16; i += 4) {
-            const float4 sbq = sbv[(c * 16 + i) / 4];
-            acc[c * 16 + i] = fmaf(__uint_as_float(v[i]) * sav, sbq.x, acc[c * 16 + i]);
-            acc[c * 16 + i + 1] = fmaf(__uint_as_float(v[i + 1]) * sav, sbq.y, acc[c * 16 + i + 1]);
-            acc[c * 16 + i + 2] = fmaf(__uint_as_float(v[i + 2]) * sav, sbq.z, acc[c * 16 + i + 2]);
-            acc[c * 16 + i + 3] = fmaf(__uint_as_float(v[i + 3]) * sav, sbq.w, acc[c * 16 + i + 3]);
-          }
-        }
-        tc_fence_before();
-        mbar_arrive(&acce[buf]);
-        if (kb + 1 < nkb) {  // scales of the next block, loaded before its wait
-          sav = __ldg(sap + (size_t)(kb + 1) * sta);
-          const float4* sbn = reinterpret_cast<const float4*>(sbp + (size_t)(kb + 1) * stb);
-#pragma unroll
-          for (int i = 0; i < 16; ++i) sbv[i] = __ldg(sbn + i);
-        }
+      const uint32_t buf = t % NACC;
+      if (!warp_wait(&accf[buf], (t / NACC) & 1, abort)) {
+        live = false;
+        continue;
       }
-      if (!live || rc < 0) continue;
+      tc_fence_after();
+      uint32_t v[4][16];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) tmem_ld16(tl + buf * TILE + c * 16, v[c]);
+      tmem_wait_ld();
+      tc_fence_before();
+      mbar_arrive(&acce[buf]);  // the accumulator may take the next tile
+      if (rc < 0) continue;
       float* Cr = P.C + rc;
 #pragma unroll
       for (int i = 0; i < 64; ++i) {
         const int64_t ci = cc[h * 64 + i];
         if (ci < 0) continue;
-        float x = P.alpha * acc[i];
+        float x = P.alpha * __uint_as_float(v[i / 16][i % 16]);
         if (P.beta != 0.0f) x = fmaf(P.beta, Cr[ci], x);
         Cr[ci] = x;
       }
@@ -422,9 +472,10 @@ Fp8Layout fp8_layout(const GemmArgs& a) {
   L.nkb = (a.K + fp8::KB - 1) / fp8::KB;
   L.off_qa = 0;
   L.off_qb = align256((size_t)L.tiles_m * L.nkb * fp8::CHUNK);
+  L.ngroups = (L.nkb + 3) / 4;
   L.off_sa = L.off_qb + align256((size_t)L.tiles_n * L.nkb * fp8::CHUNK);
-  L.off_sb = L.off_sa + align256((size_t)L.nkb * L.tiles_m * fp8::TILE * 4);
-  L.bytes = L.off_sb + align256((size_t)L.nkb * L.tiles_n * fp8::TILE * 4);
+  L.off_sb = L.off_sa + align256((size_t)L.tiles_m * L.ngroups * 512);
+  L.bytes = L.off_sb + align256((size_t)L.tiles_n * L.ngroups * 512);
   return L;
 }
 
@@ -447,14 +498,15 @@ tc_status launch_gemm_fp8(const GemmArgs& a, void* ws, void* stream) {
   pk.in[1] = static_cast<const float*>(a.B);
   pk.q[0] = w + L.off_qa;
   pk.q[1] = w + L.off_qb;
-  pk.scale[0] = reinterpret_cast<float*>(w + L.off_sa);
-  pk.scale[1] = reinterpret_cast<float*>(w + L.off_sb);
+  pk.sf[0] = w + L.off_sa;
+  pk.sf[1] = w + L.off_sb;
   pk.rows[0] = a.M;
   pk.rows[1] = a.N;
   pk.K = a.K;
   pk.tiles[0] = (int32_t)L.tiles_m;
   pk.tiles[1] = (int32_t)L.tiles_n;
   pk.nkb = (int32_t)L.nkb;
+  pk.ngroups = (int32_t)L.ngroups;
   pk.nblocks0 = L.tiles_m * L.nkb;
   pk.rows_fast[0] = a.a_contig == CONTIG_MN;
   pk.rows_fast[1] = a.b_contig == CONTIG_MN;
@@ -469,8 +521,8 @@ tc_status launch_gemm_fp8(const GemmArgs& a, void* ws, void* stream) {
   g.gn = a.gn;
   g.qa = pk.q[0];
   g.qb = pk.q[1];
-  g.sa = pk.scale[0];
-  g.sb = pk.scale[1];
+  g.sfa = pk.sf[0];
+  g.sfb = pk.sf[1];
   g.C = static_cast<float*>(a.C);
   g.M = a.M;
   g.N = a.N;
@@ -480,6 +532,7 @@ tc_status launch_gemm_fp8(const GemmArgs& a, void* ws, void* stream) {
   g.tiles_m = (int32_t)L.tiles_m;
   g.tiles_n = (int32_t)L.tiles_n;
   g.nkb = (int32_t)L.nkb;
+  g.ngroups = (int32_t)L.ngroups;
   g.raster = a.raster;
   const int grid = (int)std::min<int64_t>(g.ntiles, sms);
   fp8::k_gemm_fp8<<<grid, fp8::kThreads, sm, s>>>(g);

@@ -115,15 +115,18 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
       : "memory");
 }
 
-// D[tmem] (+)= A[smem] * B[smem]^T, kind::f8f6f4 (E4M3 inputs, FP32
-// accumulate); K = 32 per instruction.
-__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t idesc, uint32_t accumulate) {
+// D[tmem] (+)= (A[smem] x 2^sa) * (B[smem] x 2^sb)^T, kind::mxf8f6f4 with one
+// UE8M0 scale per row of A and column of B for each K = 32 step, read from
+// tensor memory at sfa / sfb (the byte chosen by the instruction descriptor).
+__device__ __forceinline__ void mma_mx_e4m3(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                            uint32_t idesc, uint32_t sfa, uint32_t sfb,
+                                            uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      "setp.ne.b32 p, %6, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::mxf8f6f4.block_scale.scale_vec::1X [%0], %1, %2, %3, [%4], "
+      "[%5], p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accumulate)
       : "memory");
 }
 
@@ -164,6 +167,12 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16
       : "memory");
 }
 
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t (&r)[4]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr),
+               "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3])
+               : "memory");
+}
+
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -193,12 +202,15 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
          | ((uint32_t)(M >> 4) << 24);  // M / 16
 }
 
-// Instruction descriptor of kind::f8f6f4: E4M3 A and B (format code 0), FP32
-// D, both K-major.
-__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
-  return (1u << 4)                      // D format: F32
+// Instruction descriptor of kind::mxf8f6f4: E4M3 A and B, FP32 D, K-major,
+// UE8M0 scales (bit 23), scale bytes sfa_id / sfb_id of the scale cells.
+__host__ __device__ constexpr uint32_t idesc_mx_e4m3(int M, int N, uint32_t sfa_id,
+                                                     uint32_t sfb_id) {
+  return ((sfb_id & 3u) << 4)           // B scale byte
          | ((uint32_t)(N >> 3) << 17)   // N / 8
-         | ((uint32_t)(M >> 4) << 24);  // M / 16
+         | (1u << 23)                   // scale type UE8M0
+         | ((uint32_t)(M >> 4) << 24)   // M / 16
+         | ((sfa_id & 3u) << 29);       // A scale byte
 }
 
 // Two FP32 values rounded to nearest E4M3 (ties to even, saturating to

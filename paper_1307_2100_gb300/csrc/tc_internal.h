@@ -117,7 +117,7 @@ int tc_chunk_kb(int math, int tile);
 
 // FP8 form: workspace layout of the packed operands (byte offsets).
 struct Fp8Layout {
-  int64_t tiles_m, tiles_n, nkb;
+  int64_t tiles_m, tiles_n, nkb, ngroups;
   size_t off_qa, off_qb, off_sa, off_sb, bytes;
 };
 Fp8Layout fp8_layout(const GemmArgs& a);

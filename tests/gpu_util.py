@@ -213,14 +213,11 @@ def sample_outputs_fp8(p, samples, block=128):
 def fp8_bound(p, block=128):
     """Accumulation bound of the FP8 kernel against the FP8 oracle, as a
     multiple of sum |qa||qb| (<= 1.13 sum |a||b|, E4M3 rounding being <= 2^-4
-    relative): each block of `block` exact products is summed by the tensor
-    cores in FP32 (at most one unit of the running sum, 2^-23, per 16-product
-    step) and the scaled block sums are added with one rounding (2^-24) each,
-    plus the final alpha/beta rounding."""
+    relative).  The scaled products are exact; the block-scaled tensor cores
+    add each K = 32 step into one FP32 accumulator over all of K (allowed two
+    units of the running sum, 2^-22, per step), then alpha/beta round once."""
     K = 1
     for l, e in zip(p.A.labels, p.A.extents):
         if l in p.B.labels:
             K *= int(e)
-    nblk = -(-K // block)
-    u = 2.0 ** -23
-    return 1.13 * ((min(K, block) / 16 + 1) * u + (nblk + 2) * u / 2)
+    return 1.13 * ((K / 32 + 1) * 2.0 ** -22 + 2.0 ** -23)

@@ -175,8 +175,9 @@ def test_fp8_plans():
     assert tc.KERNEL_NAME[info.kernel] == "gemm_fp8"
     assert tc.MAPPING_NAME[info.mapping] == "fused_gemm"
     tm, tn, nkb = -(-info.M // 128), -(-info.N // 128), -(-info.K // 128)
+    ng = -(-nkb // 4)                                   # scale bytes: 512 per 4 blocks
     r = lambda x: -(-x // 256) * 256
-    want = r(tm * nkb * 16384) + r(tn * nkb * 16384) + r(nkb * tm * 512) + r(nkb * tn * 512)
+    want = r(tm * nkb * 16384) + r(tn * nkb * 16384) + r(tm * ng * 512) + r(tn * ng * 512)
     assert info.workspace == want
     f8 = tc.MATH["fp8"]
     x = (ts.lab("i"), [5], None)

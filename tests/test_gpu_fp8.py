@@ -3,8 +3,8 @@
 Reference: the FP8 oracle (oracle.precision.contract_fp8), which rounds the
 same blocks to E4M3 with the same scales (a decision taken on exact FP32
 values in both programs, so the E4M3 codes agree bit for bit) and sums the
-dequantised products exactly in FP64.  The kernel differs from it only by its
-FP32 accumulation (gpu_util.fp8_bound).  A wrong block membership, a wrong
+dequantised products exactly in FP64.  The kernel differs from it only by the
+tensor cores' FP32 accumulation (gpu_util.fp8_bound).  A wrong block membership, a wrong
 scale or a dropped block changes the result by about 2^-5 relative, far above
 that bound, and the block-order case below checks that the test can see it.
 Integer inputs in [-4, 4] are exact in every step, so the kernel must then
