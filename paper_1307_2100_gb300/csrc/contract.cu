@@ -16,7 +16,8 @@ extern "C" tc_status tc_contract(tc_plan_t plan, double alpha, const void* A, co
   if (P->empty_out) return TC_OK;
   if (!C) return TC_ERR_INVALID_ARG;
   if (P->workspace > 0 && (!workspace || ws_bytes < P->workspace)) return TC_ERR_WORKSPACE;
-  if (P->kernel == K_GEMM_FP8 && (reinterpret_cast<uintptr_t>(workspace) & 15) != 0)
+  const bool packed = P->kernel == K_GEMM_FP8 || (P->kernel == K_GEMM_TC && P->tile == kTilePacked);
+  if (packed && (reinterpret_cast<uintptr_t>(workspace) & 15) != 0)
     return TC_ERR_INVALID_ARG;  // the packed operands are moved by 16-byte bulk copies
   if (P->empty_k || alpha == 0.0)
     return launch_scale(P->gc, C, beta, P->dtype, P->c_elems_span, stream);
@@ -44,7 +45,9 @@ extern "C" tc_status tc_contract(tc_plan_t plan, double alpha, const void* A, co
   }
   switch (P->kernel) {
     case K_GEMM_SIMT: return launch_gemm_simt(a, P->dtype, P->tile, stream);
-    case K_GEMM_TC: return launch_gemm_tc(a, P->math, stream);
+    case K_GEMM_TC:
+      return P->tile == kTilePacked ? launch_gemm_tc_packed(a, P->math, ws, stream)
+                                    : launch_gemm_tc(a, P->math, stream);
     case K_GEMM_FP8: return launch_gemm_fp8(a, ws, stream);
     case K_GEMV: return launch_gemv(a, P->dtype, P->tile, stream);
     case K_DOT: return launch_dot(a, P->dtype, P->tile, stream);
@@ -75,9 +78,10 @@ extern "C" tc_status tc_selftest_wait_timeout(int64_t timeout_ns, void* stream) 
 
 extern "C" tc_status tc_device_status(void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  int h0 = 0, h1 = 0, h2 = 0;
+  int h0 = 0, h1 = 0, h2 = 0, h3 = 0;
   if (read_clear_status(&h0, s) != cudaSuccess || tc_gemm_read_status(&h1, s) != TC_OK ||
-      tc_fp8_read_status(&h2, s) != TC_OK || cudaStreamSynchronize(s) != cudaSuccess)
+      tc_fp8_read_status(&h2, s) != TC_OK || tc_pk_read_status(&h3, s) != TC_OK ||
+      cudaStreamSynchronize(s) != cudaSuccess)
     return TC_ERR_CUDA;
-  return (h0 || h1 || h2) ? TC_ERR_TIMEOUT : TC_OK;
+  return (h0 || h1 || h2 || h3) ? TC_ERR_TIMEOUT : TC_OK;
 }

@@ -67,7 +67,7 @@ constexpr int kPackThreads = 256;
 constexpr int kLd = KB + 1;               // shared-memory row pitch of the pack tile (floats)
 constexpr uint32_t kPackSmem = TILE * kLd * 4 + 2 * TILE * 8 + TILE * 4;
 
-constexpr int S = 6;                      // stages of the operand ring
+constexpr int S = 7;                      // stages of the operand ring
 constexpr int NACC = 2;                   // accumulators in tensor memory (128 columns each)
 constexpr int NG = 4;                     // groups of scale columns in tensor memory
 constexpr uint32_t COL_SF = NACC * TILE;  // first scale column; 8 per group (A 0-3, B 4-7)
@@ -79,7 +79,7 @@ constexpr uint32_t OFF_COLC = S * 2 * CHUNK;                    // int64 colC[2]
 constexpr uint32_t OFF_BAR = OFF_COLC + 2 * TILE * 8;
 constexpr uint32_t NBAR = 2 * S + 2 * NACC + 2 * NG + 1;
 constexpr uint32_t OFF_MISC = OFF_BAR + NBAR * 8;
-constexpr uint32_t kGemmSmem = OFF_MISC + 16 + 1024;            // + alignment slack
+constexpr uint32_t kGemmSmem = OFF_MISC + 16 + 128;             // + alignment slack
 
 // Scale bytes of one operand: per (tile, group of 4 blocks) 512 bytes laid
 // out as the tensor-memory cells of one lane quadrant: [l][c][j] = row
@@ -127,10 +127,12 @@ __global__ void __launch_bounds__(kPackThreads) k_fp8_pack(const __grid_constant
   // the operand's contiguous index.  Sixteen loads are issued before their
   // sixteen shared-memory stores, so that each thread has them in flight at once.
   const float* __restrict__ X = P.in[o];
-  constexpr int NJ = TILE * KB / kPackThreads, U = 16;
+  constexpr int NJ = TILE * KB / kPackThreads, U = 32;
+  float* pmax = qmul;  // partial row maxima of the two threads of a row (rows_fast)
   if (P.rows_fast[o]) {
     const int r = tid & (TILE - 1), k0 = tid >> 7;
     const int64_t ro = roff[r];
+    float m = 0.0f;
 #pragma unroll
     for (int j0 = 0; j0 < NJ; j0 += U) {
       float v[U];
@@ -140,8 +142,14 @@ __global__ void __launch_bounds__(kPackThreads) k_fp8_pack(const __grid_constant
         v[j] = (ro >= 0 && ko >= 0) ? __ldg(X + ro + ko) : 0.0f;
       }
 #pragma unroll
-      for (int j = 0; j < U; ++j) tile[r * kLd + k0 + 2 * (j0 + j)] = v[j];
+      for (int j = 0; j < U; ++j) {
+        tile[r * kLd + k0 + 2 * (j0 + j)] = v[j];
+        m = fmaxf(m, fabsf(v[j]));
+      }
     }
+    if (k0 == 1) pmax[r] = m;
+    __syncthreads();
+    if (k0 == 0) pmax[r] = fmaxf(pmax[r], m);
   } else {
     const int k = tid & (KB - 1), r0 = tid >> 7;
     const int64_t ko = koff[k];
@@ -156,26 +164,27 @@ __global__ void __launch_bounds__(kPackThreads) k_fp8_pack(const __grid_constant
 #pragma unroll
       for (int j = 0; j < U; ++j) tile[(r0 + 2 * (j0 + j)) * kLd + k] = v[j];
     }
+    __syncthreads();
+    if (tid < TILE) {  // one thread per row: consecutive rows fall in distinct banks
+      float m = 0.0f;
+#pragma unroll 8
+      for (int j = 0; j < KB; ++j) m = fmaxf(m, fabsf(tile[tid * kLd + j]));
+      pmax[tid] = m;
+    }
   }
   __syncthreads();
 
-  // exponent of each row: two threads per row
-  {
-    const int r = tid >> 1, h = tid & 1;
-    float m = 0.0f;
-#pragma unroll 8
-    for (int j = 0; j < KB / 2; ++j) m = fmaxf(m, fabsf(tile[r * kLd + h * (KB / 2) + j]));
-    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
-    if (h == 0) {
-      // m = f * 2^E with f in [1, 2): m <= 448 * 2^e  <=>  e >= E - 8 (f <= 1.75)
-      // or e >= E - 7 (f > 1.75); zero and FP32-subnormal maxima give -126.
-      const uint32_t b = __float_as_uint(m);
-      const int be = (int)(b >> 23);
-      int e = be == 0 ? -126 : be - 135 + ((b & 0x7FFFFFu) > 0x600000u ? 1 : 0);
-      e = max(e, -126);
-      qmul[r] = __uint_as_float((uint32_t)(127 - e) << 23);                 // 2^-e
-      P.sf[o][sf_index(t, P.ngroups, kb, r)] = (uint8_t)(127 + e);
-    }
+  // exponent of each row
+  if (tid < TILE) {
+    // m = f * 2^E with f in [1, 2): m <= 448 * 2^e  <=>  e >= E - 8 (f <= 1.75)
+    // or e >= E - 7 (f > 1.75); zero and FP32-subnormal maxima give -126.
+    const int r = tid;
+    const uint32_t b = __float_as_uint(pmax[r]);
+    const int be = (int)(b >> 23);
+    int e = be == 0 ? -126 : be - 135 + ((b & 0x7FFFFFu) > 0x600000u ? 1 : 0);
+    e = max(e, -126);
+    qmul[r] = __uint_as_float((uint32_t)(127 - e) << 23);                   // 2^-e
+    P.sf[o][sf_index(t, P.ngroups, kb, r)] = (uint8_t)(127 + e);
   }
   __syncthreads();
 
@@ -228,8 +237,9 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volati
 
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_fp8(const __grid_constant__ GemmFp8 P) {
   extern __shared__ uint8_t fp8_smem_raw[];
+  // the operand layouts have no swizzle: 128-byte alignment is enough
   uint8_t* smem = reinterpret_cast<uint8_t*>(
-      (reinterpret_cast<uintptr_t>(fp8_smem_raw) + 1023) & ~(uintptr_t)1023);
+      (reinterpret_cast<uintptr_t>(fp8_smem_raw) + 127) & ~(uintptr_t)127);
   int64_t* colC = reinterpret_cast<int64_t*>(smem + OFF_COLC);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OFF_BAR);
   uint64_t* full = bars;
@@ -351,26 +361,44 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_fp8(const __grid_constant_
     const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
     uint32_t G = 0;
     bool ok = true;
-    for (int64_t w = blockIdx.x; ok && w < P.ntiles; w += gridDim.x) {
+    // the bytes of the next group are loaded while the current one waits
+    int64_t w = blockIdx.x;
+    int gi = 0;
+    auto load = [&](int64_t ww, int g, uint4& va, uint4& vb) {
       int tm, tn;
-      tile_coords(P, w, tm, tn);
-      const uint4* pa = reinterpret_cast<const uint4*>(P.sfa + sf_index(tm, ngroups, 0, 0)) + lane;
-      const uint4* pb = reinterpret_cast<const uint4*>(P.sfb + sf_index(tn, ngroups, 0, 0)) + lane;
-      for (int gi = 0; gi < ngroups; ++gi, ++G) {
-        const uint4 va = __ldg(pa + gi * 32), vb = __ldg(pb + gi * 32);
-        const uint32_t slot = G % NG;
-        if (G >= (uint32_t)NG && !warp_wait(&sfe[slot], ((G / NG) - 1) & 1, abort)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t ra[4] = {va.x, va.y, va.z, va.w}, rb[4] = {vb.x, vb.y, vb.z, vb.w};
-        tmem_st4(tl + COL_SF + slot * 8, ra);
-        tmem_st4(tl + COL_SF + slot * 8 + 4, rb);
-        tmem_wait_st();
-        tc_fence_before();
-        mbar_arrive(&sff[slot]);
+      tile_coords(P, ww, tm, tn);
+      va = __ldg(reinterpret_cast<const uint4*>(P.sfa + sf_index(tm, ngroups, 4 * g, 0)) + lane);
+      vb = __ldg(reinterpret_cast<const uint4*>(P.sfb + sf_index(tn, ngroups, 4 * g, 0)) + lane);
+    };
+    uint4 va, vb;
+    if (w < P.ntiles) load(w, 0, va, vb);
+    while (ok && w < P.ntiles) {
+      // position of the next group
+      int64_t w2 = w;
+      int g2 = gi + 1;
+      if (g2 == ngroups) {
+        g2 = 0;
+        w2 += gridDim.x;
       }
+      uint4 na = va, nb = vb;
+      if (w2 < P.ntiles) load(w2, g2, na, nb);
+      const uint32_t slot = G % NG;
+      if (G >= (uint32_t)NG && !warp_wait(&sfe[slot], ((G / NG) - 1) & 1, abort)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t ra[4] = {va.x, va.y, va.z, va.w}, rb[4] = {vb.x, vb.y, vb.z, vb.w};
+      tmem_st4(tl + COL_SF + slot * 8, ra);
+      tmem_st4(tl + COL_SF + slot * 8 + 4, rb);
+      tmem_wait_st();
+      tc_fence_before();
+      mbar_arrive(&sff[slot]);
+      ++G;
+      w = w2;
+      gi = g2;
+      va = na;
+      vb = nb;
     }
   } else {
     // ------------------------------------------------------------- epilogue

@@ -611,8 +611,10 @@ uint64_t tiles_of(const GemmArgs& a) {
 // Tile configurations of the tensor-core GEMM: K blocks (of 32) per chunk of
 // the main accumulator.  Tile 0: one chunk for plain BF16 (its error is that of
 // the BF16 inputs), 256-K chunks for the split forms; tile 1: 64-K chunks;
-// tile 2: 1024-K chunks.
-int num_tiles_tc() { return 3; }
+// tile 2: 1024-K chunks; tile 3: the chunks of tile 0 on packed operands
+// (k_tcpk.cu: a pack pass splits the operands once, the GEMM moves the terms
+// with bulk copies).
+int num_tiles_tc() { return 4; }
 int tc_chunk_kb(int math, int tile) {
   if (tile == 1) return 2;
   if (tile == 2) return 32;

@@ -1,0 +1,549 @@
+// k_tcpk.cu -- the split-BF16 forms of a Class 3 contraction with packed
+// operands: a pack pass and a GEMM fed by bulk copies (sm_103a, tcgen05).
+//
+// Same arithmetic as k_tc.cu (x = x0 + x1 + x2, BF16 terms of the residuals;
+// BF16 keeps a0 b0, BF16x3 adds a0 b1 + a1 b0, BF16x6 adds a0 b2 + a1 b1 +
+// a2 b0; the main product a0 b0 and the correction products in separate FP32
+// accumulators, the main one emptied every K chunk into a compensated sum),
+// but the FP32 operands are split once, not once per output tile:
+//   k_bf16_pack<NT>  one CTA per (128-row tile, 128 K) of each operand:
+//                    gathers the FP32 elements through the index groups,
+//                    splits them into NT BF16 terms and writes, per 32-K
+//                    block, NT canonical K-major blocks of 8 KB (byte
+//                    (k / 8) * 2048 + row * 16 + (k % 8) * 2), term after term.
+//   k_gemm_pk<NT>    persistent, one CTA per SM over 128 x 128 output tiles:
+//                    warp 0     one thread moves each 32-K block of both
+//                               operands (NT terms each) into a shared-memory
+//                               ring with two bulk copies;
+//                    warp 1     tensor-memory allocation; one thread issues
+//                               the MMAs (main product into a double-buffered
+//                               accumulator per K chunk, correction products
+//                               into one accumulator per tile);
+//                    warps 2-9  epilogue: two warps per lane quadrant, 64
+//                               columns each; drain each K chunk into the
+//                               compensated sum (TwoSum: high word in tensor
+//                               memory, low word in registers); finish with
+//                               hi + (lo + corrections), alpha, beta and a
+//                               strided store.
+// Tensor memory (512 columns): [0,256) main accumulators, [256,384) the
+// correction accumulator, [384,512) the high word of the chunk sum.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "groups.cuh"
+#include "sm100.cuh"
+#include "tc_internal.h"
+
+namespace tc {
+
+namespace pk {
+
+constexpr int TILE = 128;
+constexpr int BK = 32;                       // K per block (one stage)
+constexpr int PK = 128;                      // K per pack CTA (4 blocks)
+constexpr uint32_t TERM = TILE * BK * 2;     // bytes of one term of one block
+constexpr int kPackThreads = 256;
+constexpr int kLd = PK + 1;
+constexpr uint32_t kPackSmem = TILE * kLd * 4 + 2 * TILE * 8;
+
+constexpr int kEpiThreads = 256;
+constexpr int kThreads = 64 + kEpiThreads;
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t COL_CORR = 256, COL_HI = 384;
+constexpr uint64_t kTimeoutNs = 2000000000ull;
+constexpr uint32_t kRing = 192 * 1024;       // bytes of the stage ring
+
+template <int NT>
+struct Cfg {
+  static constexpr uint32_t STAGE = 2 * NT * TERM;   // A terms then B terms
+  static constexpr int S = (int)(kRing / STAGE);      // 12, 6, 4
+  static constexpr uint32_t OFF_COLC = S * STAGE;
+  static constexpr uint32_t OFF_BAR = OFF_COLC + 2 * TILE * 8;
+  static constexpr uint32_t NBAR = 2 * S + 4 + 1;
+  static constexpr uint32_t OFF_MISC = OFF_BAR + NBAR * 8;
+  static constexpr uint32_t BYTES = OFF_MISC + 16 + 1024;
+};
+
+struct PackArgs {
+  Group gr[2];          // rows of operand o (the M and N groups); strides in slot o
+  Group gk;             // K group; operand o's strides in slot o
+  const float* in[2];
+  uint8_t* q[2];        // [tile][block][term][TERM]
+  int64_t rows[2];
+  int64_t K;
+  int64_t nblocks0;     // CTAs of operand 0
+  int32_t tiles[2];
+  int32_t nkb;          // 32-K blocks
+  int32_t npk;          // pack CTAs per tile (128 K each)
+  int32_t rows_fast[2];
+};
+
+template <int NT>
+__global__ void __launch_bounds__(kPackThreads) k_bf16_pack(const __grid_constant__ PackArgs P) {
+  extern __shared__ float4 pk_smem[];
+  float* tile = reinterpret_cast<float*>(pk_smem);
+  int64_t* roff = reinterpret_cast<int64_t*>(tile + TILE * kLd);
+  int64_t* koff = roff + TILE;
+
+  int64_t bid = blockIdx.x;
+  const int o = bid < P.nblocks0 ? 0 : 1;
+  if (o) bid -= P.nblocks0;
+  const int t = (int)(bid / P.npk), kc = (int)(bid % P.npk);
+  const int tid = threadIdx.x;
+  if (tid < TILE) {
+    const int64_t r = (int64_t)t * TILE + tid;
+    roff[tid] = r < P.rows[o] ? goff(P.gr[o], o, (uint32_t)r) : -1;
+  } else {
+    const int64_t k = (int64_t)kc * PK + (tid - TILE);
+    koff[tid - TILE] = k < P.K ? goff(P.gk, o, (uint32_t)k) : -1;
+  }
+  __syncthreads();
+
+  // gather (sixteen loads in flight per thread, then their stores)
+  const float* __restrict__ X = P.in[o];
+  constexpr int NJ = TILE * PK / kPackThreads, U = 16;
+  if (P.rows_fast[o]) {
+    const int r = tid & (TILE - 1), k0 = tid >> 7;
+    const int64_t ro = roff[r];
+#pragma unroll
+    for (int j0 = 0; j0 < NJ; j0 += U) {
+      float v[U];
+#pragma unroll
+      for (int j = 0; j < U; ++j) {
+        const int64_t ko = koff[k0 + 2 * (j0 + j)];
+        v[j] = (ro >= 0 && ko >= 0) ? __ldg(X + ro + ko) : 0.0f;
+      }
+#pragma unroll
+      for (int j = 0; j < U; ++j) tile[r * kLd + k0 + 2 * (j0 + j)] = v[j];
+    }
+  } else {
+    const int k = tid & (PK - 1), r0 = tid >> 7;
+    const int64_t ko = koff[k];
+#pragma unroll
+    for (int j0 = 0; j0 < NJ; j0 += U) {
+      float v[U];
+#pragma unroll
+      for (int j = 0; j < U; ++j) {
+        const int64_t ro = roff[r0 + 2 * (j0 + j)];
+        v[j] = (ro >= 0 && ko >= 0) ? __ldg(X + ro + ko) : 0.0f;
+      }
+#pragma unroll
+      for (int j = 0; j < U; ++j) tile[(r0 + 2 * (j0 + j)) * kLd + k] = v[j];
+    }
+  }
+  __syncthreads();
+
+  // split and store: unit u = (k8 chunk) * 128 + row is one 16-byte row of a
+  // core matrix (8 BF16 along K), at byte u * 16 of its term block
+  const int nb = min(PK / BK, P.nkb - kc * (PK / BK));   // blocks of this CTA
+  uint8_t* __restrict__ Q = P.q[o] + ((int64_t)t * P.nkb + (int64_t)kc * (PK / BK)) * NT * TERM;
+  for (int u = tid; u < nb * (BK / 8) * TILE; u += kPackThreads) {
+    const int blk = u / ((BK / 8) * TILE);
+    const int w = u % ((BK / 8) * TILE);
+    const int c8 = w >> 7, r = w & (TILE - 1);
+    const float* src = tile + r * kLd + blk * BK + c8 * 8;
+    float v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = src[i];
+    uint8_t* dst = Q + (size_t)blk * NT * TERM + (size_t)w * 16;
+#pragma unroll
+    for (int tt = 0; tt < NT; ++tt) {
+      uint32_t wd[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        wd[i] = pack_bf16x2(v[2 * i], v[2 * i + 1]);
+        if (tt + 1 < NT) {  // exact FP32 residuals
+          v[2 * i] = __fsub_rn(v[2 * i], bf16_lo(wd[i]));
+          v[2 * i + 1] = __fsub_rn(v[2 * i + 1], bf16_hi(wd[i]));
+        }
+      }
+      *reinterpret_cast<uint4*>(dst + (size_t)tt * TERM) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+    }
+  }
+}
+
+struct GemmPk {
+  Group gm, gn;          // C offsets in slot 2
+  const uint8_t* qa;
+  const uint8_t* qb;
+  float* C;
+  int64_t M, N, ntiles;
+  float alpha, beta;
+  int32_t tiles_m, tiles_n, nkb, chunk_kb, raster, pad_;
+};
+
+__constant__ int8_t kProdA[6] = {0, 0, 1, 0, 1, 2};
+__constant__ int8_t kProdB[6] = {0, 1, 0, 2, 1, 0};
+__host__ __device__ constexpr int nprod(int nt) { return nt == 1 ? 1 : nt == 2 ? 3 : 6; }
+
+__device__ __forceinline__ void tile_coords(const GemmPk& P, int64_t w, int& tm, int& tn) {
+  if (P.raster) {
+    tn = (int)(w % P.tiles_n);
+    tm = (int)(w / P.tiles_n);
+  } else {
+    tm = (int)(w % P.tiles_m);
+    tn = (int)(w / P.tiles_m);
+  }
+}
+
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  bool ok = (*abort == 0) && mbar_wait(bar, parity, abort, kTimeoutNs);
+  return __all_sync(0xffffffffu, ok);
+}
+
+// s + e == a + b exactly (Knuth's TwoSum).
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+  const float s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  const float ap = __fsub_rn(s, bp);
+  e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+  return s;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(kThreads, 1) k_gemm_pk(const __grid_constant__ GemmPk P) {
+  using G = Cfg<NT>;
+  constexpr int S = G::S;
+  extern __shared__ uint8_t pk_gemm_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(pk_gemm_raw) + 1023) & ~(uintptr_t)1023);
+  int64_t* colC = reinterpret_cast<int64_t*>(smem + G::OFF_COLC);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + G::OFF_BAR);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + S;
+  uint64_t* accf = bars + 2 * S;
+  uint64_t* acce = accf + 2;
+  uint64_t* done = acce + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + G::OFF_MISC);
+  volatile int* abort = reinterpret_cast<volatile int*>(smem + G::OFF_MISC + 4);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&accf[i], 1);
+      mbar_init(&acce[i], kEpiThreads);
+    }
+    mbar_init(done, 1);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t sbase = smem_u32(smem);
+  const int nkb = P.nkb;
+  const int ckb = max(P.chunk_kb, 1);
+  const int nchunks = (nkb + ckb - 1) / ckb;
+  constexpr uint32_t OPB = NT * TERM;          // bytes of one operand's block
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------------------ producer
+      uint32_t g = 0;
+      bool ok = true;
+      for (int64_t w = blockIdx.x; ok && w < P.ntiles; w += gridDim.x) {
+        int tm, tn;
+        tile_coords(P, w, tm, tn);
+        const uint8_t* a = P.qa + (size_t)tm * nkb * OPB;
+        const uint8_t* b = P.qb + (size_t)tn * nkb * OPB;
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int s = (int)(g % S);
+          if (g >= (uint32_t)S && !mbar_wait(&empty[s], ((g / S) - 1) & 1, abort, kTimeoutNs)) {
+            ok = false;
+            break;
+          }
+          const uint32_t dst = sbase + (uint32_t)s * G::STAGE;
+          mbar_arrive_expect_tx(&full[s], 2 * OPB);
+          bulk_g2s(dst, a + (size_t)kb * OPB, OPB, &full[s]);
+          bulk_g2s(dst + OPB, b + (size_t)kb * OPB, OPB, &full[s]);
+        }
+      }
+      volatile int never = 0;
+      for (uint32_t i = g > (uint32_t)S ? g - S : 0; i < g; ++i)
+        mbar_wait(&full[i % S], (i / S) & 1, &never, kTimeoutNs);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ----------------------------------------------------------- MMA issue
+      constexpr uint32_t idesc = idesc_bf16(TILE, TILE);
+      constexpr uint32_t LBO = (TILE / 8) * 128;
+      uint32_t g = 0, gc = 0;
+      bool ok = true;
+      for (int64_t w = blockIdx.x; ok && w < P.ntiles; w += gridDim.x) {
+        // the correction accumulator and both main buffers are free once the
+        // previous tile's last chunk has been drained
+        if (gc >= 1 && !mbar_wait(&acce[(gc - 1) & 1], ((gc - 1) >> 1) & 1, abort, kTimeoutNs)) {
+          ok = false;
+          break;
+        }
+        int kb = 0;
+        for (int j = 0; ok && j < nchunks; ++j, ++gc) {
+          const uint32_t buf = gc & 1;
+          if (gc >= 2 && !mbar_wait(&acce[buf], ((gc >> 1) - 1) & 1, abort, kTimeoutNs)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t dmain = tmem + buf * TILE;
+          const int kend = min(nkb, (j + 1) * ckb), kstart = kb;
+          for (; kb < kend; ++kb, ++g) {
+            const int s = (int)(g % S);
+            if (!mbar_wait(&full[s], (g / S) & 1, abort, kTimeoutNs)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sa = sbase + (uint32_t)s * G::STAGE, sb = sa + OPB;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              mma_bf16(dmain, smem_desc(sa + kk * 2 * LBO, LBO, 128),
+                       smem_desc(sb + kk * 2 * LBO, LBO, 128), idesc,
+                       (kb > kstart || kk > 0) ? 1u : 0u);
+#pragma unroll
+              for (int pi = 1; pi < nprod(NT); ++pi)
+                mma_bf16(tmem + COL_CORR,
+                         smem_desc(sa + kProdA[pi] * TERM + kk * 2 * LBO, LBO, 128),
+                         smem_desc(sb + kProdB[pi] * TERM + kk * 2 * LBO, LBO, 128), idesc,
+                         (kb > 0 || kk > 0 || pi > 1) ? 1u : 0u);
+            }
+            mma_commit(&empty[s]);
+          }
+          if (!ok) break;
+          mma_commit(&accf[buf]);
+        }
+      }
+      mma_commit(done);
+      volatile int never = 0;
+      mbar_wait(done, 0, &never, kTimeoutNs);
+    }
+  } else {
+    // ------------------------------------------------------------- epilogue
+    const int ew = warp - 2;
+    const int q = warp & 3;
+    const int h = ew >> 2;
+    const int row = q * 32 + lane;
+    const int etid = ew * 32 + lane;
+    const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)h * 64;
+    uint32_t gc = 0;
+    int64_t it = 0;
+    bool live = true;
+    for (int64_t w = blockIdx.x; w < P.ntiles; w += gridDim.x, ++it) {
+      int tm, tn;
+      tile_coords(P, w, tm, tn);
+      int64_t* cc = colC + (it & 1) * TILE;
+      if (etid < TILE) {
+        const int64_t n = (int64_t)tn * TILE + etid;
+        cc[etid] = n < P.N ? goff(P.gn, 2, (uint32_t)n) : -1;
+      }
+      named_bar_sync(1, kEpiThreads);
+      if (!live) continue;
+      const int64_t m = (int64_t)tm * TILE + row;
+      const int64_t rc = m < P.M ? goff(P.gm, 2, (uint32_t)m) : -1;
+      float lo[64];
+#pragma unroll
+      for (int i = 0; i < 64; ++i) lo[i] = 0.0f;
+      for (int j = 0; j < nchunks; ++j, ++gc) {
+        const uint32_t buf = gc & 1;
+        if (!warp_wait(&accf[buf], (gc >> 1) & 1, abort)) {
+          live = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t tmain = tl + buf * TILE;
+        if (j + 1 < nchunks) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            uint32_t mv[16], hv[16];
+            tmem_ld16(tmain + c * 16, mv);
+            if (j > 0) tmem_ld16(tl + COL_HI + c * 16, hv);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const float hi0 = j > 0 ? __uint_as_float(hv[i]) : 0.0f;
+              float e;
+              const float s = two_sum(hi0, __uint_as_float(mv[i]), e);
+              lo[c * 16 + i] = __fadd_rn(lo[c * 16 + i], e);
+              hv[i] = __float_as_uint(s);
+            }
+            tmem_st16(tl + COL_HI + c * 16, hv);
+          }
+          tmem_wait_st();
+          tc_fence_before();
+          mbar_arrive(&acce[buf]);
+        } else {
+          // the finished sums replace the low words in lo[]
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            uint32_t mv[16], hv[16], cv[16];
+            tmem_ld16(tmain + c * 16, mv);
+            if (j > 0) tmem_ld16(tl + COL_HI + c * 16, hv);
+            if (NT > 1) tmem_ld16(tl + COL_CORR + c * 16, cv);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const float hi0 = j > 0 ? __uint_as_float(hv[i]) : 0.0f;
+              float e;
+              const float s = two_sum(hi0, __uint_as_float(mv[i]), e);
+              float r = __fadd_rn(lo[c * 16 + i], e);
+              if (NT > 1) r = __fadd_rn(r, __uint_as_float(cv[i]));
+              lo[c * 16 + i] = __fadd_rn(s, r);
+            }
+          }
+          tc_fence_before();
+          mbar_arrive(&acce[buf]);  // main, correction and high word are free
+          if (rc >= 0) {
+            float* Cr = P.C + rc;
+#pragma unroll
+            for (int i = 0; i < 64; ++i) {
+              const int64_t ci = cc[h * 64 + i];
+              if (ci < 0) continue;
+              float x = P.alpha * lo[i];
+              if (P.beta != 0.0f) x = fmaf(P.beta, Cr[ci], x);
+              Cr[ci] = x;
+            }
+          }
+        }
+      }
+    }
+  }
+
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      n = 0;
+  }
+  return n;
+}
+
+template <int NT>
+int set_smem() {
+  static int bytes = 0;
+  if (bytes == 0) {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess)
+      return -1;
+    if (optin < (int)Cfg<NT>::BYTES) return -2;
+    if (cudaFuncSetAttribute(k_bf16_pack<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kPackSmem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_gemm_pk<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Cfg<NT>::BYTES) != cudaSuccess)
+      return -1;
+    bytes = (int)Cfg<NT>::BYTES;
+  }
+  return bytes;
+}
+
+template <int NT>
+tc_status launch(const GemmArgs& a, const PkLayout& L, void* ws, cudaStream_t s) {
+  const int sm = set_smem<NT>();
+  if (sm == -2) return TC_ERR_UNSUPPORTED;
+  const int sms = num_sms();
+  if (sm < 0 || sms <= 0) return TC_ERR_CUDA;
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  PackArgs pa;
+  std::memset(&pa, 0, sizeof(pa));
+  pa.gr[0] = a.gm;
+  pa.gr[1] = a.gn;
+  pa.gk = a.gk;
+  pa.in[0] = static_cast<const float*>(a.A);
+  pa.in[1] = static_cast<const float*>(a.B);
+  pa.q[0] = w + L.off_qa;
+  pa.q[1] = w + L.off_qb;
+  pa.rows[0] = a.M;
+  pa.rows[1] = a.N;
+  pa.K = a.K;
+  pa.tiles[0] = (int32_t)L.tiles_m;
+  pa.tiles[1] = (int32_t)L.tiles_n;
+  pa.nkb = (int32_t)L.nkb;
+  pa.npk = (int32_t)((L.nkb + PK / BK - 1) / (PK / BK));
+  pa.nblocks0 = L.tiles_m * pa.npk;
+  pa.rows_fast[0] = a.a_contig == CONTIG_MN;
+  pa.rows_fast[1] = a.b_contig == CONTIG_MN;
+  const int64_t nblocks = (L.tiles_m + L.tiles_n) * pa.npk;
+  if (nblocks > 0x7fffffffll) return TC_ERR_UNSUPPORTED;
+  k_bf16_pack<NT><<<(unsigned)nblocks, kPackThreads, kPackSmem, s>>>(pa);
+  if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;
+
+  GemmPk g;
+  std::memset(&g, 0, sizeof(g));
+  g.gm = a.gm;
+  g.gn = a.gn;
+  g.qa = pa.q[0];
+  g.qb = pa.q[1];
+  g.C = static_cast<float*>(a.C);
+  g.M = a.M;
+  g.N = a.N;
+  g.ntiles = L.tiles_m * L.tiles_n;
+  g.alpha = (float)a.alpha;
+  g.beta = (float)a.beta;
+  g.tiles_m = (int32_t)L.tiles_m;
+  g.tiles_n = (int32_t)L.tiles_n;
+  g.nkb = (int32_t)L.nkb;
+  g.chunk_kb = a.chunk_kb;
+  g.raster = a.raster;
+  const int grid = (int)std::min<int64_t>(g.ntiles, sms);
+  k_gemm_pk<NT><<<grid, kThreads, sm, s>>>(g);
+  return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+}
+
+}  // namespace pk
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static int terms_of(int math) {
+  return math == TC_MATH_BF16 ? 1 : math == TC_MATH_BF16X3 ? 2 : math == TC_MATH_BF16X6 ? 3 : 0;
+}
+
+PkLayout pk_layout(const GemmArgs& a, int math) {
+  PkLayout L;
+  std::memset(&L, 0, sizeof(L));
+  const int nt = terms_of(math);
+  L.tiles_m = (a.M + pk::TILE - 1) / pk::TILE;
+  L.tiles_n = (a.N + pk::TILE - 1) / pk::TILE;
+  L.nkb = (a.K + pk::BK - 1) / pk::BK;
+  L.off_qa = 0;
+  L.off_qb = align256((size_t)L.tiles_m * L.nkb * nt * pk::TERM);
+  L.bytes = L.off_qb + align256((size_t)L.tiles_n * L.nkb * nt * pk::TERM);
+  return L;
+}
+
+tc_status launch_gemm_tc_packed(const GemmArgs& a, int math, void* ws, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const PkLayout L = pk_layout(a, math);
+  if (L.tiles_m == 0 || L.tiles_n == 0 || L.nkb == 0) return TC_OK;
+  switch (math) {
+    case TC_MATH_BF16: return pk::launch<1>(a, L, ws, s);
+    case TC_MATH_BF16X3: return pk::launch<2>(a, L, ws, s);
+    case TC_MATH_BF16X6: return pk::launch<3>(a, L, ws, s);
+    default: return TC_ERR_UNSUPPORTED;
+  }
+}
+
+tc_status tc_pk_read_status(int* h, void* stream) {
+  return read_clear_status(h, static_cast<cudaStream_t>(stream)) == cudaSuccess ? TC_OK
+                                                                                : TC_ERR_CUDA;
+}
+
+}  // namespace tc

@@ -558,11 +558,19 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
     delete P;
     return TC_ERR_UNSUPPORTED;
   }
+  if (kernel == K_GEMM_TC && tile == kTilePacked && Bt > 1) {
+    delete P;  // packed operands: one GEMM, no batch group
+    return TC_ERR_UNSUPPORTED;
+  }
   if (tile < 0) {
     if (kernel == K_GEMM_SIMT) {
       // enough 64x64 tiles to fill the GPU twice, else the small tile
       int64_t t64 = ((M + 63) / 64) * ((N + 63) / 64) * std::max<int64_t>(Bt, 1);
       tile = t64 >= 2 * 152 ? 0 : 1;
+    } else if (kernel == K_GEMM_TC) {
+      // packed operands (split once, moved by bulk copies) for one GEMM; the
+      // gathering kernel for a batch of GEMMs (the slicing mapping)
+      tile = Bt == 1 ? kTilePacked : 0;
     } else {
       tile = 0;
     }
@@ -579,6 +587,7 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   ws = (ws + 255) & ~(size_t)255;
   if (P->copy_which) ws += ((size_t)P->copy_elems * es + 255) & ~(size_t)255;
   if (kernel == K_GEMM_FP8) ws += fp8_layout(g).bytes;
+  if (kernel == K_GEMM_TC && tile == kTilePacked) ws += pk_layout(g, math).bytes;
   P->workspace = ws;
 
   info.mapping = map;

@@ -124,6 +124,17 @@ Fp8Layout fp8_layout(const GemmArgs& a);
 // Pack both operands into `ws` (16-byte aligned) and run the FP8 GEMM.
 tc_status launch_gemm_fp8(const GemmArgs& a, void* ws, void* stream);
 tc_status tc_fp8_read_status(int* h, void* stream);
+
+// Split-BF16 forms with packed operands (tile configuration kTilePacked of
+// the tensor-core GEMM): workspace layout and launcher.
+constexpr int kTilePacked = 3;
+struct PkLayout {
+  int64_t tiles_m, tiles_n, nkb;
+  size_t off_qa, off_qb, bytes;
+};
+PkLayout pk_layout(const GemmArgs& a, int math);
+tc_status launch_gemm_tc_packed(const GemmArgs& a, int math, void* ws, void* stream);
+tc_status tc_pk_read_status(int* h, void* stream);
 int num_tiles_simt(tc_dtype dt);
 int num_tiles_gemv();
 

@@ -208,3 +208,20 @@ def test_fp8_k_order_follows_a_whichever_operand_is_first():
     p = ts.problem("kord", "aij", "jib", "ba", dict(a=150, i=20, j=30, b=140), 71)
     info = plan_info(p, tc.MATH["fp8"], dtype=tc.TC_F32)
     assert info.swapped == 1 and info.K == 600
+
+
+def test_tensor_core_tile_defaults():
+    # one GEMM: packed operands (tile 3) with a workspace; a batch of GEMMs
+    # (the slicing mapping): the gathering kernel, no workspace
+    p = ts.fused_permute_48(n=40)
+    bf = tc.MATH["bf16x6"]
+    info = plan_info(p, bf, dtype=tc.TC_F32)
+    assert info.tile == 3 and info.batch == 1
+    tm, tn, nkb = -(-info.M // 128), -(-info.N // 128), -(-info.K // 32)
+    r = lambda x: -(-x // 256) * 256
+    assert info.workspace == r(tm * nkb * 3 * 8192) + r(tn * nkb * 3 * 8192)
+    s = ts.slice_gemm_48()
+    info = plan_info(s, bf, tc.MAPPING["slice_gemm"], dtype=tc.TC_F32)
+    assert info.batch > 1 and info.tile == 0 and info.workspace == 0
+    assert tc.tc_plan_status(_t(s.A), _t(s.B), _t(s.C), tc.TC_F32, bf,
+                             tc.MAPPING["slice_gemm"], 3) == 5

@@ -41,18 +41,25 @@ def shapes():
     ]
 
 
+# tile 0: operands gathered and split inside the GEMM; tile 3: packed operands
+# (a pack pass splits them once, the GEMM moves the terms with bulk copies)
+TILES = [0, 3]
+
+
+@pytest.mark.parametrize("tile", TILES)
 @pytest.mark.parametrize("form", FORMS)
-def test_integer_inputs_exact(form):
+def test_integer_inputs_exact(form, tile):
     p = ts.problem("int", "iajb", "jcid", "abcd", dict(i=9, a=70, j=11, b=3, c=65, d=2), 61,
                    dist="int", dtype=np.float32, lo=-4, hi=4)
-    got = run(p, form, "auto")
+    got = run(p, form, "fused_gemm", tile)
     np.testing.assert_array_equal(got, oracle.contract_problem(p))
 
 
+@pytest.mark.parametrize("tile", TILES)
 @pytest.mark.parametrize("form", FORMS)
-def test_forms_against_method_and_fp64_oracles(form):
+def test_forms_against_method_and_fp64_oracles(form, tile):
     for p in shapes():
-        got = run(p, form, "auto")
+        got = run(p, form, "fused_gemm", tile)
         mag = magnitude(p)
         acc, tot = tc_bounds(p, form)
         ok, d = within(got, op.contract_form(p, form), mag, p.C, acc)
@@ -79,13 +86,29 @@ def test_chunk_configurations(tile):
         assert within(got, op.contract_form(p, form), mag, p.C, acc)[0], (tile, form)
 
 
-def test_alpha_beta_tc():
+@pytest.mark.parametrize("tile", TILES)
+def test_alpha_beta_tc(tile):
     p = f32(ts.direct_gemm_64(n=21))
     p.C.data = np.linspace(-2, 2, p.C.data.size).astype(np.float32)
     p.alpha, p.beta = -1.5, 0.25
-    got = run(p, "bf16x6", "auto")
+    got = run(p, "bf16x6", "fused_gemm", tile)
     acc, _ = tc_bounds(p, "bf16x6")
-    assert within(got, op.contract_form(p, "bf16x6"), magnitude(p), p.C, acc)[0]
+    mag = magnitude(p) + abs(p.beta) * np.abs(p.C.data.astype(np.float64))
+    assert within(got, op.contract_form(p, "bf16x6"), mag, p.C, acc)[0]
+
+
+def test_packed_ragged_and_long_k():
+    """Packed operands: K not a multiple of 32 or 128, one-row tiles, K spanning
+    many chunks, every form."""
+    cases = [f32(ts.problem("r1", "ai", "ib", "ab", dict(a=129, i=45, b=131), 81)),
+             f32(ts.problem("r2", "aijb", "ijc", "abc", dict(a=3, i=7, j=5, b=70, c=200), 82)),
+             f32(ts.problem("r3", "ai", "ib", "ab", dict(a=200, i=3000, b=150), 83))]
+    for p in cases:
+        for form in FORMS:
+            got = run(p, form, "fused_gemm", 3)
+            acc, _ = tc_bounds(p, form)
+            ok, d = within(got, op.contract_form(p, form), magnitude(p), p.C, acc)
+            assert ok, (p.name, form, d)
 
 
 def test_precision_workload_full_size_sampled():
@@ -101,8 +124,8 @@ def test_precision_workload_full_size_sampled():
     pm.A.data = np.abs(p.A.data)
     pm.B.data = np.abs(p.B.data)
     mag = sample_outputs(pm, s)
-    for form in FORMS:
-        got = run(p, form, "auto")
+    for form, tile in [(f, t) for f in FORMS for t in TILES]:
+        got = run(p, form, "fused_gemm", tile)
         g = gather(got, p.C, s)
         acc, tot = tc_bounds(p, form)
         assert np.linalg.norm(g - sample_outputs_form(p, s, form)) <= acc * np.linalg.norm(mag), form
