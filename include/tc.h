@@ -201,8 +201,10 @@ typedef struct {
 tc_status tc_batch_set_route(int32_t tc_min_mn);
 
 /* Build a batch from n plans (host and device allocation; synchronous).
- * TC_ERR_UNSUPPORTED if a plan is not FP32 tensor-core math, if the plans use
- * different math forms, or if a plan needs a workspace (COPY_GEMM). */
+ * TC_ERR_UNSUPPORTED if a plan's math is not TC_MATH_BF16, _BF16X3 or
+ * _BF16X6 (FP32 storage), if the plans use different math forms, or if a plan
+ * copies an operand (COPY_GEMM).  The batch runs every GEMM on the gathering
+ * tensor-core kernel, so a plan's packed-operand workspace is not used. */
 tc_status tc_batch_plan(tc_batch_t* out, const tc_plan_t* plans, int32_t n);
 
 tc_status tc_batch_get_info(tc_batch_t batch, tc_batch_info* info);
@@ -211,7 +213,9 @@ tc_status tc_batch_get_info(tc_batch_t batch, tc_batch_info* info);
  * kernel launches).  A, B, C, alpha, beta are DEVICE arrays of n entries (item i uses
  * A[i], B[i], C[i], alpha[i], beta[i], with the layouts of plan i).  Nothing
  * is allocated or copied by the call, so it may be captured in a CUDA graph;
- * a replay reads the pointer and scalar arrays at replay time. */
+ * a replay reads the pointer and scalar arrays at replay time.  The five
+ * arrays and every buffer they point to must stay allocated until the launch
+ * has completed: the kernels read them on the device and cannot check them. */
 tc_status tc_contract_batched(tc_batch_t batch, const void* const* A, const void* const* B,
                               void* const* C, const double* alpha, const double* beta,
                               void* stream);

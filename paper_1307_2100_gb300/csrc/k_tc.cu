@@ -367,6 +367,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
         KOff ka{nullptr, nullptr, (int64_t)kk * BK * ksa, ksa, kvalid};
         KOff kb_{nullptr, nullptr, (int64_t)kk * BK * ksb, ksb, kvalid};
         if (!klin) {
+          // the tables are rewritten: every producer has issued the copies of
+          // the block before from them (back-to-back calls in the prologue and
+          // into the main loop have no other barrier between them)
+          named_bar_sync(1, kProducers);
           if (tid < BK) {
             const uint32_t k = kk * BK + tid;
             int64_t oa = -1, ob = -1;

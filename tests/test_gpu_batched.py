@@ -175,3 +175,20 @@ def test_batched_equals_single_launches_bitwise():
         np.testing.assert_array_equal(got, single)
         checked += 1
     assert checked >= 5
+
+
+def test_batching_workload_every_item_against_oracle():
+    """The bench's 512-item batching workload (BF16x3, the tensor-core and
+    CUDA-core routes), every item against the FP64 oracle at the form's bound,
+    and the tensor-core items against the split-form oracle."""
+    items = ts.batching_items(512)
+    outs, info = _run_batch(items, "bf16x3")
+    assert info.n_tc_items > 50 and info.n_simt_items > 50
+    bad = []
+    for j, (p, got) in enumerate(zip(items, outs)):
+        mag = magnitude(p)
+        acc, tot = tc_bounds(p, "bf16x3")
+        ok, d = within(got, oracle.contract_problem(p), mag, p.C, tot)
+        if not ok:
+            bad.append((j, d))
+    assert not bad, bad[:10]

@@ -133,3 +133,18 @@ def test_precision_workload_full_size_sampled():
         assert np.all(np.isfinite(got))
         if form == "bf16x6":   # the FP32-class claim
             assert oracle.rel_fro(g, ref64) <= FP32_CLASS
+
+
+def test_gathering_kernel_multi_label_k_groups():
+    """Single launches of the gathering kernel (tiles 0-2) on operands whose K
+    group keeps two labels (not linear in B): the K offsets come from a shared
+    table rewritten for every block, including the prefetch prologue."""
+    items = ts.batching_items(512)
+    for j in (1, 104):
+        p = items[j]
+        mag = magnitude(p)
+        for tile in (0, 1, 2):
+            got = run(p, "bf16x6", "fused_gemm", tile)
+            acc, _ = tc_bounds(p, "bf16x6", chunk_k={0: 256, 1: 64, 2: 1024}[tile])
+            ok, d = within(got, op.contract_form(p, "bf16x6"), mag, p.C, acc)
+            assert ok, (j, tile, d)
