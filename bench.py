@@ -46,9 +46,9 @@ def env_rank():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
-def workloads(alloc=None, only=None, kind="class3_fp64"):
+def workloads(alloc=None, only=None, kind="class3_fp64", precision_v=128):
     if kind == "precision":
-        return [ts.precision_ccd()]
+        return [ts.precision_ccd(v=precision_v)]
     makers = {"direct_gemm_64": ts.direct_gemm_64, "fused_permute_48": ts.fused_permute_48,
               "gemv_1024": lambda: ts.gemv_1024_full(alloc=alloc)}
     names = list(makers) if not only else [n for n in only.split(",") if n]
@@ -253,7 +253,8 @@ def run_ours(args):
                         pin_memory=True)
         return t.numpy()
 
-    probs = workloads(alloc=pinned, only=args.only, kind=args.workload)
+    probs = workloads(alloc=pinned, only=args.only, kind=args.workload,
+                      precision_v=args.precision_v)
     fp64 = args.workload == "class3_fp64"
     math = "fp64" if fp64 else args.math
     tdt = torch.float64 if fp64 else torch.float32
@@ -399,7 +400,8 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if fp64 else "f32 storage, " + math,
         "data": "synthetic (seeded uniform[-1,1), shapes of the paper's Eq. xy and Class 2)",
-        "config": {"workload": WORKLOAD if fp64 else "precision: CCD-like 128^4 x 128^2*32^2",
+        "config": {"workload": WORKLOAD if fp64 else
+                   f"precision: CCD-like {args.precision_v}^4 x {args.precision_v}^2*32^2",
                    "mapping": "auto (recipe)", "math": math,
                    "l2": "flushed between steps (256 MiB write, outside timing)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -565,6 +567,9 @@ def main(argv=None):
                     choices=["bf16", "bf16x3", "bf16x6", "fp8", "fp32"],
                     help="math of the precision workload")
     ap.add_argument("--tile", type=int, default=-1)
+    ap.add_argument("--precision-v", type=int, default=128,
+                    help="precision workload: virtual extent a=b=e=f (128 is the named "
+                         "configuration; smaller values are profiling cases)")
     ap.add_argument("--only", default="", help="comma-separated subset of the workload "
                     "(direct_gemm_64, fused_permute_48, gemv_1024), for profiling")
     args = ap.parse_args(argv)

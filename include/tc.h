@@ -234,12 +234,16 @@ tc_status tc_device_status(void* stream);
  * Sec. 3.2, where the stride-1 indices sit, the extents the recipe leaves
  * unsliced, flops and bytes).  A selector file, written by the training
  * driver (paper_1307_2100_gb300/selector.py), holds a network that predicts
- * the log2 runtime of each candidate mapping from them.  Once loaded, tc_plan
- * with TC_MAP_AUTO runs the network on the host and uses the candidate with
- * the smallest prediction among those able to compute the contraction; with
- * no selector loaded, for another dtype/math, or when a feature lies outside
- * the range seen in training, AUTO falls back to the paper's recipe. */
+ * the log2 runtime of each candidate from them.  A candidate is a mapping
+ * and, optionally, a tile configuration, encoded as
+ * TC_SELECTOR_CANDIDATE(mapping, tile) (tile -1: the plan's default).  Once
+ * loaded, tc_plan with TC_MAP_AUTO runs the network on the host and uses the
+ * candidate with the smallest prediction among those able to compute the
+ * contraction (its tile too, unless tc_plan was given one); with no selector
+ * loaded, for another dtype/math, or when a feature lies outside the range
+ * seen in training, AUTO falls back to the paper's recipe. */
 #define TC_SELECTOR_FEATURES 23
+#define TC_SELECTOR_CANDIDATE(mapping, tile) ((int32_t)(mapping) | (((int32_t)(tile) + 1) << 8))
 
 tc_status tc_plan_features(tc_plan_t plan, float* out, int32_t n);
 /* Load (replacing any loaded one) or unload the process-wide selector.
@@ -247,8 +251,9 @@ tc_status tc_plan_features(tc_plan_t plan, float* out, int32_t n);
 tc_status tc_selector_load(const char* path);
 tc_status tc_selector_unload(void);
 /* Host prediction for n feature vectors (n x TC_SELECTOR_FEATURES floats):
- * out is n x n_cand log2 runtimes, cand receives the candidates' tc_mapping
- * values (array of at least 16).  TC_ERR_NO_SELECTOR if none is loaded. */
+ * out is n x n_cand log2 runtimes, cand receives the candidates
+ * (TC_SELECTOR_CANDIDATE values, array of at least 16).  TC_ERR_NO_SELECTOR if
+ * none is loaded. */
 tc_status tc_selector_predict(const float* features, int32_t n, float* out, int32_t* cand,
                               int32_t* n_cand);
 

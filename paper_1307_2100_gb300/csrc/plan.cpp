@@ -398,6 +398,7 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   }
 
   int32_t map = mapping;
+  int32_t sel_tile = -1;  // tile configuration of the selector's candidate
   if (map == TC_MAP_AUTO) {
     int32_t cand[16], nc = 0;
     float pred[16];
@@ -405,12 +406,17 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
     if (selector_predict(P->features, dtype, math, cand, pred, &nc)) {
       const bool class3 = an.cls == 31 || an.cls == 32;
       float best = 0;
+      bool found = false;
       for (int i = 0; i < nc; ++i) {
+        const int32_t cm = cand[i] & 0xFF, ct = (cand[i] >> 8) - 1;
         const bool feasible =
-            class3 || (cand[i] != TC_MAP_SLICE_GEMM && cand[i] != TC_MAP_COPY_GEMM);
-        if (feasible && (map == TC_MAP_RECIPE || pred[i] < best)) {
-          map = cand[i];
+            cm >= TC_MAP_SLICE_GEMM && cm <= TC_MAP_DOT &&
+            (class3 || (cm != TC_MAP_SLICE_GEMM && cm != TC_MAP_COPY_GEMM));
+        if (feasible && (!found || pred[i] < best)) {
+          map = cm;
+          sel_tile = ct;
           best = pred[i];
+          found = true;
         }
       }
     }
@@ -558,6 +564,17 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
     delete P;
     return TC_ERR_UNSUPPORTED;
   }
+  // packed operands (split once, moved by bulk copies) suit one GEMM unless
+  // padding a skinny operand to 128-row tiles would more than double its
+  // packed size (beyond 64 MB of slack)
+  bool packed_ok = false;
+  if (kernel == K_GEMM_TC && Bt == 1) {
+    const double terms = math == TC_MATH_BF16 ? 1 : math == TC_MATH_BF16X3 ? 2 : 3;
+    const double dense = 2.0 * terms * 2.0 * (double)(M + N) * (double)Kt;
+    packed_ok = (double)pk_layout(g, math).bytes <= 2.0 * dense + 64.0 * (1 << 20);
+  }
+  if (tile < 0 && sel_tile >= 0 && kernel == K_GEMM_TC && (sel_tile != kTilePacked || packed_ok))
+    tile = sel_tile;  // the selector's tile configuration, where it applies
   if (kernel == K_GEMM_TC && tile == kTilePacked && Bt > 1) {
     delete P;  // packed operands: one GEMM, no batch group
     return TC_ERR_UNSUPPORTED;
@@ -568,9 +585,9 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
       int64_t t64 = ((M + 63) / 64) * ((N + 63) / 64) * std::max<int64_t>(Bt, 1);
       tile = t64 >= 2 * 152 ? 0 : 1;
     } else if (kernel == K_GEMM_TC) {
-      // packed operands (split once, moved by bulk copies) for one GEMM; the
-      // gathering kernel for a batch of GEMMs (the slicing mapping)
-      tile = Bt == 1 ? kTilePacked : 0;
+      // the gathering kernel for a batch of GEMMs (the slicing mapping) and
+      // for skinny operands
+      tile = packed_ok ? kTilePacked : 0;
     } else {
       tile = 0;
     }

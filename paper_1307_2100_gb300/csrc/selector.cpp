@@ -130,7 +130,10 @@ extern "C" tc_status tc_selector_load(const char* path) {
       dst[i]->resize(sz[i]);
       for (size_t k = 0; k < sz[i] && ok; ++k) (*dst[i])[k] = half_to_float(h[k]);
     }
-    for (int i = 0; i < C && ok; ++i) ok = S->cand[i] >= TC_MAP_SLICE_GEMM && S->cand[i] <= TC_MAP_DOT;
+    for (int i = 0; i < C && ok; ++i) {  // TC_SELECTOR_CANDIDATE(mapping, tile), tile -1..14
+      const int32_t m = S->cand[i] & 0xFF, t = S->cand[i] >> 8;
+      ok = m >= TC_MAP_SLICE_GEMM && m <= TC_MAP_DOT && t >= 0 && t <= 15;
+    }
     uint8_t extra;
     ok = ok && std::fread(&extra, 1, 1, f) == 0;  // nothing after the parameters
   }

@@ -1,12 +1,14 @@
 """The learned mapping selector: timing dataset, training and evaluation.
 
     python -m paper_1307_2100_gb300.selector generate --n 20000 --out sel_data.npz
+    python -m paper_1307_2100_gb300.selector fill --data sel_data.npz --out sel_data.npz
     python -m paper_1307_2100_gb300.selector train --data sel_data.npz --out selector.bin
     python -m paper_1307_2100_gb300.selector evaluate --data sel_data.npz --weights selector.bin
 
-Every descriptor is planned under each candidate mapping (FP32 storage,
-BF16x6 math, the FP32-class form) and timed by CUDA events (median of a few
-runs after a warm-up).  The network (libtc's tc_mlp_* kernels: forward,
+Every descriptor is planned under each candidate -- a mapping and, for the
+fused and COPY+GEMM mappings, the packed-operand or the gathering tensor-core
+kernel -- (FP32 storage, BF16x6 math, the FP32-class form) and timed by CUDA
+events (median of a few runs after a warm-up).  The network (libtc's tc_mlp_* kernels: forward,
 masked-MSE backward, Adam; FP16 working weights) learns the log2 runtime of
 every candidate from the plan's features (tc_plan_features).  Regret of a
 choice is t(choice) / t(best) - 1 against the same exhaustive timing table;
@@ -26,8 +28,20 @@ import numpy as np
 
 from . import tc
 
-CANDIDATES = ["fused_gemm", "slice_gemm", "copy_gemm", "gemv", "dot"]
-CAND_IDS = [tc.MAPPING[c] for c in CANDIDATES]
+# (name, mapping, tile configuration; -1 = the plan's default).  The fused and
+# COPY+GEMM mappings run on packed operands (tile 3) or on the gathering
+# tensor-core kernel (tile 0); the slicing mapping's batches on the latter.
+CANDIDATE_SPECS = [
+    ("fused_gemm", "fused_gemm", 3),
+    ("fused_gemm_gather", "fused_gemm", 0),
+    ("slice_gemm", "slice_gemm", -1),
+    ("copy_gemm", "copy_gemm", 3),
+    ("copy_gemm_gather", "copy_gemm", 0),
+    ("gemv", "gemv", -1),
+    ("dot", "dot", -1),
+]
+CANDIDATES = [c[0] for c in CANDIDATE_SPECS]
+CAND_IDS = [tc.MAPPING[m] | ((t + 1) << 8) for _, m, t in CANDIDATE_SPECS]
 MATH = "bf16x6"
 HIDDEN = 128
 
@@ -42,19 +56,66 @@ def _span(t):
     return 1 + sum((e - 1) * s for e, s in zip(t.extents, t.strides))
 
 
-def generate(n, seed, out, reps=5, checkpoint=500, log=sys.stderr):
-    """Time every candidate on n descriptors; save features, times (ms; NaN if
-    the candidate cannot compute it), class and the recipe's choice."""
+def _timer(ws_bytes):
+    """Device buffers and a function timing one planned candidate (median of
+    `reps` runs after a warm-up, ms; None if the workspace does not fit)."""
     import torch
-    import tcsynth as ts
     dev = torch.device("cuda", 0)
-    descs = ts.selector_descriptors(n, seed=seed)
-    big = max(max(_span(a), _span(b), _span(c)) for a, b, c in descs)
-    arena = [torch.rand(big, device=dev) * 2 - 1 for _ in range(2)]
-    cbuf = torch.zeros(big, device=dev)
-    ws = torch.empty(1 << 28, dtype=torch.uint8, device=dev)
+    state = {"big": 0, "arena": None, "cbuf": None}
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
     s = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def ensure(big):
+        if big > state["big"]:
+            state["arena"] = [torch.rand(big, device=dev) * 2 - 1 for _ in range(2)]
+            state["cbuf"] = torch.zeros(big, device=dev)
+            state["big"] = big
+
+    def time_plan(h, reps):
+        w = tc.tc_plan_get_info(h).workspace
+        if w > ws.numel():
+            return None
+        arena, cbuf = state["arena"], state["cbuf"]
+        args = (h, 1.0, arena[0].data_ptr(), arena[1].data_ptr(), 0.0, cbuf.data_ptr(),
+                ws.data_ptr(), ws.numel(), s.cuda_stream)
+        tc.tc_contract(*args)                        # warm-up
+        times = []
+        for _ in range(reps):
+            e0.record(s)
+            tc.tc_contract(*args)
+            e1.record(s)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            if times[0] > 50.0:                       # long runs: one sample
+                break
+        return float(np.median(times))
+
+    return ensure, time_plan, s
+
+
+def _time_candidates(desc, j, time_plan, reps):
+    A, B, C = desc
+    _, mname, tile = CANDIDATE_SPECS[j]
+    try:
+        h = tc.tc_plan(_desc(A), _desc(B), _desc(C), tc.TC_F32, tc.MATH[MATH],
+                       tc.MAPPING[mname], tile)
+    except tc.TcError:
+        return None
+    try:
+        return time_plan(h, reps)
+    finally:
+        tc.tc_plan_destroy(h)
+
+
+def generate(n, seed, out, reps=5, checkpoint=500, ws_bytes=1 << 28, log=sys.stderr):
+    """Time every candidate on n descriptors; save features, times (ms; NaN if
+    the candidate cannot compute it or its workspace exceeds ws_bytes), class
+    and the recipe's choice."""
+    import tcsynth as ts
+    descs = ts.selector_descriptors(n, seed=seed)
+    ensure, time_plan, s = _timer(ws_bytes)
+    ensure(max(max(_span(a), _span(b), _span(c)) for a, b, c in descs))
     F = np.zeros((n, tc.N_FEATURES), np.float32)
     T = np.full((n, len(CANDIDATES)), np.nan, np.float64)
     cls = np.zeros(n, np.int32)
@@ -74,31 +135,10 @@ def generate(n, seed, out, reps=5, checkpoint=500, log=sys.stderr):
         cls[i] = info.cls
         recipe[i] = info.mapping
         tc.tc_plan_destroy(h)
-        for j, cname in enumerate(CANDIDATES):
-            try:
-                h = tc.tc_plan(_desc(A), _desc(B), _desc(C), tc.TC_F32, tc.MATH[MATH],
-                               tc.MAPPING[cname])
-            except tc.TcError:
-                continue
-            try:
-                w = tc.tc_plan_get_info(h).workspace
-                if w > ws.numel():
-                    continue
-                args = (h, 1.0, arena[0].data_ptr(), arena[1].data_ptr(), 0.0, cbuf.data_ptr(),
-                        ws.data_ptr(), ws.numel(), s.cuda_stream)
-                tc.tc_contract(*args)                        # warm-up
-                times = []
-                for r in range(reps):
-                    e0.record(s)
-                    tc.tc_contract(*args)
-                    e1.record(s)
-                    e1.synchronize()
-                    times.append(e0.elapsed_time(e1))
-                    if times[0] > 50.0:                       # long runs: one sample
-                        break
-                T[i, j] = float(np.median(times))
-            finally:
-                tc.tc_plan_destroy(h)
+        for j in range(len(CANDIDATES)):
+            t = _time_candidates(descs[i], j, time_plan, reps)
+            if t is not None:
+                T[i, j] = t
         if (i + 1) % checkpoint == 0 or i + 1 == n:
             np.savez(out + ".partial.npz", F=F, T=T, cls=cls, recipe=recipe, done=i + 1)
             print(f"[selector] {i + 1}/{n} descriptors, {time.time() - t0:.0f} s", file=log,
@@ -109,6 +149,32 @@ def generate(n, seed, out, reps=5, checkpoint=500, log=sys.stderr):
              seed=seed)
     if os.path.exists(out + ".partial.npz"):
         os.remove(out + ".partial.npz")
+    return out
+
+
+def fill(data, out, reps=5, ws_bytes=1 << 31, log=sys.stderr):
+    """Time the candidates a dataset lacks (NaN) whose plans exist and whose
+    workspace fits ws_bytes; write the completed dataset to out."""
+    import tcsynth as ts
+    z = dict(np.load(data))
+    T = z["T"].copy()
+    descs = ts.selector_descriptors(len(T), seed=int(z["seed"]))
+    ensure, time_plan, s = _timer(ws_bytes)
+    todo = [(i, j) for i, j in zip(*np.where(~np.isfinite(T)))]
+    rows = sorted({i for i, _ in todo})
+    if rows:
+        ensure(max(max(_span(a), _span(b), _span(c)) for a, b, c in (descs[i] for i in rows)))
+    filled = 0
+    for i, j in todo:
+        t = _time_candidates(descs[i], j, time_plan, reps)
+        if t is not None:
+            T[i, j] = t
+            filled += 1
+    if tc.tc_device_status(s.cuda_stream) != tc.TC_OK:
+        raise RuntimeError("device status not ok after timing")
+    print(f"[selector] filled {filled} of {len(todo)} missing timings", file=log, flush=True)
+    z["T"] = T
+    np.savez(out, **z)
     return out
 
 
@@ -207,9 +273,32 @@ def feasible(cls):
     COPY+GEMM need a free index in each operand (Class 3)."""
     ok = np.ones((len(cls), len(CANDIDATES)), bool)
     c3 = np.isin(cls, [31, 32])
-    ok[~c3, CANDIDATES.index("slice_gemm")] = False
-    ok[~c3, CANDIDATES.index("copy_gemm")] = False
+    for j, (_, mname, _t) in enumerate(CANDIDATE_SPECS):
+        if mname in ("slice_gemm", "copy_gemm"):
+            ok[~c3, j] = False
     return ok
+
+
+def planned_candidates(seed, n, holdout, mapping="recipe"):
+    """Candidate index of what tc_plan decides (mapping and tile) for each
+    held-out descriptor, planned again on the host: mapping "recipe" is the
+    paper's recipe, "auto" the loaded selector."""
+    import tcsynth as ts
+    descs = ts.selector_descriptors(n, seed=seed)
+    _, te = split(n, holdout)
+    spec = {(tc.MAPPING[m], t): j for j, (_, m, t) in enumerate(CANDIDATE_SPECS)}
+    out = np.zeros(len(te), np.int64)
+    for r, i in enumerate(te):
+        A, B, C = descs[i]
+        h = tc.tc_plan(_desc(A), _desc(B), _desc(C), tc.TC_F32, tc.MATH[MATH],
+                       tc.MAPPING[mapping])
+        try:
+            info = tc.tc_plan_get_info(h)
+        finally:
+            tc.tc_plan_destroy(h)
+        m, t = int(info.mapping), int(info.tile)
+        out[r] = spec.get((m, t), spec.get((m, -1), 0))
+    return out
 
 
 def regret_stats(choice_t, best_t):
@@ -230,17 +319,19 @@ def evaluate(data, weights, holdout=2000, use_gpu=True):
     F, T, cls, recipe, ran = F[keep], T[keep], cls[keep], recipe[keep], ran[keep]
     ok = feasible(cls) & ran
     best = np.where(ok, T, np.inf).min(axis=1)
+    seed, n_all = int(z["seed"]), len(z["F"])
     tc.tc_selector_load(weights)
     try:
         pred, cand = tc.tc_selector_predict(F)
+        # what tc_plan(AUTO) runs with this network loaded
+        choice = planned_candidates(seed, n_all, holdout, "auto")[keep]
     finally:
         tc.tc_selector_unload()
     gpu_pred = None
     if use_gpu:
         gpu_pred = gpu_forward(weights, F)
-    choice = np.argmin(np.where(ok, pred, np.inf), axis=1)
     t_choice = T[np.arange(len(T)), choice]
-    rec_idx = np.array([CAND_IDS.index(m) if m in CAND_IDS else 0 for m in recipe])
+    rec_idx = planned_candidates(seed, n_all, holdout, "recipe")[keep]
     t_recipe = np.where(ok[np.arange(len(T)), rec_idx], T[np.arange(len(T)), rec_idx], np.inf)
     res = {"n": int(len(T)), "network": regret_stats(t_choice, best),
            "recipe": regret_stats(t_recipe, best),
@@ -297,6 +388,10 @@ def main(argv=None):
     t.add_argument("--out", required=True)
     t.add_argument("--epochs", type=int, default=400)
     t.add_argument("--holdout", type=int, default=2000)
+    fl = sub.add_parser("fill")
+    fl.add_argument("--data", required=True)
+    fl.add_argument("--out", required=True)
+    fl.add_argument("--ws-gb", type=float, default=2.0)
     e = sub.add_parser("evaluate")
     e.add_argument("--data", required=True)
     e.add_argument("--weights", required=True)
@@ -304,6 +399,8 @@ def main(argv=None):
     a = ap.parse_args(argv)
     if a.cmd == "generate":
         generate(a.n, a.seed, a.out, a.reps)
+    elif a.cmd == "fill":
+        fill(a.data, a.out, ws_bytes=int(a.ws_gb * (1 << 30)))
     elif a.cmd == "train":
         train(a.data, a.out, a.holdout, a.epochs)
     else:

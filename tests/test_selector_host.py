@@ -54,16 +54,25 @@ def test_malformed_selector_file_is_rejected(tmp_path):
     assert e.value.status == 9   # no selector loaded
 
 
-def _plan_mapping(p):
+def _plan_choice(p):
     h = tc.tc_plan((p.A.labels, p.A.extents, p.A.strides), (p.B.labels, p.B.extents, p.B.strides),
                    (p.C.labels, p.C.extents, p.C.strides), tc.TC_F32, tc.MATH["bf16x6"])
     try:
-        return tc.MAPPING_NAME[tc.tc_plan_get_info(h).mapping]
+        info = tc.tc_plan_get_info(h)
+        return tc.MAPPING_NAME[info.mapping], info.tile
     finally:
         tc.tc_plan_destroy(h)
 
 
-@pytest.mark.parametrize("favoured", ["dot", "copy_gemm", "gemv"])
+def _plan_mapping(p):
+    return _plan_choice(p)[0]
+
+
+SPEC = {name: (m, t) for name, m, t in sel.CANDIDATE_SPECS}
+
+
+@pytest.mark.parametrize("favoured", ["dot", "copy_gemm", "copy_gemm_gather", "gemv",
+                                      "fused_gemm_gather"])
 def test_auto_mapping_follows_the_selector(tmp_path, favoured):
     # a network whose output is its bias alone: the favoured candidate is fastest
     n = mlp.n_params(F, H, C)
@@ -75,22 +84,51 @@ def test_auto_mapping_follows_the_selector(tmp_path, favoured):
     _write(path, params)
     p3 = ts.fused_permute_48(n=6)           # Class 3.1
     p2 = ts.gemv_1024(a=6, b=5, i=7)        # Class 2
-    assert _plan_mapping(p3) == "fused_gemm"  # the recipe without a selector
+    assert _plan_choice(p3) == ("fused_gemm", 3)  # the recipe without a selector
     tc.tc_selector_load(path)
     try:
-        assert _plan_mapping(p3) == favoured
-        # copy_gemm cannot compute a Class 2 contraction: the next best is used
-        want2 = favoured if favoured != "copy_gemm" else "fused_gemm"
-        assert _plan_mapping(p2) == want2
+        m, t = SPEC[favoured]
+        got = _plan_choice(p3)
+        assert got[0] == m and (t < 0 or got[1] == t), got
+        # COPY+GEMM cannot compute a Class 2 contraction: the first of the
+        # equally predicted others (fused_gemm on packed operands) is used
+        m2, t2 = (m, t) if m != "copy_gemm" else ("fused_gemm", 3)
+        got2 = _plan_choice(p2)
+        assert got2[0] == m2 and (t2 < 0 or got2[1] == t2), got2
     finally:
         tc.tc_selector_unload()
-    assert _plan_mapping(p3) == "fused_gemm"
+    assert _plan_choice(p3) == ("fused_gemm", 3)
+
+
+def test_explicit_tile_overrides_the_selector(tmp_path):
+    n = mlp.n_params(F, H, C)
+    params = np.zeros(n, np.float32)
+    b3 = np.full(C, 10.0, np.float32)
+    b3[sel.CANDIDATES.index("fused_gemm_gather")] = 1.0
+    params[-C:] = b3
+    path = str(tmp_path / "sel.bin")
+    _write(path, params)
+    p = ts.fused_permute_48(n=6)
+    tc.tc_selector_load(path)
+    try:
+        h = tc.tc_plan(_t(p.A), _t(p.B), _t(p.C), tc.TC_F32, tc.MATH["bf16x6"], 0, 3)
+        try:
+            info = tc.tc_plan_get_info(h)
+            assert tc.MAPPING_NAME[info.mapping] == "fused_gemm" and info.tile == 3
+        finally:
+            tc.tc_plan_destroy(h)
+    finally:
+        tc.tc_selector_unload()
+
+
+def _t(t):
+    return (t.labels, t.extents, t.strides)
 
 
 def test_auto_falls_back_to_recipe_outside_training_range(tmp_path):
     n = mlp.n_params(F, H, C)
     params = np.zeros(n, np.float32)
-    params[-C:] = np.array([5, 5, 5, 5, 1], np.float32)   # would pick dot
+    params[-C:] = np.where(np.array(sel.CANDIDATES) == "dot", 1.0, 5.0)   # would pick dot
     lo = np.full(F, 10.0, np.float32)                      # every feature below range
     hi = np.full(F, 11.0, np.float32)
     path = str(tmp_path / "sel.bin")
