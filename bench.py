@@ -463,13 +463,20 @@ def run_batching(args):
                                  (p.C.labels, p.C.extents, p.C.strides), "f32", math, "auto"))
         bufs.append((torch.from_numpy(p.A.data).to(dev), torch.from_numpy(p.B.data).to(dev),
                      torch.empty(max(p.C.data.size, 1), dtype=torch.float32, device=dev)))
-    batch = tc.tc_batch_plan([pl.handle for pl in plans])
-    info = tc.tc_batch_get_info(batch)
     ptr = lambda k: torch.tensor([b[k].data_ptr() for b in bufs], dtype=torch.int64, device=dev)
     pa, pb, pc = ptr(0), ptr(1), ptr(2)
     al = torch.ones(len(items), dtype=torch.float64, device=dev)
     be = torch.zeros(len(items), dtype=torch.float64, device=dev)
     s = torch.cuda.Stream(device=dev)
+    handles = [pl.handle for pl in plans]
+    tuned = None
+    if args.no_autotune:
+        batch = tc.tc_batch_plan(handles)
+    else:  # routes per size bucket, chosen by timing (outside the timed region)
+        from paper_1307_2100_gb300 import autotune
+        routes, tuned = autotune.tune_routes(handles, (pa, pb, pc, al, be), s)
+        batch = tc.tc_batch_plan_routes(handles, routes)
+    info = tc.tc_batch_get_info(batch)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     ws = [pl.workspace(dev) for pl in plans]
 
@@ -534,7 +541,9 @@ def run_batching(args):
         "config": {"workload": f"batching: {len(items)} contractions, orders 2-5, extents "
                                "log-uniform [8,192], 1-3 contracted, random storage orders",
                    "l2": "flushed between steps (256 MiB write, outside timing)",
-                   "launch": "one CUDA graph of tc_contract_batched"},
+                   "launch": "one CUDA graph of tc_contract_batched",
+                   "routes": "threshold rule" if args.no_autotune else
+                   "autotuned per size bucket (paper_1307_2100_gb300/autotune.py)"},
         "roofline": {"bound": "hbm" if info.min_bytes / (hbm * 1e9) >
                      flops * NPROD[math] / (bf16_peak * 1e12) else "tensor",
                      "achieved_ms": t_graph, "roofline_ms": roof_ms, "frac": roof_ms / t_graph,
@@ -543,10 +552,14 @@ def run_batching(args):
                                 "speedup": t_sep / t_graph},
         "routes": {"tensor_core_items": info.n_tc_items, "cuda_core_items": info.n_simt_items,
                    "tc_tiles": info.n_tiles, "simt_work": info.n_simt_work},
+        "autotune": None if tuned is None else {
+            "buckets": tuned["buckets"], "default_ms": tuned["default_ms"],
+            "tuned_ms": tuned["tuned_ms"],
+            "flipped": [t["bucket"] for t in tuned["trials"] if t["kept"]]},
         "rel_err_vs_fp64_oracle": {"max": float(np.max(errs)), "median": float(np.median(errs))},
         "sum_flops": flops, "sum_bytes": info.min_bytes, "clocks": clk,
         "device_status": tc.tc_status_string(status),
-        "gpu_launches": args.steps * (int(info.n_tiles > 0) + 2 * int(info.n_simt_work > 0)),
+        "gpu_launches": args.steps * (2 * int(info.n_tiles > 0) + 2 * int(info.n_simt_work > 0)),
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -563,6 +576,8 @@ def main(argv=None):
     ap.add_argument("--workload", default="class3_fp64",
                     choices=["class3_fp64", "precision", "batching"])
     ap.add_argument("--items", type=int, default=512, help="batching: number of contractions")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batching: the threshold route rule instead of tuned routes")
     ap.add_argument("--math", default="bf16x6",
                     choices=["bf16", "bf16x3", "bf16x6", "fp8", "fp32"],
                     help="math of the precision workload")

@@ -203,14 +203,26 @@ tc_status tc_batch_set_route(int32_t tc_min_mn);
 /* Build a batch from n plans (host and device allocation; synchronous).
  * TC_ERR_UNSUPPORTED if a plan's math is not TC_MATH_BF16, _BF16X3 or
  * _BF16X6 (FP32 storage), if the plans use different math forms, or if a plan
- * copies an operand (COPY_GEMM).  The batch runs every GEMM on the gathering
- * tensor-core kernel, so a plan's packed-operand workspace is not used. */
+ * copies an operand (COPY_GEMM).  The batch packs the operands of its
+ * tensor-core items into device memory of its own (a plan's workspace is not
+ * used); plans with a batch group (the slicing mapping) take the CUDA-core
+ * route. */
 tc_status tc_batch_plan(tc_batch_t* out, const tc_plan_t* plans, int32_t n);
+
+/* tc_batch_plan with a route per plan (routes may be NULL: all -1):
+ *   -1  the threshold rule of tc_batch_set_route,
+ *    0  the CUDA-core route,
+ *    1  the tensor-core route (TC_ERR_UNSUPPORTED for a plan with a batch
+ *       group); any other value is TC_ERR_INVALID_ARG.
+ * An autotuner (paper_1307_2100_gb300/autotune.py) picks routes by timing. */
+tc_status tc_batch_plan_routes(tc_batch_t* out, const tc_plan_t* plans, const int32_t* routes,
+                               int32_t n);
 
 tc_status tc_batch_get_info(tc_batch_t batch, tc_batch_info* info);
 
-/* Run every contraction of the batch asynchronously on `stream` (at most three
- * kernel launches).  A, B, C, alpha, beta are DEVICE arrays of n entries (item i uses
+/* Run every contraction of the batch asynchronously on `stream` (at most four
+ * kernel launches: pack, tensor-core GEMM, CUDA-core partial sums and final
+ * sums).  A, B, C, alpha, beta are DEVICE arrays of n entries (item i uses
  * A[i], B[i], C[i], alpha[i], beta[i], with the layouts of plan i).  Nothing
  * is allocated or copied by the call, so it may be captured in a CUDA graph;
  * a replay reads the pointer and scalar arrays at replay time.  The five

@@ -2,17 +2,21 @@
 // tc_contract_batched).
 //
 // Each contraction of a batch is routed by its GEMM view:
-//   * tensor-core route: M and N both at least `tc_min_mn` (64 by default):
-//     its 128x128 tiles join one work list, longest K first, processed by the
-//     persistent tcgen05 kernel (one CTA per SM);
+//   * tensor-core route: one GEMM (no batch group) with M and N both at least
+//     `tc_min_mn` (64 by default):
+//     one batched pack pass splits the operands of every such contraction into
+//     BF16 terms in the batch's own device memory (one CTA per operand tile and
+//     128 K), then their 128x128 tiles join one work list, longest K first,
+//     processed by the persistent packed tcgen05 kernel (one CTA per SM);
 //   * SIMT route: the low-arithmetic-intensity contractions (Class 1 and 2 and
-//     skinny Class 3 ones; the paper's BLAS-1/2 cases of Sec. 3.2.1-3.2.2),
+//     skinny Class 3 ones; the paper's BLAS-1/2 cases of Sec. 3.2.1-3.2.2) and
+//     plans of the slicing mapping (a batch group of GEMMs),
 //     where a 128x128 tile would waste most of its work: a batched CUDA-core
 //     kernel computes partial sums over K segments into the batch's own
 //     workspace and a second kernel adds the segments of each output in order
 //     (deterministic) and applies alpha and beta.  Long K is split so that even
 //     a single-output contraction spreads over many SMs.
-// The three kernels are launched back to back on the caller's stream; nothing
+// The four kernels are launched back to back on the caller's stream; nothing
 // is allocated or copied per call, so tc_contract_batched may be captured in a
 // CUDA graph.
 #include <cuda_runtime.h>
@@ -57,12 +61,15 @@ struct Batch {
   int32_t math;
   double flops, min_bytes;
   int32_t n_tc_items, n_simt_items;
-  int64_t n_tc_work, n_simt_work, n_simt_final;
+  int64_t n_tc_work, n_simt_work, n_simt_final, n_pack;
   GemmArgs* d_items;
   TcWork* d_tc_work;
   SimtWork* d_simt_work;
   SimtFinal* d_simt_final;
   double* d_partials;
+  PkItem* d_pk;          // per item: the packed GEMM of tensor-core items
+  int32_t* d_pack;       // pack entries (item, operand, row tile, 128-K chunk)
+  uint8_t* d_pkws;       // packed operands of every tensor-core item
 };
 
 template <typename T>
@@ -205,6 +212,9 @@ void free_batch(Batch* B) {
   cudaFree(B->d_simt_work);
   cudaFree(B->d_simt_final);
   cudaFree(B->d_partials);
+  cudaFree(B->d_pk);
+  cudaFree(B->d_pack);
+  cudaFree(B->d_pkws);
   delete B;
 }
 
@@ -223,9 +233,18 @@ extern "C" tc_status tc_batch_set_route(int32_t tc_min_mn) {
 }
 
 extern "C" tc_status tc_batch_plan(tc_batch_t* out, const tc_plan_t* plans, int32_t n) {
+  return tc_batch_plan_routes(out, plans, nullptr, n);
+}
+
+extern "C" tc_status tc_batch_plan_routes(tc_batch_t* out, const tc_plan_t* plans,
+                                          const int32_t* routes, int32_t n) {
   if (!out || (!plans && n > 0) || n < 0) return TC_ERR_INVALID_ARG;
   *out = nullptr;
   std::vector<GemmArgs> items((size_t)n);
+  std::vector<PkItem> pk((size_t)n);
+  std::vector<size_t> pk_off((size_t)n, 0);   // packed operands of item i in the workspace
+  std::vector<int32_t> pack;                   // (item, operand, row tile, 128-K chunk)
+  size_t pk_bytes = 0;
   std::vector<std::pair<uint64_t, TcWork>> tcw;  // (cost, entry)
   std::vector<SimtWork> sw;
   std::vector<SimtFinal> sf;
@@ -248,9 +267,39 @@ extern "C" tc_status tc_batch_plan(tc_batch_t* out, const tc_plan_t* plans, int3
     items[i] = a;
     flops += P->info.flops;
     bytes += P->info.min_bytes;
-    if (a.M >= g_tc_min_mn && a.N >= g_tc_min_mn) {
+    const int32_t route = routes ? routes[i] : -1;
+    if (route < -1 || route > 1) return TC_ERR_INVALID_ARG;
+    if (route == 1 && a.nbatch != 1) return TC_ERR_UNSUPPORTED;
+    const bool to_tc =
+        route == 1 || (route == -1 && a.M >= g_tc_min_mn && a.N >= g_tc_min_mn && a.nbatch == 1);
+    if (to_tc) {
       ++ntc;
-      const uint64_t t = tc_gemm_tiles(a);
+      const PkLayout L = pk_layout(a, math);
+      pk_off[i] = pk_bytes;
+      pk_bytes += L.bytes;
+      PkItem& it = pk[i];
+      std::memset(&it, 0, sizeof(it));
+      it.gm = a.gm;
+      it.gn = a.gn;
+      it.M = a.M;
+      it.N = a.N;
+      it.tiles_m = (int32_t)L.tiles_m;
+      it.tiles_n = (int32_t)L.tiles_n;
+      it.nkb = (int32_t)L.nkb;
+      it.chunk_kb = a.chunk_kb;
+      it.raster = 0;
+      it.qa = reinterpret_cast<const uint8_t*>(L.off_qa);   // offsets until allocation
+      it.qb = reinterpret_cast<const uint8_t*>(L.off_qb);
+      const int32_t npk = (int32_t)((L.nkb + 3) / 4);
+      for (int32_t o = 0; o < 2; ++o)
+        for (int32_t t = 0; t < (o ? L.tiles_n : L.tiles_m); ++t)
+          for (int32_t kc = 0; kc < npk; ++kc) {
+            pack.push_back(i);
+            pack.push_back(o);
+            pack.push_back(t);
+            pack.push_back(kc);
+          }
+      const uint64_t t = (uint64_t)L.tiles_m * (uint64_t)L.tiles_n;
       const uint64_t cost = (uint64_t)((a.K + 63) / 64) + 2;  // per tile
       for (uint64_t k = 0; k < t; ++k) tcw.push_back({cost, TcWork{i, (int32_t)k}});
     } else {
@@ -299,7 +348,18 @@ extern "C" tc_status tc_batch_plan(tc_batch_t* out, const tc_plan_t* plans, int3
   B->n_tc_work = (int64_t)tw.size();
   B->n_simt_work = (int64_t)sw.size();
   B->n_simt_final = (int64_t)sf.size();
+  B->n_pack = (int64_t)(pack.size() / 4);
+  if (pk_bytes > 0 && cudaMalloc(reinterpret_cast<void**>(&B->d_pkws), pk_bytes) != cudaSuccess) {
+    free_batch(B);
+    return TC_ERR_CUDA;
+  }
+  for (int32_t i = 0; i < n; ++i)
+    if (pk[i].nkb > 0) {  // tensor-core items: offsets -> device addresses
+      pk[i].qa = B->d_pkws + pk_off[i] + reinterpret_cast<size_t>(pk[i].qa);
+      pk[i].qb = B->d_pkws + pk_off[i] + reinterpret_cast<size_t>(pk[i].qb);
+    }
   if (upload(&B->d_items, items) != cudaSuccess || upload(&B->d_tc_work, tw) != cudaSuccess ||
+      upload(&B->d_pk, pk) != cudaSuccess || upload(&B->d_pack, pack) != cudaSuccess ||
       upload(&B->d_simt_work, sw) != cudaSuccess || upload(&B->d_simt_final, sf) != cudaSuccess ||
       (slots > 0 && cudaMalloc(reinterpret_cast<void**>(&B->d_partials),
                                sizeof(double) * (size_t)slots) != cudaSuccess)) {
@@ -333,8 +393,14 @@ extern "C" tc_status tc_contract_batched(tc_batch_t batch, const void* const* A,
   if (!A || !B || !C || !alpha || !beta) return TC_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (Bt->n_tc_work > 0) {
-    tc_status st = launch_gemm_tc_batch(Bt->d_items, Bt->d_tc_work, Bt->n_tc_work, A, B, C,
-                                        alpha, beta, Bt->math, stream);
+    PkBatch pb;
+    pb.items = Bt->d_items;
+    pb.pk = Bt->d_pk;
+    pb.pack_work = Bt->d_pack;
+    pb.n_pack = Bt->n_pack;
+    pb.work = reinterpret_cast<const int32_t*>(Bt->d_tc_work);
+    pb.n_work = Bt->n_tc_work;
+    tc_status st = launch_gemm_tc_packed_batch(pb, A, B, C, alpha, beta, Bt->math, stream);
     if (st != TC_OK) return st;
   }
   if (Bt->n_simt_work > 0) {

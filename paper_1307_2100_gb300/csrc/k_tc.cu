@@ -1,5 +1,6 @@
-// k_tc.cu -- the tensor-core GEMM over gathered index groups (sm_103a, tcgen05),
-// for one contraction or a batch of contractions in one persistent launch.
+// k_tc.cu -- the tensor-core GEMM over gathered index groups (sm_103a, tcgen05):
+// tile configurations 0-2 of a single contraction, and the slicing mapping's
+// batches of GEMMs (whose batch group the packed kernel does not take).
 //
 // C[m, n, b] = alpha * sum_k A[m, k, b] * B[k, n, b] + beta * C[m, n, b] for
 // FP32 tensors of any layout, computed as a sum of BF16 products:
@@ -57,20 +58,9 @@ constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t COL_MAIN = 0, COL_CORR = 256, COL_HI = 384;
 constexpr uint64_t kTimeoutNs = 2000000000ull;  // 2 s per wait
 
-struct Work {
-  int32_t item, tile;
-};
-
 struct Launch {
-  GemmArgs single;             // one contraction (items == nullptr)
-  const GemmArgs* items;       // batch: per-item arguments (device)
-  const Work* work;            // batch: (item, tile) entries (device)
-  int64_t nwork;
-  const void* const* Ap;       // batch: device arrays of per-item pointers and scalars
-  const void* const* Bp;
-  void* const* Cp;
-  const double* alpha;
-  const double* beta;
+  GemmArgs single;             // the contraction
+  int64_t nwork;               // its tiles
 };
 
 template <int NT>
@@ -278,33 +268,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
 
   uint32_t g_kb = 0;     // K blocks processed by this CTA (stage ring position)
   uint32_t g_chunk = 0;  // K chunks processed by this CTA (accumulator ring position)
-  int cur_item = -2;
+  {  // the contraction's arguments, once
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&L.single);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(sargs);
+    for (int i = tid; i < (int)(sizeof(GemmArgs) / 4); i += kThreads) dst[i] = src[i];
+  }
 
   for (int64_t w = blockIdx.x; w < L.nwork; w += gridDim.x) {
-    // ---- the tile's arguments
-    int item = -1;
-    uint32_t tile = (uint32_t)w;
-    if (L.items) {
-      const Work wk = L.work[w];
-      item = wk.item;
-      tile = (uint32_t)wk.tile;
-    }
-    if (item != cur_item) {
-      const uint32_t* src = item >= 0 ? reinterpret_cast<const uint32_t*>(L.items + item)
-                                      : reinterpret_cast<const uint32_t*>(&L.single);
-      uint32_t* dst = reinterpret_cast<uint32_t*>(sargs);
-      for (int i = tid; i < (int)(sizeof(GemmArgs) / 4); i += kThreads) dst[i] = src[i];
-      __syncthreads();
-      if (item >= 0 && tid == 0) {
-        const bool sw = sargs->swapped != 0;
-        sargs->A = sw ? L.Bp[item] : L.Ap[item];
-        sargs->B = sw ? L.Ap[item] : L.Bp[item];
-        sargs->C = L.Cp[item];
-        sargs->alpha = L.alpha[item];
-        sargs->beta = L.beta[item];
-      }
-      cur_item = item;
-    }
+    const uint32_t tile = (uint32_t)w;
     __syncthreads();
     const GemmArgs& p = *sargs;
     const uint32_t M = (uint32_t)p.M, N = (uint32_t)p.N, K = (uint32_t)p.K;
@@ -638,23 +609,5 @@ tc_status launch_gemm_tc(const GemmArgs& a, int math, void* stream) {
   if ((uint64_t)L.nwork > 0x7fffffffull) return TC_ERR_UNSUPPORTED;
   return tcg::launch_math(L, math, static_cast<cudaStream_t>(stream));
 }
-
-tc_status launch_gemm_tc_batch(const GemmArgs* d_items, const void* d_work, int64_t nwork,
-                               const void* const* A, const void* const* B, void* const* C,
-                               const double* alpha, const double* beta, int math, void* stream) {
-  tcg::Launch L;
-  std::memset(&L, 0, sizeof(L));
-  L.items = d_items;
-  L.work = static_cast<const tcg::Work*>(d_work);
-  L.nwork = nwork;
-  L.Ap = A;
-  L.Bp = B;
-  L.Cp = C;
-  L.alpha = alpha;
-  L.beta = beta;
-  return tcg::launch_math(L, math, static_cast<cudaStream_t>(stream));
-}
-
-uint64_t tc_gemm_tiles(const GemmArgs& a) { return tcg::tiles_of(a); }
 
 }  // namespace tc

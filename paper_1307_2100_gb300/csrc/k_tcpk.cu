@@ -80,31 +80,45 @@ struct PackArgs {
   int32_t rows_fast[2];
 };
 
-template <int NT>
-__global__ void __launch_bounds__(kPackThreads) k_bf16_pack(const __grid_constant__ PackArgs P) {
-  extern __shared__ float4 pk_smem[];
-  float* tile = reinterpret_cast<float*>(pk_smem);
-  int64_t* roff = reinterpret_cast<int64_t*>(tile + TILE * kLd);
-  int64_t* koff = roff + TILE;
+// Shared memory of one pack CTA: the FP32 block and its row / K offsets.
+struct PackSmem {
+  float* tile;
+  int64_t* roff;
+  int64_t* koff;
+};
 
-  int64_t bid = blockIdx.x;
-  const int o = bid < P.nblocks0 ? 0 : 1;
-  if (o) bid -= P.nblocks0;
-  const int t = (int)(bid / P.npk), kc = (int)(bid % P.npk);
+__device__ __forceinline__ PackSmem pack_smem(float4* raw) {
+  PackSmem m;
+  m.tile = reinterpret_cast<float*>(raw);
+  m.roff = reinterpret_cast<int64_t*>(m.tile + TILE * kLd);
+  m.koff = m.roff + TILE;
+  return m;
+}
+
+// Rows [128 t, 128 t + 128) x K [128 kc, 128 kc + 128) of operand o (strides
+// in slot o of gr and gk), split into NT BF16 terms and stored in the
+// operand's packed blocks Q (block kb of tile t at (t * nkb + kb) * NT * TERM).
+template <int NT>
+__device__ __forceinline__ void pack_body(const Group& gr, const Group& gk, int o,
+                                          const float* __restrict__ X, int64_t rows, int64_t K,
+                                          int t, int kc, int nkb, bool rows_fast,
+                                          uint8_t* __restrict__ Qop, const PackSmem& sm) {
+  float* tile = sm.tile;
+  int64_t* roff = sm.roff;
+  int64_t* koff = sm.koff;
   const int tid = threadIdx.x;
   if (tid < TILE) {
     const int64_t r = (int64_t)t * TILE + tid;
-    roff[tid] = r < P.rows[o] ? goff(P.gr[o], o, (uint32_t)r) : -1;
+    roff[tid] = r < rows ? goff(gr, o, (uint32_t)r) : -1;
   } else {
     const int64_t k = (int64_t)kc * PK + (tid - TILE);
-    koff[tid - TILE] = k < P.K ? goff(P.gk, o, (uint32_t)k) : -1;
+    koff[tid - TILE] = k < K ? goff(gk, o, (uint32_t)k) : -1;
   }
   __syncthreads();
 
   // gather (sixteen loads in flight per thread, then their stores)
-  const float* __restrict__ X = P.in[o];
   constexpr int NJ = TILE * PK / kPackThreads, U = 16;
-  if (P.rows_fast[o]) {
+  if (rows_fast) {
     const int r = tid & (TILE - 1), k0 = tid >> 7;
     const int64_t ro = roff[r];
 #pragma unroll
@@ -137,8 +151,8 @@ __global__ void __launch_bounds__(kPackThreads) k_bf16_pack(const __grid_constan
 
   // split and store: unit u = (k8 chunk) * 128 + row is one 16-byte row of a
   // core matrix (8 BF16 along K), at byte u * 16 of its term block
-  const int nb = min(PK / BK, P.nkb - kc * (PK / BK));   // blocks of this CTA
-  uint8_t* __restrict__ Q = P.q[o] + ((int64_t)t * P.nkb + (int64_t)kc * (PK / BK)) * NT * TERM;
+  const int nb = min(PK / BK, nkb - kc * (PK / BK));   // blocks of this CTA
+  uint8_t* __restrict__ Q = Qop + ((int64_t)t * nkb + (int64_t)kc * (PK / BK)) * NT * TERM;
   for (int u = tid; u < nb * (BK / 8) * TILE; u += kPackThreads) {
     const int blk = u / ((BK / 8) * TILE);
     const int w = u % ((BK / 8) * TILE);
@@ -164,29 +178,103 @@ __global__ void __launch_bounds__(kPackThreads) k_bf16_pack(const __grid_constan
   }
 }
 
-struct GemmPk {
-  Group gm, gn;          // C offsets in slot 2
-  const uint8_t* qa;
-  const uint8_t* qb;
-  float* C;
-  int64_t M, N, ntiles;
-  float alpha, beta;
-  int32_t tiles_m, tiles_n, nkb, chunk_kb, raster, pad_;
+template <int NT>
+__global__ void __launch_bounds__(kPackThreads) k_bf16_pack(const __grid_constant__ PackArgs P) {
+  extern __shared__ float4 pk_smem[];
+  int64_t bid = blockIdx.x;
+  const int o = bid < P.nblocks0 ? 0 : 1;
+  if (o) bid -= P.nblocks0;
+  const int t = (int)(bid / P.npk), kc = (int)(bid % P.npk);
+  pack_body<NT>(P.gr[o], P.gk, o, P.in[o], P.rows[o], P.K, t, kc, P.nkb, P.rows_fast[o] != 0,
+                P.q[o], pack_smem(pk_smem));
+}
+
+// Batched pack pass: one CTA per entry (item, operand, row tile, 128-K
+// chunk); the item's index groups are copied to shared memory first.
+struct PackWork {
+  int32_t item, o, t, kc;
 };
+
+template <int NT>
+__global__ void __launch_bounds__(kPackThreads) k_bf16_pack_batch(
+    const GemmArgs* __restrict__ items, const PkItem* __restrict__ pk, const PackWork* work,
+    const void* const* Ap, const void* const* Bp) {
+  extern __shared__ float4 pk_smem[];
+  __shared__ Group sg[2];
+  const PackWork wk = work[blockIdx.x];
+  const GemmArgs& a = items[wk.item];
+  {
+    const uint32_t* src0 = reinterpret_cast<const uint32_t*>(wk.o ? &a.gn : &a.gm);
+    const uint32_t* src1 = reinterpret_cast<const uint32_t*>(&a.gk);
+    uint32_t* d0 = reinterpret_cast<uint32_t*>(&sg[0]);
+    uint32_t* d1 = reinterpret_cast<uint32_t*>(&sg[1]);
+    for (int i = threadIdx.x; i < (int)(sizeof(Group) / 4); i += kPackThreads) {
+      d0[i] = src0[i];
+      d1[i] = src1[i];
+    }
+  }
+  __syncthreads();
+  const bool sw = a.swapped != 0;
+  const float* X = static_cast<const float*>(
+      wk.o == 0 ? (sw ? Bp[wk.item] : Ap[wk.item]) : (sw ? Ap[wk.item] : Bp[wk.item]));
+  const PkItem& it = pk[wk.item];
+  pack_body<NT>(sg[0], sg[1], wk.o, X, wk.o ? a.N : a.M, a.K, wk.t, wk.kc, it.nkb,
+                (wk.o ? a.b_contig : a.a_contig) == CONTIG_MN,
+                const_cast<uint8_t*>(wk.o ? it.qb : it.qa), pack_smem(pk_smem));
+}
+
+// One GEMM on packed operands (a single contraction, or one item of a batch).
+// The launch holds it in kernel parameters, a batch in device memory.
+struct PkLaunch {
+  PkItem single;             // items == nullptr: tiles 0 .. nwork - 1 of this GEMM
+  float* C;
+  float alpha, beta;
+  const PkItem* items;       // batch: per-item GEMMs and (item, tile) work entries
+  const int32_t* work;
+  void* const* Cp;
+  const double* alpha_p;
+  const double* beta_p;
+  int64_t nwork;
+};
+
+// The tile of work entry w.
+struct Job {
+  const PkItem* it;
+  int tm, tn;
+  float* C;
+  float alpha, beta;
+};
+
+__device__ __forceinline__ Job job_of(const PkLaunch& L, int64_t w) {
+  Job j;
+  int64_t tile = w;
+  if (L.items) {
+    const int32_t item = L.work[2 * w];
+    tile = L.work[2 * w + 1];
+    j.it = L.items + item;
+    j.C = static_cast<float*>(L.Cp[item]);
+    j.alpha = (float)L.alpha_p[item];
+    j.beta = (float)L.beta_p[item];
+  } else {
+    j.it = &L.single;
+    j.C = L.C;
+    j.alpha = L.alpha;
+    j.beta = L.beta;
+  }
+  const PkItem& P = *j.it;
+  if (P.raster) {
+    j.tn = (int)(tile % P.tiles_n);
+    j.tm = (int)(tile / P.tiles_n);
+  } else {
+    j.tm = (int)(tile % P.tiles_m);
+    j.tn = (int)(tile / P.tiles_m);
+  }
+  return j;
+}
 
 __constant__ int8_t kProdA[6] = {0, 0, 1, 0, 1, 2};
 __constant__ int8_t kProdB[6] = {0, 1, 0, 2, 1, 0};
 __host__ __device__ constexpr int nprod(int nt) { return nt == 1 ? 1 : nt == 2 ? 3 : 6; }
-
-__device__ __forceinline__ void tile_coords(const GemmPk& P, int64_t w, int& tm, int& tn) {
-  if (P.raster) {
-    tn = (int)(w % P.tiles_n);
-    tm = (int)(w / P.tiles_n);
-  } else {
-    tm = (int)(w % P.tiles_m);
-    tn = (int)(w / P.tiles_m);
-  }
-}
 
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
   bool ok = (*abort == 0) && mbar_wait(bar, parity, abort, kTimeoutNs);
@@ -203,7 +291,7 @@ __device__ __forceinline__ float two_sum(float a, float b, float& e) {
 }
 
 template <int NT>
-__global__ void __launch_bounds__(kThreads, 1) k_gemm_pk(const __grid_constant__ GemmPk P) {
+__global__ void __launch_bounds__(kThreads, 1) k_gemm_pk(const __grid_constant__ PkLaunch L) {
   using G = Cfg<NT>;
   constexpr int S = G::S;
   extern __shared__ uint8_t pk_gemm_raw[];
@@ -239,9 +327,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_pk(const __grid_constant__
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const uint32_t sbase = smem_u32(smem);
-  const int nkb = P.nkb;
-  const int ckb = max(P.chunk_kb, 1);
-  const int nchunks = (nkb + ckb - 1) / ckb;
   constexpr uint32_t OPB = NT * TERM;          // bytes of one operand's block
 
   if (warp == 0) {
@@ -249,11 +334,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_pk(const __grid_constant__
       // ------------------------------------------------------------ producer
       uint32_t g = 0;
       bool ok = true;
-      for (int64_t w = blockIdx.x; ok && w < P.ntiles; w += gridDim.x) {
-        int tm, tn;
-        tile_coords(P, w, tm, tn);
-        const uint8_t* a = P.qa + (size_t)tm * nkb * OPB;
-        const uint8_t* b = P.qb + (size_t)tn * nkb * OPB;
+      for (int64_t w = blockIdx.x; ok && w < L.nwork; w += gridDim.x) {
+        const Job J = job_of(L, w);
+        const int nkb = J.it->nkb;
+        const uint8_t* a = J.it->qa + (size_t)J.tm * nkb * OPB;
+        const uint8_t* b = J.it->qb + (size_t)J.tn * nkb * OPB;
         for (int kb = 0; kb < nkb; ++kb, ++g) {
           const int s = (int)(g % S);
           if (g >= (uint32_t)S && !mbar_wait(&empty[s], ((g / S) - 1) & 1, abort, kTimeoutNs)) {
@@ -277,7 +362,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_pk(const __grid_constant__
       constexpr uint32_t LBO = (TILE / 8) * 128;
       uint32_t g = 0, gc = 0;
       bool ok = true;
-      for (int64_t w = blockIdx.x; ok && w < P.ntiles; w += gridDim.x) {
+      for (int64_t w = blockIdx.x; ok && w < L.nwork; w += gridDim.x) {
+        const Job J = job_of(L, w);
+        const int nkb = J.it->nkb;
+        const int ckb = max(J.it->chunk_kb, 1);
+        const int nchunks = (nkb + ckb - 1) / ckb;
         // the correction accumulator and both main buffers are free once the
         // previous tile's last chunk has been drained
         if (gc >= 1 && !mbar_wait(&acce[(gc - 1) & 1], ((gc - 1) >> 1) & 1, abort, kTimeoutNs)) {
@@ -334,19 +423,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_pk(const __grid_constant__
     const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)h * 64;
     uint32_t gc = 0;
     int64_t it = 0;
-    bool live = true;
-    for (int64_t w = blockIdx.x; w < P.ntiles; w += gridDim.x, ++it) {
-      int tm, tn;
-      tile_coords(P, w, tm, tn);
+    bool live = true;  // after a wait gave up, tiles are walked without work so
+                       // that every epilogue warp still meets each named barrier
+    for (int64_t w = blockIdx.x; w < L.nwork; w += gridDim.x, ++it) {
+      const Job J = job_of(L, w);
+      const PkItem& P = *J.it;
       int64_t* cc = colC + (it & 1) * TILE;
       if (etid < TILE) {
-        const int64_t n = (int64_t)tn * TILE + etid;
+        const int64_t n = (int64_t)J.tn * TILE + etid;
         cc[etid] = n < P.N ? goff(P.gn, 2, (uint32_t)n) : -1;
       }
       named_bar_sync(1, kEpiThreads);
       if (!live) continue;
-      const int64_t m = (int64_t)tm * TILE + row;
+      const int64_t m = (int64_t)J.tm * TILE + row;
       const int64_t rc = m < P.M ? goff(P.gm, 2, (uint32_t)m) : -1;
+      const int ckb = max(P.chunk_kb, 1);
+      const int nchunks = (P.nkb + ckb - 1) / ckb;
       float lo[64];
 #pragma unroll
       for (int i = 0; i < 64; ++i) lo[i] = 0.0f;
@@ -400,13 +492,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_pk(const __grid_constant__
           tc_fence_before();
           mbar_arrive(&acce[buf]);  // main, correction and high word are free
           if (rc >= 0) {
-            float* Cr = P.C + rc;
+            float* Cr = J.C + rc;
 #pragma unroll
             for (int i = 0; i < 64; ++i) {
               const int64_t ci = cc[h * 64 + i];
               if (ci < 0) continue;
-              float x = P.alpha * lo[i];
-              if (P.beta != 0.0f) x = fmaf(P.beta, Cr[ci], x);
+              float x = J.alpha * lo[i];
+              if (J.beta != 0.0f) x = fmaf(J.beta, Cr[ci], x);
               Cr[ci] = x;
             }
           }
@@ -447,6 +539,8 @@ int set_smem() {
     if (optin < (int)Cfg<NT>::BYTES) return -2;
     if (cudaFuncSetAttribute(k_bf16_pack<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kPackSmem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_bf16_pack_batch<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kPackSmem) != cudaSuccess ||
         cudaFuncSetAttribute(k_gemm_pk<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Cfg<NT>::BYTES) != cudaSuccess)
       return -1;
@@ -486,24 +580,52 @@ tc_status launch(const GemmArgs& a, const PkLayout& L, void* ws, cudaStream_t s)
   k_bf16_pack<NT><<<(unsigned)nblocks, kPackThreads, kPackSmem, s>>>(pa);
   if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;
 
-  GemmPk g;
+  PkLaunch g;
   std::memset(&g, 0, sizeof(g));
-  g.gm = a.gm;
-  g.gn = a.gn;
-  g.qa = pa.q[0];
-  g.qb = pa.q[1];
+  PkItem& it = g.single;
+  it.gm = a.gm;
+  it.gn = a.gn;
+  it.qa = pa.q[0];
+  it.qb = pa.q[1];
+  it.M = a.M;
+  it.N = a.N;
+  it.tiles_m = (int32_t)L.tiles_m;
+  it.tiles_n = (int32_t)L.tiles_n;
+  it.nkb = (int32_t)L.nkb;
+  it.chunk_kb = a.chunk_kb;
+  it.raster = a.raster;
   g.C = static_cast<float*>(a.C);
-  g.M = a.M;
-  g.N = a.N;
-  g.ntiles = L.tiles_m * L.tiles_n;
   g.alpha = (float)a.alpha;
   g.beta = (float)a.beta;
-  g.tiles_m = (int32_t)L.tiles_m;
-  g.tiles_n = (int32_t)L.tiles_n;
-  g.nkb = (int32_t)L.nkb;
-  g.chunk_kb = a.chunk_kb;
-  g.raster = a.raster;
-  const int grid = (int)std::min<int64_t>(g.ntiles, sms);
+  g.nwork = L.tiles_m * L.tiles_n;
+  const int grid = (int)std::min<int64_t>(g.nwork, sms);
+  k_gemm_pk<NT><<<grid, kThreads, sm, s>>>(g);
+  return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+}
+
+template <int NT>
+tc_status launch_batch(const PkBatch& b, const void* const* A, const void* const* B,
+                       void* const* C, const double* alpha, const double* beta, cudaStream_t s) {
+  if (b.n_work == 0) return TC_OK;
+  const int sm = set_smem<NT>();
+  if (sm == -2) return TC_ERR_UNSUPPORTED;
+  const int sms = num_sms();
+  if (sm < 0 || sms <= 0) return TC_ERR_CUDA;
+  if (b.n_pack > 0x7fffffffll) return TC_ERR_UNSUPPORTED;
+  if (b.n_pack > 0) {
+    k_bf16_pack_batch<NT><<<(unsigned)b.n_pack, kPackThreads, kPackSmem, s>>>(
+        b.items, b.pk, reinterpret_cast<const PackWork*>(b.pack_work), A, B);
+    if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;
+  }
+  PkLaunch g;
+  std::memset(&g, 0, sizeof(g));
+  g.items = b.pk;
+  g.work = b.work;
+  g.Cp = C;
+  g.alpha_p = alpha;
+  g.beta_p = beta;
+  g.nwork = b.n_work;
+  const int grid = (int)std::min<int64_t>(g.nwork, sms);
   k_gemm_pk<NT><<<grid, kThreads, sm, s>>>(g);
   return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
 }
@@ -537,6 +659,18 @@ tc_status launch_gemm_tc_packed(const GemmArgs& a, int math, void* ws, void* str
     case TC_MATH_BF16: return pk::launch<1>(a, L, ws, s);
     case TC_MATH_BF16X3: return pk::launch<2>(a, L, ws, s);
     case TC_MATH_BF16X6: return pk::launch<3>(a, L, ws, s);
+    default: return TC_ERR_UNSUPPORTED;
+  }
+}
+
+tc_status launch_gemm_tc_packed_batch(const PkBatch& b, const void* const* A,
+                                      const void* const* B, void* const* C, const double* alpha,
+                                      const double* beta, int math, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  switch (math) {
+    case TC_MATH_BF16: return pk::launch_batch<1>(b, A, B, C, alpha, beta, s);
+    case TC_MATH_BF16X3: return pk::launch_batch<2>(b, A, B, C, alpha, beta, s);
+    case TC_MATH_BF16X6: return pk::launch_batch<3>(b, A, B, C, alpha, beta, s);
     default: return TC_ERR_UNSUPPORTED;
   }
 }

@@ -106,11 +106,6 @@ tc_status launch_scale(const Group& gc, void* C, double beta, tc_dtype dt, int64
 tc_status launch_gemm_tc(const GemmArgs& a, int math, void* stream);
 int dot_partials(const GemmArgs& a, int tile);
 int num_tiles_tc();
-// Tensor-core GEMM over a device work list of (item, tile) pairs, int32 each.
-tc_status launch_gemm_tc_batch(const GemmArgs* d_items, const void* d_work, int64_t nwork,
-                               const void* const* A, const void* const* B, void* const* C,
-                               const double* alpha, const double* beta, int math, void* stream);
-uint64_t tc_gemm_tiles(const GemmArgs& a);  // 128x128 output tiles of a GEMM view
 // Enqueue a read-and-clear of the tensor-core kernels' timeout flag into *h.
 tc_status tc_gemm_read_status(int* h, void* stream);
 int tc_chunk_kb(int math, int tile);
@@ -135,6 +130,29 @@ struct PkLayout {
 PkLayout pk_layout(const GemmArgs& a, int math);
 tc_status launch_gemm_tc_packed(const GemmArgs& a, int math, void* ws, void* stream);
 tc_status tc_pk_read_status(int* h, void* stream);
+
+// One GEMM on packed operands as the packed kernel sees it.
+struct PkItem {
+  Group gm, gn;          // C offsets (slot 2) of the GEMM's rows and columns
+  const uint8_t* qa;     // packed terms of the first and second operand
+  const uint8_t* qb;
+  int64_t M, N;
+  int32_t tiles_m, tiles_n, nkb, chunk_kb, raster, pad_;
+};
+// Tensor-core route of a batch on packed operands (device tables owned by
+// the batch): the pack entries (item, operand, row tile, 128-K chunk; int32
+// x 4) and the GEMM's (item, tile) entries (int32 x 2).
+struct PkBatch {
+  const GemmArgs* items;
+  const PkItem* pk;
+  const int32_t* pack_work;
+  int64_t n_pack;
+  const int32_t* work;
+  int64_t n_work;
+};
+tc_status launch_gemm_tc_packed_batch(const PkBatch& b, const void* const* A,
+                                      const void* const* B, void* const* C, const double* alpha,
+                                      const double* beta, int math, void* stream);
 int num_tiles_simt(tc_dtype dt);
 int num_tiles_gemv();
 

@@ -86,6 +86,8 @@ def _load():
     lib.tc_batch_set_route.argtypes = [ctypes.c_int32]
     lib.tc_batch_plan.restype = ctypes.c_int
     lib.tc_batch_plan.argtypes = [ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_int32]
+    lib.tc_batch_plan_routes.restype = ctypes.c_int
+    lib.tc_batch_plan_routes.argtypes = [ctypes.POINTER(P), ctypes.POINTER(P), P, ctypes.c_int32]
     lib.tc_batch_get_info.restype = ctypes.c_int
     lib.tc_batch_get_info.argtypes = [P, ctypes.POINTER(BatchInfo)]
     lib.tc_contract_batched.restype = ctypes.c_int
@@ -203,6 +205,21 @@ def tc_batch_plan(plans) -> int:
     st = lib.tc_batch_plan(ctypes.byref(out), arr, len(plans))
     if st != TC_OK:
         raise TcError(st, "tc_batch_plan")
+    return out.value
+
+
+def tc_batch_plan_routes(plans, routes) -> int:
+    """routes: one of -1 (threshold rule), 0 (CUDA cores), 1 (tensor cores) per plan."""
+    import numpy as np
+    arr = (ctypes.c_void_p * max(len(plans), 1))(*plans)
+    r = np.ascontiguousarray(routes, np.int32)
+    if len(r) != len(plans):
+        raise ValueError("one route per plan")
+    out = ctypes.c_void_p()
+    st = lib.tc_batch_plan_routes(ctypes.byref(out), arr, ctypes.c_void_p(r.ctypes.data),
+                                  len(plans))
+    if st != TC_OK:
+        raise TcError(st, "tc_batch_plan_routes")
     return out.value
 
 

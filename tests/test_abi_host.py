@@ -225,3 +225,30 @@ def test_tensor_core_tile_defaults():
     assert info.batch > 1 and info.tile == 0 and info.workspace == 0
     assert tc.tc_plan_status(_t(s.A), _t(s.B), _t(s.C), tc.TC_F32, bf,
                              tc.MAPPING["slice_gemm"], 3) == 5
+
+
+def test_batch_routes_are_checked_before_any_allocation():
+    bf = tc.MATH["bf16x6"]
+    p = ts.fused_permute_48(n=6)
+    s = ts.slice_gemm_48()
+    h1 = tc.tc_plan(_t(p.A), _t(p.B), _t(p.C), tc.TC_F32, bf)
+    h2 = tc.tc_plan(_t(s.A), _t(s.B), _t(s.C), tc.TC_F32, bf, tc.MAPPING["slice_gemm"])
+    try:
+        for bad in ([2, -1], [-2, 0]):
+            with pytest.raises(tc.TcError) as e:
+                tc.tc_batch_plan_routes([h1, h2], bad)
+            assert e.value.status == 1
+        # the slicing mapping's batch group cannot take the tensor-core route
+        with pytest.raises(tc.TcError) as e:
+            tc.tc_batch_plan_routes([h1, h2], [-1, 1])
+        assert e.value.status == 5
+    finally:
+        tc.tc_plan_destroy(h1)
+        tc.tc_plan_destroy(h2)
+
+
+def test_autotune_buckets():
+    from paper_1307_2100_gb300 import autotune
+    assert autotune.bucket_of(3201, 520, 300) == (9, 4)
+    assert autotune.bucket_of(1, 7, 1) == (0, 0)
+    assert autotune.bucket_of(1 << 20, 1 << 20, 1 << 30) == (10, 10)

@@ -155,8 +155,9 @@ def test_batched_graph_capture_and_replay():
 
 def test_batched_equals_single_launches_bitwise():
     """With every item routed to the tensor cores, the batched launch runs the
-    same tiles with the same chunking as a lone tc_contract of a tensor-core
-    plan on the gathering kernel (tile 0), so those results agree bit for bit."""
+    same packed tiles with the same chunking as a lone tc_contract of a
+    tensor-core plan on packed operands (tile 3), so those results agree bit
+    for bit."""
     from gpu_util import run
     from paper_1307_2100_gb300 import tc
     items = small_items(20, seed=ts.BASE_SEED + 33)
@@ -168,10 +169,13 @@ def test_batched_equals_single_launches_bitwise():
     assert info.n_simt_items == 0
     checked = 0
     for p, got in zip(items, outs):
-        meta = []
-        single = run(p, "bf16x6", "auto", tile=0, plan_out=meta)
-        if meta[0]["kernel_name"] != "gemm_tc":
+        from paper_1307_2100_gb300 import Contraction
+        plan = Contraction((p.A.labels, p.A.extents, p.A.strides),
+                           (p.B.labels, p.B.extents, p.B.strides),
+                           (p.C.labels, p.C.extents, p.C.strides), "f32", "bf16x6", "auto")
+        if plan.info.as_dict()["kernel_name"] != "gemm_tc" or plan.info.batch != 1:
             continue
+        single = run(p, "bf16x6", "auto", tile=3)
         np.testing.assert_array_equal(got, single)
         checked += 1
     assert checked >= 5
@@ -192,3 +196,34 @@ def test_batching_workload_every_item_against_oracle():
         if not ok:
             bad.append((j, d))
     assert not bad, bad[:10]
+
+
+def test_autotuned_routes():
+    """The route autotuner over the 512-item batching workload: the tuned
+    batch is no slower than the threshold rule it starts from, every route is
+    one of the two, and the tuned batch is within every item's bound of the
+    FP64 oracle (routes change the arithmetic: BF16x3 or FP32)."""
+    import torch
+    from paper_1307_2100_gb300 import autotune, tc
+    items = ts.batching_items(512)
+    plans, bufs = _plans_and_buffers(items, "bf16x3")
+    pa, pb, pc, al, be = _pointer_arrays(bufs, items)
+    s = torch.cuda.Stream()
+    routes, rep = autotune.tune_routes([pl.handle for pl in plans], (pa, pb, pc, al, be), s,
+                                       reps=3)
+    assert set(np.unique(routes)) <= {0, 1}
+    assert rep["tuned_ms"] <= rep["default_ms"]
+    batch = tc.tc_batch_plan_routes([pl.handle for pl in plans], routes)
+    try:
+        for _, _, C in bufs:
+            C.fill_(float("nan"))
+        tc.tc_contract_batched(batch, pa.data_ptr(), pb.data_ptr(), pc.data_ptr(), al.data_ptr(),
+                               be.data_ptr(), s.cuda_stream)
+        torch.cuda.synchronize()
+    finally:
+        tc.tc_batch_destroy(batch)
+    for p, (_, _, C) in zip(items, bufs):
+        got = C.cpu().numpy().astype(np.float64)[: p.C.data.size]
+        _, tot = tc_bounds(p, "bf16x3")
+        ok, d = within(got, oracle.contract_problem(p), magnitude(p), p.C, tot)
+        assert ok, (p.name, d)
