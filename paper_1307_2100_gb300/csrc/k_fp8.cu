@@ -21,23 +21,27 @@
 //                matrices: byte (k / 16) * 2048 + row * 16 + k % 16), plus each
 //                row's scale as an exponent byte e + 127 (UE8M0).  The operand
 //                is read from HBM once; the GEMM never touches the FP32 data.
-//   k_gemm_fp8   persistent, one CTA per SM over 128 x 128 output tiles, on
+//   k_gemm_fp8   persistent, one CTA per SM over 128 x 256 output tiles, on
 //                the block-scaled MMA (kind::mxf8f6f4): the tensor cores
 //                multiply each K = 32 step by 2^(e_A + e_B) of its rows and
 //                columns and accumulate all of K in FP32 in tensor memory.
-//                warp 0     one thread moves each (tile, block) pair of packed
-//                           blocks into a 6-stage shared-memory ring with two
-//                           bulk copies (cp.async.bulk, mbarrier transaction
-//                           count);
+//                Each block of A feeds two N = 128 MMAs (one per half of the
+//                tile), a third more multiply-adds per byte moved than a
+//                128 x 128 tile.
+//                warp 0     one thread moves each (tile, block) triple of packed
+//                           blocks (A and both halves of B) into a 4-stage
+//                           shared-memory ring with bulk copies
+//                           (cp.async.bulk, mbarrier transaction count);
 //                warp 1     tensor-memory allocation; one thread issues the
-//                           four K = 32 MMAs of each block;
+//                           eight K = 32 MMAs of each block;
 //                warps 2-5  one per lane quadrant: write the scale bytes of
 //                           four consecutive blocks into tensor memory (a ring
-//                           of 4 x 8 columns) ahead of the MMAs;
+//                           of 4 x 12 columns) ahead of the MMAs;
 //                warps 6-13 epilogue, once per tile: two warps per lane
-//                           quadrant read 64 accumulator columns each (double
-//                           buffered, 2 x 128 columns), apply alpha and beta
-//                           and store through C's strides.
+//                           quadrant, one per half, read 64 accumulator
+//                           columns at a time (the accumulator, 256 columns,
+//                           is released after the last read), apply alpha and
+//                           beta and store through C's strides.
 // Scale bytes in tensor memory (one layout for A and B, in all four lane
 // quadrants): lane 32 q + l, column c of a group, byte j holds the exponent of
 // row (A) or column (B) 32 c + l for the group's block j.  The MMA takes row
@@ -67,17 +71,20 @@ constexpr int kPackThreads = 256;
 constexpr int kLd = KB + 1;               // shared-memory row pitch of the pack tile (floats)
 constexpr uint32_t kPackSmem = TILE * kLd * 4 + 2 * TILE * 8 + TILE * 4;
 
-constexpr int S = 7;                      // stages of the operand ring
-constexpr int NACC = 2;                   // accumulators in tensor memory (128 columns each)
+// The GEMM's output tile is 128 x 256: two N = 128 halves share each block
+// of the first operand (one 16 KB block of A and two of B per stage).
+constexpr int S = 4;                      // stages of the operand ring
+constexpr uint32_t STAGE = 3 * CHUNK;
 constexpr int NG = 4;                     // groups of scale columns in tensor memory
-constexpr uint32_t COL_SF = NACC * TILE;  // first scale column; 8 per group (A 0-3, B 4-7)
+constexpr uint32_t COL_SF = 2 * TILE;     // accumulator halves at 0 and 128; then the scales,
+                                          // 12 columns per group (A 0-3, B halves 4-7, 8-11)
 constexpr int kEpiThreads = 256;
 constexpr int kThreads = 64 + 128 + kEpiThreads;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
-constexpr uint32_t OFF_COLC = S * 2 * CHUNK;                    // int64 colC[2][128]
-constexpr uint32_t OFF_BAR = OFF_COLC + 2 * TILE * 8;
-constexpr uint32_t NBAR = 2 * S + 2 * NACC + 2 * NG + 1;
+constexpr uint32_t OFF_COLC = S * STAGE;                        // int64 colC[2][256]
+constexpr uint32_t OFF_BAR = OFF_COLC + 2 * 2 * TILE * 8;
+constexpr uint32_t NBAR = 2 * S + 2 + 2 * NG + 1;
 constexpr uint32_t OFF_MISC = OFF_BAR + NBAR * 8;
 constexpr uint32_t kGemmSmem = OFF_MISC + 16 + 128;             // + alignment slack
 
@@ -217,16 +224,18 @@ struct GemmFp8 {
   float* C;
   int64_t M, N, ntiles;
   float alpha, beta;
-  int32_t tiles_m, tiles_n, nkb, ngroups, raster, pad_;
+  int32_t tiles_m, tiles_n, tiles_p, nkb, ngroups, raster;  // tiles_p: pairs of 128-column tiles
 };
 
-__device__ __forceinline__ void tile_coords(const GemmFp8& P, int64_t w, int& tm, int& tn) {
+// Output tile w: 128-row tile tm and the pair tp of 128-column tiles 2 tp and
+// 2 tp + 1 (the second exists when 2 tp + 1 < tiles_n).
+__device__ __forceinline__ void tile_coords(const GemmFp8& P, int64_t w, int& tm, int& tp) {
   if (P.raster) {
-    tn = (int)(w % P.tiles_n);
-    tm = (int)(w / P.tiles_n);
+    tp = (int)(w % P.tiles_p);
+    tm = (int)(w / P.tiles_p);
   } else {
     tm = (int)(w % P.tiles_m);
-    tn = (int)(w / P.tiles_m);
+    tp = (int)(w / P.tiles_m);
   }
 }
 
@@ -245,8 +254,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_fp8(const __grid_constant_
   uint64_t* full = bars;
   uint64_t* empty = bars + S;
   uint64_t* accf = bars + 2 * S;
-  uint64_t* acce = accf + NACC;
-  uint64_t* sff = acce + NACC;
+  uint64_t* acce = accf + 1;
+  uint64_t* sff = acce + 1;
   uint64_t* sfe = sff + NG;
   uint64_t* done = sfe + NG;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + OFF_MISC);
@@ -258,10 +267,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_fp8(const __grid_constant_
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int i = 0; i < NACC; ++i) {
-      mbar_init(&accf[i], 1);
-      mbar_init(&acce[i], kEpiThreads);
-    }
+    mbar_init(accf, 1);
+    mbar_init(acce, kEpiThreads);
     for (int i = 0; i < NG; ++i) {
       mbar_init(&sff[i], 128);
       mbar_init(&sfe[i], 1);
@@ -284,20 +291,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_fp8(const __grid_constant_
       uint32_t g = 0;
       bool ok = true;
       for (int64_t w = blockIdx.x; ok && w < P.ntiles; w += gridDim.x) {
-        int tm, tn;
-        tile_coords(P, w, tm, tn);
+        int tm, tp;
+        tile_coords(P, w, tm, tp);
+        const bool h1 = 2 * tp + 1 < P.tiles_n;
         const uint8_t* a = P.qa + (size_t)tm * nkb * CHUNK;
-        const uint8_t* b = P.qb + (size_t)tn * nkb * CHUNK;
+        const uint8_t* b = P.qb + (size_t)(2 * tp) * nkb * CHUNK;
         for (int kb = 0; kb < nkb; ++kb, ++g) {
           const int s = (int)(g % S);
           if (g >= (uint32_t)S && !mbar_wait(&empty[s], ((g / S) - 1) & 1, abort, kTimeoutNs)) {
             ok = false;
             break;
           }
-          const uint32_t dst = sbase + (uint32_t)s * 2 * CHUNK;
-          mbar_arrive_expect_tx(&full[s], 2 * CHUNK);
+          const uint32_t dst = sbase + (uint32_t)s * STAGE;
+          mbar_arrive_expect_tx(&full[s], (h1 ? 3 : 2) * CHUNK);
           bulk_g2s(dst, a + (size_t)kb * CHUNK, CHUNK, &full[s]);
           bulk_g2s(dst + CHUNK, b + (size_t)kb * CHUNK, CHUNK, &full[s]);
+          if (h1) bulk_g2s(dst + 2 * CHUNK, b + (size_t)(nkb + kb) * CHUNK, CHUNK, &full[s]);
         }
       }
       // the copies still in flight (at most the last S blocks) land before exit
@@ -312,14 +321,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_fp8(const __grid_constant_
       uint32_t g = 0, G = 0, t = 0;
       bool ok = true;
       for (int64_t w = blockIdx.x; ok && w < P.ntiles; w += gridDim.x, ++t) {
-        const uint32_t buf = t % NACC;
-        if (t >= (uint32_t)NACC &&
-            !mbar_wait(&acce[buf], ((t / NACC) - 1) & 1, abort, kTimeoutNs)) {
+        int tm, tp;
+        tile_coords(P, w, tm, tp);
+        const bool h1 = 2 * tp + 1 < P.tiles_n;
+        // the accumulator is free once the epilogue has read the previous tile
+        if (t >= 1 && !mbar_wait(acce, (t - 1) & 1, abort, kTimeoutNs)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        const uint32_t d = tmem + buf * TILE;
         for (int kb = 0; kb < nkb; ++kb, ++g) {
           const uint32_t slot = G % NG;
           if ((kb & 3) == 0) {  // the group's scale columns are written
@@ -334,15 +344,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_fp8(const __grid_constant_
             break;
           }
           tc_fence_after();
-          const uint32_t sa = sbase + (uint32_t)s * 2 * CHUNK, sb = sa + CHUNK;
+          const uint32_t sa = sbase + (uint32_t)s * STAGE;
           const uint32_t id = (uint32_t)(kb & 3);
           const uint32_t idesc = idesc_mx_e4m3(TILE, TILE, id, id);
-          const uint32_t tsf = tmem + COL_SF + slot * 8;
+          const uint32_t tsf = tmem + COL_SF + slot * 12;
 #pragma unroll
-          for (int kk = 0; kk < KB / 32; ++kk)
-            mma_mx_e4m3(d, smem_desc(sa + kk * 2 * LBO, LBO, 128),
-                        smem_desc(sb + kk * 2 * LBO, LBO, 128), idesc, tsf, tsf + 4,
-                        (kb > 0 || kk > 0) ? 1u : 0u);
+          for (int kk = 0; kk < KB / 32; ++kk) {
+            const uint64_t da = smem_desc(sa + kk * 2 * LBO, LBO, 128);
+            const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+            mma_mx_e4m3(tmem, da, smem_desc(sa + CHUNK + kk * 2 * LBO, LBO, 128), idesc, tsf,
+                        tsf + 4, acc);
+            if (h1)
+              mma_mx_e4m3(tmem + TILE, da, smem_desc(sa + 2 * CHUNK + kk * 2 * LBO, LBO, 128),
+                          idesc, tsf, tsf + 8, acc);
+          }
           mma_commit(&empty[s]);
           if ((kb & 3) == 3 || kb == nkb - 1) {
             mma_commit(&sfe[slot]);  // the group's scale columns may be rewritten
@@ -350,7 +365,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_fp8(const __grid_constant_
           }
         }
         if (!ok) break;
-        mma_commit(&accf[buf]);
+        mma_commit(accf);
       }
       mma_commit(done);  // arrives once every MMA issued above has completed
       volatile int never = 0;
@@ -364,33 +379,42 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_fp8(const __grid_constant_
     // the bytes of the next group are loaded while the current one waits
     int64_t w = blockIdx.x;
     int gi = 0;
-    auto load = [&](int64_t ww, int g, uint4& va, uint4& vb) {
-      int tm, tn;
-      tile_coords(P, ww, tm, tn);
-      va = __ldg(reinterpret_cast<const uint4*>(P.sfa + sf_index(tm, ngroups, 4 * g, 0)) + lane);
-      vb = __ldg(reinterpret_cast<const uint4*>(P.sfb + sf_index(tn, ngroups, 4 * g, 0)) + lane);
+    auto load = [&](int64_t ww, int gg, uint4& va, uint4& vb0, uint4& vb1) {
+      int tm, tp;
+      tile_coords(P, ww, tm, tp);
+      va = __ldg(reinterpret_cast<const uint4*>(P.sfa + sf_index(tm, ngroups, 4 * gg, 0)) + lane);
+      vb0 = __ldg(reinterpret_cast<const uint4*>(P.sfb + sf_index(2 * tp, ngroups, 4 * gg, 0)) +
+                  lane);
+      if (2 * tp + 1 < P.tiles_n)
+        vb1 = __ldg(
+            reinterpret_cast<const uint4*>(P.sfb + sf_index(2 * tp + 1, ngroups, 4 * gg, 0)) +
+            lane);
+      else
+        vb1 = vb0;  // no second half: its columns are not read
     };
-    uint4 va, vb;
-    if (w < P.ntiles) load(w, 0, va, vb);
+    uint4 va, vb0, vb1;
+    if (w < P.ntiles) load(w, 0, va, vb0, vb1);
     while (ok && w < P.ntiles) {
-      // position of the next group
       int64_t w2 = w;
       int g2 = gi + 1;
       if (g2 == ngroups) {
         g2 = 0;
         w2 += gridDim.x;
       }
-      uint4 na = va, nb = vb;
-      if (w2 < P.ntiles) load(w2, g2, na, nb);
+      uint4 na = va, nb0 = vb0, nb1 = vb1;
+      if (w2 < P.ntiles) load(w2, g2, na, nb0, nb1);
       const uint32_t slot = G % NG;
       if (G >= (uint32_t)NG && !warp_wait(&sfe[slot], ((G / NG) - 1) & 1, abort)) {
         ok = false;
         break;
       }
       tc_fence_after();
-      const uint32_t ra[4] = {va.x, va.y, va.z, va.w}, rb[4] = {vb.x, vb.y, vb.z, vb.w};
-      tmem_st4(tl + COL_SF + slot * 8, ra);
-      tmem_st4(tl + COL_SF + slot * 8 + 4, rb);
+      const uint32_t ra[4] = {va.x, va.y, va.z, va.w};
+      const uint32_t r0[4] = {vb0.x, vb0.y, vb0.z, vb0.w};
+      const uint32_t r1[4] = {vb1.x, vb1.y, vb1.z, vb1.w};
+      tmem_st4(tl + COL_SF + slot * 12, ra);
+      tmem_st4(tl + COL_SF + slot * 12 + 4, r0);
+      tmem_st4(tl + COL_SF + slot * 12 + 8, r1);
       tmem_wait_st();
       tc_fence_before();
       mbar_arrive(&sff[slot]);
@@ -398,52 +422,59 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_fp8(const __grid_constant_
       w = w2;
       gi = g2;
       va = na;
-      vb = nb;
+      vb0 = nb0;
+      vb1 = nb1;
     }
   } else {
     // ------------------------------------------------------------- epilogue
     const int ew = warp - 6;
     const int q = warp & 3;                 // tensor-memory lane quadrant of this warp
-    const int h = ew >> 2;                  // column half
+    const int h = ew >> 2;                  // 128-column half of the tile
     const int row = q * 32 + lane;
     const int etid = ew * 32 + lane;
-    const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)h * 64;
+    const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)h * TILE;
     uint32_t t = 0;
     bool live = true;  // after a wait gave up, tiles are walked without work so
                        // that every epilogue warp still meets each named barrier
     for (int64_t w = blockIdx.x; w < P.ntiles; w += gridDim.x, ++t) {
-      int tm, tn;
-      tile_coords(P, w, tm, tn);
-      int64_t* cc = colC + (t & 1) * TILE;
-      if (etid < TILE) {
-        const int64_t n = (int64_t)tn * TILE + etid;
+      int tm, tp;
+      tile_coords(P, w, tm, tp);
+      int64_t* cc = colC + (t & 1) * 2 * TILE;
+      {
+        const int64_t n = (int64_t)tp * 2 * TILE + etid;   // 256 columns, one per thread
         cc[etid] = n < P.N ? goff(P.gn, 2, (uint32_t)n) : -1;
       }
       named_bar_sync(1, kEpiThreads);
       if (!live) continue;
       const int64_t m = (int64_t)tm * TILE + row;
       const int64_t rc = m < P.M ? goff(P.gm, 2, (uint32_t)m) : -1;
-      const uint32_t buf = t % NACC;
-      if (!warp_wait(&accf[buf], (t / NACC) & 1, abort)) {
+      if (!warp_wait(accf, t & 1, abort)) {
         live = false;
         continue;
       }
       tc_fence_after();
-      uint32_t v[4][16];
+      // two passes of 64 columns; the accumulator is released after the last load
 #pragma unroll
-      for (int c = 0; c < 4; ++c) tmem_ld16(tl + buf * TILE + c * 16, v[c]);
-      tmem_wait_ld();
-      tc_fence_before();
-      mbar_arrive(&acce[buf]);  // the accumulator may take the next tile
-      if (rc < 0) continue;
-      float* Cr = P.C + rc;
+      for (int pass = 0; pass < 2; ++pass) {
+        uint32_t v[4][16];
 #pragma unroll
-      for (int i = 0; i < 64; ++i) {
-        const int64_t ci = cc[h * 64 + i];
-        if (ci < 0) continue;
-        float x = P.alpha * __uint_as_float(v[i / 16][i % 16]);
-        if (P.beta != 0.0f) x = fmaf(P.beta, Cr[ci], x);
-        Cr[ci] = x;
+        for (int c = 0; c < 4; ++c) tmem_ld16(tl + pass * 64 + c * 16, v[c]);
+        tmem_wait_ld();
+        if (pass == 1) {
+          tc_fence_before();
+          mbar_arrive(acce);  // the accumulator may take the next tile
+        }
+        if (rc >= 0) {
+          float* Cr = P.C + rc;
+#pragma unroll
+          for (int i = 0; i < 64; ++i) {
+            const int64_t ci = cc[h * TILE + pass * 64 + i];
+            if (ci < 0) continue;
+            float x = P.alpha * __uint_as_float(v[i / 16][i % 16]);
+            if (P.beta != 0.0f) x = fmaf(P.beta, Cr[ci], x);
+            Cr[ci] = x;
+          }
+        }
       }
     }
   }
@@ -554,7 +585,8 @@ tc_status launch_gemm_fp8(const GemmArgs& a, void* ws, void* stream) {
   g.C = static_cast<float*>(a.C);
   g.M = a.M;
   g.N = a.N;
-  g.ntiles = L.tiles_m * L.tiles_n;
+  g.tiles_p = (int32_t)((L.tiles_n + 1) / 2);
+  g.ntiles = L.tiles_m * g.tiles_p;
   g.alpha = (float)a.alpha;
   g.beta = (float)a.beta;
   g.tiles_m = (int32_t)L.tiles_m;
