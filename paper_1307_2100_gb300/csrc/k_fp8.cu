@@ -67,9 +67,11 @@ namespace fp8 {
 constexpr int TILE = 128;                 // rows of a tile (M and N)
 constexpr int KB = 128;                   // K block: one scale, one pipeline stage
 constexpr uint32_t CHUNK = TILE * KB;     // bytes of one packed (tile, block)
-constexpr int kPackThreads = 256;
+constexpr int kPackThreads = 512;
+constexpr int kRowThreads = kPackThreads / TILE;  // threads sharing one row (or one k)
 constexpr int kLd = KB + 1;               // shared-memory row pitch of the pack tile (floats)
-constexpr uint32_t kPackSmem = TILE * kLd * 4 + 2 * TILE * 8 + TILE * 4;
+constexpr uint32_t kPackSmem =
+    TILE * kLd * 4 + 2 * TILE * 8 + TILE * 4 + kRowThreads * TILE * 4;
 
 // The GEMM's output tile is 128 x 256: two N = 128 halves share each block
 // of the first operand (one 16 KB block of A and two of B per stage).
@@ -115,6 +117,7 @@ __global__ void __launch_bounds__(kPackThreads) k_fp8_pack(const __grid_constant
   int64_t* roff = reinterpret_cast<int64_t*>(tile + TILE * kLd);
   int64_t* koff = roff + TILE;
   float* qmul = reinterpret_cast<float*>(koff + KB);
+  float* pmax4 = qmul + TILE;  // [kRowThreads][128] partial row maxima (rows_fast)
 
   int64_t bid = blockIdx.x;
   const int o = bid < P.nblocks0 ? 0 : 1;
@@ -124,53 +127,52 @@ __global__ void __launch_bounds__(kPackThreads) k_fp8_pack(const __grid_constant
   if (tid < TILE) {
     const int64_t r = (int64_t)t * TILE + tid;
     roff[tid] = r < P.rows[o] ? goff(P.gr[o], o, (uint32_t)r) : -1;
-  } else {
+  } else if (tid < 2 * TILE) {
     const int64_t k = (int64_t)kb * KB + (tid - TILE);
     koff[tid - TILE] = k < P.K ? goff(P.gk, o, (uint32_t)k) : -1;
   }
   __syncthreads();
 
   // gather the FP32 block; consecutive threads take consecutive elements of
-  // the operand's contiguous index.  Sixteen loads are issued before their
-  // sixteen shared-memory stores, so that each thread has them in flight at once.
+  // the operand's contiguous index.  All of a thread's loads are issued before
+  // their shared-memory stores, so that they are in flight at once.
   const float* __restrict__ X = P.in[o];
-  constexpr int NJ = TILE * KB / kPackThreads, U = 32;
-  float* pmax = qmul;  // partial row maxima of the two threads of a row (rows_fast)
+  constexpr int NJ = TILE * KB / kPackThreads;
+  float* pmax = qmul;  // row maxima, then (below) the rows' quantisation factors
   if (P.rows_fast[o]) {
-    const int r = tid & (TILE - 1), k0 = tid >> 7;
+    const int r = tid & (TILE - 1), k0 = tid / TILE;
     const int64_t ro = roff[r];
+    float v[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      const int64_t ko = koff[k0 + kRowThreads * j];
+      v[j] = (ro >= 0 && ko >= 0) ? __ldg(X + ro + ko) : 0.0f;
+    }
     float m = 0.0f;
 #pragma unroll
-    for (int j0 = 0; j0 < NJ; j0 += U) {
-      float v[U];
-#pragma unroll
-      for (int j = 0; j < U; ++j) {
-        const int64_t ko = koff[k0 + 2 * (j0 + j)];
-        v[j] = (ro >= 0 && ko >= 0) ? __ldg(X + ro + ko) : 0.0f;
-      }
-#pragma unroll
-      for (int j = 0; j < U; ++j) {
-        tile[r * kLd + k0 + 2 * (j0 + j)] = v[j];
-        m = fmaxf(m, fabsf(v[j]));
-      }
+    for (int j = 0; j < NJ; ++j) {
+      tile[r * kLd + k0 + kRowThreads * j] = v[j];
+      m = fmaxf(m, fabsf(v[j]));
     }
-    if (k0 == 1) pmax[r] = m;
+    pmax4[k0 * TILE + r] = m;
     __syncthreads();
-    if (k0 == 0) pmax[r] = fmaxf(pmax[r], m);
-  } else {
-    const int k = tid & (KB - 1), r0 = tid >> 7;
-    const int64_t ko = koff[k];
+    if (tid < TILE) {
+      float mm = pmax4[tid];
 #pragma unroll
-    for (int j0 = 0; j0 < NJ; j0 += U) {
-      float v[U];
-#pragma unroll
-      for (int j = 0; j < U; ++j) {
-        const int64_t ro = roff[r0 + 2 * (j0 + j)];
-        v[j] = (ro >= 0 && ko >= 0) ? __ldg(X + ro + ko) : 0.0f;
-      }
-#pragma unroll
-      for (int j = 0; j < U; ++j) tile[(r0 + 2 * (j0 + j)) * kLd + k] = v[j];
+      for (int i = 1; i < kRowThreads; ++i) mm = fmaxf(mm, pmax4[i * TILE + tid]);
+      pmax[tid] = mm;
     }
+  } else {
+    const int k = tid & (KB - 1), r0 = tid / KB;
+    const int64_t ko = koff[k];
+    float v[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      const int64_t ro = roff[r0 + kRowThreads * j];
+      v[j] = (ro >= 0 && ko >= 0) ? __ldg(X + ro + ko) : 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) tile[(r0 + kRowThreads * j) * kLd + k] = v[j];
     __syncthreads();
     if (tid < TILE) {  // one thread per row: consecutive rows fall in distinct banks
       float m = 0.0f;
