@@ -44,7 +44,8 @@ constexpr int TILE = 128;
 constexpr int BK = 32;                       // K per block (one stage)
 constexpr int PK = 128;                      // K per pack CTA (4 blocks)
 constexpr uint32_t TERM = TILE * BK * 2;     // bytes of one term of one block
-constexpr int kPackThreads = 256;
+constexpr int kPackThreads = 512;
+constexpr int kRowThreads = kPackThreads / TILE;   // threads sharing one row (or one k)
 constexpr int kLd = PK + 1;
 constexpr uint32_t kPackSmem = TILE * kLd * 4 + 2 * TILE * 8;
 
@@ -110,42 +111,36 @@ __device__ __forceinline__ void pack_body(const Group& gr, const Group& gk, int 
   if (tid < TILE) {
     const int64_t r = (int64_t)t * TILE + tid;
     roff[tid] = r < rows ? goff(gr, o, (uint32_t)r) : -1;
-  } else {
+  } else if (tid < 2 * TILE) {
     const int64_t k = (int64_t)kc * PK + (tid - TILE);
     koff[tid - TILE] = k < K ? goff(gk, o, (uint32_t)k) : -1;
   }
   __syncthreads();
 
-  // gather (sixteen loads in flight per thread, then their stores)
-  constexpr int NJ = TILE * PK / kPackThreads, U = 16;
+  // gather: all of a thread's loads in flight, then their stores
+  constexpr int NJ = TILE * PK / kPackThreads;
   if (rows_fast) {
-    const int r = tid & (TILE - 1), k0 = tid >> 7;
+    const int r = tid & (TILE - 1), k0 = tid / TILE;
     const int64_t ro = roff[r];
+    float v[NJ];
 #pragma unroll
-    for (int j0 = 0; j0 < NJ; j0 += U) {
-      float v[U];
-#pragma unroll
-      for (int j = 0; j < U; ++j) {
-        const int64_t ko = koff[k0 + 2 * (j0 + j)];
-        v[j] = (ro >= 0 && ko >= 0) ? __ldg(X + ro + ko) : 0.0f;
-      }
-#pragma unroll
-      for (int j = 0; j < U; ++j) tile[r * kLd + k0 + 2 * (j0 + j)] = v[j];
+    for (int j = 0; j < NJ; ++j) {
+      const int64_t ko = koff[k0 + kRowThreads * j];
+      v[j] = (ro >= 0 && ko >= 0) ? __ldg(X + ro + ko) : 0.0f;
     }
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) tile[r * kLd + k0 + kRowThreads * j] = v[j];
   } else {
-    const int k = tid & (PK - 1), r0 = tid >> 7;
+    const int k = tid & (PK - 1), r0 = tid / PK;
     const int64_t ko = koff[k];
+    float v[NJ];
 #pragma unroll
-    for (int j0 = 0; j0 < NJ; j0 += U) {
-      float v[U];
-#pragma unroll
-      for (int j = 0; j < U; ++j) {
-        const int64_t ro = roff[r0 + 2 * (j0 + j)];
-        v[j] = (ro >= 0 && ko >= 0) ? __ldg(X + ro + ko) : 0.0f;
-      }
-#pragma unroll
-      for (int j = 0; j < U; ++j) tile[(r0 + 2 * (j0 + j)) * kLd + k] = v[j];
+    for (int j = 0; j < NJ; ++j) {
+      const int64_t ro = roff[r0 + kRowThreads * j];
+      v[j] = (ro >= 0 && ko >= 0) ? __ldg(X + ro + ko) : 0.0f;
     }
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) tile[(r0 + kRowThreads * j) * kLd + k] = v[j];
   }
   __syncthreads();
 
