@@ -100,7 +100,13 @@ typedef enum {
  *                      index is sliced is first permuted into workspace.
  *   TC_MAP_GEMV        matrix-vector products (Sec. 3.2.2); for Class 3 one GEMV per
  *                      value of B's free indices (slicing (c) of Sec. 2.4).
- *   TC_MAP_DOT         one inner product per output element (Sec. 3.2.1, F3). */
+ *   TC_MAP_DOT         one inner product per output element (Sec. 3.2.1, F3).
+ *   TC_MAP_GER         rank-K update for tiny contracted ranges, the sum-of-GERs
+ *                      slicing of Sec. 2.2 done in one pass: every output's K
+ *                      products are summed in registers and C is written once;
+ *                      K <= TC_GER_MAX_K (else TC_ERR_UNSUPPORTED).  Computes in
+ *                      the storage precision (FP64, or FP32 for FP32 storage
+ *                      whatever the math form; FP8 has only the fused mapping). */
 typedef enum {
   TC_MAP_AUTO = 0,
   TC_MAP_RECIPE = 1,
@@ -108,8 +114,10 @@ typedef enum {
   TC_MAP_FUSED_GEMM = 3,
   TC_MAP_COPY_GEMM = 4,
   TC_MAP_GEMV = 5,
-  TC_MAP_DOT = 6
+  TC_MAP_DOT = 6,
+  TC_MAP_GER = 7
 } tc_mapping;
+#define TC_GER_MAX_K 32
 
 /* A tensor: `order` indices with labels (distinct int32 values), extents
  * (>= 0) and strides in elements (NULL = column-major).  The arrays are read
@@ -137,7 +145,7 @@ typedef struct {
   uint32_t slice_b;      /* recipe slicing vector s(B) */
   int32_t mapping;       /* tc_mapping in use (never AUTO or RECIPE) */
   int32_t kernel;        /* kernel family: 1 GEMM-SIMT, 2 GEMM-tcgen05, 3 GEMV, 4 DOT,
-                            5 GEMM-tcgen05 FP8 (pack pass + GEMM) */
+                            5 GEMM-tcgen05 FP8 (pack pass + GEMM), 6 GER */
   int32_t tile;          /* tile configuration index of that kernel */
   int32_t swapped;       /* 1 when the kernel's first operand is B */
   int64_t M, N, K, batch;   /* GEMM view after mode merging */

@@ -51,6 +51,7 @@ extern "C" tc_status tc_contract(tc_plan_t plan, double alpha, const void* A, co
     case K_GEMM_FP8: return launch_gemm_fp8(a, ws, stream);
     case K_GEMV: return launch_gemv(a, P->dtype, P->tile, stream);
     case K_DOT: return launch_dot(a, P->dtype, P->tile, stream);
+    case K_GER: return launch_ger(a, P->dtype, stream);
     default: return TC_ERR_UNSUPPORTED;
   }
 }

@@ -281,7 +281,7 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   *out = nullptr;
   if (dtype != TC_F64 && dtype != TC_F32) return TC_ERR_INVALID_ARG;
   if (math < TC_MATH_FP64 || math > TC_MATH_FP8) return TC_ERR_INVALID_ARG;
-  if (mapping < TC_MAP_AUTO || mapping > TC_MAP_DOT) return TC_ERR_INVALID_ARG;
+  if (mapping < TC_MAP_AUTO || mapping > TC_MAP_GER) return TC_ERR_INVALID_ARG;
   if ((math == TC_MATH_FP64) != (dtype == TC_F64)) return TC_ERR_UNSUPPORTED;
 
   Tens A, B, C;
@@ -405,13 +405,16 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
     map = TC_MAP_RECIPE;
     if (selector_predict(P->features, dtype, math, cand, pred, &nc)) {
       const bool class3 = an.cls == 31 || an.cls == 32;
+      double kprod = 1.0;
+      for (auto l : an.con) kprod *= (double)an.ext[l];
       float best = 0;
       bool found = false;
       for (int i = 0; i < nc; ++i) {
         const int32_t cm = cand[i] & 0xFF, ct = (cand[i] >> 8) - 1;
         const bool feasible =
-            cm >= TC_MAP_SLICE_GEMM && cm <= TC_MAP_DOT &&
-            (class3 || (cm != TC_MAP_SLICE_GEMM && cm != TC_MAP_COPY_GEMM));
+            cm >= TC_MAP_SLICE_GEMM && cm <= TC_MAP_GER &&
+            (class3 || (cm != TC_MAP_SLICE_GEMM && cm != TC_MAP_COPY_GEMM)) &&
+            (cm != TC_MAP_GER || kprod <= TC_GER_MAX_K);
         if (feasible && (!found || pred[i] < best)) {
           map = cm;
           sel_tile = ct;
@@ -439,6 +442,7 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   const bool tensor_core = math == TC_MATH_BF16 || math == TC_MATH_BF16X3 || math == TC_MATH_BF16X6;
   int32_t kernel = fp8 ? K_GEMM_FP8
                  : gemm_family ? (tensor_core ? K_GEMM_TC : K_GEMM_SIMT)
+                 : map == TC_MAP_GER ? K_GER
                                : (map == TC_MAP_GEMV ? K_GEMV : K_DOT);
 
   // ---- operand roles: the kernel's first operand X provides M
@@ -523,7 +527,8 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
             make_group(ln, an.ext, nullptr, Yp, &C, g.gn, N) &&
             make_group(lk, an.ext, Xp, Yp, nullptr, g.gk, Kt) &&
             make_group(lb, an.ext, Xp, Yp, &C, g.gb, Bt);
-  if (!ok || M > INT_MAX || N > INT_MAX || Kt > INT_MAX || Bt > INT_MAX) {
+  if (!ok || M > INT_MAX || N > INT_MAX || Kt > INT_MAX || Bt > INT_MAX ||
+      (kernel == K_GER && Kt > TC_GER_MAX_K)) {
     delete P;
     return TC_ERR_UNSUPPORTED;
   }

@@ -132,7 +132,7 @@ extern "C" tc_status tc_selector_load(const char* path) {
     }
     for (int i = 0; i < C && ok; ++i) {  // TC_SELECTOR_CANDIDATE(mapping, tile), tile -1..14
       const int32_t m = S->cand[i] & 0xFF, t = S->cand[i] >> 8;
-      ok = m >= TC_MAP_SLICE_GEMM && m <= TC_MAP_DOT && t >= 0 && t <= 15;
+      ok = m >= TC_MAP_SLICE_GEMM && m <= TC_MAP_GER && t >= 0 && t <= 15;
     }
     uint8_t extra;
     ok = ok && std::fread(&extra, 1, 1, f) == 0;  // nothing after the parameters

@@ -26,7 +26,8 @@ enum Kernel : int32_t {
   K_GEMM_TC = 2,
   K_GEMV = 3,
   K_DOT = 4,
-  K_GEMM_FP8 = 5
+  K_GEMM_FP8 = 5,
+  K_GER = 6
 };
 
 // Operand contiguity (how the loader can coalesce):
@@ -100,6 +101,7 @@ bool selector_predict(const float* features, tc_dtype dtype, tc_math math, int32
 tc_status launch_gemm_simt(const GemmArgs& a, tc_dtype dt, int tile, void* stream);
 tc_status launch_gemv(const GemmArgs& a, tc_dtype dt, int tile, void* stream);
 tc_status launch_dot(const GemmArgs& a, tc_dtype dt, int tile, void* stream);
+tc_status launch_ger(const GemmArgs& a, tc_dtype dt, void* stream);
 tc_status launch_perm(const PermArgs& a, tc_dtype dt, void* stream);
 tc_status launch_scale(const Group& gc, void* C, double beta, tc_dtype dt, int64_t total,
                        void* stream);

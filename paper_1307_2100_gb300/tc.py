@@ -22,9 +22,10 @@ STATUS = {0: "TC_OK", 1: "TC_ERR_INVALID_ARG", 2: "TC_ERR_LABEL", 3: "TC_ERR_EXT
 TC_F64, TC_F32 = 0, 1
 MATH = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16x3": 3, "bf16x6": 4, "fp8": 5}
 MAPPING = {"auto": 0, "recipe": 1, "slice_gemm": 2, "fused_gemm": 3, "copy_gemm": 4, "gemv": 5,
-           "dot": 6}
+           "dot": 6, "ger": 7}
 MAPPING_NAME = {v: k for k, v in MAPPING.items()}
-KERNEL_NAME = {0: "none", 1: "gemm_simt", 2: "gemm_tc", 3: "gemv", 4: "dot", 5: "gemm_fp8"}
+KERNEL_NAME = {0: "none", 1: "gemm_simt", 2: "gemm_tc", 3: "gemv", 4: "dot", 5: "gemm_fp8",
+               6: "ger"}
 MAX_ORDER = 12
 N_FEATURES = 23
 

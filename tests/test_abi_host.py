@@ -252,3 +252,20 @@ def test_autotune_buckets():
     assert autotune.bucket_of(3201, 520, 300) == (9, 4)
     assert autotune.bucket_of(1, 7, 1) == (0, 0)
     assert autotune.bucket_of(1 << 20, 1 << 20, 1 << 30) == (10, 10)
+
+
+def test_ger_mapping_limits():
+    ger = tc.MAPPING["ger"]
+    for K, want in ((32, 0), (33, 5), (1, 0)):
+        A = (ts.lab("ai"), [40, K], None)
+        B = (ts.lab("ib"), [K, 30], None)
+        C = (ts.lab("ab"), [40, 30], None)
+        assert tc.tc_plan_status(A, B, C, tc.TC_F64, 0, ger) == want, K
+    A = (ts.lab("aij"), [40, 4, 4], None)
+    B = (ts.lab("ijb"), [4, 4, 30], None)
+    h = tc.tc_plan(A, B, (ts.lab("ab"), [40, 30], None), tc.TC_F32, tc.MATH["bf16x6"], ger)
+    try:
+        info = tc.tc_plan_get_info(h)
+        assert tc.KERNEL_NAME[info.kernel] == "ger" and info.K == 16 and info.workspace == 0
+    finally:
+        tc.tc_plan_destroy(h)
