@@ -167,6 +167,23 @@ tc_status tc_plan_get_info(tc_plan_t plan, tc_plan_info* info);
 /* Free a plan (NULL is allowed). */
 tc_status tc_plan_destroy(tc_plan_t plan);
 
+/* Storage-layout advice (the guideline of Sec. 3.3: store tensors so that no
+ * stride-1 index is contracted).  For a Class 3.1 contraction, the operand to
+ * re-store once (the smaller; B on a tie) and the storage order that gives it
+ * a free stride-1 index (its largest free index first, then its other indices
+ * in their present stride order, column-major in that order), which makes the
+ * contraction Class 3.2; for any other class, operand 0 (keep the layouts).
+ * The paper has no such report; it states the guideline. */
+typedef struct {
+  int32_t operand;                        /* 0 keep, 1 re-store A, 2 re-store B */
+  int32_t order;                          /* entries of storage_order */
+  int32_t storage_order[TC_MAX_ORDER];    /* index positions of that operand, fastest first */
+  int32_t cls_after;                      /* class after re-storing (32), else the class */
+  double copy_bytes;                      /* one-time re-layout traffic: read + write */
+} tc_layout_advice;
+
+tc_status tc_plan_layout_advice(tc_plan_t plan, tc_layout_advice* out);
+
 /* Run the contraction asynchronously on `stream` (a cudaStream_t; NULL = the
  * legacy default stream).  A, B, C are device pointers to elements of the
  * plan's dtype laid out as described at tc_plan time; C is read only when

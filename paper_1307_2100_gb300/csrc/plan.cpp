@@ -344,6 +344,36 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   const size_t es = elem_size(dtype);
   info.min_bytes = (double)(A.numel() + B.numel() + C.numel()) * (double)es;
 
+  // ---- storage-layout advice (Sec. 3.3): give the smaller operand of a
+  // Class 3.1 contraction a free stride-1 index
+  {
+    tc_layout_advice& adv = P->advice;
+    std::memset(&adv, 0, sizeof(adv));
+    adv.cls_after = an.cls;
+    if (an.cls == 31) {
+      const bool re_a = A.numel() < B.numel();
+      const Tens& T = re_a ? A : B;
+      const std::vector<int32_t>& fr = re_a ? an.fa : an.fb;
+      int32_t first = -1;
+      for (auto l : fr)
+        if (an.ext[l] > 1 && (first < 0 || an.ext[l] > an.ext[first])) first = l;
+      if (first >= 0) {
+        std::vector<int> pos(T.lab.size());
+        for (size_t i = 0; i < pos.size(); ++i) pos[i] = (int)i;
+        std::stable_sort(pos.begin(), pos.end(), [&](int x, int y) {
+          const bool fx = T.lab[x] == first, fy = T.lab[y] == first;
+          if (fx != fy) return fx;
+          return T.st[x] < T.st[y];
+        });
+        adv.operand = re_a ? 1 : 2;
+        adv.order = (int32_t)pos.size();
+        for (size_t i = 0; i < pos.size(); ++i) adv.storage_order[i] = pos[i];
+        adv.cls_after = 32;
+        adv.copy_bytes = 2.0 * (double)T.numel() * (double)elem_size(dtype);
+      }
+    }
+  }
+
   // ---- mapping
   // ---- descriptor features (the selector's input; computed for every plan)
   {
@@ -629,6 +659,12 @@ extern "C" tc_status tc_plan_features(tc_plan_t plan, float* out, int32_t n) {
   if (!plan || !out || n < 0) return TC_ERR_INVALID_ARG;
   const Plan* P = reinterpret_cast<const Plan*>(plan);
   for (int32_t i = 0; i < n && i < TC_SELECTOR_FEATURES; ++i) out[i] = P->features[i];
+  return TC_OK;
+}
+
+extern "C" tc_status tc_plan_layout_advice(tc_plan_t plan, tc_layout_advice* out) {
+  if (!plan || !out) return TC_ERR_INVALID_ARG;
+  *out = reinterpret_cast<Plan*>(plan)->advice;
   return TC_OK;
 }
 

@@ -87,6 +87,7 @@ struct Plan {
   Group gc;              // C's own labels (for beta-only scaling)
   size_t workspace;
   float features[TC_SELECTOR_FEATURES];  // descriptor features (selector input)
+  tc_layout_advice advice;               // storage-layout advice (Sec. 3.3)
 };
 
 size_t elem_size(tc_dtype dt);

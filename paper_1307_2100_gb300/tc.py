@@ -60,6 +60,12 @@ class PlanInfo(ctypes.Structure):
         return d
 
 
+class LayoutAdvice(ctypes.Structure):
+    _fields_ = [("operand", ctypes.c_int32), ("order", ctypes.c_int32),
+                ("storage_order", ctypes.c_int32 * MAX_ORDER), ("cls_after", ctypes.c_int32),
+                ("copy_bytes", ctypes.c_double)]
+
+
 class BatchInfo(ctypes.Structure):
     _fields_ = [("n_items", ctypes.c_int32), ("math", ctypes.c_int32),
                 ("n_tiles", ctypes.c_int64), ("flops", ctypes.c_double),
@@ -78,6 +84,8 @@ def _load():
                             ctypes.c_int, ctypes.c_int, ctypes.c_int32]
     lib.tc_plan_get_info.restype = ctypes.c_int
     lib.tc_plan_get_info.argtypes = [P, ctypes.POINTER(PlanInfo)]
+    lib.tc_plan_layout_advice.restype = ctypes.c_int
+    lib.tc_plan_layout_advice.argtypes = [P, ctypes.POINTER(LayoutAdvice)]
     lib.tc_plan_destroy.restype = ctypes.c_int
     lib.tc_plan_destroy.argtypes = [P]
     lib.tc_contract.restype = ctypes.c_int
@@ -171,6 +179,13 @@ def tc_plan_status(A, B, C, dtype: int, math: int, mapping: int = 0, tile: int =
         return e.status
     tc_plan_destroy(h)
     return TC_OK
+
+
+def tc_plan_layout_advice(plan: int) -> LayoutAdvice:
+    adv = LayoutAdvice()
+    _check(lib.tc_plan_layout_advice(ctypes.c_void_p(plan), ctypes.byref(adv)),
+           "tc_plan_layout_advice")
+    return adv
 
 
 def tc_plan_get_info(plan: int) -> PlanInfo:

@@ -269,3 +269,51 @@ def test_ger_mapping_limits():
         assert tc.KERNEL_NAME[info.kernel] == "ger" and info.K == 16 and info.workspace == 0
     finally:
         tc.tc_plan_destroy(h)
+
+
+def _restored(t, order):
+    """Tensor t stored column-major in the given order of its index positions."""
+    import copy
+    u = copy.copy(t)
+    u.strides = ts.storage_strides(t.extents, order)
+    return u
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_layout_advice_turns_class_31_into_32(seed):
+    rng = np.random.Generator(np.random.PCG64(2000 + seed))
+    seen = 0
+    for _ in range(6000):
+        if seen >= 15:
+            break
+        p = ts.random_problem(rng, max_order=5, max_ext=4, min_ext=1, max_p=3)
+        h = tc.tc_plan(_t(p.A), _t(p.B), _t(p.C), tc.TC_F64, 0)
+        try:
+            info, adv = tc.tc_plan_get_info(h), tc.tc_plan_layout_advice(h)
+        finally:
+            tc.tc_plan_destroy(h)
+        if info.cls != 31:
+            assert adv.operand == 0 and adv.cls_after == info.cls
+            continue
+        seen += 1
+        assert adv.operand in (1, 2) and adv.cls_after == 32
+        t = p.A if adv.operand == 1 else p.B
+        order = list(adv.storage_order[: adv.order])
+        assert sorted(order) == list(range(t.order))
+        assert adv.copy_bytes == 2 * 8 * int(np.prod(t.extents))
+        A2 = _restored(p.A, order) if adv.operand == 1 else p.A
+        B2 = _restored(p.B, order) if adv.operand == 2 else p.B
+        assert oc.classify(A2, B2, p.C).cls == 32
+    assert seen >= 15
+
+
+def test_layout_advice_on_the_paper_case():
+    # Eq. xy (b): C[a,b,c,d] = sum A[i,a,j,b] B[j,c,i,d], Class 3.1; equal sizes: re-store B
+    p = ts.fused_permute_48(n=8)
+    h = tc.tc_plan(_t(p.A), _t(p.B), _t(p.C), tc.TC_F64, 0)
+    try:
+        adv = tc.tc_plan_layout_advice(h)
+    finally:
+        tc.tc_plan_destroy(h)
+    assert adv.operand == 2 and adv.cls_after == 32
+    assert ts.lab("jcid")[adv.storage_order[0]] in ts.lab("cd")   # a free index of B first
