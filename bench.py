@@ -565,6 +565,103 @@ def run_batching(args):
     return 0
 
 
+SKEWED = [(30, 100), (30, 300), (30, 600), (100, 4), (300, 4)]   # (free a=c=d, occupied i=j)
+
+
+def run_skewed(args):
+    """The skewed CCD / GR suite of Sec. 4.2: R[a,b,c,d] = sum_{i,j}
+    X[i,a,j,b] Y[i,c,j,d] with a = c = d = free, b = 8, i = j = occ; short free
+    and long contracted extents (CCD) and the GR case i = j = 4.  Each shape
+    runs in FP64 on the recipe's mapping (and on GER where K <= 32), and with
+    FP32 storage in BF16x6 on the selector's choice (the packaged GB300
+    selector; outside its training range it falls back to the recipe), on
+    packed operands, and on GER where K <= 32.  Sampled outputs against the
+    FP64 oracle for every run."""
+    import torch
+    from paper_1307_2100_gb300 import build as _b
+    _b.build()
+    from paper_1307_2100_gb300 import Contraction, tc
+    import os
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    sel = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1307_2100_gb300",
+                       "data", "selector_gb300.bin")
+    tc.tc_selector_load(sel)
+    s = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    clocks = ClockSampler(0)
+    clocks.start()
+    parts = []
+    for free, occ in SKEWED:
+        p64 = ts.ccd_skewed(free, occ)
+        p32 = ts.ccd_skewed(free, occ, dtype=np.float32)
+        K = occ * occ
+        runs = [("fp64", "recipe", -1, p64), ("bf16x6", "auto", -1, p32),
+                ("bf16x6", "fused_gemm", 3, p32)]
+        if K <= 32:
+            runs += [("fp64", "ger", -1, p64), ("fp32", "ger", -1, p32)]
+        for math, mapping, tile, p in runs:
+            dt = "f64" if p.A.data.dtype == np.float64 else "f32"
+            plan = Contraction((p.A.labels, p.A.extents, p.A.strides),
+                               (p.B.labels, p.B.extents, p.B.strides),
+                               (p.C.labels, p.C.extents, p.C.strides), dt, math, mapping, tile)
+            A = torch.from_numpy(p.A.data).to(dev)
+            B = torch.from_numpy(p.B.data).to(dev)
+            C = torch.zeros(p.C.data.size, dtype=A.dtype, device=dev)
+            ws = plan.workspace(dev)
+            call = lambda: tc.tc_contract(plan.handle, 1.0, A.data_ptr(), B.data_ptr(), 0.0,
+                                          C.data_ptr(), ws.data_ptr() if ws is not None else 0,
+                                          ws.numel() if ws is not None else 0, s.cuda_stream)
+            times = []
+            with torch.cuda.stream(s):
+                for _ in range(args.warmup):
+                    call()
+                for _ in range(args.steps):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(s)
+                    call()
+                    e1.record(s)
+                    e1.synchronize()
+                    times.append(e0.elapsed_time(e1))
+            ms = float(np.median(times))
+            info = plan.info
+            err = sampled_error(p, C.cpu().numpy().astype(np.float64))
+            parts.append({"shape": p.name, "free": free, "occ": occ, "M": int(info.M),
+                          "N": int(info.N), "K": int(info.K), "math": math,
+                          "mapping_asked": mapping, "mapping": tc.MAPPING_NAME[info.mapping],
+                          "kernel": tc.KERNEL_NAME[info.kernel], "tile": int(info.tile), "ms": ms,
+                          "tflops": p.flops() / (ms / 1e3) / 1e12,
+                          "rel_err_vs_fp64_oracle_sampled": err})
+            del A, B, C, ws, plan
+            torch.cuda.empty_cache()
+    clk = clocks.stop()
+    tc.tc_selector_unload()
+    status = tc.tc_device_status(s.cuda_stream)
+    best64 = {}
+    for q in parts:
+        if q["math"] == "fp64":
+            best64[q["shape"]] = min(best64.get(q["shape"], 1e30), q["ms"])
+    total64 = sum(best64.values())
+    best32 = {}
+    for q in parts:
+        if q["math"] != "fp64":
+            best32[q["shape"]] = min(best32.get(q["shape"], 1e30), q["ms"])
+    line = {
+        "metric": "skewed CCD/GR suite: ms per shape (FP64 recipe vs reduced-precision choices)",
+        "value": sum(best32.values()), "unit": "ms (sum over shapes, fastest FP32-storage run)",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 and f32 storage", "data": "synthetic (seeded uniform[-1,1))",
+        "config": {"workload": "skewed: X[i,a,j,b] Y[i,c,j,d], a=c=d=free, b=8, i=j=occ, "
+                               "(free, occ) in " + str(SKEWED),
+                   "l2": "flushed between steps (256 MiB write, outside timing)"},
+        "fp64_best_ms_sum": total64, "parts": parts, "clocks": clk,
+        "device_status": tc.tc_status_string(status)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -574,7 +671,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
     ap.add_argument("--workload", default="class3_fp64",
-                    choices=["class3_fp64", "precision", "batching"])
+                    choices=["class3_fp64", "precision", "batching", "skewed"])
     ap.add_argument("--items", type=int, default=512, help="batching: number of contractions")
     ap.add_argument("--no-autotune", action="store_true",
                     help="batching: the threshold route rule instead of tuned routes")
@@ -590,6 +687,8 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "skewed":
+        return run_skewed(args)
     if args.workload == "batching":
         if args.math == "bf16x6" and "--math" not in (argv or sys.argv):
             args.math = "bf16x3"

@@ -39,11 +39,11 @@ extern "C" {
 typedef enum {
   TC_OK = 0,
   TC_ERR_INVALID_ARG = 1,     /* null pointer, negative extent, order out of range */
-  TC_ERR_LABEL = 2,           /* repeated label, label of C not in exactly one operand,
+  TC_ERR_LABEL = 2,           /* repeated label, label of C in neither operand,
                                  label of A/B in neither C nor the other operand */
   TC_ERR_EXTENT_MISMATCH = 3, /* a label has different extents in two tensors */
   TC_ERR_STRIDE = 4,          /* non-positive stride (extent > 1) or aliasing output */
-  TC_ERR_UNSUPPORTED = 5,     /* label in A, B and C; dtype/math/mapping combination */
+  TC_ERR_UNSUPPORTED = 5,     /* dtype/math/mapping/tile combination */
   TC_ERR_WORKSPACE = 6,       /* workspace missing or smaller than tc_plan_info.workspace */
   TC_ERR_CUDA = 7,            /* a CUDA call failed */
   TC_ERR_TIMEOUT = 8,         /* a bounded device wait ran out */
@@ -156,7 +156,12 @@ typedef struct {
 
 /* Build a plan (host only; no device work).  `mapping` forces a mapping
  * (TC_ERR_UNSUPPORTED if it cannot compute this contraction); `tile` forces a
- * tile configuration, -1 = default.  On success *out owns a new plan. */
+ * tile configuration, -1 = default.  On success *out owns a new plan.
+ * A label in A, B and C is a batch (Hadamard) label, beyond the paper's
+ * definition: A, B and C are indexed by the same value, and the plan is one
+ * contraction per value (the GEMM view's batch group).  The class and the
+ * slicing vectors are those of one batch slice (batch labels count as sliced);
+ * the FP8 form and the COPY+GEMM mapping do not take batch labels. */
 tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* A, const tc_tensor_desc* B,
                   const tc_tensor_desc* C, tc_dtype dtype, tc_math math,
                   tc_mapping mapping, int32_t tile);

@@ -7,6 +7,9 @@
  * The oracle is the definition written out (Sec. 2.1, Sec. 2.3 Einstein
  * convention, Appendix "index contraction"): for every output multi-index,
  * a plain loop over every contracted multi-index accumulating A*B in double.
+ * A label of A, B and C (a batch, or Hadamard, index; beyond the paper's
+ * definition, which pairs every label) is an output label that indexes both
+ * operands: the output loop supplies its value to A, B and C.
  * Compiled with -O2 -ffp-contract=off so each step is a separate multiply
  * and add.  Parallelism (optional OpenMP) is over output elements only; each
  * output is summed by one thread in a fixed order, so the result does not
@@ -59,14 +62,15 @@ int tco_contract_f64(const tco_desc* A, const double* a, const tco_desc* B, cons
   int st;
   if ((st = check_desc(A)) || (st = check_desc(B)) || (st = check_desc(C))) return st;
 
-  /* Output labels: each must come from exactly one operand, with equal extent. */
+  /* Output labels: each comes from one operand, or from both (a batch label),
+   * with equal extents. */
   group_t out;
   memset(&out, 0, sizeof(out));
   out.n = C->order;
   for (int i = 0; i < C->order; ++i) {
     int32_t l = C->labels[i];
     int pa = find(A, l), pb = find(B, l);
-    if ((pa >= 0) == (pb >= 0)) return 2;
+    if (pa < 0 && pb < 0) return 2;
     int64_t e = C->extents[i];
     if (pa >= 0 && A->extents[pa] != e) return 3;
     if (pb >= 0 && B->extents[pb] != e) return 3;
@@ -85,9 +89,8 @@ int tco_contract_f64(const tco_desc* A, const double* a, const tco_desc* B, cons
   for (int i = 0; i < A->order; ++i) {
     int32_t l = A->labels[i];
     int pb = find(B, l), pc = find(C, l);
-    if (pb >= 0 && pc >= 0) return 2;
     if (pb < 0 && pc < 0) return 2;
-    if (pb >= 0) {
+    if (pb >= 0 && pc < 0) {
       if (A->extents[i] != B->extents[pb]) return 3;
       cl[nc++] = l;
     }

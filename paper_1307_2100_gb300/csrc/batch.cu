@@ -288,6 +288,8 @@ extern "C" tc_status tc_batch_plan_routes(tc_batch_t* out, const tc_plan_t* plan
       it.nkb = (int32_t)L.nkb;
       it.chunk_kb = a.chunk_kb;
       it.raster = 0;
+      it.ksplit = 1;
+      it.part = nullptr;
       it.qa = reinterpret_cast<const uint8_t*>(L.off_qa);   // offsets until allocation
       it.qb = reinterpret_cast<const uint8_t*>(L.off_qb);
       const int32_t npk = (int32_t)((L.nkb + 3) / 4);

@@ -360,80 +360,92 @@ tc_status launch_gemv(const GemmArgs& a, tc_dtype dt, int, void* stream) {
 
 // ---------------------------------------------------------------------------
 // GER: rank-K update for K <= TC_GER_MAX_K (the sum-of-GERs slicing of Sec. 2.2
-// done in one pass).  A CTA owns 256 rows x 32 columns of C: each thread loads
-// its row's K values of the first operand into registers, the CTA stages the
-// 32 columns' K values of the second operand in shared memory, and each
-// thread writes its 32 outputs (consecutive threads on consecutive rows, the
-// planner's choice of C's stride-1 index).  KB, the register width, is K
-// rounded up to 4, 8, 16 or 32 (zero-padded).
+// done in one pass).  A CTA owns 256 rows of C and a chunk of its columns:
+// each thread loads its row's K values of the first operand into registers
+// once, then for every 32 columns of the chunk the CTA stages their K values
+// of the second operand in shared memory and each thread writes its 32
+// outputs (consecutive threads on consecutive rows, the planner's choice of
+// C's stride-1 index).  KB, the register width, is K rounded up to 4, 8, 16
+// or 32 (zero-padded).
 // ---------------------------------------------------------------------------
 constexpr int kGerThreads = 256, kGerN = 32;
 
 template <typename T, int KB>
-__global__ void __launch_bounds__(kGerThreads) k_ger(const __grid_constant__ GemmArgs p) {
+__global__ void __launch_bounds__(kGerThreads) k_ger(const __grid_constant__ GemmArgs p,
+                                                     uint32_t tiles_per_chunk) {
   __shared__ T sB[KB][kGerN];
   __shared__ int64_t sC[kGerN];
   const T* __restrict__ X = static_cast<const T*>(p.A);
   const T* __restrict__ Y = static_cast<const T*>(p.B);
   T* __restrict__ Cp = static_cast<T*>(p.C);
   const uint32_t M = (uint32_t)p.M, N = (uint32_t)p.N, K = (uint32_t)p.K;
-  const uint32_t mb = (M + kGerThreads - 1) / kGerThreads, nb = (N + kGerN - 1) / kGerN;
+  const uint32_t mb = (M + kGerThreads - 1) / kGerThreads, nt = (N + kGerN - 1) / kGerN;
+  const uint32_t nchunks = (nt + tiles_per_chunk - 1) / tiles_per_chunk;
+  const T alpha = (T)p.alpha, beta = (T)p.beta;
   const int tid = threadIdx.x;
-  for (uint64_t w = blockIdx.x; w < (uint64_t)mb * nb * (uint64_t)p.nbatch; w += gridDim.x) {
+  for (uint64_t w = blockIdx.x; w < (uint64_t)mb * nchunks * (uint64_t)p.nbatch;
+       w += gridDim.x) {
     const uint32_t bm = (uint32_t)(w % mb);
     const uint64_t r = w / mb;
-    const uint32_t bn = (uint32_t)(r % nb), b = (uint32_t)(r / nb);
+    const uint32_t ch = (uint32_t)(r % nchunks), b = (uint32_t)(r / nchunks);
     int64_t bX, bY, bC;
     goff3(p.gb, b, bX, bY, bC);
-    __syncthreads();  // the previous tile's shared values are no longer read
-    for (int i = tid; i < KB * kGerN; i += kGerThreads) {
-      const int k = i / kGerN, j = i % kGerN;
-      const uint32_t n = bn * kGerN + j;
-      T v = T(0);
-      if (k < (int)K && n < N) {
-        const int64_t oy = goff(p.gn, 1, n) + goff(p.gk, 1, (uint32_t)k);
-        v = Y[bY + oy];
-      }
-      sB[k][j] = v;
-    }
-    if (tid < kGerN) {
-      const uint32_t n = bn * kGerN + tid;
-      sC[tid] = n < N ? goff(p.gn, 2, n) : -1;
-    }
-    __syncthreads();
     const uint32_t m = bm * kGerThreads + tid;
-    if (m >= M) continue;
-    int64_t oxm, ocm;
-    goff2(p.gm, 0, 2, m, oxm, ocm);
+    const bool row_ok = m < M;
+    int64_t oxm = 0, ocm = 0;
+    if (row_ok) goff2(p.gm, 0, 2, m, oxm, ocm);
     T a[KB];
 #pragma unroll
     for (int k = 0; k < KB; ++k)
-      a[k] = k < (int)K ? X[bX + oxm + goff(p.gk, 0, (uint32_t)k)] : T(0);
+      a[k] = (row_ok && k < (int)K) ? X[bX + oxm + goff(p.gk, 0, (uint32_t)k)] : T(0);
     T* Crow = Cp + bC + ocm;
+    const uint32_t t_end = min(nt, (ch + 1) * tiles_per_chunk);
+    for (uint32_t bn = ch * tiles_per_chunk; bn < t_end; ++bn) {
+      __syncthreads();  // the previous columns' shared values are no longer read
+      for (int i = tid; i < KB * kGerN; i += kGerThreads) {
+        const int k = i / kGerN, j = i % kGerN;
+        const uint32_t n = bn * kGerN + j;
+        T v = T(0);
+        if (k < (int)K && n < N) v = Y[bY + goff(p.gn, 1, n) + goff(p.gk, 1, (uint32_t)k)];
+        sB[k][j] = v;
+      }
+      if (tid < kGerN) {
+        const uint32_t n = bn * kGerN + tid;
+        sC[tid] = n < N ? goff(p.gn, 2, n) : -1;
+      }
+      __syncthreads();
+      if (!row_ok) continue;
 #pragma unroll 4
-    for (int j = 0; j < kGerN; ++j) {
-      const int64_t cj = sC[j];
-      if (cj < 0) break;
-      T acc = T(0);
+      for (int j = 0; j < kGerN; ++j) {
+        const int64_t cj = sC[j];
+        if (cj < 0) break;
+        T acc = T(0);
 #pragma unroll
-      for (int k = 0; k < KB; ++k) acc = fma(a[k], sB[k][j], acc);
-      T v = (T)(p.alpha * (double)acc);
-      if (p.beta != 0.0) v = (T)((double)v + p.beta * (double)Crow[cj]);
-      Crow[cj] = v;
+        for (int k = 0; k < KB; ++k) acc = fma(a[k], sB[k][j], acc);
+        // alpha and beta in the storage precision (FP64 is the slow pipe on
+        // this GPU: FP32 outputs stay in FP32)
+        T v = alpha * acc;
+        if (beta != T(0)) v = fma(beta, Crow[cj], v);
+        Crow[cj] = v;
+      }
     }
   }
 }
 
 template <typename T>
 static tc_status ger_t(const GemmArgs& a, cudaStream_t s) {
-  const uint64_t tiles = (uint64_t)((a.M + kGerThreads - 1) / kGerThreads) *
-                         (uint64_t)((a.N + kGerN - 1) / kGerN) * (uint64_t)a.nbatch;
-  if (tiles == 0) return TC_OK;
-  const int grid = (int)std::min<uint64_t>(tiles, 152 * 16);
-  if (a.K <= 4) k_ger<T, 4><<<grid, kGerThreads, 0, s>>>(a);
-  else if (a.K <= 8) k_ger<T, 8><<<grid, kGerThreads, 0, s>>>(a);
-  else if (a.K <= 16) k_ger<T, 16><<<grid, kGerThreads, 0, s>>>(a);
-  else if (a.K <= TC_GER_MAX_K) k_ger<T, TC_GER_MAX_K><<<grid, kGerThreads, 0, s>>>(a);
+  const uint64_t mb = (uint64_t)((a.M + kGerThreads - 1) / kGerThreads) * (uint64_t)a.nbatch;
+  const uint64_t nt = (uint64_t)((a.N + kGerN - 1) / kGerN);
+  if (mb == 0 || nt == 0) return TC_OK;
+  // enough CTAs for 8 per SM, each over as many column tiles as that leaves
+  const uint64_t want_chunks = std::max<uint64_t>(1, (152 * 8 + mb - 1) / mb);
+  const uint32_t tpc = (uint32_t)std::max<uint64_t>(1, (nt + want_chunks - 1) / want_chunks);
+  const uint64_t ctas = mb * ((nt + tpc - 1) / tpc);
+  const int grid = (int)std::min<uint64_t>(ctas, 152 * 16);
+  if (a.K <= 4) k_ger<T, 4><<<grid, kGerThreads, 0, s>>>(a, tpc);
+  else if (a.K <= 8) k_ger<T, 8><<<grid, kGerThreads, 0, s>>>(a, tpc);
+  else if (a.K <= 16) k_ger<T, 16><<<grid, kGerThreads, 0, s>>>(a, tpc);
+  else if (a.K <= TC_GER_MAX_K) k_ger<T, TC_GER_MAX_K><<<grid, kGerThreads, 0, s>>>(a, tpc);
   else return TC_ERR_UNSUPPORTED;
   return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
 }

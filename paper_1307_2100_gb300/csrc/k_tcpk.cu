@@ -232,10 +232,13 @@ struct PkLaunch {
   int64_t nwork;
 };
 
-// The tile of work entry w.
+// The tile and K range of work entry w (one contraction: split-major, the
+// ksplit ranges of every tile; a batch: one range per tile).
 struct Job {
   const PkItem* it;
   int tm, tn;
+  int64_t tile;
+  int split, k0, k1;  // K blocks [k0, k1)
   float* C;
   float alpha, beta;
 };
@@ -243,6 +246,7 @@ struct Job {
 __device__ __forceinline__ Job job_of(const PkLaunch& L, int64_t w) {
   Job j;
   int64_t tile = w;
+  j.split = 0;
   if (L.items) {
     const int32_t item = L.work[2 * w];
     tile = L.work[2 * w + 1];
@@ -255,8 +259,15 @@ __device__ __forceinline__ Job job_of(const PkLaunch& L, int64_t w) {
     j.C = L.C;
     j.alpha = L.alpha;
     j.beta = L.beta;
+    const int64_t ntiles = (int64_t)L.single.tiles_m * L.single.tiles_n;
+    j.split = (int)(w / ntiles);
+    tile = w % ntiles;
   }
   const PkItem& P = *j.it;
+  j.tile = tile;
+  // balanced K ranges, none empty (ksplit <= nkb)
+  j.k0 = (int)((int64_t)j.split * P.nkb / P.ksplit);
+  j.k1 = (int)((int64_t)(j.split + 1) * P.nkb / P.ksplit);
   if (P.raster) {
     j.tn = (int)(tile % P.tiles_n);
     j.tm = (int)(tile / P.tiles_n);
@@ -334,7 +345,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_pk(const __grid_constant__
         const int nkb = J.it->nkb;
         const uint8_t* a = J.it->qa + (size_t)J.tm * nkb * OPB;
         const uint8_t* b = J.it->qb + (size_t)J.tn * nkb * OPB;
-        for (int kb = 0; kb < nkb; ++kb, ++g) {
+        for (int kb = J.k0; kb < J.k1; ++kb, ++g) {
           const int s = (int)(g % S);
           if (g >= (uint32_t)S && !mbar_wait(&empty[s], ((g / S) - 1) & 1, abort, kTimeoutNs)) {
             ok = false;
@@ -359,16 +370,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_pk(const __grid_constant__
       bool ok = true;
       for (int64_t w = blockIdx.x; ok && w < L.nwork; w += gridDim.x) {
         const Job J = job_of(L, w);
-        const int nkb = J.it->nkb;
         const int ckb = max(J.it->chunk_kb, 1);
-        const int nchunks = (nkb + ckb - 1) / ckb;
+        const int nchunks = (J.k1 - J.k0 + ckb - 1) / ckb;
         // the correction accumulator and both main buffers are free once the
         // previous tile's last chunk has been drained
         if (gc >= 1 && !mbar_wait(&acce[(gc - 1) & 1], ((gc - 1) >> 1) & 1, abort, kTimeoutNs)) {
           ok = false;
           break;
         }
-        int kb = 0;
+        int kb = J.k0;
         for (int j = 0; ok && j < nchunks; ++j, ++gc) {
           const uint32_t buf = gc & 1;
           if (gc >= 2 && !mbar_wait(&acce[buf], ((gc >> 1) - 1) & 1, abort, kTimeoutNs)) {
@@ -377,7 +387,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_pk(const __grid_constant__
           }
           tc_fence_after();
           const uint32_t dmain = tmem + buf * TILE;
-          const int kend = min(nkb, (j + 1) * ckb), kstart = kb;
+          const int kend = min(J.k1, J.k0 + (j + 1) * ckb), kstart = kb;
           for (; kb < kend; ++kb, ++g) {
             const int s = (int)(g % S);
             if (!mbar_wait(&full[s], (g / S) & 1, abort, kTimeoutNs)) {
@@ -396,7 +406,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_pk(const __grid_constant__
                 mma_bf16(tmem + COL_CORR,
                          smem_desc(sa + kProdA[pi] * TERM + kk * 2 * LBO, LBO, 128),
                          smem_desc(sb + kProdB[pi] * TERM + kk * 2 * LBO, LBO, 128), idesc,
-                         (kb > 0 || kk > 0 || pi > 1) ? 1u : 0u);
+                         (kb > J.k0 || kk > 0 || pi > 1) ? 1u : 0u);
             }
             mma_commit(&empty[s]);
           }
@@ -433,7 +443,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_pk(const __grid_constant__
       const int64_t m = (int64_t)J.tm * TILE + row;
       const int64_t rc = m < P.M ? goff(P.gm, 2, (uint32_t)m) : -1;
       const int ckb = max(P.chunk_kb, 1);
-      const int nchunks = (P.nkb + ckb - 1) / ckb;
+      const int nchunks = (J.k1 - J.k0 + ckb - 1) / ckb;
+      const bool partial = P.ksplit > 1;
+      // partial sums of this K range: [split][tile][col][row], the compensated
+      // pair (s, r) in FP32 (the FP64 sum is formed by the reduction)
+      float2* pp = partial ? P.part + ((size_t)J.split * P.tiles_m * P.tiles_n + J.tile) *
+                                          (size_t)(TILE * TILE) + (size_t)h * 64 * TILE + row
+                           : nullptr;
       float lo[64];
 #pragma unroll
       for (int i = 0; i < 64; ++i) lo[i] = 0.0f;
@@ -481,12 +497,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_pk(const __grid_constant__
               const float s = two_sum(hi0, __uint_as_float(mv[i]), e);
               float r = __fadd_rn(lo[c * 16 + i], e);
               if (NT > 1) r = __fadd_rn(r, __uint_as_float(cv[i]));
-              lo[c * 16 + i] = __fadd_rn(s, r);
+              if (partial) pp[(size_t)(c * 16 + i) * TILE] = make_float2(s, r);
+              else lo[c * 16 + i] = __fadd_rn(s, r);
             }
           }
           tc_fence_before();
           mbar_arrive(&acce[buf]);  // main, correction and high word are free
-          if (rc >= 0) {
+          if (!partial && rc >= 0) {
             float* Cr = J.C + rc;
 #pragma unroll
             for (int i = 0; i < 64; ++i) {
@@ -508,6 +525,37 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_pk(const __grid_constant__
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// Split-K: C = alpha * (sum of the K ranges' partial sums, in order) + beta * C.
+__global__ void __launch_bounds__(256) k_pk_reduce(const __grid_constant__ PkLaunch L) {
+  const PkItem& P = L.single;
+  const int64_t ntiles = (int64_t)P.tiles_m * P.tiles_n;
+  const int64_t total = ntiles * TILE * TILE;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t tile = e / (TILE * TILE);
+    const int col = (int)((e / TILE) % TILE), row = (int)(e % TILE);
+    int tm, tn;
+    if (P.raster) {
+      tn = (int)(tile % P.tiles_n);
+      tm = (int)(tile / P.tiles_n);
+    } else {
+      tm = (int)(tile % P.tiles_m);
+      tn = (int)(tile / P.tiles_m);
+    }
+    const int64_t m = (int64_t)tm * TILE + row, n = (int64_t)tn * TILE + col;
+    if (m >= P.M || n >= P.N) continue;
+    double t = 0.0;
+    for (int sp = 0; sp < P.ksplit; ++sp) {
+      const float2 v = P.part[(size_t)sp * total + e];
+      t += (double)v.x + (double)v.y;
+    }
+    float* dst = L.C + goff(P.gm, 2, (uint32_t)m) + goff(P.gn, 2, (uint32_t)n);
+    float x = (float)(L.alpha * t);
+    if (L.beta != 0.0f) x = fmaf(L.beta, *dst, x);
+    *dst = x;
   }
 }
 
@@ -589,13 +637,22 @@ tc_status launch(const GemmArgs& a, const PkLayout& L, void* ws, cudaStream_t s)
   it.nkb = (int32_t)L.nkb;
   it.chunk_kb = a.chunk_kb;
   it.raster = a.raster;
+  it.ksplit = pk_ksplit(a);
+  it.part = it.ksplit > 1 ? reinterpret_cast<float2*>(w + L.bytes) : nullptr;
   g.C = static_cast<float*>(a.C);
   g.alpha = (float)a.alpha;
   g.beta = (float)a.beta;
-  g.nwork = L.tiles_m * L.tiles_n;
+  g.nwork = L.tiles_m * L.tiles_n * it.ksplit;
   const int grid = (int)std::min<int64_t>(g.nwork, sms);
   k_gemm_pk<NT><<<grid, kThreads, sm, s>>>(g);
-  return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;
+  if (it.ksplit > 1) {
+    const int64_t total = L.tiles_m * L.tiles_n * TILE * TILE;
+    const int rgrid = (int)std::min<int64_t>((total + 255) / 256, (int64_t)sms * 8);
+    k_pk_reduce<<<rgrid, 256, 0, s>>>(g);
+    if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;
+  }
+  return TC_OK;
 }
 
 template <int NT>
@@ -631,6 +688,23 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static int terms_of(int math) {
   return math == TC_MATH_BF16 ? 1 : math == TC_MATH_BF16X3 ? 2 : math == TC_MATH_BF16X6 ? 3 : 0;
+}
+
+// Split-K: tiles fewer than the SMs share out their K blocks, so that about
+// two work entries per SM exist, each of at least 512 K (16 blocks).
+int pk_ksplit(const GemmArgs& a) {
+  const int64_t tiles = ((a.M + pk::TILE - 1) / pk::TILE) * ((a.N + pk::TILE - 1) / pk::TILE);
+  const int64_t nkb = (a.K + pk::BK - 1) / pk::BK;
+  if (tiles <= 0 || tiles >= 152) return 1;
+  const int64_t want = (2 * 152 + tiles - 1) / tiles;
+  return (int)std::max<int64_t>(1, std::min<int64_t>({want, nkb / 16, 64}));
+}
+
+size_t pk_part_bytes(const GemmArgs& a) {
+  const int sp = pk_ksplit(a);
+  if (sp <= 1) return 0;
+  const int64_t tiles = ((a.M + pk::TILE - 1) / pk::TILE) * ((a.N + pk::TILE - 1) / pk::TILE);
+  return (size_t)sp * (size_t)tiles * pk::TILE * pk::TILE * sizeof(float2);
 }
 
 PkLayout pk_layout(const GemmArgs& a, int math) {

@@ -88,6 +88,7 @@ bool output_aliases(const Tens& c) {
 
 struct Analysis {
   std::vector<int32_t> con, fa, fb;  // contracted, free of A, free of B (all extents)
+  std::vector<int32_t> bat;          // batch labels: in A, B and C
   std::map<int32_t, int64_t> ext;
   int cls = 0;
   int p = 0, da = 0, db = 0;
@@ -294,20 +295,20 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   for (size_t i = 0; i < C.lab.size(); ++i) {
     int32_t l = C.lab[i];
     int pa = A.find(l), pb = B.find(l);
-    if (pa >= 0 && pb >= 0) return TC_ERR_UNSUPPORTED;  // batch / Hadamard index
     if (pa < 0 && pb < 0) return TC_ERR_LABEL;
     int64_t e = C.ext[i];
     if ((pa >= 0 && A.ext[pa] != e) || (pb >= 0 && B.ext[pb] != e)) return TC_ERR_EXTENT_MISMATCH;
+    if (pa >= 0 && pb >= 0) an.bat.push_back(l);  // batch (Hadamard) label
     an.ext[l] = e;
   }
   for (size_t i = 0; i < A.lab.size(); ++i) {
     int32_t l = A.lab[i];
     int pb = B.find(l), pc = C.find(l);
     if (pb < 0 && pc < 0) return TC_ERR_LABEL;
-    if (pb >= 0) {
+    if (pb >= 0 && pc < 0) {
       if (A.ext[i] != B.ext[pb]) return TC_ERR_EXTENT_MISMATCH;
       an.con.push_back(l);
-    } else {
+    } else if (pb < 0) {
       an.fa.push_back(l);
     }
     an.ext[l] = A.ext[i];
@@ -322,7 +323,22 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   }
   if (output_aliases(C)) return TC_ERR_STRIDE;
 
-  classify(A, B, C, an);
+  // the class is that of one batch slice: batch labels are left out
+  if (an.bat.empty()) {
+    classify(A, B, C, an);
+  } else {
+    auto drop = [&](const Tens& T) {
+      Tens R;
+      for (size_t i = 0; i < T.lab.size(); ++i)
+        if (!contains(an.bat, T.lab[i])) {
+          R.lab.push_back(T.lab[i]);
+          R.ext.push_back(T.ext[i]);
+          R.st.push_back(T.st[i]);
+        }
+      return R;
+    };
+    classify(drop(A), drop(B), drop(C), an);
+  }
 
   Plan* P = new (std::nothrow) Plan();
   if (!P) return TC_ERR_INVALID_ARG;
@@ -444,6 +460,7 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
         const bool feasible =
             cm >= TC_MAP_SLICE_GEMM && cm <= TC_MAP_GER &&
             (class3 || (cm != TC_MAP_SLICE_GEMM && cm != TC_MAP_COPY_GEMM)) &&
+            (cm != TC_MAP_COPY_GEMM || an.bat.empty()) &&
             (cm != TC_MAP_GER || kprod <= TC_GER_MAX_K);
         if (feasible && (!found || pred[i] < best)) {
           map = cm;
@@ -458,8 +475,10 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
     map = (an.cls == 1) ? TC_MAP_DOT : (an.cls == 2) ? TC_MAP_GEMV : TC_MAP_FUSED_GEMM;
   const bool is3 = an.cls == 31 || an.cls == 32;
   const bool fp8 = math == TC_MATH_FP8;
-  if (fp8 && (!is3 || map != TC_MAP_FUSED_GEMM)) {
-    // the FP8 form is one block-scaled GEMM: Class 3, fused mapping only
+  if ((fp8 && (!is3 || map != TC_MAP_FUSED_GEMM || !an.bat.empty())) ||
+      (map == TC_MAP_COPY_GEMM && !an.bat.empty())) {
+    // the FP8 form is one block-scaled GEMM: Class 3, fused mapping, no batch
+    // labels; the COPY baseline's dense copy has no batch labels either
     delete P;
     return TC_ERR_UNSUPPORTED;
   }
@@ -504,6 +523,7 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
       if (l != mx) lb.push_back(l);
     for (auto l : fy)
       if (l != ny) lb.push_back(l);
+    for (auto l : an.bat) lb.push_back(l);
     lb = sorted_by(lb, C);
     if (kk >= 0) lk.push_back(kk);
     for (auto l : sorted_by(an.con, X))
@@ -513,6 +533,7 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
     ln = sorted_by(fy, Y);
     // the FP8 form's scale blocks follow A's strides, whichever operand is first
     lk = sorted_by(an.con, fp8 ? A : X);
+    lb = sorted_by(an.bat, C);  // batch labels: one GEMM per value
   }
 
   // COPY+GEMM: permute the copied operand (the one whose stride-1 index the
@@ -639,7 +660,8 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   ws = (ws + 255) & ~(size_t)255;
   if (P->copy_which) ws += ((size_t)P->copy_elems * es + 255) & ~(size_t)255;
   if (kernel == K_GEMM_FP8) ws += fp8_layout(g).bytes;
-  if (kernel == K_GEMM_TC && tile == kTilePacked) ws += pk_layout(g, math).bytes;
+  if (kernel == K_GEMM_TC && tile == kTilePacked)
+    ws += pk_layout(g, math).bytes + pk_part_bytes(g);  // packed terms, split-K partials
   P->workspace = ws;
 
   info.mapping = map;

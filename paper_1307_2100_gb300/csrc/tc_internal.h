@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <vector>
 
+#include <vector_types.h>  // float2
+
 #include "tc.h"
 
 namespace tc {
@@ -131,6 +133,10 @@ struct PkLayout {
   size_t off_qa, off_qb, bytes;
 };
 PkLayout pk_layout(const GemmArgs& a, int math);
+// K ranges of a packed GEMM (split-K when there are fewer tiles than SMs),
+// and the bytes of its partial sums (part of the plan's workspace).
+int pk_ksplit(const GemmArgs& a);
+size_t pk_part_bytes(const GemmArgs& a);
 tc_status launch_gemm_tc_packed(const GemmArgs& a, int math, void* ws, void* stream);
 tc_status tc_pk_read_status(int* h, void* stream);
 
@@ -140,7 +146,9 @@ struct PkItem {
   const uint8_t* qa;     // packed terms of the first and second operand
   const uint8_t* qb;
   int64_t M, N;
-  int32_t tiles_m, tiles_n, nkb, chunk_kb, raster, pad_;
+  int32_t tiles_m, tiles_n, nkb, chunk_kb, raster;
+  int32_t ksplit;        // K ranges per tile (1: the tile writes C)
+  float2* part;          // ksplit > 1: compensated partial sums [split][tile][col][row]
 };
 // Tensor-core route of a batch on packed operands (device tables owned by
 // the batch): the pack entries (item, operand, row tile, 128-K chunk; int32

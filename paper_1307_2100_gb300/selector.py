@@ -30,7 +30,9 @@ from . import tc
 
 # (name, mapping, tile configuration; -1 = the plan's default).  The fused and
 # COPY+GEMM mappings run on packed operands (tile 3) or on the gathering
-# tensor-core kernel (tile 0); the slicing mapping's batches on the latter.
+# tensor-core kernel (tile 0); the slicing mapping's batches on the latter;
+# GER (K <= 32) on the CUDA cores in FP32.  New candidates go at the end (the
+# timing tables keep their columns).
 CANDIDATE_SPECS = [
     ("fused_gemm", "fused_gemm", 3),
     ("fused_gemm_gather", "fused_gemm", 0),
@@ -39,6 +41,7 @@ CANDIDATE_SPECS = [
     ("copy_gemm_gather", "copy_gemm", 0),
     ("gemv", "gemv", -1),
     ("dot", "dot", -1),
+    ("ger", "ger", -1),
 ]
 CANDIDATES = [c[0] for c in CANDIDATE_SPECS]
 CAND_IDS = [tc.MAPPING[m] | ((t + 1) << 8) for _, m, t in CANDIDATE_SPECS]
@@ -158,6 +161,9 @@ def fill(data, out, reps=5, ws_bytes=1 << 31, log=sys.stderr):
     import tcsynth as ts
     z = dict(np.load(data))
     T = z["T"].copy()
+    if T.shape[1] < len(CANDIDATES):   # candidates added since: untimed columns
+        T = np.concatenate([T, np.full((len(T), len(CANDIDATES) - T.shape[1]), np.nan)], 1)
+        z["candidates"] = np.array(CAND_IDS, np.int32)
     descs = ts.selector_descriptors(len(T), seed=int(z["seed"]))
     ensure, time_plan, s = _timer(ws_bytes)
     todo = [(i, j) for i, j in zip(*np.where(~np.isfinite(T)))]
@@ -270,7 +276,8 @@ def write_weights(path, n_in, n_hidden, n_out, cand, lo, hi, mean, scale, ym, ys
 
 def feasible(cls):
     """Candidates able to compute a contraction of the given class: slicing and
-    COPY+GEMM need a free index in each operand (Class 3)."""
+    COPY+GEMM need a free index in each operand (Class 3); GER's limit on K
+    shows as a missing timing."""
     ok = np.ones((len(cls), len(CANDIDATES)), bool)
     c3 = np.isin(cls, [31, 32])
     for j, (_, mname, _t) in enumerate(CANDIDATE_SPECS):

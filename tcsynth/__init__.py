@@ -343,6 +343,17 @@ def gemv_1024_full(seed=BASE_SEED + 1, b=1024, alloc=None) -> Problem:
                        alloc=alloc)
 
 
+def ccd_skewed(free: int, occ: int, beta: int = 8, seed: int = BASE_SEED + 5,
+               dtype=np.float64, alloc=None) -> Problem:
+    """R[a,b,c,d] = sum_{i,j} X[i,a,j,b] Y[i,c,j,d], the CCD contraction of
+    Sec. 4.2 (X^{i alpha j beta} Y_{i gamma j delta}) with a = c = d = free,
+    b = beta fixed and i = j = occ; column-major, uniform[-1, 1) entries.
+    occ = 4 is the GR case of the same section."""
+    return big_problem(f"ccd_f{free}_o{occ}", "iajb", "icjd", "abcd",
+                       dict(i=occ, j=occ, a=free, b=beta, c=free, d=free), seed + free * 7 + occ,
+                       dtype, alloc)
+
+
 def selector_descriptors(n: int, seed: int = BASE_SEED + 4, lo: int = 4, hi: int = 256,
                          max_elems: int = 1 << 24, max_out: int = 1 << 24,
                          max_flops: float = float(1 << 35)):

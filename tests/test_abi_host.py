@@ -114,7 +114,6 @@ def _desc(ls, strides=None):
 
 
 @pytest.mark.parametrize("A,B,C,code", [
-    (_desc("ai"), _desc("ib"), _desc("abi"), 5),          # label in A, B and C
     (_desc("ai"), _desc("jb"), _desc("ab"), 2),           # label in neither C nor B
     (_desc("ai"), _desc("ib"), _desc("a"), 2),            # free label of B not in C
     (_desc("aa"), _desc("ab"), _desc("b"), 2),            # repeated label
@@ -317,3 +316,22 @@ def test_layout_advice_on_the_paper_case():
         tc.tc_plan_destroy(h)
     assert adv.operand == 2 and adv.cls_after == 32
     assert ts.lab("jcid")[adv.storage_order[0]] in ts.lab("cd")   # a free index of B first
+
+
+def test_batch_labels_form_the_batch_group():
+    # C[a,b,z] = sum_i A[a,i,z] B[i,b,z]: one GEMM per z
+    p = ts.problem("bat", "aiz", "ibz", "abz", dict(a=40, i=30, b=20, z=7), 91)
+    info = plan_info(p)
+    assert (info.cls, info.M, info.N, info.K, info.batch) == (32, 40, 20, 30, 7)
+    assert info.slice_a & 4 and info.slice_b & 4            # z counts as sliced
+    # the FP8 form and the COPY baseline take no batch labels
+    p32 = f32p = ts.problem("bat", "aiz", "ibz", "abz", dict(a=40, i=30, b=20, z=7), 91,
+                            dtype=np.float32)
+    assert tc.tc_plan_status(_t(f32p.A), _t(f32p.B), _t(f32p.C), tc.TC_F32,
+                             tc.MATH["fp8"]) == 5
+    assert tc.tc_plan_status(_t(p.A), _t(p.B), _t(p.C), tc.TC_F64, 0,
+                             tc.MAPPING["copy_gemm"]) == 5
+    # Hadamard product (nothing contracted): K = 1
+    h = ts.problem("had", "ab", "ab", "ab", dict(a=9, b=5), 92)
+    hi = plan_info(h)
+    assert hi.batch == 45 and hi.K == 1

@@ -148,3 +148,21 @@ def test_gathering_kernel_multi_label_k_groups():
             acc, _ = tc_bounds(p, "bf16x6", chunk_k={0: 256, 1: 64, 2: 1024}[tile])
             ok, d = within(got, op.contract_form(p, "bf16x6"), mag, p.C, acc)
             assert ok, (j, tile, d)
+
+
+def test_packed_split_k():
+    """Few output tiles and a long K (the CCD shape of Sec. 4.2 with short free
+    extents): the packed GEMM shares K out among CTAs and adds their FP64
+    partial sums in order; every form within its bound."""
+    p = f32(ts.problem("splitk", "iajb", "icjd", "abcd",
+                       dict(i=60, j=55, a=30, b=8, c=30, d=9), 121))
+    plans = []
+    for form in FORMS:
+        got = run(p, form, "fused_gemm", 3, plan_out=plans)
+        acc, _ = tc_bounds(p, form)
+        ok, d = within(got, op.contract_form(p, form), magnitude(p), p.C, acc)
+        assert ok, (form, d)
+    # 2 x 3 tiles of 128 x 128 and 104 K blocks: split-K workspace in the plan
+    info = plans[-1]
+    tiles = -(-info["M"] // 128) * -(-info["N"] // 128)
+    assert tiles < 152 and info["workspace"] > 0

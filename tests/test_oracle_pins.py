@@ -249,7 +249,6 @@ def test_empty_output_is_noop_and_scalar_output():
 
 @pytest.mark.parametrize("la,lb,lc,code", [
     ("aa", "ab", "b", 2),        # repeated label in one tensor
-    ("ai", "ib", "abi", 2),      # label in A, B and C (Hadamard index)
     ("ai", "ib", "a", 2),        # free label of B missing from C
     ("ai", "jb", "ab", 2),       # label in A only, not in C
 ])
@@ -268,3 +267,24 @@ def test_extent_mismatch_rejected():
     C = ts.Tensor(lab("ab"), [3, 2], [1, 3], np.zeros(6))
     with pytest.raises(oracle.OracleError, match="status 3"):
         oracle.contract(A, B, C)
+
+
+def test_batch_labels_are_batched_matrix_products():
+    # C[a,b,z] = sum_i A[a,i,z] B[i,b,z]: numpy's batched matmul, slice by slice
+    p = _prob("aiz", "ibz", "abz", dict(a=5, i=7, b=4, z=6), seed=31, dist="int", lo=-4, hi=4)
+    A = _dense(p.A)
+    B = _dense(p.B)
+    want = np.einsum("aiz,ibz->abz", A, B)
+    got = oracle.contract_problem(p).reshape(p.C.extents, order="F")
+    np.testing.assert_array_equal(got, want)
+    for z in range(6):
+        np.testing.assert_array_equal(got[:, :, z], A[:, :, z] @ B[:, :, z])
+
+
+def test_hadamard_and_batched_dot():
+    p = _prob("ab", "ab", "ab", dict(a=9, b=5), seed=32)   # no contracted label
+    np.testing.assert_allclose(oracle.contract_problem(p).reshape(9, 5, order="F"),
+                               _dense(p.A) * _dense(p.B), rtol=1e-15)
+    q = _prob("iz", "iz", "z", dict(i=50, z=7), seed=33)   # a dot product per z
+    np.testing.assert_allclose(oracle.contract_problem(q), np.sum(_dense(q.A) * _dense(q.B), 0),
+                               rtol=1e-13)
