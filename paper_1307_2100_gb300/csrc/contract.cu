@@ -42,7 +42,9 @@ extern "C" tc_status tc_contract(tc_plan_t plan, double alpha, const void* A, co
     pa.out = ws;
     if ((st = launch_perm(pa, P->dtype, stream)) != TC_OK) return st;
     if (P->copy_which == 1) a.A = ws; else a.B = ws;
+    ws += align256((size_t)P->copy_elems * elem_size(P->dtype));
   }
+  if (P->kernel == K_GEMM_SIMT && a.ksplit > 1) a.ws = ws;  // split-K partial tiles
   switch (P->kernel) {
     case K_GEMM_SIMT: return launch_gemm_simt(a, P->dtype, P->tile, stream);
     case K_GEMM_TC:

@@ -21,7 +21,10 @@ namespace tc {
 // GEMM on the CUDA cores.  CTA tile TM x TN, K step TK, each thread a 4x4
 // register tile (rows ty + i*TM/4, columns tx + j*TN/4).  Tiles are taken in
 // the order (m-tile fastest, n-tile, batch).  The next K block is fetched into
-// registers while the current one is multiplied.
+// registers while the current one is multiplied.  With p.ksplit > 1 (FP64,
+// fewer tiles than SMs) the work entries are (K range, tile), K ranges
+// slowest; each writes its partial tile [TM][TN] to the workspace and
+// k_simt_reduce adds the ranges in order.
 // ---------------------------------------------------------------------------
 template <typename T, int TM, int TN, int TK>
 __global__ void __launch_bounds__((TM / 4) * (TN / 4))
@@ -42,8 +45,15 @@ __global__ void __launch_bounds__((TM / 4) * (TN / 4))
   const uint32_t M = (uint32_t)p.M, N = (uint32_t)p.N, K = (uint32_t)p.K;
   const uint32_t tiles_m = (M + TM - 1) / TM, tiles_n = (N + TN - 1) / TN;
   const uint64_t total = (uint64_t)tiles_m * tiles_n * (uint64_t)p.nbatch;
+  const int ksplit = max(p.ksplit, 1);
+  const uint32_t nkb_all = (K + TK - 1) / TK;
 
-  for (uint64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+  for (uint64_t wk = blockIdx.x; wk < total * (uint64_t)ksplit; wk += gridDim.x) {
+    const uint64_t tile = wk % total;
+    const uint32_t split = (uint32_t)(wk / total);
+    // K blocks [kb0, kb1) of this range (balanced, none empty)
+    const uint32_t kb0 = (uint32_t)((uint64_t)split * nkb_all / ksplit);
+    const uint32_t kb1 = (uint32_t)((uint64_t)(split + 1) * nkb_all / ksplit);
     const uint32_t tm = (uint32_t)(tile % tiles_m);
     const uint64_t rest = tile / tiles_m;
     const uint32_t tn = (uint32_t)(rest % tiles_n);
@@ -75,7 +85,7 @@ __global__ void __launch_bounds__((TM / 4) * (TN / 4))
         offBk[buf][i] = ob;
       }
     };
-    k_offsets(0, 0);
+    k_offsets(0, kb0 * TK);
     __syncthreads();
 
     T ra[LA], rb[LB];
@@ -132,15 +142,14 @@ __global__ void __launch_bounds__((TM / 4) * (TN / 4))
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
 
-    const uint32_t nk = (K + TK - 1) / TK;
-    if (nk > 0) fetch(0);
-    for (uint32_t kb = 0; kb < nk; ++kb) {
-      const int buf = kb & 1;
+    if (kb0 < kb1) fetch(0);
+    for (uint32_t kb = kb0; kb < kb1; ++kb) {
+      const int buf = (kb - kb0) & 1;
       __syncthreads();  // everyone is done reading As/Bs of the previous block
       stash();
-      if (kb + 1 < nk) k_offsets(buf ^ 1, (kb + 1) * TK);
+      if (kb + 1 < kb1) k_offsets(buf ^ 1, (kb + 1) * TK);
       __syncthreads();
-      if (kb + 1 < nk) fetch(buf ^ 1);
+      if (kb + 1 < kb1) fetch(buf ^ 1);
 #pragma unroll
       for (int kk = 0; kk < TK; ++kk) {
         T a[4], bv[4];
@@ -155,6 +164,15 @@ __global__ void __launch_bounds__((TM / 4) * (TN / 4))
       }
     }
 
+    if (ksplit > 1) {  // partial tile of this K range
+      T* part = static_cast<T*>(p.ws) + (split * total + tile) * (uint64_t)(TM * TN);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          part[(ty + i * (TM / 4)) * TN + tx + j * (TN / 4)] = acc[i][j];
+      continue;
+    }
     const T alpha = (T)p.alpha, beta = (T)p.beta;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -181,20 +199,77 @@ static int grid_for(uint64_t total) {
   return (int)std::min<uint64_t>(total, (uint64_t)1 << 30);
 }
 
+// Split-K: C = alpha * (sum of the K ranges' partial tiles, in order) + beta * C.
+template <typename T, int TM, int TN>
+__global__ void __launch_bounds__(256) k_simt_reduce(const __grid_constant__ GemmArgs p) {
+  const uint32_t M = (uint32_t)p.M, N = (uint32_t)p.N;
+  const uint32_t tiles_m = (M + TM - 1) / TM, tiles_n = (N + TN - 1) / TN;
+  const uint64_t total = (uint64_t)tiles_m * tiles_n * (uint64_t)p.nbatch;
+  const uint64_t elems = total * (uint64_t)(TM * TN);
+  const T* part = static_cast<const T*>(p.ws);
+  T* C = static_cast<T*>(p.C);
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < elems;
+       e += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t tile = e / (TM * TN);
+    const int ml = (int)((e / TN) % TM), nl = (int)(e % TN);
+    const uint32_t tm = (uint32_t)(tile % tiles_m);
+    const uint64_t rest = tile / tiles_m;
+    const uint32_t tn = (uint32_t)(rest % tiles_n), b = (uint32_t)(rest / tiles_n);
+    const uint32_t m = tm * TM + ml, n = tn * TN + nl;
+    if (m >= M || n >= N) continue;
+    T t = T(0);
+    for (int sp = 0; sp < p.ksplit; ++sp) t += part[(uint64_t)sp * elems + e];
+    int64_t bA, bB, bC;
+    goff3(p.gb, b, bA, bB, bC);
+    T* dst = C + bC + goff(p.gm, 2, m) + goff(p.gn, 2, n);
+    T v = (T)p.alpha * t;
+    if (p.beta != 0.0) v = fma((T)p.beta, *dst, v);
+    *dst = v;
+  }
+}
+
+// FP64 split-K: with fewer 64 x 64 tiles than SMs and a long K, at most two
+// (K range, tile) entries per SM (two CTAs of 256 threads fit one SM), so that
+// they run in one wave, each of at least 512 K (32 blocks of 16).
+int simt_ksplit(const GemmArgs& a, tc_dtype dt, int tile) {
+  if (dt != TC_F64 || tile != 0) return 1;
+  const int64_t tiles = ((a.M + 63) / 64) * ((a.N + 63) / 64) * std::max<int64_t>(a.nbatch, 1);
+  const int64_t nkb = (a.K + 15) / 16;
+  if (tiles <= 0 || tiles >= 152) return 1;
+  const int64_t want = (2 * 152) / tiles;
+  return (int)std::max<int64_t>(1, std::min<int64_t>({want, nkb / 32, 64}));
+}
+
+size_t simt_part_bytes(const GemmArgs& a, tc_dtype dt, int tile) {
+  const int sp = simt_ksplit(a, dt, tile);
+  if (sp <= 1) return 0;
+  const int64_t tiles = ((a.M + 63) / 64) * ((a.N + 63) / 64) * std::max<int64_t>(a.nbatch, 1);
+  return (size_t)sp * (size_t)tiles * 64 * 64 * sizeof(double);
+}
+
 template <typename T>
 static tc_status gemm_simt_t(const GemmArgs& a, int tile, cudaStream_t s) {
   const SimtTile t = kSimtTiles[tile];
   const uint64_t total = (uint64_t)((a.M + t.tm - 1) / t.tm) * (uint64_t)((a.N + t.tn - 1) / t.tn) *
                          (uint64_t)a.nbatch;
   if (total == 0) return TC_OK;
-  const int grid = grid_for(total);
+  const int ksplit = std::max(a.ksplit, 1);
+  if (ksplit > 1 && (!a.ws || t.tm != 64 || t.tn != 64)) return TC_ERR_WORKSPACE;
+  const int grid = grid_for(total * (uint64_t)ksplit);
   if (t.tm == 64 && t.tn == 64)
     k_gemm_simt<T, 64, 64, 16><<<grid, 256, 0, s>>>(a);
   else if (t.tm == 32 && t.tn == 32)
     k_gemm_simt<T, 32, 32, 16><<<grid, 64, 0, s>>>(a);
   else
     k_gemm_simt<T, 128, 64, 16><<<grid, 512, 0, s>>>(a);
-  return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;
+  if (ksplit > 1) {
+    const uint64_t elems = total * 64 * 64;
+    k_simt_reduce<T, 64, 64><<<grid_for(std::min<uint64_t>((elems + 255) / 256, 152 * 16)), 256,
+                               0, s>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;
+  }
+  return TC_OK;
 }
 
 tc_status launch_gemm_simt(const GemmArgs& a, tc_dtype dt, int tile, void* stream) {

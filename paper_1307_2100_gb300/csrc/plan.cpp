@@ -637,9 +637,12 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   }
   if (tile < 0) {
     if (kernel == K_GEMM_SIMT) {
-      // enough 64x64 tiles to fill the GPU twice, else the small tile
+      // enough 64x64 tiles to fill the GPU twice, else the small tile; FP64
+      // with a long K keeps the 64x64 tile and splits K instead
       int64_t t64 = ((M + 63) / 64) * ((N + 63) / 64) * std::max<int64_t>(Bt, 1);
       tile = t64 >= 2 * 152 ? 0 : 1;
+      g.ksplit = 1;
+      if (tile == 1 && simt_ksplit(g, dtype, 0) > 1) tile = 0;
     } else if (kernel == K_GEMM_TC) {
       // the gathering kernel for a batch of GEMMs (the slicing mapping) and
       // for skinny operands
@@ -662,6 +665,10 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   if (kernel == K_GEMM_FP8) ws += fp8_layout(g).bytes;
   if (kernel == K_GEMM_TC && tile == kTilePacked)
     ws += pk_layout(g, math).bytes + pk_part_bytes(g);  // packed terms, split-K partials
+  if (kernel == K_GEMM_SIMT) {
+    g.ksplit = simt_ksplit(g, dtype, tile);
+    ws += simt_part_bytes(g, dtype, tile);               // FP64 split-K partial tiles
+  }
   P->workspace = ws;
 
   info.mapping = map;

@@ -53,8 +53,8 @@ struct GemmArgs {
   int32_t raster;              // tensor-core GEMM: 1 = n-tiles fastest in launch order
   int32_t chunk_kb;            // tensor-core GEMM: K blocks per FP32 accumulation chunk
   int32_t swapped;             // batched items: the kernel's first operand is B
-  int32_t pad_;
-  void* ws;                    // workspace (DOT partials)
+  int32_t ksplit;              // FP64 CUDA-core GEMM: K ranges per tile (1: tiles write C)
+  void* ws;                    // workspace (DOT partials; split-K partial tiles)
   int64_t ws_elems;
 };
 
@@ -102,6 +102,10 @@ bool selector_predict(const float* features, tc_dtype dtype, tc_math math, int32
 
 // Kernel launchers (k_simt.cu); `stream` is a cudaStream_t.
 tc_status launch_gemm_simt(const GemmArgs& a, tc_dtype dt, int tile, void* stream);
+// FP64 CUDA-core GEMM split-K: K ranges per tile for tile configuration
+// `tile`, and the bytes of their partial tiles (part of the workspace).
+int simt_ksplit(const GemmArgs& a, tc_dtype dt, int tile);
+size_t simt_part_bytes(const GemmArgs& a, tc_dtype dt, int tile);
 tc_status launch_gemv(const GemmArgs& a, tc_dtype dt, int tile, void* stream);
 tc_status launch_dot(const GemmArgs& a, tc_dtype dt, int tile, void* stream);
 tc_status launch_ger(const GemmArgs& a, tc_dtype dt, void* stream);

@@ -226,6 +226,25 @@ def test_tensor_core_tile_defaults():
                              tc.MAPPING["slice_gemm"], 3) == 5
 
 
+def test_fp64_split_k_workspace():
+    # FP64 on the CUDA cores with fewer 64 x 64 tiles than SMs and a long K:
+    # min(floor(2 * 152 / tiles), K blocks of 16 / 32, 64) ranges, each with
+    # FP64 partial tiles in the workspace; other tiles, dtypes, shapes: none
+    p = ts.problem("sk", "ai", "ib", "ab", dict(a=130, i=5003, b=70), 61)
+    info = plan_info(p)
+    tiles = 3 * 2
+    ks = min(304 // tiles, (5003 + 15) // 16 // 32, 64)
+    assert info.kernel == 1 and info.tile == 0 and ks == 9
+    assert info.workspace == ks * tiles * 64 * 64 * 8
+    for tile in (1, 2):
+        assert plan_info(p, tile=tile).workspace == 0
+    assert plan_info(p, tc.MATH["fp32"], dtype=tc.TC_F32).workspace == 0
+    short = ts.problem("sk_short", "ai", "ib", "ab", dict(a=130, i=900, b=70), 61)
+    assert plan_info(short).workspace == 0          # under 64 K blocks: one range
+    wide = ts.problem("sk_wide", "ai", "ib", "ab", dict(a=1100, i=5003, b=1100), 61)
+    assert plan_info(wide).workspace == 0           # 18 x 18 tiles fill the GPU
+
+
 def test_batch_routes_are_checked_before_any_allocation():
     bf = tc.MATH["bf16x6"]
     p = ts.fused_permute_48(n=6)

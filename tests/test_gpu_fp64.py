@@ -135,3 +135,31 @@ def test_fp64_full_size_gemv_sampled():
     ref = sample_outputs(p, s)
     assert oracle.rel_fro(gather(got, p.C, s), ref) <= TOL_FP64
     assert np.all(np.isfinite(got))
+
+
+def test_fp64_split_k_long_k():
+    """Few output tiles and a long K: the 64 x 64 tiles split K into ranges
+    whose partial tiles are summed in order (ragged M, N and K, several
+    contracted labels, alpha/beta, the copying mapping)."""
+    cases = [ts.problem("sk_ragged", "ai", "ib", "ab", dict(a=130, i=5003, b=70), 61),
+             ts.problem("sk_multik", "aijb", "ijc", "abc", dict(a=3, i=41, j=37, b=40, c=67), 62),
+             ts.problem("sk_perm", "iajb", "jcid", "abcd",
+                        dict(i=45, a=9, j=47, b=7, c=5, d=11), 63)]
+    for p in cases:
+        info = []
+        ref = oracle.contract_problem(p)
+        got = run(p, "fp64", "auto", plan_out=info)
+        assert info[0]["kernel_name"] == "gemm_simt" and info[0]["workspace"] > 0, info[0]
+        assert compare(got, ref, p.C) <= TOL_FP64, p.name
+    p = cases[0]
+    p.C.data = np.linspace(-3, 3, p.C.data.size)
+    p.alpha, p.beta = 0.75, -1.25
+    assert compare(run(p, "fp64", "fused_gemm"), oracle.contract_problem(p), p.C) <= TOL_FP64
+    p = cases[2]
+    assert compare(run(p, "fp64", "copy_gemm"), oracle.contract_problem(p), p.C) <= TOL_FP64
+
+
+def test_fp64_split_k_integer_bitwise():
+    p = ts.problem("sk_int", "ai", "ib", "ab", dict(a=65, i=4099, b=64), 64,
+                   dist="int", lo=-4, hi=4)
+    np.testing.assert_array_equal(run(p, "fp64", "fused_gemm"), oracle.contract_problem(p))
