@@ -210,9 +210,11 @@ tc_status tc_contract(tc_plan_t plan, double alpha, const void* A, const void* B
  *   - M and N both >= the route threshold (64 by default): its 128x128 output
  *     tiles join the work list of one persistent tensor-core launch (one CTA
  *     per SM, longest K first);
- *   - otherwise (the BLAS-1/2 cases of Sec. 3.2.1-3.2.2 and skinny GEMMs): a
- *     batched CUDA-core kernel sums K segments in compensated FP32 and a
- *     second kernel adds each output's segments in order. */
+ *   - otherwise (the BLAS-1/2 cases of Sec. 3.2.1-3.2.2 and skinny GEMMs):
+ *     CUDA-core kernels sum K segments in compensated FP32 -- 32x32 output
+ *     tiles with operand blocks in shared memory where min(M, N) >= 16, a
+ *     thread (or a block) per output otherwise -- and a last kernel adds each
+ *     output's segments in order. */
 typedef struct tc_batch_s* tc_batch_t;
 
 typedef struct {
@@ -223,7 +225,8 @@ typedef struct {
   double min_bytes;      /* sum over items of |A| + |B| + |C| bytes */
   int32_t n_tc_items;    /* items on the tensor-core route */
   int32_t n_simt_items;  /* items on the CUDA-core route */
-  int64_t n_simt_work;   /* CUDA-core partial-sum work entries */
+  int64_t n_simt_work;   /* CUDA-core partial-sum work entries, per output */
+  int64_t n_simt_tiles;  /* CUDA-core partial-sum work entries, 32x32 tiles */
 } tc_batch_info;
 
 /* Route threshold used by later tc_batch_plan calls (process-wide): a
@@ -250,9 +253,9 @@ tc_status tc_batch_plan_routes(tc_batch_t* out, const tc_plan_t* plans, const in
 
 tc_status tc_batch_get_info(tc_batch_t batch, tc_batch_info* info);
 
-/* Run every contraction of the batch asynchronously on `stream` (at most four
- * kernel launches: pack, tensor-core GEMM, CUDA-core partial sums and final
- * sums).  A, B, C, alpha, beta are DEVICE arrays of n entries (item i uses
+/* Run every contraction of the batch asynchronously on `stream` (at most five
+ * kernel launches: pack, tensor-core GEMM, CUDA-core partial sums per output
+ * and per 32x32 tile, final sums).  A, B, C, alpha, beta are DEVICE arrays of n entries (item i uses
  * A[i], B[i], C[i], alpha[i], beta[i], with the layouts of plan i).  Nothing
  * is allocated or copied by the call, so it may be captured in a CUDA graph;
  * a replay reads the pointer and scalar arrays at replay time.  The five

@@ -11,12 +11,14 @@
 //   * SIMT route: the low-arithmetic-intensity contractions (Class 1 and 2 and
 //     skinny Class 3 ones; the paper's BLAS-1/2 cases of Sec. 3.2.1-3.2.2) and
 //     plans of the slicing mapping (a batch group of GEMMs),
-//     where a 128x128 tile would waste most of its work: a batched CUDA-core
-//     kernel computes partial sums over K segments into the batch's own
-//     workspace and a second kernel adds the segments of each output in order
+//     where a 128x128 tile would waste most of its work: batched CUDA-core
+//     kernels compute partial sums over K segments into the batch's own
+//     workspace -- 32x32 output tiles with operand blocks staged in shared
+//     memory where min(M, N) >= 16, a thread (or a block) per output
+//     otherwise -- and a last kernel adds the segments of each output in order
 //     (deterministic) and applies alpha and beta.  Long K is split so that even
 //     a single-output contraction spreads over many SMs.
-// The four kernels are launched back to back on the caller's stream; nothing
+// The (up to five) kernels are launched back to back on the caller's stream; nothing
 // is allocated or copied per call, so tc_contract_batched may be captured in a
 // CUDA graph.
 #include <cuda_runtime.h>
@@ -50,6 +52,21 @@ struct SimtWork {
   int32_t pad_;
 };
 
+// One entry of the SIMT tile kernel: a kTile x kTile tile of outputs of an
+// item over a K segment.
+struct SimtTileWork {
+  int32_t item;
+  int32_t nseg;    // segments of this item
+  int64_t tile;    // (m-tile fastest, n-tile, batch)
+  int64_t k0, k1;  // K segment [k0, k1)
+  int64_t slot;    // partial-sum slot of the item's output 0, segment 0
+  int64_t seg;     // this entry's segment
+};
+
+constexpr int kTile = 32;      // tile kernel: outputs per tile side
+constexpr int kTileK = 32;     // K per shared-memory block
+constexpr int kTileMin = 16;   // items with min(M, N) at least this take the tile kernel
+
 // One entry of the SIMT final kernel: 256 consecutive outputs of an item.
 struct SimtFinal {
   int32_t item, nseg;
@@ -61,10 +78,11 @@ struct Batch {
   int32_t math;
   double flops, min_bytes;
   int32_t n_tc_items, n_simt_items;
-  int64_t n_tc_work, n_simt_work, n_simt_final, n_pack;
+  int64_t n_tc_work, n_simt_work, n_simt_tiles, n_simt_final, n_pack;
   GemmArgs* d_items;
   TcWork* d_tc_work;
   SimtWork* d_simt_work;
+  SimtTileWork* d_simt_tile;
   SimtFinal* d_simt_final;
   double* d_partials;
   PkItem* d_pk;          // per item: the packed GEMM of tensor-core items
@@ -166,6 +184,119 @@ __global__ void __launch_bounds__(kThreads) k_simt_partial(
   }
 }
 
+// Partial sums of a 32 x 32 tile of outputs over one K segment: operand
+// blocks of 32 K are gathered into shared memory (the thread order follows
+// each operand's contiguous index), each thread accumulates a 2 x 2 register
+// tile in FP32 over the block and adds the block sums into Neumaier-compensated
+// (s, c) pairs, so that the error stays at 32 FP32 roundings of the block plus
+// the compensated sum.  Partials go to the same slots as the thread mode
+// (output o, segment s at slot + o * nseg + s).
+__global__ void __launch_bounds__(kThreads) k_simt_tile(
+    const GemmArgs* __restrict__ items, const SimtTileWork* __restrict__ work, int64_t nwork,
+    const void* const* Ap, const void* const* Bp, double* __restrict__ partials) {
+  __shared__ GemmArgs sa;
+  __shared__ int64_t oX[kChunk], oY[kChunk];
+  __shared__ int64_t offXm[kTile], offYn[kTile];
+  __shared__ float Xs[kTileK][kTile + 1], Ys[kTileK][kTile + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  int cur = -1;
+  for (int64_t w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const SimtTileWork wk = work[w];
+    __syncthreads();
+    if (wk.item != cur) {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(items + wk.item);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&sa);
+      for (int i = tid; i < (int)(sizeof(GemmArgs) / 4); i += kThreads) dst[i] = src[i];
+      cur = wk.item;
+      __syncthreads();
+    }
+    const GemmArgs& p = sa;
+    const float* X = static_cast<const float*>(p.swapped ? Bp[wk.item] : Ap[wk.item]);
+    const float* Y = static_cast<const float*>(p.swapped ? Ap[wk.item] : Bp[wk.item]);
+    const uint32_t M = (uint32_t)p.M, N = (uint32_t)p.N;
+    const uint32_t tiles_m = (M + kTile - 1) / kTile, tiles_n = (N + kTile - 1) / kTile;
+    const uint32_t tm = (uint32_t)(wk.tile % tiles_m);
+    const uint64_t rest = (uint64_t)wk.tile / tiles_m;
+    const uint32_t tn = (uint32_t)(rest % tiles_n), b = (uint32_t)(rest / tiles_n);
+    int64_t bX, bY, bC;
+    goff3(p.gb, b, bX, bY, bC);
+    if (tid < kTile) {
+      const uint32_t m = tm * kTile + tid;
+      int64_t ox = -1, oc;
+      if (m < M) { goff2(p.gm, 0, 2, m, ox, oc); ox += bX; }
+      offXm[tid] = ox;
+    } else if (tid < 2 * kTile) {
+      const uint32_t n = tn * kTile + (tid - kTile);
+      int64_t oy = -1, oc;
+      if (n < N) { goff2(p.gn, 1, 2, n, oy, oc); oy += bY; }
+      offYn[tid - kTile] = oy;
+    }
+    float s[2][2], c[2][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) s[i][j] = c[i][j] = 0.0f;
+    const bool x_mn = p.a_contig == CONTIG_MN, y_mn = p.b_contig == CONTIG_MN;
+    for (int64_t c0 = wk.k0; c0 < wk.k1; c0 += kChunk) {
+      const int kn = (int)min((int64_t)kChunk, wk.k1 - c0);
+      __syncthreads();  // previous chunk's blocks are done with the tables
+      for (int i = tid; i < kn; i += kThreads) {
+        int64_t ox, oy;
+        goff2(p.gk, 0, 1, (uint32_t)(c0 + i), ox, oy);
+        oX[i] = ox;
+        oY[i] = oy;
+      }
+      for (int kb = 0; kb < kn; kb += kTileK) {
+        __syncthreads();  // tables written; previous block's Xs, Ys read
+#pragma unroll
+        for (int r = 0; r < kTile * kTileK / kThreads; ++r) {
+          const int e = tid + r * kThreads;
+          int ml, kl;
+          if (x_mn) { ml = e % kTile; kl = e / kTile; } else { kl = e % kTileK; ml = e / kTileK; }
+          const int64_t om = offXm[ml];
+          Xs[kl][ml] = (om >= 0 && kb + kl < kn) ? X[om + oX[kb + kl]] : 0.0f;
+          int nl, kl2;
+          if (y_mn) { nl = e % kTile; kl2 = e / kTile; } else { kl2 = e % kTileK; nl = e / kTileK; }
+          const int64_t on = offYn[nl];
+          Ys[kl2][nl] = (on >= 0 && kb + kl2 < kn) ? Y[on + oY[kb + kl2]] : 0.0f;
+        }
+        __syncthreads();
+        float a0[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+#pragma unroll
+        for (int kk = 0; kk < kTileK; ++kk) {
+          const float x0 = Xs[kk][ty], x1 = Xs[kk][ty + 16];
+          const float y0 = Ys[kk][tx], y1 = Ys[kk][tx + 16];
+          a0[0][0] = fmaf(x0, y0, a0[0][0]);
+          a0[0][1] = fmaf(x0, y1, a0[0][1]);
+          a0[1][0] = fmaf(x1, y0, a0[1][0]);
+          a0[1][1] = fmaf(x1, y1, a0[1][1]);
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {  // Neumaier: (s, c) += block sum
+            const float x = a0[i][j], t = __fadd_rn(s[i][j], x);
+            if (fabsf(s[i][j]) >= fabsf(x))
+              c[i][j] = __fadd_rn(c[i][j], __fadd_rn(__fsub_rn(s[i][j], t), x));
+            else
+              c[i][j] = __fadd_rn(c[i][j], __fadd_rn(__fsub_rn(x, t), s[i][j]));
+            s[i][j] = t;
+          }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const uint32_t m = tm * kTile + ty + 16 * i, n = tn * kTile + tx + 16 * j;
+        if (m >= M || n >= N) continue;
+        const uint64_t o = (uint64_t)m + (uint64_t)M * ((uint64_t)n + (uint64_t)N * b);
+        partials[wk.slot + (int64_t)o * wk.nseg + wk.seg] = (double)s[i][j] + (double)c[i][j];
+      }
+  }
+}
+
 // C = alpha * (sum of an output's segments, in order) + beta * C.
 __global__ void __launch_bounds__(kThreads) k_simt_final(
     const GemmArgs* __restrict__ items, const SimtFinal* __restrict__ fin, int64_t nfin,
@@ -210,6 +341,7 @@ void free_batch(Batch* B) {
   cudaFree(B->d_items);
   cudaFree(B->d_tc_work);
   cudaFree(B->d_simt_work);
+  cudaFree(B->d_simt_tile);
   cudaFree(B->d_simt_final);
   cudaFree(B->d_partials);
   cudaFree(B->d_pk);
@@ -247,6 +379,7 @@ extern "C" tc_status tc_batch_plan_routes(tc_batch_t* out, const tc_plan_t* plan
   size_t pk_bytes = 0;
   std::vector<std::pair<uint64_t, TcWork>> tcw;  // (cost, entry)
   std::vector<SimtWork> sw;
+  std::vector<SimtTileWork> stw;
   std::vector<SimtFinal> sf;
   int64_t slots = 0;
   int32_t math = -1;
@@ -308,7 +441,19 @@ extern "C" tc_status tc_batch_plan_routes(tc_batch_t* out, const tc_plan_t* plan
       ++nsimt;
       const int64_t outs = a.M * a.N * a.nbatch;
       const int64_t K = a.K;
-      if (outs < kThreads) {  // a block per output and K segment
+      if (std::min(a.M, a.N) >= kTileMin) {  // 32x32 tiles; split K when there are few
+        const int64_t tiles = ((a.M + kTile - 1) / kTile) * ((a.N + kTile - 1) / kTile) * a.nbatch;
+        int64_t nseg = std::max<int64_t>(1, std::min<int64_t>((K + 511) / 512, 1216 / tiles));
+        const int64_t KS = (K + nseg - 1) / nseg;
+        nseg = (K + KS - 1) / KS;
+        for (int64_t sg = 0; sg < nseg; ++sg)
+          for (int64_t t = 0; t < tiles; ++t)
+            stw.push_back(SimtTileWork{i, (int32_t)nseg, t, sg * KS, std::min(K, (sg + 1) * KS),
+                                       slots, sg});
+        for (int64_t o0 = 0; o0 < outs; o0 += kThreads)
+          sf.push_back(SimtFinal{i, (int32_t)nseg, o0, slots + o0 * nseg});
+        slots += outs * nseg;
+      } else if (outs < kThreads) {  // a block per output and K segment
         const int64_t KS = std::max<int64_t>(4096, (K + 255) / 256);
         const int32_t nseg = (int32_t)((K + KS - 1) / KS);
         for (int64_t o = 0; o < outs; ++o)
@@ -349,6 +494,7 @@ extern "C" tc_status tc_batch_plan_routes(tc_batch_t* out, const tc_plan_t* plan
   B->n_simt_items = nsimt;
   B->n_tc_work = (int64_t)tw.size();
   B->n_simt_work = (int64_t)sw.size();
+  B->n_simt_tiles = (int64_t)stw.size();
   B->n_simt_final = (int64_t)sf.size();
   B->n_pack = (int64_t)(pack.size() / 4);
   if (pk_bytes > 0 && cudaMalloc(reinterpret_cast<void**>(&B->d_pkws), pk_bytes) != cudaSuccess) {
@@ -362,7 +508,8 @@ extern "C" tc_status tc_batch_plan_routes(tc_batch_t* out, const tc_plan_t* plan
     }
   if (upload(&B->d_items, items) != cudaSuccess || upload(&B->d_tc_work, tw) != cudaSuccess ||
       upload(&B->d_pk, pk) != cudaSuccess || upload(&B->d_pack, pack) != cudaSuccess ||
-      upload(&B->d_simt_work, sw) != cudaSuccess || upload(&B->d_simt_final, sf) != cudaSuccess ||
+      upload(&B->d_simt_work, sw) != cudaSuccess || upload(&B->d_simt_tile, stw) != cudaSuccess ||
+      upload(&B->d_simt_final, sf) != cudaSuccess ||
       (slots > 0 && cudaMalloc(reinterpret_cast<void**>(&B->d_partials),
                                sizeof(double) * (size_t)slots) != cudaSuccess)) {
     free_batch(B);
@@ -383,6 +530,7 @@ extern "C" tc_status tc_batch_get_info(tc_batch_t batch, tc_batch_info* info) {
   info->n_tc_items = B->n_tc_items;
   info->n_simt_items = B->n_simt_items;
   info->n_simt_work = B->n_simt_work;
+  info->n_simt_tiles = B->n_simt_tiles;
   return TC_OK;
 }
 
@@ -409,11 +557,18 @@ extern "C" tc_status tc_contract_batched(tc_batch_t batch, const void* const* A,
     const int g1 = (int)std::min<int64_t>(Bt->n_simt_work, 152 * 8);
     k_simt_partial<<<g1, kThreads, 0, s>>>(Bt->d_items, Bt->d_simt_work, Bt->n_simt_work, A, B,
                                            Bt->d_partials);
+  }
+  if (Bt->n_simt_tiles > 0) {
+    const int g1 = (int)std::min<int64_t>(Bt->n_simt_tiles, 152 * 8);
+    k_simt_tile<<<g1, kThreads, 0, s>>>(Bt->d_items, Bt->d_simt_tile, Bt->n_simt_tiles, A, B,
+                                        Bt->d_partials);
+  }
+  if (Bt->n_simt_final > 0) {
     const int g2 = (int)std::min<int64_t>(Bt->n_simt_final, 152 * 8);
     k_simt_final<<<g2, kThreads, 0, s>>>(Bt->d_items, Bt->d_simt_final, Bt->n_simt_final, C,
                                          alpha, beta, Bt->d_partials);
-    if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;
   }
+  if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;
   return TC_OK;
 }
 

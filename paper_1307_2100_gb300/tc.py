@@ -70,7 +70,8 @@ class BatchInfo(ctypes.Structure):
     _fields_ = [("n_items", ctypes.c_int32), ("math", ctypes.c_int32),
                 ("n_tiles", ctypes.c_int64), ("flops", ctypes.c_double),
                 ("min_bytes", ctypes.c_double), ("n_tc_items", ctypes.c_int32),
-                ("n_simt_items", ctypes.c_int32), ("n_simt_work", ctypes.c_int64)]
+                ("n_simt_items", ctypes.c_int32), ("n_simt_work", ctypes.c_int64),
+                ("n_simt_tiles", ctypes.c_int64)]
 
 
 def _load():

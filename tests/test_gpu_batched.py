@@ -93,6 +93,37 @@ def test_batched_routes_and_long_k_items():
         assert ok, (p.name, p.A.labels, p.B.labels, d)
 
 
+def test_batched_cuda_core_tiles():
+    """Skinny GEMMs (16 <= min(M, N) < the route threshold) take the 32 x 32
+    tile kernel of the CUDA-core route: ragged tiles, K split into segments,
+    several contracted labels, permuted storage orders, a batch label,
+    alpha/beta.  Each block of 32 products is summed in FP32 (at most 32
+    roundings of sum |a||b|), the block sums with Neumaier compensation, the
+    result rounded once to FP32: 40 * 2^-24 of sum |a||b| covers it."""
+    f32 = np.float32
+    items = [
+        ts.problem("t_longk", "ai", "ib", "ab", dict(a=38, i=20011, b=45), 91, dtype=f32),
+        ts.problem("t_perm", "iajb", "jcid", "abcd", dict(i=7, a=20, j=9, b=3, c=17, d=2), 92,
+                   dtype=f32),
+        ts.problem("t_order", "kai", "ikb", "ab", dict(k=13, i=11, a=50, b=33), 93, dtype=f32,
+                   order_a=[2, 0, 1], order_b=[1, 2, 0], order_c=[1, 0]),
+        ts.problem("t_wide", "ai", "ib", "ab", dict(a=20, i=21, b=5000), 94, dtype=f32),
+        ts.problem("t_batch", "aix", "ibx", "abx", dict(a=30, i=50, b=40, x=3), 95, dtype=f32),
+        ts.problem("t_ab", "ia", "ib", "ab", dict(a=17, i=300, b=16), 96, dtype=f32),
+    ]
+    ab = items[-1]
+    ab.C.data = np.linspace(-2, 2, ab.C.data.size).astype(f32)
+    ab.alpha, ab.beta = -0.5, 1.5
+    outs, info = _run_batch(items, "bf16x6")
+    assert info.n_tc_items == 0 and info.n_simt_tiles > 0 and info.n_simt_work == 0
+    for p, got in zip(items, outs):
+        mag = magnitude(p)
+        if p.beta != 0.0:  # outputs with beta = 0 start as NaN: C must not be read
+            mag = mag + abs(p.beta) * np.abs(p.C.data.astype(np.float64))
+        ok, d = within(got, oracle.contract_problem(p), mag, p.C, 40 * 2.0 ** -24)
+        assert ok, (p.name, d)
+
+
 @pytest.mark.parametrize("form", ["bf16x3", "bf16x6"])
 def test_batched_items_against_oracles(form):
     items = small_items()
