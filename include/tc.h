@@ -211,10 +211,11 @@ tc_status tc_contract(tc_plan_t plan, double alpha, const void* A, const void* B
  *     tiles join the work list of one persistent tensor-core launch (one CTA
  *     per SM, longest K first);
  *   - otherwise (the BLAS-1/2 cases of Sec. 3.2.1-3.2.2 and skinny GEMMs):
- *     CUDA-core kernels sum K segments in compensated FP32 -- 32x32 output
- *     tiles with operand blocks in shared memory where min(M, N) >= 16, a
- *     thread (or a block) per output otherwise -- and a last kernel adds each
- *     output's segments in order. */
+ *     CUDA-core kernels sum K segments -- short runs of FP32 products by
+ *     fused multiply-adds, the runs added with Neumaier compensation; 32x32
+ *     output tiles with operand blocks in shared memory where min(M, N) >= 16,
+ *     a thread (or, below 256 outputs, a warp) per output otherwise -- and a
+ *     last kernel adds each output's segments in order (FP64). */
 typedef struct tc_batch_s* tc_batch_t;
 
 typedef struct {
@@ -255,12 +256,17 @@ tc_status tc_batch_get_info(tc_batch_t batch, tc_batch_info* info);
 
 /* Run every contraction of the batch asynchronously on `stream` (at most five
  * kernel launches: pack, tensor-core GEMM, CUDA-core partial sums per output
- * and per 32x32 tile, final sums).  A, B, C, alpha, beta are DEVICE arrays of n entries (item i uses
- * A[i], B[i], C[i], alpha[i], beta[i], with the layouts of plan i).  Nothing
- * is allocated or copied by the call, so it may be captured in a CUDA graph;
- * a replay reads the pointer and scalar arrays at replay time.  The five
- * arrays and every buffer they point to must stay allocated until the launch
- * has completed: the kernels read them on the device and cannot check them. */
+ * and per 32x32 tile, final sums).  When both routes have work, the CUDA-core
+ * kernels run on a stream the batch owns, forked from `stream` and joined
+ * back to it by events, so that the two routes overlap; work queued on
+ * `stream` afterwards still sees every result.  A, B, C, alpha, beta are
+ * DEVICE arrays of n entries (item i uses A[i], B[i], C[i], alpha[i],
+ * beta[i], with the layouts of plan i).  Nothing is allocated or copied by
+ * the call, so it may be captured in a CUDA graph; a replay reads the pointer
+ * and scalar arrays at replay time.  Launches of one batch must not overlap
+ * one another (they share its partial-sum workspace).  The five arrays and
+ * every buffer they point to must stay allocated until the launch has
+ * completed: the kernels read them on the device and cannot check them. */
 tc_status tc_contract_batched(tc_batch_t batch, const void* const* A, const void* const* B,
                               void* const* C, const double* alpha, const double* beta,
                               void* stream);

@@ -36,6 +36,7 @@ namespace bat {
 
 constexpr int kThreads = 256;
 constexpr int kChunk = 512;     // K offsets staged in shared memory at a time
+constexpr int kRun = 8;         // thread mode: products per FP32 run
 
 struct TcWork {
   int32_t item, tile;
@@ -44,7 +45,7 @@ struct TcWork {
 // One entry of the SIMT partial-sum kernel.
 struct SimtWork {
   int32_t item;    // index into the batch's items
-  int32_t mode;    // 0: a thread per output (256 consecutive outputs), 1: a block per output
+  int32_t mode;    // 0: a thread per output (256 consecutive outputs), 1: a warp per output (8)
   int64_t out0;    // first output of the entry
   int64_t k0, k1;  // K segment [k0, k1)
   int64_t slot;    // partial-sum slot of the first output (thread mode: + thread index)
@@ -88,15 +89,15 @@ struct Batch {
   PkItem* d_pk;          // per item: the packed GEMM of tensor-core items
   int32_t* d_pack;       // pack entries (item, operand, row tile, 128-K chunk)
   uint8_t* d_pkws;       // packed operands of every tensor-core item
+  cudaStream_t side;     // the CUDA-core route's stream when both routes have work
+  cudaEvent_t fork, join;
 };
 
-template <typename T>
-struct Acc;
-template <>
-struct Acc<float> {  // Neumaier's compensated summation
+// Neumaier's compensated summation of FP32 terms (here: the sums of short
+// runs of FP32 fused multiply-adds).
+struct Neumaier {
   float s = 0.0f, c = 0.0f;
-  __device__ __forceinline__ void add(float a, float b) {
-    const float x = __fmul_rn(a, b);
+  __device__ __forceinline__ void add(float x) {
     const float t = __fadd_rn(s, x);
     if (fabsf(s) >= fabsf(x)) c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, t), x));
     else c = __fadd_rn(c, __fadd_rn(__fsub_rn(x, t), s));
@@ -112,14 +113,20 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // Partial sums of one K segment.  Operand pointers come from the device
-// pointer arrays (exchanged for items whose plan swapped the operands).
+// pointer arrays (exchanged for items whose plan swapped the operands).  The
+// K offsets of both operands are staged in shared memory as pairs, kChunk at a
+// time.  Thread mode: a thread per output, runs of kRun products summed by
+// FP32 fused multiply-adds (loads of a run issued together), the run sums
+// added with Neumaier compensation.  Warp mode: up to 8 outputs of an item
+// per block, a warp per output with lanes along K (each lane's run is its
+// share of a chunk), lanes combined in FP64; the offset table of a chunk
+// serves all of them.
 __global__ void __launch_bounds__(kThreads) k_simt_partial(
     const GemmArgs* __restrict__ items, const SimtWork* __restrict__ work, int64_t nwork,
     const void* const* Ap, const void* const* Bp, double* __restrict__ partials) {
   __shared__ GemmArgs sa;
-  __shared__ int64_t oX[kChunk], oY[kChunk];
-  __shared__ double red[kThreads / 32];
-  const int tid = threadIdx.x;
+  __shared__ longlong2 oXY[kChunk];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int cur = -1;
   for (int64_t w = blockIdx.x; w < nwork; w += gridDim.x) {
     const SimtWork wk = work[w];
@@ -136,8 +143,8 @@ __global__ void __launch_bounds__(kThreads) k_simt_partial(
     const float* Y = static_cast<const float*>(p.swapped ? Ap[wk.item] : Bp[wk.item]);
     const uint64_t M = (uint64_t)p.M, N = (uint64_t)p.N;
     const uint64_t outs = M * N * (uint64_t)p.nbatch;
-    // output of this thread (thread mode) or of the block (block mode)
-    const uint64_t o = wk.mode == 0 ? (uint64_t)wk.out0 + tid : (uint64_t)wk.out0;
+    // output of this thread (thread mode) or of this warp (warp mode)
+    const uint64_t o = (uint64_t)wk.out0 + (wk.mode == 0 ? tid : warp);
     int64_t xo = 0, yo = 0;
     const bool valid = o < outs;
     if (valid) {
@@ -151,35 +158,53 @@ __global__ void __launch_bounds__(kThreads) k_simt_partial(
       xo = bX + oXm;
       yo = bY + oYn;
     }
-    Acc<float> acc;
+    Neumaier acc;
     for (int64_t c0 = wk.k0; c0 < wk.k1; c0 += kChunk) {
       const int kn = (int)min((int64_t)kChunk, wk.k1 - c0);
       __syncthreads();
       for (int i = tid; i < kn; i += kThreads) {
         int64_t ox, oy;
         goff2(p.gk, 0, 1, (uint32_t)(c0 + i), ox, oy);
-        oX[i] = ox;
-        oY[i] = oy;
+        oXY[i] = make_longlong2(ox, oy);
       }
       __syncthreads();
+      if (!valid) continue;
       if (wk.mode == 0) {
-        if (valid)
-          for (int i = 0; i < kn; ++i) acc.add(X[xo + oX[i]], Y[yo + oY[i]]);
+        int i = 0;
+        for (; i + kRun <= kn; i += kRun) {
+          float xv[kRun], yv[kRun];
+#pragma unroll
+          for (int u = 0; u < kRun; ++u) {
+            const longlong2 q = oXY[i + u];
+            xv[u] = X[xo + q.x];
+            yv[u] = Y[yo + q.y];
+          }
+          float run = 0.0f;
+#pragma unroll
+          for (int u = 0; u < kRun; ++u) run = fmaf(xv[u], yv[u], run);
+          acc.add(run);
+        }
+        float run = 0.0f;
+        for (; i < kn; ++i) {
+          const longlong2 q = oXY[i];
+          run = fmaf(X[xo + q.x], Y[yo + q.y], run);
+        }
+        acc.add(run);
       } else {
-        for (int i = tid; i < kn; i += kThreads) acc.add(X[xo + oX[i]], Y[yo + oY[i]]);
+        float run = 0.0f;
+#pragma unroll 4
+        for (int i = lane; i < kn; i += 32) {
+          const longlong2 q = oXY[i];
+          run = fmaf(X[xo + q.x], Y[yo + q.y], run);
+        }
+        acc.add(run);
       }
     }
     if (wk.mode == 0) {
       if (valid) partials[wk.slot + (int64_t)tid * wk.nseg] = acc.value();
     } else {
       const double v = warp_sum(acc.value());
-      if ((tid & 31) == 0) red[tid >> 5] = v;
-      __syncthreads();
-      if (tid == 0) {
-        double t = 0.0;
-        for (int i = 0; i < kThreads / 32; ++i) t += red[i];
-        partials[wk.slot] = t;
-      }
+      if (valid && lane == 0) partials[wk.slot + (int64_t)warp * wk.nseg] = v;
     }
   }
 }
@@ -247,21 +272,40 @@ __global__ void __launch_bounds__(kThreads) k_simt_tile(
         oX[i] = ox;
         oY[i] = oy;
       }
-      for (int kb = 0; kb < kn; kb += kTileK) {
-        __syncthreads();  // tables written; previous block's Xs, Ys read
+      // this thread's elements of a block: (row, k) of X and (column, k) of Y,
+      // fetched one block ahead into registers
+      constexpr int R = kTile * kTileK / kThreads;
+      float rx[R], ry[R];
+      auto fetch = [&](int kb) {
 #pragma unroll
-        for (int r = 0; r < kTile * kTileK / kThreads; ++r) {
+        for (int r = 0; r < R; ++r) {
           const int e = tid + r * kThreads;
           int ml, kl;
           if (x_mn) { ml = e % kTile; kl = e / kTile; } else { kl = e % kTileK; ml = e / kTileK; }
           const int64_t om = offXm[ml];
-          Xs[kl][ml] = (om >= 0 && kb + kl < kn) ? X[om + oX[kb + kl]] : 0.0f;
+          rx[r] = (om >= 0 && kb + kl < kn) ? X[om + oX[kb + kl]] : 0.0f;
           int nl, kl2;
           if (y_mn) { nl = e % kTile; kl2 = e / kTile; } else { kl2 = e % kTileK; nl = e / kTileK; }
           const int64_t on = offYn[nl];
-          Ys[kl2][nl] = (on >= 0 && kb + kl2 < kn) ? Y[on + oY[kb + kl2]] : 0.0f;
+          ry[r] = (on >= 0 && kb + kl2 < kn) ? Y[on + oY[kb + kl2]] : 0.0f;
+        }
+      };
+      __syncthreads();  // tables written
+      fetch(0);
+      for (int kb = 0; kb < kn; kb += kTileK) {
+        __syncthreads();  // previous block's Xs, Ys read
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int e = tid + r * kThreads;
+          int ml, kl;
+          if (x_mn) { ml = e % kTile; kl = e / kTile; } else { kl = e % kTileK; ml = e / kTileK; }
+          Xs[kl][ml] = rx[r];
+          int nl, kl2;
+          if (y_mn) { nl = e % kTile; kl2 = e / kTile; } else { kl2 = e % kTileK; nl = e / kTileK; }
+          Ys[kl2][nl] = ry[r];
         }
         __syncthreads();
+        if (kb + kTileK < kn) fetch(kb + kTileK);
         float a0[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
 #pragma unroll
         for (int kk = 0; kk < kTileK; ++kk) {
@@ -347,6 +391,9 @@ void free_batch(Batch* B) {
   cudaFree(B->d_pk);
   cudaFree(B->d_pack);
   cudaFree(B->d_pkws);
+  if (B->join) cudaEventDestroy(B->join);
+  if (B->fork) cudaEventDestroy(B->fork);
+  if (B->side) cudaStreamDestroy(B->side);
   delete B;
 }
 
@@ -453,10 +500,10 @@ extern "C" tc_status tc_batch_plan_routes(tc_batch_t* out, const tc_plan_t* plan
         for (int64_t o0 = 0; o0 < outs; o0 += kThreads)
           sf.push_back(SimtFinal{i, (int32_t)nseg, o0, slots + o0 * nseg});
         slots += outs * nseg;
-      } else if (outs < kThreads) {  // a block per output and K segment
-        const int64_t KS = std::max<int64_t>(4096, (K + 255) / 256);
+      } else if (outs < kThreads) {  // a warp per output, 8 outputs per block, K segments
+        const int64_t KS = std::max<int64_t>(2048, (K + 255) / 256);
         const int32_t nseg = (int32_t)((K + KS - 1) / KS);
-        for (int64_t o = 0; o < outs; ++o)
+        for (int64_t o = 0; o < outs; o += kThreads / 32)
           for (int32_t s = 0; s < nseg; ++s)
             sw.push_back(SimtWork{i, 1, o, s * KS, std::min(K, (s + 1) * KS),
                                   slots + o * nseg + s, nseg, 0});
@@ -515,6 +562,16 @@ extern "C" tc_status tc_batch_plan_routes(tc_batch_t* out, const tc_plan_t* plan
     free_batch(B);
     return TC_ERR_CUDA;
   }
+  // both routes: the CUDA-core kernels run on a stream of the batch's own,
+  // forked from and joined back to the caller's stream, beside the tensor-core
+  // kernels (which leave most of each SM's threads idle)
+  if (B->n_tc_work > 0 && B->n_simt_work + B->n_simt_tiles > 0 &&
+      (cudaStreamCreateWithFlags(&B->side, cudaStreamNonBlocking) != cudaSuccess ||
+       cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) != cudaSuccess ||
+       cudaEventCreateWithFlags(&B->join, cudaEventDisableTiming) != cudaSuccess)) {
+    free_batch(B);
+    return TC_ERR_CUDA;
+  }
   *out = reinterpret_cast<tc_batch_t>(B);
   return TC_OK;
 }
@@ -542,6 +599,13 @@ extern "C" tc_status tc_contract_batched(tc_batch_t batch, const void* const* A,
   if (Bt->n == 0) return TC_OK;
   if (!A || !B || !C || !alpha || !beta) return TC_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaStream_t ss = s;  // the CUDA-core route's stream
+  if (Bt->side) {
+    if (cudaEventRecord(Bt->fork, s) != cudaSuccess ||
+        cudaStreamWaitEvent(Bt->side, Bt->fork, 0) != cudaSuccess)
+      return TC_ERR_CUDA;
+    ss = Bt->side;
+  }
   if (Bt->n_tc_work > 0) {
     PkBatch pb;
     pb.items = Bt->d_items;
@@ -555,20 +619,23 @@ extern "C" tc_status tc_contract_batched(tc_batch_t batch, const void* const* A,
   }
   if (Bt->n_simt_work > 0) {
     const int g1 = (int)std::min<int64_t>(Bt->n_simt_work, 152 * 8);
-    k_simt_partial<<<g1, kThreads, 0, s>>>(Bt->d_items, Bt->d_simt_work, Bt->n_simt_work, A, B,
+    k_simt_partial<<<g1, kThreads, 0, ss>>>(Bt->d_items, Bt->d_simt_work, Bt->n_simt_work, A, B,
                                            Bt->d_partials);
   }
   if (Bt->n_simt_tiles > 0) {
     const int g1 = (int)std::min<int64_t>(Bt->n_simt_tiles, 152 * 8);
-    k_simt_tile<<<g1, kThreads, 0, s>>>(Bt->d_items, Bt->d_simt_tile, Bt->n_simt_tiles, A, B,
+    k_simt_tile<<<g1, kThreads, 0, ss>>>(Bt->d_items, Bt->d_simt_tile, Bt->n_simt_tiles, A, B,
                                         Bt->d_partials);
   }
   if (Bt->n_simt_final > 0) {
     const int g2 = (int)std::min<int64_t>(Bt->n_simt_final, 152 * 8);
-    k_simt_final<<<g2, kThreads, 0, s>>>(Bt->d_items, Bt->d_simt_final, Bt->n_simt_final, C,
+    k_simt_final<<<g2, kThreads, 0, ss>>>(Bt->d_items, Bt->d_simt_final, Bt->n_simt_final, C,
                                          alpha, beta, Bt->d_partials);
   }
   if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;
+  if (Bt->side && (cudaEventRecord(Bt->join, Bt->side) != cudaSuccess ||
+                   cudaStreamWaitEvent(s, Bt->join, 0) != cudaSuccess))
+    return TC_ERR_CUDA;
   return TC_OK;
 }
 
