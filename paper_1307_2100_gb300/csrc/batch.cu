@@ -112,6 +112,31 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// (m, n, batch) of output o = m + M (n + N b): 32-bit divisions while the
+// outputs of the item fit in 32 bits.
+__device__ __forceinline__ void split_output(uint64_t o, uint64_t M, uint64_t N, uint64_t outs,
+                                             uint32_t& m, uint32_t& n, uint32_t& b) {
+  if (outs <= 0xffffffffull) {
+    const uint32_t o32 = (uint32_t)o, M32 = (uint32_t)M, N32 = (uint32_t)N;
+    const uint32_t r = o32 / M32;
+    m = o32 - r * M32;
+    n = r % N32;
+    b = r / N32;
+  } else {
+    const uint64_t r = o / M;
+    m = (uint32_t)(o - r * M);
+    n = (uint32_t)(r % N);
+    b = (uint32_t)(r / N);
+  }
+}
+
+// C = alpha * v + beta * C of one output, in FP64 (C is not read when beta == 0).
+__device__ __forceinline__ void store_output(float* dst, double v, double alpha, double beta) {
+  double x = alpha * v;
+  if (beta != 0.0) x += beta * (double)*dst;
+  *dst = (float)x;
+}
+
 // Partial sums of one K segment.  Operand pointers come from the device
 // pointer arrays (exchanged for items whose plan swapped the operands).  The
 // K offsets of both operands are staged in shared memory as pairs, kChunk at a
@@ -123,7 +148,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 // serves all of them.
 __global__ void __launch_bounds__(kThreads) k_simt_partial(
     const GemmArgs* __restrict__ items, const SimtWork* __restrict__ work, int64_t nwork,
-    const void* const* Ap, const void* const* Bp, double* __restrict__ partials) {
+    const void* const* Ap, const void* const* Bp, void* const* Cp, const double* alpha,
+    const double* beta, double* __restrict__ partials) {
   __shared__ GemmArgs sa;
   __shared__ longlong2 oXY[kChunk];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -145,18 +171,18 @@ __global__ void __launch_bounds__(kThreads) k_simt_partial(
     const uint64_t outs = M * N * (uint64_t)p.nbatch;
     // output of this thread (thread mode) or of this warp (warp mode)
     const uint64_t o = (uint64_t)wk.out0 + (wk.mode == 0 ? tid : warp);
-    int64_t xo = 0, yo = 0;
+    int64_t xo = 0, yo = 0, co = 0;
     const bool valid = o < outs;
     if (valid) {
-      const uint32_t m = (uint32_t)(o % M);
-      const uint64_t r = o / M;
-      const uint32_t n = (uint32_t)(r % N), b = (uint32_t)(r / N);
+      uint32_t m, n, b;
+      split_output(o, M, N, outs, m, n, b);
       int64_t bX, bY, bC, oXm, oCm, oYn, oCn;
       goff3(p.gb, b, bX, bY, bC);
       goff2(p.gm, 0, 2, m, oXm, oCm);
       goff2(p.gn, 1, 2, n, oYn, oCn);
       xo = bX + oXm;
       yo = bY + oYn;
+      co = bC + oCm + oCn;
     }
     Neumaier acc;
     for (int64_t c0 = wk.k0; c0 < wk.k1; c0 += kChunk) {
@@ -200,11 +226,14 @@ __global__ void __launch_bounds__(kThreads) k_simt_partial(
         acc.add(run);
       }
     }
-    if (wk.mode == 0) {
-      if (valid) partials[wk.slot + (int64_t)tid * wk.nseg] = acc.value();
-    } else {
-      const double v = warp_sum(acc.value());
-      if (valid && lane == 0) partials[wk.slot + (int64_t)warp * wk.nseg] = v;
+    // one segment: the output itself; else its partial-sum slot
+    double v = acc.value();
+    if (wk.mode != 0) v = warp_sum(v);
+    if (valid && (wk.mode == 0 || lane == 0)) {
+      if (wk.nseg == 1)
+        store_output(static_cast<float*>(Cp[wk.item]) + co, v, alpha[wk.item], beta[wk.item]);
+      else
+        partials[wk.slot + (int64_t)(wk.mode == 0 ? tid : warp) * wk.nseg] = v;
     }
   }
 }
@@ -212,17 +241,18 @@ __global__ void __launch_bounds__(kThreads) k_simt_partial(
 // Partial sums of a 32 x 32 tile of outputs over one K segment: operand
 // blocks of 32 K are gathered into shared memory (the thread order follows
 // each operand's contiguous index), each thread accumulates a 2 x 2 register
-// tile in FP32 over the block and adds the block sums into Neumaier-compensated
+// tile (two adjacent rows and columns, read as float2) in FP32 over the block and adds the block sums into Neumaier-compensated
 // (s, c) pairs, so that the error stays at 32 FP32 roundings of the block plus
 // the compensated sum.  Partials go to the same slots as the thread mode
 // (output o, segment s at slot + o * nseg + s).
-__global__ void __launch_bounds__(kThreads) k_simt_tile(
+__global__ void __launch_bounds__(kThreads, 3) k_simt_tile(
     const GemmArgs* __restrict__ items, const SimtTileWork* __restrict__ work, int64_t nwork,
-    const void* const* Ap, const void* const* Bp, double* __restrict__ partials) {
+    const void* const* Ap, const void* const* Bp, void* const* Cp, const double* alpha,
+    const double* beta, double* __restrict__ partials) {
   __shared__ GemmArgs sa;
   __shared__ int64_t oX[kChunk], oY[kChunk];
-  __shared__ int64_t offXm[kTile], offYn[kTile];
-  __shared__ float Xs[kTileK][kTile + 1], Ys[kTileK][kTile + 1];
+  __shared__ int64_t offXm[kTile], offYn[kTile], offCm[kTile], offCn[kTile];
+  __shared__ __align__(16) float Xs[kTileK][kTile + 2], Ys[kTileK][kTile + 2];
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
   int cur = -1;
@@ -248,23 +278,51 @@ __global__ void __launch_bounds__(kThreads) k_simt_tile(
     goff3(p.gb, b, bX, bY, bC);
     if (tid < kTile) {
       const uint32_t m = tm * kTile + tid;
-      int64_t ox = -1, oc;
+      int64_t ox = -1, oc = 0;
       if (m < M) { goff2(p.gm, 0, 2, m, ox, oc); ox += bX; }
       offXm[tid] = ox;
+      offCm[tid] = bC + oc;
     } else if (tid < 2 * kTile) {
       const uint32_t n = tn * kTile + (tid - kTile);
-      int64_t oy = -1, oc;
+      int64_t oy = -1, oc = 0;
       if (n < N) { goff2(p.gn, 1, 2, n, oy, oc); oy += bY; }
       offYn[tid - kTile] = oy;
+      offCn[tid - kTile] = oc;
     }
     float s[2][2], c[2][2];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
       for (int j = 0; j < 2; ++j) s[i][j] = c[i][j] = 0.0f;
+    // this thread's elements of a block: (row, k) of X and (column, k) of Y,
+    // in the order of each operand's contiguous index, fetched one block ahead
+    // into registers
     const bool x_mn = p.a_contig == CONTIG_MN, y_mn = p.b_contig == CONTIG_MN;
+    constexpr int R = kTile * kTileK / kThreads;
+    // element r of this thread: row / column and k in the block
+    auto xrow = [&](int r) { const int e = tid + r * kThreads; return x_mn ? e % kTile : e / kTileK; };
+    auto xkk = [&](int r) { const int e = tid + r * kThreads; return x_mn ? e / kTile : e % kTileK; };
+    auto ycol = [&](int r) { const int e = tid + r * kThreads; return y_mn ? e % kTile : e / kTileK; };
+    auto ykk = [&](int r) { const int e = tid + r * kThreads; return y_mn ? e / kTile : e % kTileK; };
+    int64_t xo[R], yo[R];
+    float rx[R], ry[R];
+    __syncthreads();  // row and column offsets written
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      xo[r] = offXm[xrow(r)];
+      yo[r] = offYn[ycol(r)];
+    }
+    int kn = 0;
+    auto fetch = [&](int kb) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int kx = kb + xkk(r), ky = kb + ykk(r);
+        rx[r] = (xo[r] >= 0 && kx < kn) ? X[xo[r] + oX[kx]] : 0.0f;
+        ry[r] = (yo[r] >= 0 && ky < kn) ? Y[yo[r] + oY[ky]] : 0.0f;
+      }
+    };
     for (int64_t c0 = wk.k0; c0 < wk.k1; c0 += kChunk) {
-      const int kn = (int)min((int64_t)kChunk, wk.k1 - c0);
+      kn = (int)min((int64_t)kChunk, wk.k1 - c0);
       __syncthreads();  // previous chunk's blocks are done with the tables
       for (int i = tid; i < kn; i += kThreads) {
         int64_t ox, oy;
@@ -272,49 +330,26 @@ __global__ void __launch_bounds__(kThreads) k_simt_tile(
         oX[i] = ox;
         oY[i] = oy;
       }
-      // this thread's elements of a block: (row, k) of X and (column, k) of Y,
-      // fetched one block ahead into registers
-      constexpr int R = kTile * kTileK / kThreads;
-      float rx[R], ry[R];
-      auto fetch = [&](int kb) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const int e = tid + r * kThreads;
-          int ml, kl;
-          if (x_mn) { ml = e % kTile; kl = e / kTile; } else { kl = e % kTileK; ml = e / kTileK; }
-          const int64_t om = offXm[ml];
-          rx[r] = (om >= 0 && kb + kl < kn) ? X[om + oX[kb + kl]] : 0.0f;
-          int nl, kl2;
-          if (y_mn) { nl = e % kTile; kl2 = e / kTile; } else { kl2 = e % kTileK; nl = e / kTileK; }
-          const int64_t on = offYn[nl];
-          ry[r] = (on >= 0 && kb + kl2 < kn) ? Y[on + oY[kb + kl2]] : 0.0f;
-        }
-      };
       __syncthreads();  // tables written
       fetch(0);
       for (int kb = 0; kb < kn; kb += kTileK) {
         __syncthreads();  // previous block's Xs, Ys read
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-          const int e = tid + r * kThreads;
-          int ml, kl;
-          if (x_mn) { ml = e % kTile; kl = e / kTile; } else { kl = e % kTileK; ml = e / kTileK; }
-          Xs[kl][ml] = rx[r];
-          int nl, kl2;
-          if (y_mn) { nl = e % kTile; kl2 = e / kTile; } else { kl2 = e % kTileK; nl = e / kTileK; }
-          Ys[kl2][nl] = ry[r];
+          Xs[xkk(r)][xrow(r)] = rx[r];
+          Ys[ykk(r)][ycol(r)] = ry[r];
         }
         __syncthreads();
         if (kb + kTileK < kn) fetch(kb + kTileK);
         float a0[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
 #pragma unroll
         for (int kk = 0; kk < kTileK; ++kk) {
-          const float x0 = Xs[kk][ty], x1 = Xs[kk][ty + 16];
-          const float y0 = Ys[kk][tx], y1 = Ys[kk][tx + 16];
-          a0[0][0] = fmaf(x0, y0, a0[0][0]);
-          a0[0][1] = fmaf(x0, y1, a0[0][1]);
-          a0[1][0] = fmaf(x1, y0, a0[1][0]);
-          a0[1][1] = fmaf(x1, y1, a0[1][1]);
+          const float2 xv = *reinterpret_cast<const float2*>(&Xs[kk][2 * ty]);
+          const float2 yv = *reinterpret_cast<const float2*>(&Ys[kk][2 * tx]);
+          a0[0][0] = fmaf(xv.x, yv.x, a0[0][0]);
+          a0[0][1] = fmaf(xv.x, yv.y, a0[0][1]);
+          a0[1][0] = fmaf(xv.y, yv.x, a0[1][0]);
+          a0[1][1] = fmaf(xv.y, yv.y, a0[1][1]);
         }
 #pragma unroll
         for (int i = 0; i < 2; ++i)
@@ -333,10 +368,16 @@ __global__ void __launch_bounds__(kThreads) k_simt_tile(
     for (int i = 0; i < 2; ++i)
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
-        const uint32_t m = tm * kTile + ty + 16 * i, n = tn * kTile + tx + 16 * j;
+        const uint32_t m = tm * kTile + 2 * ty + i, n = tn * kTile + 2 * tx + j;
         if (m >= M || n >= N) continue;
-        const uint64_t o = (uint64_t)m + (uint64_t)M * ((uint64_t)n + (uint64_t)N * b);
-        partials[wk.slot + (int64_t)o * wk.nseg + wk.seg] = (double)s[i][j] + (double)c[i][j];
+        const double v = (double)s[i][j] + (double)c[i][j];
+        if (wk.nseg == 1) {  // one segment: the output itself
+          store_output(static_cast<float*>(Cp[wk.item]) + offCm[2 * ty + i] + offCn[2 * tx + j], v,
+                       alpha[wk.item], beta[wk.item]);
+        } else {
+          const uint64_t o = (uint64_t)m + (uint64_t)M * ((uint64_t)n + (uint64_t)N * b);
+          partials[wk.slot + (int64_t)o * wk.nseg + wk.seg] = v;
+        }
       }
   }
 }
@@ -356,17 +397,14 @@ __global__ void __launch_bounds__(kThreads) k_simt_final(
     const double* ps = partials + f.slot0 + (int64_t)threadIdx.x * f.nseg;
     double s = 0.0;
     for (int i = 0; i < f.nseg; ++i) s += ps[i];
-    const uint32_t m = (uint32_t)(o % M);
-    const uint64_t r = o / M;
-    const uint32_t n = (uint32_t)(r % N), b = (uint32_t)(r / N);
+    uint32_t m, n, b;
+    split_output(o, M, N, outs, m, n, b);
     int64_t bX, bY, bC, oXm, oCm, oYn, oCn;
     goff3(p.gb, b, bX, bY, bC);
     goff2(p.gm, 0, 2, m, oXm, oCm);
     goff2(p.gn, 1, 2, n, oYn, oCn);
-    float* dst = static_cast<float*>(Cp[f.item]) + bC + oCm + oCn;
-    double v = alpha[f.item] * s;
-    if (beta[f.item] != 0.0) v += beta[f.item] * (double)*dst;
-    *dst = (float)v;
+    store_output(static_cast<float*>(Cp[f.item]) + bC + oCm + oCn, s, alpha[f.item],
+                 beta[f.item]);
   }
 }
 
@@ -497,9 +535,11 @@ extern "C" tc_status tc_batch_plan_routes(tc_batch_t* out, const tc_plan_t* plan
           for (int64_t t = 0; t < tiles; ++t)
             stw.push_back(SimtTileWork{i, (int32_t)nseg, t, sg * KS, std::min(K, (sg + 1) * KS),
                                        slots, sg});
-        for (int64_t o0 = 0; o0 < outs; o0 += kThreads)
-          sf.push_back(SimtFinal{i, (int32_t)nseg, o0, slots + o0 * nseg});
-        slots += outs * nseg;
+        if (nseg > 1) {  // one segment: the tiles write C themselves
+          for (int64_t o0 = 0; o0 < outs; o0 += kThreads)
+            sf.push_back(SimtFinal{i, (int32_t)nseg, o0, slots + o0 * nseg});
+          slots += outs * nseg;
+        }
       } else if (outs < kThreads) {  // a warp per output, 8 outputs per block, K segments
         const int64_t KS = std::max<int64_t>(2048, (K + 255) / 256);
         const int32_t nseg = (int32_t)((K + KS - 1) / KS);
@@ -507,9 +547,11 @@ extern "C" tc_status tc_batch_plan_routes(tc_batch_t* out, const tc_plan_t* plan
           for (int32_t s = 0; s < nseg; ++s)
             sw.push_back(SimtWork{i, 1, o, s * KS, std::min(K, (s + 1) * KS),
                                   slots + o * nseg + s, nseg, 0});
-        for (int64_t o0 = 0; o0 < outs; o0 += kThreads)
-          sf.push_back(SimtFinal{i, nseg, o0, slots + o0 * nseg});
-        slots += outs * nseg;
+        if (nseg > 1) {
+          for (int64_t o0 = 0; o0 < outs; o0 += kThreads)
+            sf.push_back(SimtFinal{i, nseg, o0, slots + o0 * nseg});
+          slots += outs * nseg;
+        }
       } else {  // a thread per output; split K when there are few output blocks
         const int64_t blocks = (outs + kThreads - 1) / kThreads;
         int64_t nseg = std::max<int64_t>(1, std::min<int64_t>((K + 255) / 256, 1216 / blocks));
@@ -519,9 +561,10 @@ extern "C" tc_status tc_batch_plan_routes(tc_batch_t* out, const tc_plan_t* plan
           for (int64_t s = 0; s < nseg; ++s)
             sw.push_back(SimtWork{i, 0, bl * kThreads, s * KS, std::min(K, (s + 1) * KS),
                                   slots + bl * kThreads * nseg + s, (int32_t)nseg, 0});
-          sf.push_back(SimtFinal{i, (int32_t)nseg, bl * kThreads, slots + bl * kThreads * nseg});
+          if (nseg > 1)
+            sf.push_back(SimtFinal{i, (int32_t)nseg, bl * kThreads, slots + bl * kThreads * nseg});
         }
-        slots += blocks * kThreads * nseg;
+        if (nseg > 1) slots += blocks * kThreads * nseg;
       }
     }
   }
@@ -620,12 +663,12 @@ extern "C" tc_status tc_contract_batched(tc_batch_t batch, const void* const* A,
   if (Bt->n_simt_work > 0) {
     const int g1 = (int)std::min<int64_t>(Bt->n_simt_work, 152 * 8);
     k_simt_partial<<<g1, kThreads, 0, ss>>>(Bt->d_items, Bt->d_simt_work, Bt->n_simt_work, A, B,
-                                           Bt->d_partials);
+                                            C, alpha, beta, Bt->d_partials);
   }
   if (Bt->n_simt_tiles > 0) {
     const int g1 = (int)std::min<int64_t>(Bt->n_simt_tiles, 152 * 8);
     k_simt_tile<<<g1, kThreads, 0, ss>>>(Bt->d_items, Bt->d_simt_tile, Bt->n_simt_tiles, A, B,
-                                        Bt->d_partials);
+                                         C, alpha, beta, Bt->d_partials);
   }
   if (Bt->n_simt_final > 0) {
     const int g2 = (int)std::min<int64_t>(Bt->n_simt_final, 152 * 8);

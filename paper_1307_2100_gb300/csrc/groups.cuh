@@ -3,13 +3,20 @@
 // A group index is split column-major into the group's labels (first label
 // fastest) and each label adds index * stride of the tensor slot asked for
 // (0 = the kernel's first operand, 1 = its second operand, 2 = C).  Groups
-// hold fewer than 2^31 elements, so the splits use 32-bit division.
+// hold fewer than 2^31 elements, so the splits use 32-bit division, done as a
+// multiply and a shift by each extent's precomputed constants.
 #pragma once
 #include <cstdint>
 
 #include "tc_internal.h"
 
 namespace tc {
+
+// idx / ext[i] of a group index (idx < 2^31 whenever dmul[i] is set).
+__device__ __forceinline__ uint32_t gdiv(const Group& g, int i, uint32_t idx) {
+  const uint32_t m = g.dmul[i];
+  return m ? (uint32_t)(((uint64_t)idx * m) >> g.dsh[i]) : idx / (uint32_t)g.ext[i];
+}
 
 // Offset of group index `idx` in tensor slot `t` (0 = first operand, 1 =
 // second operand, 2 = C).  Groups are < 2^31 elements, so 32-bit division.
@@ -18,7 +25,7 @@ __device__ __forceinline__ int64_t goff(const Group& g, int t, uint32_t idx) {
   int64_t off = 0;
   for (int i = 0; i < g.n; ++i) {
     uint32_t e = (uint32_t)g.ext[i];
-    uint32_t q = idx / e;
+    uint32_t q = gdiv(g, i, idx);
     off += (int64_t)(idx - q * e) * g.st[t][i];
     idx = q;
   }
@@ -32,7 +39,7 @@ __device__ __forceinline__ void goff2(const Group& g, int t0, int t1, uint32_t i
   o1 = 0;
   for (int i = 0; i < g.n; ++i) {
     uint32_t e = (uint32_t)g.ext[i];
-    uint32_t q = idx / e;
+    uint32_t q = gdiv(g, i, idx);
     uint32_t r = idx - q * e;
     o0 += (int64_t)r * g.st[t0][i];
     o1 += (int64_t)r * g.st[t1][i];
@@ -45,7 +52,7 @@ __device__ __forceinline__ void goff3(const Group& g, uint32_t idx, int64_t& o0,
   o0 = o1 = o2 = 0;
   for (int i = 0; i < g.n; ++i) {
     uint32_t e = (uint32_t)g.ext[i];
-    uint32_t q = idx / e;
+    uint32_t q = gdiv(g, i, idx);
     uint32_t r = idx - q * e;
     o0 += (int64_t)r * g.st[0][i];
     o1 += (int64_t)r * g.st[1][i];

@@ -227,6 +227,23 @@ uint32_t slice_bits(const Tens& T, const std::vector<int32_t>& keep) {
   return bits;
 }
 
+// With d in [1, 2^31), l = ceil(log2 d) and m = ceil(2^(31+l) / d):
+// 2^(31+l) <= m d < 2^(31+l) + 2^l, so floor(n / d) = floor(n m / 2^(31+l))
+// for every n < 2^31 (Granlund and Montgomery 1994, Theorem 4.2), and
+// m < 2^32.  Groups of 2^31 or more elements keep the division.
+void group_divisors(Group& g, int64_t total) {
+  for (int i = 0; i < kGroupMax; ++i) g.dmul[i] = g.dsh[i] = 0;
+  if (total <= 0 || total >= ((int64_t)1 << 31)) return;
+  for (int i = 0; i < g.n; ++i) {
+    const uint64_t d = (uint64_t)g.ext[i];
+    if (d == 0) continue;
+    uint32_t l = 0;
+    while (((uint64_t)1 << l) < d) ++l;
+    g.dmul[i] = (uint32_t)((((uint64_t)1 << (31 + l)) + d - 1) / d);
+    g.dsh[i] = 31 + l;
+  }
+}
+
 // Build a group from labels in the given order: strides from X, Y, C; drop
 // extent-1 labels; merge runs linear in every tensor.
 bool make_group(const std::vector<int32_t>& labels, const std::map<int32_t, int64_t>& ext,
@@ -259,6 +276,7 @@ bool make_group(const std::vector<int32_t>& labels, const std::map<int32_t, int6
     g.n = 1;
     g.ext[0] = 0;
   }
+  group_divisors(g, total);
   return true;
 }
 

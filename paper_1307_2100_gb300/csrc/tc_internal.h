@@ -20,7 +20,14 @@ struct Group {
   int32_t pad_;
   int64_t ext[kGroupMax];
   int64_t st[3][kGroupMax];
+  // Division by ext[i] as a multiply and a shift (Granlund and Montgomery,
+  // "Division by invariant integers using multiplication", 1994, with a
+  // 31-bit dividend): for idx < 2^31, idx / ext[i] = (idx * dmul[i]) >> dsh[i].
+  // dmul[i] == 0: divide (the group has 2^31 or more elements).
+  uint32_t dmul[kGroupMax];
+  uint32_t dsh[kGroupMax];
 };
+
 
 enum Kernel : int32_t {
   K_NONE = 0,
