@@ -580,7 +580,7 @@ def run_batching(args):
                                 "speedup": t_sep / t_graph},
         "routes": {"tensor_core_items": info.n_tc_items, "cuda_core_items": info.n_simt_items,
                    "tc_tiles": info.n_tiles, "simt_work": info.n_simt_work,
-                   "simt_tiles": info.n_simt_tiles},
+                   "simt_tiles": info.n_simt_tiles, "tc_split_tiles": info.n_tc_split},
         "autotune": None if tuned is None else {
             "buckets": tuned["buckets"], "default_ms": tuned["default_ms"],
             "tuned_ms": tuned["tuned_ms"],
@@ -588,7 +588,8 @@ def run_batching(args):
         "rel_err_vs_fp64_oracle": {"max": float(np.max(errs)), "median": float(np.median(errs))},
         "sum_flops": flops, "sum_bytes": info.min_bytes, "clocks": clk,
         "device_status": tc.tc_status_string(status),
-        "gpu_launches": args.steps * (2 * int(info.n_tiles > 0) + int(info.n_simt_work > 0) +
+        "gpu_launches": args.steps * (2 * int(info.n_tiles > 0) + int(info.n_tc_split > 0) +
+                                      int(info.n_simt_work > 0) +
                                       int(info.n_simt_tiles > 0) +
                                       int(info.n_simt_work + info.n_simt_tiles > 0)),
     }

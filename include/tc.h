@@ -209,7 +209,8 @@ tc_status tc_contract(tc_plan_t plan, double alpha, const void* A, const void* B
  * destroyed afterwards.  Each contraction is routed by its GEMM view:
  *   - M and N both >= the route threshold (64 by default): its 128x128 output
  *     tiles join the work list of one persistent tensor-core launch (one CTA
- *     per SM, longest K first);
+ *     per SM, longest K first); a tile with more K than half of one SM's
+ *     share is split into K ranges, added afterwards in range order;
  *   - otherwise (the BLAS-1/2 cases of Sec. 3.2.1-3.2.2 and skinny GEMMs):
  *     CUDA-core kernels sum K segments -- short runs of FP32 products by
  *     fused multiply-adds, the runs added with Neumaier compensation; 32x32
@@ -228,6 +229,7 @@ typedef struct {
   int32_t n_simt_items;  /* items on the CUDA-core route */
   int64_t n_simt_work;   /* CUDA-core partial-sum work entries, per output */
   int64_t n_simt_tiles;  /* CUDA-core partial-sum work entries, 32x32 tiles */
+  int64_t n_tc_split;    /* tensor-core tiles whose K is split into ranges */
 } tc_batch_info;
 
 /* Route threshold used by later tc_batch_plan calls (process-wide): a
@@ -254,9 +256,9 @@ tc_status tc_batch_plan_routes(tc_batch_t* out, const tc_plan_t* plans, const in
 
 tc_status tc_batch_get_info(tc_batch_t batch, tc_batch_info* info);
 
-/* Run every contraction of the batch asynchronously on `stream` (at most five
- * kernel launches: pack, tensor-core GEMM, CUDA-core partial sums per output
- * and per 32x32 tile, final sums).  When both routes have work, the CUDA-core
+/* Run every contraction of the batch asynchronously on `stream` (at most six
+ * kernel launches: pack, tensor-core GEMM, its split-K sums, CUDA-core
+ * partial sums per output and per 32x32 tile, final sums).  When both routes have work, the CUDA-core
  * kernels run on a stream the batch owns, forked from `stream` and joined
  * back to it by events, so that the two routes overlap; work queued on
  * `stream` afterwards still sees every result.  A, B, C, alpha, beta are

@@ -8,6 +8,8 @@
 //     BF16 terms in the batch's own device memory (one CTA per operand tile and
 //     128 K), then their 128x128 tiles join one work list, longest K first,
 //     processed by the persistent packed tcgen05 kernel (one CTA per SM);
+//     tiles with more K than half an SM's share are split into K ranges whose
+//     partial sums a reduction kernel adds;
 //   * SIMT route: the low-arithmetic-intensity contractions (Class 1 and 2 and
 //     skinny Class 3 ones; the paper's BLAS-1/2 cases of Sec. 3.2.1-3.2.2) and
 //     plans of the slicing mapping (a batch group of GEMMs),
@@ -18,7 +20,7 @@
 //     otherwise -- and a last kernel adds the segments of each output in order
 //     (deterministic) and applies alpha and beta.  Long K is split so that even
 //     a single-output contraction spreads over many SMs.
-// The (up to five) kernels are launched back to back on the caller's stream; nothing
+// The (up to six) kernels are launched back to back on the caller's stream; nothing
 // is allocated or copied per call, so tc_contract_batched may be captured in a
 // CUDA graph.
 #include <cuda_runtime.h>
@@ -39,7 +41,7 @@ constexpr int kChunk = 512;     // K offsets staged in shared memory at a time
 constexpr int kRun = 8;         // thread mode: products per FP32 run
 
 struct TcWork {
-  int32_t item, tile;
+  int32_t item, tile, split;  // split: the K range of the item's tile
 };
 
 // One entry of the SIMT partial-sum kernel.
@@ -67,6 +69,7 @@ struct SimtTileWork {
 constexpr int kTile = 32;      // tile kernel: outputs per tile side
 constexpr int kTileK = 32;     // K per shared-memory block
 constexpr int kTileMin = 16;   // items with min(M, N) at least this take the tile kernel
+constexpr int kTcTile = 128;   // output tile side of the packed tensor-core kernel
 
 // One entry of the SIMT final kernel: 256 consecutive outputs of an item.
 struct SimtFinal {
@@ -89,6 +92,9 @@ struct Batch {
   PkItem* d_pk;          // per item: the packed GEMM of tensor-core items
   int32_t* d_pack;       // pack entries (item, operand, row tile, 128-K chunk)
   uint8_t* d_pkws;       // packed operands of every tensor-core item
+  float2* d_pkpart;      // split-K partial sums of tensor-core items
+  int32_t* d_red;        // split-K reduction entries (item, tile)
+  int64_t n_red;
   cudaStream_t side;     // the CUDA-core route's stream when both routes have work
   cudaEvent_t fork, join;
 };
@@ -429,6 +435,8 @@ void free_batch(Batch* B) {
   cudaFree(B->d_pk);
   cudaFree(B->d_pack);
   cudaFree(B->d_pkws);
+  cudaFree(B->d_pkpart);
+  cudaFree(B->d_red);
   if (B->join) cudaEventDestroy(B->join);
   if (B->fork) cudaEventDestroy(B->fork);
   if (B->side) cudaStreamDestroy(B->side);
@@ -463,6 +471,11 @@ extern "C" tc_status tc_batch_plan_routes(tc_batch_t* out, const tc_plan_t* plan
   std::vector<int32_t> pack;                   // (item, operand, row tile, 128-K chunk)
   size_t pk_bytes = 0;
   std::vector<std::pair<uint64_t, TcWork>> tcw;  // (cost, entry)
+  std::vector<int32_t> tc_items;               // tensor-core items, in order
+  int64_t tc_blocks = 0;                       // their tiles' 32-K blocks
+  std::vector<int32_t> red;                    // split-K reductions (item, tile)
+  size_t part_bytes = 0;
+  std::vector<size_t> part_off((size_t)n, 0);
   std::vector<SimtWork> sw;
   std::vector<SimtTileWork> stw;
   std::vector<SimtFinal> sf;
@@ -519,9 +532,8 @@ extern "C" tc_status tc_batch_plan_routes(tc_batch_t* out, const tc_plan_t* plan
             pack.push_back(t);
             pack.push_back(kc);
           }
-      const uint64_t t = (uint64_t)L.tiles_m * (uint64_t)L.tiles_n;
-      const uint64_t cost = (uint64_t)((a.K + 63) / 64) + 2;  // per tile
-      for (uint64_t k = 0; k < t; ++k) tcw.push_back({cost, TcWork{i, (int32_t)k}});
+      tc_items.push_back(i);
+      tc_blocks += (int64_t)L.tiles_m * L.tiles_n * L.nkb;
     } else {
       ++nsimt;
       const int64_t outs = a.M * a.N * a.nbatch;
@@ -568,6 +580,33 @@ extern "C" tc_status tc_batch_plan_routes(tc_batch_t* out, const tc_plan_t* plan
       }
     }
   }
+  // Tensor-core work entries.  A tile whose K blocks exceed half of one SM's
+  // share of the route's blocks is split into K ranges (each >= 16 blocks,
+  // at most 64), so that no single long-K tile holds the launch up; the
+  // ranges write FP32 (s, r) partial sums that a last kernel adds in order.
+  const int64_t half_share = std::max<int64_t>(16, tc_blocks / (2 * 152));
+  for (int32_t i : tc_items) {
+    PkItem& it = pk[i];
+    const int64_t t = (int64_t)it.tiles_m * it.tiles_n;
+    int64_t ks = std::min<int64_t>({(it.nkb + half_share - 1) / half_share, it.nkb / 16, 64});
+    const size_t pb = (size_t)t * kTcTile * kTcTile * sizeof(float2);
+    if (ks > 1 && part_bytes + (size_t)ks * pb > ((size_t)256 << 20)) ks = 1;  // bounded partials
+    if (ks < 1) ks = 1;
+    it.ksplit = (int32_t)ks;
+    if (ks > 1) {
+      part_off[i] = part_bytes;
+      part_bytes += (size_t)ks * pb;
+      for (int64_t k = 0; k < t; ++k) {
+        red.push_back(i);
+        red.push_back((int32_t)k);
+      }
+    }
+    for (int64_t sp = 0; sp < ks; ++sp) {
+      const int64_t k0 = sp * it.nkb / ks, k1 = (sp + 1) * it.nkb / ks;
+      const uint64_t cost = (uint64_t)(k1 - k0) + 2;
+      for (int64_t k = 0; k < t; ++k) tcw.push_back({cost, TcWork{i, (int32_t)k, (int32_t)sp}});
+    }
+  }
   std::stable_sort(tcw.begin(), tcw.end(),
                    [](const auto& x, const auto& y) { return x.first > y.first; });
   std::vector<TcWork> tw(tcw.size());
@@ -591,15 +630,23 @@ extern "C" tc_status tc_batch_plan_routes(tc_batch_t* out, const tc_plan_t* plan
     free_batch(B);
     return TC_ERR_CUDA;
   }
+  if (part_bytes > 0 &&
+      cudaMalloc(reinterpret_cast<void**>(&B->d_pkpart), part_bytes) != cudaSuccess) {
+    free_batch(B);
+    return TC_ERR_CUDA;
+  }
   for (int32_t i = 0; i < n; ++i)
     if (pk[i].nkb > 0) {  // tensor-core items: offsets -> device addresses
       pk[i].qa = B->d_pkws + pk_off[i] + reinterpret_cast<size_t>(pk[i].qa);
       pk[i].qb = B->d_pkws + pk_off[i] + reinterpret_cast<size_t>(pk[i].qb);
+      if (pk[i].ksplit > 1)
+        pk[i].part = B->d_pkpart + part_off[i] / sizeof(float2);
     }
+  B->n_red = (int64_t)(red.size() / 2);
   if (upload(&B->d_items, items) != cudaSuccess || upload(&B->d_tc_work, tw) != cudaSuccess ||
       upload(&B->d_pk, pk) != cudaSuccess || upload(&B->d_pack, pack) != cudaSuccess ||
       upload(&B->d_simt_work, sw) != cudaSuccess || upload(&B->d_simt_tile, stw) != cudaSuccess ||
-      upload(&B->d_simt_final, sf) != cudaSuccess ||
+      upload(&B->d_simt_final, sf) != cudaSuccess || upload(&B->d_red, red) != cudaSuccess ||
       (slots > 0 && cudaMalloc(reinterpret_cast<void**>(&B->d_partials),
                                sizeof(double) * (size_t)slots) != cudaSuccess)) {
     free_batch(B);
@@ -631,6 +678,7 @@ extern "C" tc_status tc_batch_get_info(tc_batch_t batch, tc_batch_info* info) {
   info->n_simt_items = B->n_simt_items;
   info->n_simt_work = B->n_simt_work;
   info->n_simt_tiles = B->n_simt_tiles;
+  info->n_tc_split = B->n_red;
   return TC_OK;
 }
 
@@ -657,6 +705,8 @@ extern "C" tc_status tc_contract_batched(tc_batch_t batch, const void* const* A,
     pb.n_pack = Bt->n_pack;
     pb.work = reinterpret_cast<const int32_t*>(Bt->d_tc_work);
     pb.n_work = Bt->n_tc_work;
+    pb.red = Bt->d_red;
+    pb.n_red = Bt->n_red;
     tc_status st = launch_gemm_tc_packed_batch(pb, A, B, C, alpha, beta, Bt->math, stream);
     if (st != TC_OK) return st;
   }

@@ -224,7 +224,7 @@ struct PkLaunch {
   PkItem single;             // items == nullptr: tiles 0 .. nwork - 1 of this GEMM
   float* C;
   float alpha, beta;
-  const PkItem* items;       // batch: per-item GEMMs and (item, tile) work entries
+  const PkItem* items;       // batch: per-item GEMMs and (item, tile, K range) work entries
   const int32_t* work;
   void* const* Cp;
   const double* alpha_p;
@@ -233,7 +233,7 @@ struct PkLaunch {
 };
 
 // The tile and K range of work entry w (one contraction: split-major, the
-// ksplit ranges of every tile; a batch: one range per tile).
+// ksplit ranges of every tile; a batch: as listed in its work entries).
 struct Job {
   const PkItem* it;
   int tm, tn;
@@ -248,8 +248,9 @@ __device__ __forceinline__ Job job_of(const PkLaunch& L, int64_t w) {
   int64_t tile = w;
   j.split = 0;
   if (L.items) {
-    const int32_t item = L.work[2 * w];
-    tile = L.work[2 * w + 1];
+    const int32_t item = L.work[3 * w];
+    tile = L.work[3 * w + 1];
+    j.split = L.work[3 * w + 2];
     j.it = L.items + item;
     j.C = static_cast<float*>(L.Cp[item]);
     j.alpha = (float)L.alpha_p[item];
@@ -430,18 +431,35 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_pk(const __grid_constant__
     int64_t it = 0;
     bool live = true;  // after a wait gave up, tiles are walked without work so
                        // that every epilogue warp still meets each named barrier
-    for (int64_t w = blockIdx.x; w < L.nwork; w += gridDim.x, ++it) {
-      const Job J = job_of(L, w);
+    // A tile's setup (its job, the C offsets of its columns and of this
+    // thread's row) is done one tile ahead, while the MMAs of the tile before
+    // run: column offsets go to the other half of the double-buffered table.
+    auto setup = [&](int64_t w, int64_t* cc, Job& J, int64_t& rc) {
+      J = job_of(L, w);
       const PkItem& P = *J.it;
-      int64_t* cc = colC + (it & 1) * TILE;
       if (etid < TILE) {
         const int64_t n = (int64_t)J.tn * TILE + etid;
         cc[etid] = n < P.N ? goff(P.gn, 2, (uint32_t)n) : -1;
       }
-      named_bar_sync(1, kEpiThreads);
-      if (!live) continue;
       const int64_t m = (int64_t)J.tm * TILE + row;
-      const int64_t rc = m < P.M ? goff(P.gm, 2, (uint32_t)m) : -1;
+      rc = m < P.M ? goff(P.gm, 2, (uint32_t)m) : -1;
+    };
+    Job Jn;
+    int64_t rcn = -1;
+    if (blockIdx.x < L.nwork) setup(blockIdx.x, colC, Jn, rcn);
+    named_bar_sync(1, kEpiThreads);
+    for (int64_t w = blockIdx.x; w < L.nwork; w += gridDim.x, ++it) {
+      const Job J = Jn;
+      const int64_t rc = rcn;
+      const PkItem& P = *J.it;
+      int64_t* cc = colC + (it & 1) * TILE;
+      // the other half was last read by the stores of the tile before, which
+      // every epilogue thread finished before the barrier that ended it
+      if (w + gridDim.x < L.nwork) setup(w + gridDim.x, colC + ((it + 1) & 1) * TILE, Jn, rcn);
+      if (!live) {
+        named_bar_sync(1, kEpiThreads);
+        continue;
+      }
       const int ckb = max(P.chunk_kb, 1);
       const int nchunks = (J.k1 - J.k0 + ckb - 1) / ckb;
       const bool partial = P.ksplit > 1;
@@ -516,6 +534,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_pk(const __grid_constant__
           }
         }
       }
+      named_bar_sync(1, kEpiThreads);  // this tile's columns read; the next tile's written
     }
   }
 
@@ -556,6 +575,39 @@ __global__ void __launch_bounds__(256) k_pk_reduce(const __grid_constant__ PkLau
     float x = (float)(L.alpha * t);
     if (L.beta != 0.0f) x = fmaf(L.beta, *dst, x);
     *dst = x;
+  }
+}
+
+// Batched split-K: each block adds the K ranges of one (item, tile), in
+// order, applies the item's alpha and beta and stores through its groups.
+__global__ void __launch_bounds__(256) k_pk_reduce_batch(const PkItem* __restrict__ items,
+                                                         const int32_t* __restrict__ red,
+                                                         int64_t n_red, void* const* Cp,
+                                                         const double* alpha_p,
+                                                         const double* beta_p) {
+  for (int64_t r = blockIdx.x; r < n_red; r += gridDim.x) {
+    const int32_t item = red[2 * r];
+    const int64_t tile = red[2 * r + 1];
+    const PkItem& P = items[item];
+    const int64_t ntiles = (int64_t)P.tiles_m * P.tiles_n;
+    const int64_t total = ntiles * TILE * TILE;
+    const int tm = (int)(tile % P.tiles_m), tn = (int)(tile / P.tiles_m);
+    const float alpha = (float)alpha_p[item], beta = (float)beta_p[item];
+    float* C = static_cast<float*>(Cp[item]);
+    for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
+      const int col = e / TILE, row = e % TILE;
+      const int64_t m = (int64_t)tm * TILE + row, n = (int64_t)tn * TILE + col;
+      if (m >= P.M || n >= P.N) continue;
+      double t = 0.0;
+      for (int sp = 0; sp < P.ksplit; ++sp) {
+        const float2 v = P.part[(size_t)sp * total + (size_t)tile * TILE * TILE + e];
+        t += (double)v.x + (double)v.y;
+      }
+      float* dst = C + goff(P.gm, 2, (uint32_t)m) + goff(P.gn, 2, (uint32_t)n);
+      float x = (float)(alpha * t);
+      if (beta != 0.0f) x = fmaf(beta, *dst, x);
+      *dst = x;
+    }
   }
 }
 
@@ -679,7 +731,13 @@ tc_status launch_batch(const PkBatch& b, const void* const* A, const void* const
   g.nwork = b.n_work;
   const int grid = (int)std::min<int64_t>(g.nwork, sms);
   k_gemm_pk<NT><<<grid, kThreads, sm, s>>>(g);
-  return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;
+  if (b.n_red > 0) {
+    const int rgrid = (int)std::min<int64_t>(b.n_red, (int64_t)sms * 8);
+    k_pk_reduce_batch<<<rgrid, 256, 0, s>>>(b.pk, b.red, b.n_red, C, alpha, beta);
+    if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;
+  }
+  return TC_OK;
 }
 
 }  // namespace pk

@@ -169,8 +169,10 @@ struct PkBatch {
   const PkItem* pk;
   const int32_t* pack_work;
   int64_t n_pack;
-  const int32_t* work;
+  const int32_t* work;  // (item, tile, K range) per entry
   int64_t n_work;
+  const int32_t* red;   // split-K reductions: (item, tile) per entry
+  int64_t n_red;
 };
 tc_status launch_gemm_tc_packed_batch(const PkBatch& b, const void* const* A,
                                       const void* const* B, void* const* C, const double* alpha,

@@ -71,7 +71,7 @@ class BatchInfo(ctypes.Structure):
                 ("n_tiles", ctypes.c_int64), ("flops", ctypes.c_double),
                 ("min_bytes", ctypes.c_double), ("n_tc_items", ctypes.c_int32),
                 ("n_simt_items", ctypes.c_int32), ("n_simt_work", ctypes.c_int64),
-                ("n_simt_tiles", ctypes.c_int64)]
+                ("n_simt_tiles", ctypes.c_int64), ("n_tc_split", ctypes.c_int64)]
 
 
 def _load():

@@ -93,6 +93,40 @@ def test_batched_routes_and_long_k_items():
         assert ok, (p.name, p.A.labels, p.B.labels, d)
 
 
+def test_batched_split_k_tiles():
+    """Tensor-core items whose tiles hold more K than half of one SM's share of
+    the route's K blocks are split into K ranges: long-K items beside short
+    ones, ragged tiles, alpha/beta, against the FP64 oracle at the BF16x6
+    bound and against the split-form oracle."""
+    from paper_1307_2100_gb300 import tc
+    f32 = np.float32
+    items = [
+        ts.problem("s_long", "ai", "ib", "ab", dict(a=130, i=9000, b=70), 101, dtype=f32),
+        ts.problem("s_multik", "aijb", "ijc", "abc", dict(a=9, i=61, j=67, b=15, c=129), 102,
+                   dtype=f32),
+        ts.problem("s_short", "ai", "ib", "ab", dict(a=200, i=40, b=150), 103, dtype=f32),
+        ts.problem("s_ab", "ia", "ib", "ab", dict(a=100, i=5000, b=90), 104, dtype=f32),
+    ]
+    ab = items[-1]
+    ab.C.data = np.linspace(-1, 1, ab.C.data.size).astype(f32)
+    ab.alpha, ab.beta = 0.5, -2.0
+    tc.tc_batch_set_route(1)
+    try:
+        outs, info = _run_batch(items, "bf16x6")
+    finally:
+        tc.tc_batch_set_route(64)
+    assert info.n_simt_items == 0 and info.n_tc_split > 0
+    for p, got in zip(items, outs):
+        mag = magnitude(p)
+        if p.beta != 0.0:
+            mag = mag + abs(p.beta) * np.abs(p.C.data.astype(np.float64))
+        acc, tot = tc_bounds(p, "bf16x6")
+        ok, d = within(got, oracle.contract_problem(p), mag, p.C, tot)
+        assert ok, (p.name, "fp64", d)
+        ok, d = within(got, op.contract_form(p, "bf16x6"), mag, p.C, acc)
+        assert ok, (p.name, "form", d)
+
+
 def test_batched_cuda_core_tiles():
     """Skinny GEMMs (16 <= min(M, N) < the route threshold) take the 32 x 32
     tile kernel of the CUDA-core route: ragged tiles, K split into segments,
