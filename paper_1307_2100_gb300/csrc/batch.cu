@@ -67,7 +67,9 @@ struct SimtTileWork {
 };
 
 constexpr int kTile = 32;      // tile kernel: outputs per tile side
-constexpr int kTileK = 32;     // K per shared-memory block
+constexpr int kTileK = 16;     // K per shared-memory block
+constexpr int kTileRun = 2;    // blocks summed in FP32 before a compensated add
+constexpr int kTileThreads = 128;
 constexpr int kTileMin = 16;   // items with min(M, N) at least this take the tile kernel
 constexpr int kTcTile = 128;   // output tile side of the packed tensor-core kernel
 
@@ -152,7 +154,7 @@ __device__ __forceinline__ void store_output(float* dst, double v, double alpha,
 // per block, a warp per output with lanes along K (each lane's run is its
 // share of a chunk), lanes combined in FP64; the offset table of a chunk
 // serves all of them.
-__global__ void __launch_bounds__(kThreads) k_simt_partial(
+__global__ void __launch_bounds__(kThreads, 6) k_simt_partial(
     const GemmArgs* __restrict__ items, const SimtWork* __restrict__ work, int64_t nwork,
     const void* const* Ap, const void* const* Bp, void* const* Cp, const double* alpha,
     const double* beta, double* __restrict__ partials) {
@@ -244,23 +246,27 @@ __global__ void __launch_bounds__(kThreads) k_simt_partial(
   }
 }
 
-// Partial sums of a 32 x 32 tile of outputs over one K segment: operand
-// blocks of 32 K are gathered into shared memory (the thread order follows
-// each operand's contiguous index), each thread accumulates a 2 x 2 register
-// tile (two adjacent rows and columns, read as float2) in FP32 over the block and adds the block sums into Neumaier-compensated
-// (s, c) pairs, so that the error stays at 32 FP32 roundings of the block plus
-// the compensated sum.  Partials go to the same slots as the thread mode
-// (output o, segment s at slot + o * nseg + s).
-__global__ void __launch_bounds__(kThreads, 3) k_simt_tile(
+// Partial sums of a 32 x 32 tile of outputs over one K segment, 128 threads
+// (small enough to run beside the tensor-core kernel on an SM): operand
+// blocks of 16 K are gathered into shared memory in the order of each
+// operand's contiguous index (the next block prefetched into registers),
+// each thread accumulates a 2 x 4 register tile (two adjacent rows read as
+// float2, four adjacent columns as float4) in FP32 over two blocks and adds
+// those sums into Neumaier-compensated (s, c) pairs: at most 32 FP32
+// roundings per run plus the compensated sum.  Outputs of one segment are
+// stored to C; otherwise partials go to the per-output segment slots.
+__global__ void __launch_bounds__(kTileThreads, 6) k_simt_tile(
     const GemmArgs* __restrict__ items, const SimtTileWork* __restrict__ work, int64_t nwork,
     const void* const* Ap, const void* const* Bp, void* const* Cp, const double* alpha,
     const double* beta, double* __restrict__ partials) {
   __shared__ GemmArgs sa;
   __shared__ int64_t oX[kChunk], oY[kChunk];
   __shared__ int64_t offXm[kTile], offYn[kTile], offCm[kTile], offCn[kTile];
-  __shared__ __align__(16) float Xs[kTileK][kTile + 2], Ys[kTileK][kTile + 2];
+  __shared__ __align__(16) float Xs[kTileK][kTile + 2];
+  __shared__ __align__(16) float Ys[kTileK][kTile + 4];
+  constexpr int R = kTile * kTileK / kTileThreads;  // elements of each operand per thread
   const int tid = threadIdx.x;
-  const int tx = tid % 16, ty = tid / 16;
+  const int tx = tid % 8, ty = tid / 8;  // columns 4 tx .. 4 tx + 3, rows 2 ty, 2 ty + 1
   int cur = -1;
   for (int64_t w = blockIdx.x; w < nwork; w += gridDim.x) {
     const SimtTileWork wk = work[w];
@@ -268,7 +274,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_simt_tile(
     if (wk.item != cur) {
       const uint32_t* src = reinterpret_cast<const uint32_t*>(items + wk.item);
       uint32_t* dst = reinterpret_cast<uint32_t*>(&sa);
-      for (int i = tid; i < (int)(sizeof(GemmArgs) / 4); i += kThreads) dst[i] = src[i];
+      for (int i = tid; i < (int)(sizeof(GemmArgs) / 4); i += kTileThreads) dst[i] = src[i];
       cur = wk.item;
       __syncthreads();
     }
@@ -295,21 +301,17 @@ __global__ void __launch_bounds__(kThreads, 3) k_simt_tile(
       offYn[tid - kTile] = oy;
       offCn[tid - kTile] = oc;
     }
-    float s[2][2], c[2][2];
+    float s[2][4], c[2][4], a0[2][4];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
-      for (int j = 0; j < 2; ++j) s[i][j] = c[i][j] = 0.0f;
-    // this thread's elements of a block: (row, k) of X and (column, k) of Y,
-    // in the order of each operand's contiguous index, fetched one block ahead
-    // into registers
+      for (int j = 0; j < 4; ++j) s[i][j] = c[i][j] = a0[i][j] = 0.0f;
     const bool x_mn = p.a_contig == CONTIG_MN, y_mn = p.b_contig == CONTIG_MN;
-    constexpr int R = kTile * kTileK / kThreads;
     // element r of this thread: row / column and k in the block
-    auto xrow = [&](int r) { const int e = tid + r * kThreads; return x_mn ? e % kTile : e / kTileK; };
-    auto xkk = [&](int r) { const int e = tid + r * kThreads; return x_mn ? e / kTile : e % kTileK; };
-    auto ycol = [&](int r) { const int e = tid + r * kThreads; return y_mn ? e % kTile : e / kTileK; };
-    auto ykk = [&](int r) { const int e = tid + r * kThreads; return y_mn ? e / kTile : e % kTileK; };
+    auto xrow = [&](int r) { const int e = tid + r * kTileThreads; return x_mn ? e % kTile : e / kTileK; };
+    auto xkk = [&](int r) { const int e = tid + r * kTileThreads; return x_mn ? e / kTile : e % kTileK; };
+    auto ycol = [&](int r) { const int e = tid + r * kTileThreads; return y_mn ? e % kTile : e / kTileK; };
+    auto ykk = [&](int r) { const int e = tid + r * kTileThreads; return y_mn ? e / kTile : e % kTileK; };
     int64_t xo[R], yo[R];
     float rx[R], ry[R];
     __syncthreads();  // row and column offsets written
@@ -327,10 +329,25 @@ __global__ void __launch_bounds__(kThreads, 3) k_simt_tile(
         ry[r] = (yo[r] >= 0 && ky < kn) ? Y[yo[r] + oY[ky]] : 0.0f;
       }
     };
+    auto fold = [&]() {  // Neumaier: (s, c) += run sums
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float x = a0[i][j], t = __fadd_rn(s[i][j], x);
+          if (fabsf(s[i][j]) >= fabsf(x))
+            c[i][j] = __fadd_rn(c[i][j], __fadd_rn(__fsub_rn(s[i][j], t), x));
+          else
+            c[i][j] = __fadd_rn(c[i][j], __fadd_rn(__fsub_rn(x, t), s[i][j]));
+          s[i][j] = t;
+          a0[i][j] = 0.0f;
+        }
+    };
+    int nblk = 0;  // blocks in the current run
     for (int64_t c0 = wk.k0; c0 < wk.k1; c0 += kChunk) {
       kn = (int)min((int64_t)kChunk, wk.k1 - c0);
       __syncthreads();  // previous chunk's blocks are done with the tables
-      for (int i = tid; i < kn; i += kThreads) {
+      for (int i = tid; i < kn; i += kTileThreads) {
         int64_t ox, oy;
         goff2(p.gk, 0, 1, (uint32_t)(c0 + i), ox, oy);
         oX[i] = ox;
@@ -347,38 +364,32 @@ __global__ void __launch_bounds__(kThreads, 3) k_simt_tile(
         }
         __syncthreads();
         if (kb + kTileK < kn) fetch(kb + kTileK);
-        float a0[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
 #pragma unroll
         for (int kk = 0; kk < kTileK; ++kk) {
           const float2 xv = *reinterpret_cast<const float2*>(&Xs[kk][2 * ty]);
-          const float2 yv = *reinterpret_cast<const float2*>(&Ys[kk][2 * tx]);
-          a0[0][0] = fmaf(xv.x, yv.x, a0[0][0]);
-          a0[0][1] = fmaf(xv.x, yv.y, a0[0][1]);
-          a0[1][0] = fmaf(xv.y, yv.x, a0[1][0]);
-          a0[1][1] = fmaf(xv.y, yv.y, a0[1][1]);
+          const float4 yv = *reinterpret_cast<const float4*>(&Ys[kk][4 * tx]);
+          const float xa[2] = {xv.x, xv.y}, ya[4] = {yv.x, yv.y, yv.z, yv.w};
+#pragma unroll
+          for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) a0[i][j] = fmaf(xa[i], ya[j], a0[i][j]);
         }
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-          for (int j = 0; j < 2; ++j) {  // Neumaier: (s, c) += block sum
-            const float x = a0[i][j], t = __fadd_rn(s[i][j], x);
-            if (fabsf(s[i][j]) >= fabsf(x))
-              c[i][j] = __fadd_rn(c[i][j], __fadd_rn(__fsub_rn(s[i][j], t), x));
-            else
-              c[i][j] = __fadd_rn(c[i][j], __fadd_rn(__fsub_rn(x, t), s[i][j]));
-            s[i][j] = t;
-          }
+        if (++nblk == kTileRun) {
+          fold();
+          nblk = 0;
+        }
       }
     }
+    fold();
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const uint32_t m = tm * kTile + 2 * ty + i, n = tn * kTile + 2 * tx + j;
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t m = tm * kTile + 2 * ty + i, n = tn * kTile + 4 * tx + j;
         if (m >= M || n >= N) continue;
         const double v = (double)s[i][j] + (double)c[i][j];
         if (wk.nseg == 1) {  // one segment: the output itself
-          store_output(static_cast<float*>(Cp[wk.item]) + offCm[2 * ty + i] + offCn[2 * tx + j], v,
+          store_output(static_cast<float*>(Cp[wk.item]) + offCm[2 * ty + i] + offCn[4 * tx + j], v,
                        alpha[wk.item], beta[wk.item]);
         } else {
           const uint64_t o = (uint64_t)m + (uint64_t)M * ((uint64_t)n + (uint64_t)N * b);
@@ -716,8 +727,8 @@ extern "C" tc_status tc_contract_batched(tc_batch_t batch, const void* const* A,
                                             C, alpha, beta, Bt->d_partials);
   }
   if (Bt->n_simt_tiles > 0) {
-    const int g1 = (int)std::min<int64_t>(Bt->n_simt_tiles, 152 * 8);
-    k_simt_tile<<<g1, kThreads, 0, ss>>>(Bt->d_items, Bt->d_simt_tile, Bt->n_simt_tiles, A, B,
+    const int g1 = (int)std::min<int64_t>(Bt->n_simt_tiles, 152 * 12);
+    k_simt_tile<<<g1, kTileThreads, 0, ss>>>(Bt->d_items, Bt->d_simt_tile, Bt->n_simt_tiles, A, B,
                                          C, alpha, beta, Bt->d_partials);
   }
   if (Bt->n_simt_final > 0) {

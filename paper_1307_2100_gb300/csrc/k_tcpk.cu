@@ -578,14 +578,18 @@ __global__ void __launch_bounds__(256) k_pk_reduce(const __grid_constant__ PkLau
   }
 }
 
-// Batched split-K: each block adds the K ranges of one (item, tile), in
-// order, applies the item's alpha and beta and stores through its groups.
+// Batched split-K: a block adds the K ranges of 1/kRedParts of one
+// (item, tile), in order, applies the item's alpha and beta and stores
+// through its groups.
+constexpr int kRedParts = 16;
 __global__ void __launch_bounds__(256) k_pk_reduce_batch(const PkItem* __restrict__ items,
                                                          const int32_t* __restrict__ red,
                                                          int64_t n_red, void* const* Cp,
                                                          const double* alpha_p,
                                                          const double* beta_p) {
-  for (int64_t r = blockIdx.x; r < n_red; r += gridDim.x) {
+  for (int64_t rp = blockIdx.x; rp < n_red * kRedParts; rp += gridDim.x) {
+    const int64_t r = rp / kRedParts;
+    const int part = (int)(rp % kRedParts);
     const int32_t item = red[2 * r];
     const int64_t tile = red[2 * r + 1];
     const PkItem& P = items[item];
@@ -594,7 +598,8 @@ __global__ void __launch_bounds__(256) k_pk_reduce_batch(const PkItem* __restric
     const int tm = (int)(tile % P.tiles_m), tn = (int)(tile / P.tiles_m);
     const float alpha = (float)alpha_p[item], beta = (float)beta_p[item];
     float* C = static_cast<float*>(Cp[item]);
-    for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
+    constexpr int kPart = TILE * TILE / kRedParts;
+    for (int e = part * kPart + threadIdx.x; e < (part + 1) * kPart; e += blockDim.x) {
       const int col = e / TILE, row = e % TILE;
       const int64_t m = (int64_t)tm * TILE + row, n = (int64_t)tn * TILE + col;
       if (m >= P.M || n >= P.N) continue;
@@ -733,7 +738,7 @@ tc_status launch_batch(const PkBatch& b, const void* const* A, const void* const
   k_gemm_pk<NT><<<grid, kThreads, sm, s>>>(g);
   if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;
   if (b.n_red > 0) {
-    const int rgrid = (int)std::min<int64_t>(b.n_red, (int64_t)sms * 8);
+    const int rgrid = (int)std::min<int64_t>(b.n_red * kRedParts, (int64_t)sms * 8);
     k_pk_reduce_batch<<<rgrid, 256, 0, s>>>(b.pk, b.red, b.n_red, C, alpha, beta);
     if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;
   }
