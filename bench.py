@@ -46,6 +46,21 @@ def env_rank():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
+def replica_throughput(local_ms, units_per_rank, world, device="cpu"):
+    """Replicas only: every rank runs the same workload.  Returns (slowest
+    rank's ms, whole-job units per second / 1e12): the ranks' times are
+    combined by an all-reduce MAX (no collective on the data path), and the
+    units of all ranks count toward the value."""
+    ms = float(local_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * units_per_rank / (ms / 1e3) / 1e12
+
+
 def workloads(alloc=None, only=None, kind="class3_fp64", precision_v=128):
     if kind == "precision":
         return [ts.precision_ccd(v=precision_v)]
@@ -357,14 +372,8 @@ def run_ours(args):
     per = np.array([[ev[k][j][0].elapsed_time(ev[k][j][1]) for j in range(nprob)]
                     for k in range(args.steps)])        # ms
     step_ms = per.sum(axis=1)
-    total_ms = float(step_ms.sum())
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
     flops_step = sum(p.flops() for p in probs)
-    value = world * flops_step * args.steps / (total_ms / 1e3) / 1e12
+    total_ms, value = replica_throughput(step_ms.sum(), flops_step * args.steps, world, dev)
 
     # ---- e2e: host buffers, copies inside the timed region.  Inputs go up on
     # one copy stream and results come down on another, so that the copies of
@@ -407,13 +416,8 @@ def run_ours(args):
     stream.wait_stream(down)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = max(e0.elapsed_time(e1), 1e-6)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * flops_step * args.steps / (e2e_ms / 1e3) / 1e12
+    e2e_ms, e2e_value = replica_throughput(max(e0.elapsed_time(e1), 1e-6),
+                                           flops_step * args.steps, world, dev)
     status = tc.tc_device_status(sptr)
 
     if rank != 0:
