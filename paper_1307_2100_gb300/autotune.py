@@ -6,7 +6,9 @@ tc_contract_batched on the GPU.
 Buckets group the plans by log2 of min(M, N) and of K of their GEMM views.
 Starting from the threshold rule (tc_batch_set_route), the buckets are
 visited in order of decreasing flops and each one's route is flipped; a flip
-is kept when the whole batch gets faster by more than `gain` (relative).
+is kept when the whole batch gets faster by more than `gain` (relative).  The
+visit repeats (up to `passes` times) while a pass keeps a flip, since a
+bucket's best route depends on the load the others leave on each route.
 Plans with a batch group (the slicing mapping) stay on the CUDA-core route.
 """
 from __future__ import annotations
@@ -56,7 +58,8 @@ def time_routes(plans, routes, ptrs, stream, reps: int = 5) -> float:
         tc.tc_batch_destroy(batch)
 
 
-def tune_routes(plans, ptrs, stream, reps: int = 5, gain: float = 0.02, tc_min_mn: int = 64):
+def tune_routes(plans, ptrs, stream, reps: int = 5, gain: float = 0.02, tc_min_mn: int = 64,
+                passes: int = 3):
     """Routes per plan (int32 array) and a report.  `plans` are plan handles,
     `ptrs` the device arrays (A, B, C pointers; alpha, beta) that
     tc_contract_batched takes, `stream` a torch CUDA stream."""
@@ -70,17 +73,22 @@ def tune_routes(plans, ptrs, stream, reps: int = 5, gain: float = 0.02, tc_min_m
     flops = {b: sum(infos[i].flops for i in idx) for b, idx in buckets.items()}
     t0 = best = time_routes(plans, routes, ptrs, stream, reps)
     decisions = []
-    for b in sorted(buckets, key=lambda b: -flops[b]):
-        idx = buckets[b]
-        trial = routes.copy()
-        # a bucket split by the rule moves as a whole to the minority's route
-        trial[idx] = 0 if routes[idx].mean() >= 0.5 else 1
-        t = time_routes(plans, trial, ptrs, stream, reps)
-        keep = t < best * (1.0 - gain)
-        decisions.append({"bucket": list(b), "items": len(idx), "route": int(trial[idx[0]]),
-                          "ms": t, "kept": bool(keep)})
-        if keep:
-            routes, best = trial, t
+    for ps in range(passes):
+        kept = 0
+        for b in sorted(buckets, key=lambda b: -flops[b]):
+            idx = buckets[b]
+            trial = routes.copy()
+            # a bucket split by the rule moves as a whole to the minority's route
+            trial[idx] = 0 if routes[idx].mean() >= 0.5 else 1
+            t = time_routes(plans, trial, ptrs, stream, reps)
+            keep = t < best * (1.0 - gain)
+            decisions.append({"pass": ps, "bucket": list(b), "items": len(idx),
+                              "route": int(trial[idx[0]]), "ms": t, "kept": bool(keep)})
+            if keep:
+                routes, best = trial, t
+                kept += 1
+        if kept == 0:
+            break
     report = {"buckets": len(buckets), "default_ms": t0, "tuned_ms": best,
               "tensor_core_items": int(routes.sum()), "trials": decisions}
     return routes, report

@@ -354,3 +354,30 @@ def test_batch_labels_form_the_batch_group():
     h = ts.problem("had", "ab", "ab", "ab", dict(a=9, b=5), 92)
     hi = plan_info(h)
     assert hi.batch == 45 and hi.K == 1
+
+
+def test_autotune_passes_repeat_while_flips_are_kept(monkeypatch):
+    """The route search repeats its visit of the buckets while a pass keeps a
+    flip: a bucket whose flip pays only after another bucket moved is found
+    in the second pass (fake plans and a fake timer, no GPU)."""
+    from types import SimpleNamespace
+    from paper_1307_2100_gb300 import autotune
+    # bucket X (4 items) and bucket Y (2 items, most flops: visited first),
+    # all on the CUDA cores
+    infos = ([SimpleNamespace(M=8, N=8, K=4, batch=1, flops=10.0)] * 4 +
+             [SimpleNamespace(M=32, N=32, K=4, batch=1, flops=100.0)] * 2)
+    monkeypatch.setattr(autotune.tc, "tc_plan_get_info", lambda h: infos[h])
+
+    def fake_time(plans, routes, ptrs, stream, reps):
+        x, y = routes[0], routes[4]
+        # moving X to the tensor cores pays; moving Y pays only once X moved
+        return {(0, 0): 10.0, (1, 0): 8.0, (0, 1): 11.0, (1, 1): 6.0}[(int(x), int(y))]
+
+    monkeypatch.setattr(autotune, "time_routes", fake_time)
+    routes, rep = autotune.tune_routes(list(range(6)), None, None, passes=3)
+    assert list(routes) == [1, 1, 1, 1, 1, 1]
+    assert rep["default_ms"] == 10.0 and rep["tuned_ms"] == 6.0
+    kept = [(t["pass"], tuple(t["bucket"])) for t in rep["trials"] if t["kept"]]
+    assert kept == [(0, autotune.bucket_of(8, 8, 4)), (1, autotune.bucket_of(32, 32, 4))]
+    routes1, rep1 = autotune.tune_routes(list(range(6)), None, None, passes=1)
+    assert list(routes1) == [1, 1, 1, 1, 0, 0] and rep1["tuned_ms"] == 8.0
