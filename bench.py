@@ -61,11 +61,11 @@ def replica_throughput(local_ms, units_per_rank, world, device="cpu"):
     return ms, world * units_per_rank / (ms / 1e3) / 1e12
 
 
-def workloads(alloc=None, only=None, kind="class3_fp64", precision_v=128):
+def workloads(alloc=None, only=None, kind="class3_fp64", precision_v=128, gemv_b=1024):
     if kind == "precision":
         return [ts.precision_ccd(v=precision_v)]
     makers = {"direct_gemm_64": ts.direct_gemm_64, "fused_permute_48": ts.fused_permute_48,
-              "gemv_1024": lambda: ts.gemv_1024_full(alloc=alloc)}
+              "gemv_1024": lambda: ts.gemv_1024_full(b=gemv_b, alloc=alloc)}
     names = list(makers) if not only else [n for n in only.split(",") if n]
     return [makers[n]() for n in names]
 
@@ -306,7 +306,7 @@ def run_ours(args):
         return t.numpy()
 
     probs = workloads(alloc=pinned, only=args.only, kind=args.workload,
-                      precision_v=args.precision_v)
+                      precision_v=args.precision_v, gemv_b=args.gemv_b)
     fp64 = args.workload == "class3_fp64"
     math = "fp64" if fp64 else args.math
     tdt = torch.float64 if fp64 else torch.float32
@@ -315,7 +315,7 @@ def run_ours(args):
         pl = Contraction((p.A.labels, p.A.extents, p.A.strides),
                          (p.B.labels, p.B.extents, p.B.strides),
                          (p.C.labels, p.C.extents, p.C.strides), "f64" if fp64 else "f32",
-                         math, "auto", args.tile)
+                         math, args.mapping, args.tile)
         plans.append(pl)
         dA.append(torch.from_numpy(np.ascontiguousarray(p.A.data)).to(dev))
         dB.append(torch.from_numpy(np.ascontiguousarray(p.B.data)).to(dev))
@@ -467,9 +467,12 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if fp64 else "f32 storage, " + math,
         "data": "synthetic (seeded uniform[-1,1), shapes of the paper's Eq. xy and Class 2)",
-        "config": {"workload": WORKLOAD if fp64 else
+        "config": {"workload": (WORKLOAD if not args.only and args.gemv_b == 1024 else
+                                f"plain FP64: {args.only or 'three classes'}, GEMV b={args.gemv_b}")
+                   if fp64 else
                    f"precision: CCD-like {args.precision_v}^4 x {args.precision_v}^2*32^2",
-                   "mapping": "auto (recipe)", "math": math,
+                   "mapping": "auto (recipe)" if args.mapping == "auto" else args.mapping,
+                   "math": math,
                    "l2": "flushed between steps (256 MiB write, outside timing)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": dom["bound"], "kernel": dom["kernel"], "workload": dom["name"],
@@ -755,6 +758,12 @@ def main(argv=None):
                     choices=["bf16", "bf16x3", "bf16x6", "fp8", "fp32"],
                     help="math of the precision workload")
     ap.add_argument("--tile", type=int, default=-1)
+    ap.add_argument("--mapping", default="auto",
+                    choices=["auto", "recipe", "slice_gemm", "fused_gemm", "copy_gemm", "gemv",
+                             "dot", "ger"],
+                    help="mapping of every contraction of the step (profiling a kernel)")
+    ap.add_argument("--gemv-b", type=int, default=1024,
+                    help="extent b of the GEMV workload (1024: the full 17.2 GB matrix)")
     ap.add_argument("--precision-v", type=int, default=128,
                     help="precision workload: virtual extent a=b=e=f (128 is the named "
                          "configuration; smaller values are profiling cases)")
