@@ -238,8 +238,10 @@ tc_status tc_batch_set_route(int32_t tc_min_mn);
 
 /* Build a batch from n plans (host and device allocation; synchronous).
  * TC_ERR_UNSUPPORTED if a plan's math is not TC_MATH_BF16, _BF16X3 or
- * _BF16X6 (FP32 storage), if the plans use different math forms, or if a plan
- * copies an operand (COPY_GEMM).  The batch packs the operands of its
+ * _BF16X6 (FP32 storage), if the plans use different math forms, if a plan
+ * copies an operand (COPY_GEMM), or if a plan has an empty output or an empty
+ * contracted range (run those with tc_contract).  n == 0 gives an empty batch,
+ * whose launch does nothing.  The batch packs the operands of its
  * tensor-core items into device memory of its own (a plan's workspace is not
  * used); plans with a batch group (the slicing mapping) take the CUDA-core
  * route. */

@@ -243,6 +243,8 @@ def test_fp64_split_k_workspace():
     assert plan_info(short).workspace == 0          # under 64 K blocks: one range
     wide = ts.problem("sk_wide", "ai", "ib", "ab", dict(a=1100, i=5003, b=1100), 61)
     assert plan_info(wide).workspace == 0           # 18 x 18 tiles fill the GPU
+    cap = ts.problem("sk_cap", "ai", "ib", "ab", dict(a=37, i=40003, b=50), 65)
+    assert plan_info(cap).workspace == 64 * 1 * 64 * 64 * 8   # at most 64 ranges
 
 
 def test_batch_routes_are_checked_before_any_allocation():

@@ -93,6 +93,41 @@ def test_batched_routes_and_long_k_items():
         assert ok, (p.name, p.A.labels, p.B.labels, d)
 
 
+def test_batched_degenerate_batches():
+    """An empty batch runs nothing; one-item batches on either route alone (no
+    second stream); an item with an empty output or an empty contracted range
+    is refused when the batch is planned."""
+    import torch
+    from paper_1307_2100_gb300 import Contraction, tc
+    empty = tc.tc_batch_plan([])
+    try:
+        assert tc.tc_batch_get_info(empty).n_items == 0
+        tc.tc_contract_batched(empty, 0, 0, 0, 0, 0, torch.cuda.current_stream().cuda_stream)
+    finally:
+        tc.tc_batch_destroy(empty)
+    f32 = np.float32
+    gemv = ts.problem("one_gemv", "aib", "ib", "a", dict(a=300, i=70, b=9), 111, dtype=f32)
+    gemm = ts.problem("one_gemm", "ai", "ib", "ab", dict(a=150, i=300, b=140), 112, dtype=f32)
+    for p, route in ((gemv, 64), (gemm, 1)):
+        tc.tc_batch_set_route(route)
+        try:
+            outs, info = _run_batch([p], "bf16x6")
+        finally:
+            tc.tc_batch_set_route(64)
+        assert (info.n_tc_items, info.n_simt_items) == ((0, 1) if p is gemv else (1, 0))
+        acc, tot = tc_bounds(p, "bf16x6")
+        ok, d = within(outs[0], oracle.contract_problem(p), magnitude(p), p.C, tot)
+        assert ok, (p.name, d)
+    for ext in (dict(a=5, i=0, b=4), dict(a=0, i=3, b=4)):
+        q = ts.problem("zero", "ai", "ib", "ab", ext, 113, dtype=f32)
+        pl = Contraction((q.A.labels, q.A.extents, q.A.strides),
+                         (q.B.labels, q.B.extents, q.B.strides),
+                         (q.C.labels, q.C.extents, q.C.strides), "f32", "bf16x6", "auto")
+        with pytest.raises(tc.TcError) as e:
+            tc.tc_batch_plan([pl.handle])
+        assert e.value.status == 5
+
+
 def test_batched_split_k_tiles():
     """Tensor-core items whose tiles hold more K than half of one SM's share of
     the route's K blocks are split into K ranges: long-K items beside short

@@ -159,6 +159,17 @@ def test_fp64_split_k_long_k():
     assert compare(run(p, "fp64", "copy_gemm"), oracle.contract_problem(p), p.C) <= TOL_FP64
 
 
+def test_fp64_split_k_at_the_range_cap():
+    """One ragged tile and K long enough for the cap of 64 K ranges (K not a
+    multiple of the 16-wide K block nor of the range count)."""
+    p = ts.problem("sk_cap", "ai", "ib", "ab", dict(a=37, i=40003, b=50), 65)
+    info = []
+    ref = oracle.contract_problem(p)
+    got = run(p, "fp64", "auto", plan_out=info)
+    assert info[0]["workspace"] == 64 * 64 * 64 * 8, info[0]
+    assert compare(got, ref, p.C) <= TOL_FP64
+
+
 def test_fp64_split_k_integer_bitwise():
     p = ts.problem("sk_int", "ai", "ib", "ab", dict(a=65, i=4099, b=64), 64,
                    dist="int", lo=-4, hi=4)
