@@ -56,10 +56,15 @@ constexpr uint32_t COL_CORR = 256, COL_HI = 384;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 constexpr uint32_t kRing = 192 * 1024;       // bytes of the stage ring
 
+// A ring stage holds BPS consecutive 32-K blocks of A and of B.  Each stage
+// costs a fixed hand-off (the producer's wait on its empty barrier, the MMA
+// warp's wait on its full barrier, a commit), so forms whose stage holds few
+// MMA cycles take two blocks per stage.
 template <int NT>
 struct Cfg {
-  static constexpr uint32_t STAGE = 2 * NT * TERM;   // A terms then B terms
-  static constexpr int S = (int)(kRing / STAGE);      // 12, 6, 4
+  static constexpr int BPS = NT == 3 ? 1 : 2;          // blocks per stage
+  static constexpr uint32_t STAGE = 2 * BPS * NT * TERM;  // A blocks then B blocks
+  static constexpr int S = (int)(kRing / STAGE);      // 6, 3, 4
   static constexpr uint32_t OFF_COLC = S * STAGE;
   static constexpr uint32_t OFF_BAR = OFF_COLC + 2 * TILE * 8;
   static constexpr uint32_t NBAR = 2 * S + 4 + 1;
@@ -346,16 +351,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_pk(const __grid_constant__
         const int nkb = J.it->nkb;
         const uint8_t* a = J.it->qa + (size_t)J.tm * nkb * OPB;
         const uint8_t* b = J.it->qb + (size_t)J.tn * nkb * OPB;
-        for (int kb = J.k0; kb < J.k1; ++kb, ++g) {
+        for (int kb = J.k0; kb < J.k1; kb += G::BPS, ++g) {
           const int s = (int)(g % S);
           if (g >= (uint32_t)S && !mbar_wait(&empty[s], ((g / S) - 1) & 1, abort, kTimeoutNs)) {
             ok = false;
             break;
           }
+          // blocks [kb, kb + nb): consecutive, so one copy per operand
+          const uint32_t nb = (uint32_t)min(G::BPS, J.k1 - kb);
           const uint32_t dst = sbase + (uint32_t)s * G::STAGE;
-          mbar_arrive_expect_tx(&full[s], 2 * OPB);
-          bulk_g2s(dst, a + (size_t)kb * OPB, OPB, &full[s]);
-          bulk_g2s(dst + OPB, b + (size_t)kb * OPB, OPB, &full[s]);
+          mbar_arrive_expect_tx(&full[s], 2 * nb * OPB);
+          bulk_g2s(dst, a + (size_t)kb * OPB, nb * OPB, &full[s]);
+          bulk_g2s(dst + G::BPS * OPB, b + (size_t)kb * OPB, nb * OPB, &full[s]);
         }
       }
       volatile int never = 0;
@@ -389,25 +396,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_pk(const __grid_constant__
           tc_fence_after();
           const uint32_t dmain = tmem + buf * TILE;
           const int kend = min(J.k1, J.k0 + (j + 1) * ckb), kstart = kb;
-          for (; kb < kend; ++kb, ++g) {
+          // stages start at the range's first block and hold BPS blocks;
+          // chunks hold a multiple of BPS blocks, so no stage straddles one
+          for (; kb < kend; kb += G::BPS, ++g) {
             const int s = (int)(g % S);
             if (!mbar_wait(&full[s], (g / S) & 1, abort, kTimeoutNs)) {
               ok = false;
               break;
             }
             tc_fence_after();
-            const uint32_t sa = sbase + (uint32_t)s * G::STAGE, sb = sa + OPB;
+            const int nb = min(G::BPS, kend - kb);
+            for (int bi = 0; bi < nb; ++bi) {
+              const uint32_t sa = sbase + (uint32_t)s * G::STAGE + bi * OPB;
+              const uint32_t sb = sa + G::BPS * OPB;
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-              mma_bf16(dmain, smem_desc(sa + kk * 2 * LBO, LBO, 128),
-                       smem_desc(sb + kk * 2 * LBO, LBO, 128), idesc,
-                       (kb > kstart || kk > 0) ? 1u : 0u);
+              for (int kk = 0; kk < BK / 16; ++kk) {
+                const bool first = bi == 0 && kk == 0;
+                mma_bf16(dmain, smem_desc(sa + kk * 2 * LBO, LBO, 128),
+                         smem_desc(sb + kk * 2 * LBO, LBO, 128), idesc,
+                         (kb > kstart || !first) ? 1u : 0u);
 #pragma unroll
-              for (int pi = 1; pi < nprod(NT); ++pi)
-                mma_bf16(tmem + COL_CORR,
-                         smem_desc(sa + kProdA[pi] * TERM + kk * 2 * LBO, LBO, 128),
-                         smem_desc(sb + kProdB[pi] * TERM + kk * 2 * LBO, LBO, 128), idesc,
-                         (kb > J.k0 || kk > 0 || pi > 1) ? 1u : 0u);
+                for (int pi = 1; pi < nprod(NT); ++pi)
+                  mma_bf16(tmem + COL_CORR,
+                           smem_desc(sa + kProdA[pi] * TERM + kk * 2 * LBO, LBO, 128),
+                           smem_desc(sb + kProdB[pi] * TERM + kk * 2 * LBO, LBO, 128), idesc,
+                           (kb > J.k0 || !first || pi > 1) ? 1u : 0u);
+              }
             }
             mma_commit(&empty[s]);
           }
