@@ -505,6 +505,7 @@ extern "C" tc_status tc_batch_plan_routes(tc_batch_t* out, const tc_plan_t* plan
     GemmArgs a = P->args;
     a.swapped = P->swapped ? 1 : 0;
     a.chunk_kb = tc_chunk_kb(math, 0);
+    if (a.chunk_kb % pk_stage_blocks(math) != 0) return TC_ERR_UNSUPPORTED;
     a.raster = 0;
     items[i] = a;
     flops += P->info.flops;

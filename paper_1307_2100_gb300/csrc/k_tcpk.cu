@@ -707,6 +707,7 @@ tc_status launch(const GemmArgs& a, const PkLayout& L, void* ws, cudaStream_t s)
   it.tiles_n = (int32_t)L.tiles_n;
   it.nkb = (int32_t)L.nkb;
   it.chunk_kb = a.chunk_kb;
+  if (max(a.chunk_kb, 1) % Cfg<NT>::BPS != 0) return TC_ERR_UNSUPPORTED;  // a stage per chunk part
   it.raster = a.raster;
   it.ksplit = pk_ksplit(a);
   it.part = it.ksplit > 1 ? reinterpret_cast<float2*>(w + L.bytes) : nullptr;
@@ -795,6 +796,11 @@ PkLayout pk_layout(const GemmArgs& a, int math) {
   L.off_qb = align256((size_t)L.tiles_m * L.nkb * nt * pk::TERM);
   L.bytes = L.off_qb + align256((size_t)L.tiles_n * L.nkb * nt * pk::TERM);
   return L;
+}
+
+int pk_stage_blocks(int math) {
+  return math == TC_MATH_BF16 ? pk::Cfg<1>::BPS
+         : math == TC_MATH_BF16X3 ? pk::Cfg<2>::BPS : pk::Cfg<3>::BPS;
 }
 
 tc_status launch_gemm_tc_packed(const GemmArgs& a, int math, void* ws, void* stream) {
