@@ -16,13 +16,15 @@
 //     where a 128x128 tile would waste most of its work: batched CUDA-core
 //     kernels compute partial sums over K segments into the batch's own
 //     workspace -- 32x32 output tiles with operand blocks staged in shared
-//     memory where min(M, N) >= 16, a thread (or a block) per output
-//     otherwise -- and a last kernel adds the segments of each output in order
-//     (deterministic) and applies alpha and beta.  Long K is split so that even
-//     a single-output contraction spreads over many SMs.
-// The (up to six) kernels are launched back to back on the caller's stream; nothing
-// is allocated or copied per call, so tc_contract_batched may be captured in a
-// CUDA graph.
+//     memory where min(M, N) >= 16, a thread per output otherwise (a warp per
+//     output below 256 outputs) -- and a last kernel adds the segments of each
+//     output in order (deterministic) and applies alpha and beta; outputs of
+//     one segment are stored by the partial kernels themselves.  Long K is
+//     split so that even a single-output contraction spreads over many SMs.
+// The (up to six) kernels go on the caller's stream, the CUDA-core ones on a
+// stream of the batch's own forked from and joined back to it when both routes
+// have work; nothing is allocated or copied per call, so tc_contract_batched
+// may be captured in a CUDA graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
