@@ -62,9 +62,9 @@ constexpr uint32_t kRing = 192 * 1024;       // bytes of the stage ring
 // MMA cycles take two blocks per stage.
 template <int NT>
 struct Cfg {
-  static constexpr int BPS = NT == 1 ? 4 : NT == 2 ? 2 : 1;  // blocks per stage
+  static constexpr int BPS = NT == 1 ? 4 : 2;  // blocks per stage
   static constexpr uint32_t STAGE = 2 * BPS * NT * TERM;  // A blocks then B blocks
-  static constexpr int S = (int)(kRing / STAGE);      // 3, 3, 4
+  static constexpr int S = (int)(kRing / STAGE);      // 3, 3, 2
   static constexpr uint32_t OFF_COLC = S * STAGE;
   static constexpr uint32_t OFF_BAR = OFF_COLC + 2 * TILE * 8;
   static constexpr uint32_t NBAR = 2 * S + 4 + 1;
