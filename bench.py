@@ -133,11 +133,12 @@ def recorded_traffic(kernel, workload):
     if f is None or kernel not in KERNEL_SOURCES:
         return None
     try:
-        for line in open(os.path.join(ROOT, f)):
-            if line.startswith("traffic_bytes_per_launch:"):
-                w = line.split()
-                if w[2] == "sources_sha256:" and w[3] == source_hash(kernel):
-                    return float(w[1])
+        with open(os.path.join(ROOT, f)) as fh:
+            for line in fh:
+                if line.startswith("traffic_bytes_per_launch:"):
+                    w = line.split()
+                    if w[2] == "sources_sha256:" and w[3] == source_hash(kernel):
+                        return float(w[1])
     except (OSError, IndexError, ValueError):
         pass
     return None

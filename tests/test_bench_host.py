@@ -13,7 +13,8 @@ def test_recorded_traffic_follows_the_source_hash(tmp_path, monkeypatch):
     for src in bench.KERNEL_SOURCES["gemm_simt"]:
         dst = tmp_path / src
         dst.parent.mkdir(parents=True, exist_ok=True)
-        dst.write_bytes(open(os.path.join(os.path.dirname(bench.__file__), src), "rb").read())
+        with open(os.path.join(os.path.dirname(bench.__file__), src), "rb") as fh:
+            dst.write_bytes(fh.read())
     monkeypatch.setattr(bench, "TRAFFIC_FILES", {("gemm_simt", "w"): "summary.md"})
     f.write_text(f"text\ntraffic_bytes_per_launch: 1234 sources_sha256: {h}\n")
     assert bench.recorded_traffic("gemm_simt", "w") == 1234.0
@@ -24,9 +25,9 @@ def test_recorded_traffic_follows_the_source_hash(tmp_path, monkeypatch):
 
 
 def test_committed_summary_parses():
-    line = [l for l in open(os.path.join(os.path.dirname(bench.__file__),
-                                         bench.TRAFFIC_FILES[("gemm_simt", "direct_gemm_64")]))
-            if l.startswith("traffic_bytes_per_launch:")]
+    with open(os.path.join(os.path.dirname(bench.__file__),
+                           bench.TRAFFIC_FILES[("gemm_simt", "direct_gemm_64")])) as fh:
+        line = [l for l in fh if l.startswith("traffic_bytes_per_launch:")]
     assert len(line) == 1
     w = line[0].split()
     assert float(w[1]) > 0 and w[2] == "sources_sha256:" and len(w[3]) == 16
