@@ -32,6 +32,20 @@ __device__ __forceinline__ int64_t goff(const Group& g, int t, uint32_t idx) {
   return off;
 }
 
+// goff for a group of 2^31 or more elements (a whole operand or a whole C,
+// as the COPY baseline and the beta-only scaling walk them): the index is
+// split with 64-bit division, so no part of it wraps.
+__device__ __forceinline__ int64_t goff_wide(const Group& g, int t, uint64_t idx) {
+  int64_t off = 0;
+  for (int i = 0; i < g.n; ++i) {
+    const uint64_t e = (uint64_t)g.ext[i];
+    const uint64_t q = idx / e;
+    off += (int64_t)(idx - q * e) * g.st[t][i];
+    idx = q;
+  }
+  return off;
+}
+
 // Two offsets of one group index at once (first operand and C, etc.).
 __device__ __forceinline__ void goff2(const Group& g, int t0, int t1, uint32_t idx, int64_t& o0,
                                       int64_t& o1) {

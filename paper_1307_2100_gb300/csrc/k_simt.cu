@@ -541,8 +541,11 @@ constexpr int kDotBlocks = 152 * 4;
 
 int dot_partials(const GemmArgs&, int) { return kDotBlocks; }
 
+// `part` receives one FP64 partial per CTA: the plan's workspace, or the
+// library's built-in scratch array for tc_contract_dot_noalloc.
 template <typename T>
-__global__ void __launch_bounds__(kDotThreads) k_dot_partial(const __grid_constant__ GemmArgs p) {
+__global__ void __launch_bounds__(kDotThreads) k_dot_partial(const __grid_constant__ GemmArgs p,
+                                                             double* __restrict__ part) {
   __shared__ double red[kDotThreads / 32];
   const T* __restrict__ X = static_cast<const T*>(p.A);
   const T* __restrict__ Y = static_cast<const T*>(p.B);
@@ -560,14 +563,14 @@ __global__ void __launch_bounds__(kDotThreads) k_dot_partial(const __grid_consta
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < kDotThreads / 32; ++w) s += red[w];
-    static_cast<double*>(p.ws)[blockIdx.x] = s;
+    part[blockIdx.x] = s;
   }
 }
 
 template <typename T>
-__global__ void k_dot_final(const __grid_constant__ GemmArgs p, int nparts) {
+__global__ void k_dot_final(const __grid_constant__ GemmArgs p, const double* __restrict__ part,
+                            int nparts) {
   __shared__ double red[32];
-  const double* part = static_cast<const double*>(p.ws);
   double s = 0.0;
   for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[i];
   s = warp_sum(s);
@@ -584,13 +587,25 @@ __global__ void k_dot_final(const __grid_constant__ GemmArgs p, int nparts) {
 }
 
 template <typename T>
+static void dot_scalar_t(const GemmArgs& a, double* part, cudaStream_t s) {
+  k_dot_partial<T><<<kDotBlocks, kDotThreads, 0, s>>>(a, part);
+  k_dot_final<T><<<1, 256, 0, s>>>(a, part, kDotBlocks);
+}
+
+tc_status launch_dot_scalar(const GemmArgs& a, tc_dtype dt, double* part, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (dt == TC_F64) dot_scalar_t<double>(a, part, s);
+  else dot_scalar_t<float>(a, part, s);
+  return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+}
+
+template <typename T>
 static tc_status dot_t(const GemmArgs& a, cudaStream_t s) {
   const uint64_t outs = (uint64_t)a.M * a.N * (uint64_t)a.nbatch;
   if (outs == 0) return TC_OK;
   if (outs == 1) {
     if (!a.ws) return TC_ERR_WORKSPACE;
-    k_dot_partial<T><<<kDotBlocks, kDotThreads, 0, s>>>(a);
-    k_dot_final<T><<<1, 256, 0, s>>>(a, kDotBlocks);
+    dot_scalar_t<T>(a, static_cast<double*>(a.ws), s);
   } else {
     k_dot_rows<T><<<grid_for((outs + 7) / 8), 256, 0, s>>>(a);
   }
@@ -609,7 +624,9 @@ tc_status launch_dot(const GemmArgs& a, tc_dtype dt, int, void* stream) {
 // over (output-first label, input-fastest label) goes through shared memory
 // so that both the reads and the writes are coalesced.
 // ---------------------------------------------------------------------------
-template <typename T>
+// Wide: the tensor has 2^31 or more elements, so its flat index is split in
+// 64 bits (a 32-bit split would wrap and leave elements unwritten).
+template <typename T, bool Wide>
 __global__ void __launch_bounds__(256) k_perm_direct(const __grid_constant__ PermArgs p) {
   const T* __restrict__ in = static_cast<const T*>(p.in);
   T* __restrict__ out = static_cast<T*>(p.out);
@@ -617,14 +634,19 @@ __global__ void __launch_bounds__(256) k_perm_direct(const __grid_constant__ Per
   for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < (uint64_t)p.total;
        q += stride) {
     int64_t oi, oo;
-    goff2(p.g, 0, 2, (uint32_t)q, oi, oo);
+    if (Wide) {
+      oi = goff_wide(p.g, 0, q);
+      oo = goff_wide(p.g, 2, q);
+    } else {
+      goff2(p.g, 0, 2, (uint32_t)q, oi, oo);
+    }
     out[oo] = in[oi];
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_perm_tiled(const __grid_constant__ PermArgs p, int li,
-                                                    uint32_t rest_total) {
+                                                    uint64_t rest_total) {
   __shared__ T tile[32][33];
   const T* __restrict__ in = static_cast<const T*>(p.in);
   T* __restrict__ out = static_cast<T*>(p.out);
@@ -635,12 +657,12 @@ __global__ void __launch_bounds__(256) k_perm_tiled(const __grid_constant__ Perm
     const uint32_t t0 = (uint32_t)(t % t0n);
     const uint64_t r1 = t / t0n;
     const uint32_t t1 = (uint32_t)(r1 % t1n);
-    uint32_t rest = (uint32_t)(r1 / t1n);
+    uint64_t rest = r1 / t1n;  // once per 32x32 tile: 64-bit division is cheap here
     int64_t bi = 0, bo = 0;
     for (int i = 1; i < p.g.n; ++i) {  // the other labels, column-major
       if (i == li) continue;
-      uint32_t e = (uint32_t)p.g.ext[i];
-      uint32_t q = rest / e, r = rest - q * e;
+      const uint64_t e = (uint64_t)p.g.ext[i];
+      const uint64_t q = rest / e, r = rest - q * e;
       bi += (int64_t)r * p.g.st[0][i];
       bo += (int64_t)r * p.g.st[2][i];
       rest = q;
@@ -670,14 +692,17 @@ static tc_status perm_t(const PermArgs& a, cudaStream_t s) {
   for (int i = 1; i < a.g.n; ++i)
     if (a.g.st[0][i] < a.g.st[0][li]) li = i;
   if (li == 0 || a.g.st[0][li] != 1) {
-    k_perm_direct<T><<<grid_for((a.total + 255) / 256), 256, 0, s>>>(a);
+    const int grid = grid_for(std::min<uint64_t>((a.total + 255) / 256, 152 * 64));
+    if (a.total >= ((int64_t)1 << 31))
+      k_perm_direct<T, true><<<grid, 256, 0, s>>>(a);
+    else
+      k_perm_direct<T, false><<<grid, 256, 0, s>>>(a);
   } else {
     uint64_t rest = 1;
     for (int i = 1; i < a.g.n; ++i)
       if (i != li) rest *= (uint64_t)a.g.ext[i];
     const uint64_t ntiles = ((a.g.ext[0] + 31) / 32) * ((a.g.ext[li] + 31) / 32) * rest;
-    k_perm_tiled<T><<<grid_for(std::min<uint64_t>(ntiles, 152 * 64)), 256, 0, s>>>(a, li,
-                                                                                    (uint32_t)rest);
+    k_perm_tiled<T><<<grid_for(std::min<uint64_t>(ntiles, 152 * 64)), 256, 0, s>>>(a, li, rest);
   }
   return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
 }
@@ -688,11 +713,12 @@ tc_status launch_perm(const PermArgs& a, tc_dtype dt, void* stream) {
 }
 
 // C = beta * C over C's own labels (empty contraction or alpha == 0).
-template <typename T>
+// Wide: C has 2^31 or more elements (index split in 64 bits, as in k_perm_direct).
+template <typename T, bool Wide>
 __global__ void k_scale(const __grid_constant__ Group g, T* C, double beta, uint64_t total) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < total; q += stride) {
-    T* dst = C + goff(g, 2, (uint32_t)q);
+    T* dst = C + (Wide ? goff_wide(g, 2, q) : goff(g, 2, (uint32_t)q));
     *dst = beta == 0.0 ? T(0) : (T)(beta * (double)*dst);
   }
 }
@@ -702,10 +728,16 @@ tc_status launch_scale(const Group& gc, void* C, double beta, tc_dtype dt, int64
   if (total <= 0) return TC_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int grid = grid_for(std::min<uint64_t>((total + 255) / 256, 152 * 32));
-  if (dt == TC_F64)
-    k_scale<double><<<grid, 256, 0, s>>>(gc, static_cast<double*>(C), beta, (uint64_t)total);
-  else
-    k_scale<float><<<grid, 256, 0, s>>>(gc, static_cast<float*>(C), beta, (uint64_t)total);
+  const bool wide = total >= ((int64_t)1 << 31);
+  if (dt == TC_F64) {
+    double* c = static_cast<double*>(C);
+    if (wide) k_scale<double, true><<<grid, 256, 0, s>>>(gc, c, beta, (uint64_t)total);
+    else k_scale<double, false><<<grid, 256, 0, s>>>(gc, c, beta, (uint64_t)total);
+  } else {
+    float* c = static_cast<float*>(C);
+    if (wide) k_scale<float, true><<<grid, 256, 0, s>>>(gc, c, beta, (uint64_t)total);
+    else k_scale<float, false><<<grid, 256, 0, s>>>(gc, c, beta, (uint64_t)total);
+  }
   return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
 }
 
