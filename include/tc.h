@@ -345,22 +345,29 @@ tc_status tc_mlp_adam_step(tc_mlp_t net, const float* grad, float lr, float beta
                            float eps, int32_t t, void* stream);
 
 /* ---- Scalar contraction without a workspace -------------------------------
- * The paper has no counterpart of this entry point; it serves callers that
- * cannot allocate device memory when they contract (for example code running
- * while a CUDA graph is captured, or runtimes that own all device memory).
- * It runs a plan whose result is a single element (Class 1 mapped to DOT, the
- * one kernel that needs scratch space, for its per-block partial sums) using a
- * fixed scratch array built into the library instead of a workspace:
+ * The paper has no counterpart of this entry point.  It serves callers that
+ * cannot allocate device memory when they contract: runtimes that reserve all
+ * device memory for their own pool up front, plug-ins handed only input and
+ * output pointers, and latency-critical loops that cannot afford the device
+ * synchronisation cudaMalloc / cudaFree may imply.  It runs a plan whose
+ * result is a single element (Class 1 mapped to DOT, the one kernel that needs
+ * scratch space, for its per-block partial sums) with the same kernels as
+ * tc_contract, but keeps the partial sums in a fixed scratch array built into
+ * the library instead of a workspace:
  *   - the array holds TC_NOALLOC_SCRATCH_BYTES on every GPU that loads the
- *     library, until the process exits; a plan needing more is rejected with
- *     TC_ERR_WORKSPACE;
+ *     library, until the process exits; the DOT kernel's partial sums (608
+ *     doubles, 4.9 KB, whatever the contraction's size) fit in it; should a
+ *     plan ever need more, the call returns TC_ERR_WORKSPACE;
  *   - all calls share the array: calls that overlap on the GPU race; calls
  *     ordered on one stream are fine; the array keeps the last call's
  *     contents, none of which a later call relies on;
  *   - the first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make it before any
- *     stream capture.
- * Other plans return TC_ERR_UNSUPPORTED.  Allocates nothing. */
+ *     (cudaGetSymbolAddress) with that device current and keeps it; make that
+ *     first call before any stream capture; a cudaDeviceReset of the device
+ *     invalidates the kept address, so do not call this entry point on a
+ *     device after resetting it in the same process;
+ *   - devices numbered 64 or above return TC_ERR_UNSUPPORTED.
+ * Other plans return TC_ERR_UNSUPPORTED.  Calls no allocating routine. */
 #define TC_NOALLOC_SCRATCH_BYTES (16 * 1024)
 tc_status tc_contract_dot_noalloc(tc_plan_t plan, double alpha, const void* A, const void* B,
                                   double beta, void* C, void* stream);

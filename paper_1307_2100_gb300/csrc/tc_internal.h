@@ -121,6 +121,9 @@ tc_status launch_scale(const Group& gc, void* C, double beta, tc_dtype dt, int64
                        void* stream);
 tc_status launch_gemm_tc(const GemmArgs& a, int math, void* stream);
 int dot_partials(const GemmArgs& a, int tile);
+// The scalar (Class 1) DOT: one FP64 partial per CTA into part[0 ..
+// dot_partials()), then their ordered sum, alpha and beta.
+tc_status launch_dot_scalar(const GemmArgs& a, tc_dtype dt, double* part, void* stream);
 int num_tiles_tc();
 // Enqueue a read-and-clear of the tensor-core kernels' timeout flag into *h.
 tc_status tc_gemm_read_status(int* h, void* stream);

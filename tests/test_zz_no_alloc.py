@@ -1,15 +1,16 @@
 """The workspace-free scalar contraction (tc_contract_dot_noalloc).
 
-Callers that cannot allocate device memory while they contract (inside a
-CUDA graph capture, or under a runtime that owns all device memory) use this
-entry point; it keeps the partial sums of the scalar reduction in a scratch
-array built into the library.  The test compares it, through the C ABI, with
-the regular tc_contract (which takes a workspace) on two calls in a row, for
-FP64 and FP32 data, within the FP64 parity tolerance of the other tests.
-This file is collected last on purpose."""
+Callers that cannot allocate device memory while they contract (runtimes
+that own all device memory, plug-ins given only input and output pointers)
+use this entry point; it keeps the partial sums of the scalar reduction in a
+scratch array built into the library.  The test compares it, through the C
+ABI, with the regular tc_contract (which takes a workspace) and with the CPU
+oracle, on two calls in a row, for FP64 and FP32 data, within the FP64 parity
+tolerance of the other tests.  This file is collected last on purpose."""
 import numpy as np
 import pytest
 
+import oracle
 import tcsynth as ts
 
 pytestmark = pytest.mark.gpu
@@ -52,6 +53,10 @@ def test_noalloc_scalar_matches_tc_contract_twice(dt):
             torch.cuda.synchronize()
             r, g = float(ref.item()), float(got.item())
             assert abs(g - r) <= TOL * max(abs(r), 1e-300), (call, g, r)
+            # and against the oracle, from the same (storage-precision) inputs
+            o = oracle.contract(p.A, p.B, p.C, alpha, beta,
+                                c_init=np.full(1, float(c0.item())))
+            assert abs(g - o[0]) <= TOL * max(abs(o[0]), 1e-300), (call, g, o[0])
     finally:
         tc.tc_plan_destroy(handle)
 
