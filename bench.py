@@ -202,10 +202,13 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- CPU oracle
-def oracle_sample_problems(target_s: float, nthreads: int):
-    """Bounded samples of the three contractions for the CPU oracle: the last
-    free label of C is cut to s values, s chosen so each takes ~target_s."""
+def oracle_sample_problems(target_s: float, nthreads: int, fn=None):
+    """Bounded samples of the three contractions for a CPU baseline (the
+    oracle, or `fn`): the last free label of C is cut to s values, s chosen so
+    each takes ~target_s."""
     import oracle
+    if fn is None:
+        fn = lambda q, nthreads: oracle.contract_problem(q, nthreads=nthreads)
     full = [ts.direct_gemm_64(), ts.fused_permute_48(), None]
     out = []
     for j, p in enumerate(full):
@@ -226,8 +229,9 @@ def oracle_sample_problems(target_s: float, nthreads: int):
             return q
         maxs = 1024 if j == 2 else p.C.extents[-1]
         q = cut(1)
+        fn(q, nthreads)  # warm (library loads, thread pools)
         t0 = time.perf_counter()
-        oracle.contract_problem(q, nthreads=nthreads)
+        fn(q, nthreads)
         t1 = max(time.perf_counter() - t0, 1e-4)
         s = int(max(1, min(maxs, round(target_s / t1))))
         out.append(cut(s))
@@ -247,6 +251,112 @@ def cores():
         return len(os.sched_getaffinity(0))
     except Exception:
         return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------ peak probes
+PEAK_KINDS = ("dfma", "dmma", "ffma", "bf16", "bf16_n256", "fp8")
+
+
+def measure_peaks(tc, stream, target_ms=25.0, reps=3):
+    """Peak rates (TFLOP/s) of each arithmetic on this GPU, measured in this
+    process by the library's probe kernels (tc_peak_probe): a calibration
+    launch sizes each probe to about target_ms, then the best of `reps`
+    event-timed launches."""
+    import torch
+    out = {}
+    for name in PEAK_KINDS:
+        kind = tc.PEAK[name]
+        iters = 64
+        for _ in range(4):  # calibrate the length
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tc.tc_peak_probe(kind, iters, stream.cuda_stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            if ms >= 0.5 * target_ms:
+                break
+            iters = int(iters * min(64.0, max(2.0, target_ms / max(ms, 1e-3))))
+        best = 0.0
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            flops = tc.tc_peak_probe(kind, iters, stream.cuda_stream)
+            e1.record(stream)
+            e1.synchronize()
+            best = max(best, flops / (e0.elapsed_time(e1) / 1e3) / 1e12)
+        out[name] = best
+    return out
+
+
+# ------------------------------------------------- the paper's method on the CPU
+def recipe_cpu(p, nthreads=None):
+    """The paper's method on the host: the class recipe's slicing vectors
+    (Sec. 3.2), each slice one host-BLAS call through torch's CPU matmul in
+    FP64.  Sliced free indices become batch dimensions of one matmul (the loop
+    over those slices runs inside torch), sliced contracted indices are a loop
+    that accumulates into C (R2's beta = 1).  Non-unit-stride slices are
+    copied by matmul before the BLAS call, as COPY+GEMM does.  Returns C's
+    buffer (float64, C's layout)."""
+    import itertools
+    import torch
+    from oracle import classify as ocl
+    if nthreads:
+        torch.set_num_threads(int(nthreads))
+    A, B, C = p.A, p.B, p.C
+    cl = ocl.classify(A, B, C)
+    ext = {}
+    for t in (A, B, C):
+        for l, e in zip(t.labels, t.extents):
+            ext[l] = int(e)
+    con = [l for l in A.labels if l in B.labels]
+    sl_a = {l for l, f in zip(A.labels, cl.slice_a) if f}
+    sl_b = {l for l, f in zip(B.labels, cl.slice_b) if f}
+    k_loop = [l for l in con if l in sl_a or l in sl_b]       # accumulated slices
+    k_keep = [l for l in con if l not in k_loop]
+    fa_bat = [l for l in A.labels if l not in con and l in sl_a]
+    fb_bat = [l for l in B.labels if l not in con and l in sl_b]
+    fa_mat = [l for l in A.labels if l not in con and l not in sl_a]
+    fb_mat = [l for l in B.labels if l not in con and l not in sl_b]
+    cbuf = np.zeros(max(C.data.size, 1), dtype=np.float64)
+    if any(ext[l] == 0 for l in C.labels):
+        return cbuf[: C.data.size]
+    tA = torch.from_numpy(np.asarray(A.data, np.float64))
+    tB = torch.from_numpy(np.asarray(B.data, np.float64))
+    tC = torch.from_numpy(cbuf)
+
+    def view(t, labels, strides, order, off):  # None: a broadcast dimension of size 1
+        st = dict(zip(labels, strides))
+        return torch.as_strided(t, [1 if l is None else ext[l] for l in order],
+                                [0 if l is None else st[l] for l in order], off)
+
+    def flat(x, groups):  # merge consecutive dims of each group into one
+        shape, i = [], 0
+        for g in groups:
+            n = 1
+            for _ in range(g):
+                n *= x.shape[i]
+                i += 1
+            shape.append(n)
+        return x.reshape(shape)
+
+    c_order = fa_bat + fb_bat + fa_mat + fb_mat
+    cv = view(tC, C.labels, C.strides, c_order, 0)
+    for kv in itertools.product(*[range(ext[l]) for l in k_loop]):
+        fix = dict(zip(k_loop, kv))
+        oa = sum(fix[l] * s for l, s in zip(A.labels, A.strides) if l in fix)
+        ob = sum(fix[l] * s for l, s in zip(B.labels, B.strides) if l in fix)
+        av = view(tA, A.labels, A.strides, fa_bat + [None] * len(fb_bat) + fa_mat + k_keep, oa)
+        bv = view(tB, B.labels, B.strides, [None] * len(fa_bat) + fb_bat + k_keep + fb_mat, ob)
+        nb = len(fa_bat) + len(fb_bat)
+        am = flat(av, [1] * nb + [len(fa_mat), len(k_keep)])
+        bm = flat(bv, [1] * nb + [len(k_keep), len(fb_mat)])
+        r = torch.matmul(am, bm)                     # one BLAS call per batch slice
+        cv += r.reshape(cv.shape)
+    out = cbuf[: C.data.size]
+    if p.alpha != 1.0:
+        out *= p.alpha
+    return out
 
 
 def sample_desc(problems):
@@ -281,6 +391,260 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ------------------------------------------------- parts of the default line
+def _event_times(fn, stream, flush, n):
+    """Event-timed runs of fn on `stream`, the L2 flushed before each (outside
+    the events); returns the list of ms."""
+    import torch
+    out = []
+    for _ in range(n):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def precision_part(peaks, steps, warmup, v=128):
+    """The precision workload (the CCD-shaped C[a,b,i,j] = sum_{e,f}
+    A[a,b,e,f] B[e,f,i,j] of Sec. 4.2, a=b=e=f=v, i=j=32) on the plain FP64
+    path and in every reduced-precision form, on the same FP32-representable
+    inputs: time (median, L2 flushed), effective TFLOP/s, roofline fraction and
+    the sampled relative error against the FP64 oracle."""
+    import torch
+    from paper_1307_2100_gb300 import Contraction, tc
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    p = ts.precision_ccd(v=v)
+    std = peaks_std()
+    A32 = torch.from_numpy(p.A.data).to(dev)
+    B32 = torch.from_numpy(p.B.data).to(dev)
+    out = []
+    for form in ("fp64", "bf16x6", "bf16x3", "bf16", "fp8"):
+        f64 = form == "fp64"
+        A, B = (A32.double(), B32.double()) if f64 else (A32, B32)
+        C = torch.empty(p.C.data.size, dtype=A.dtype, device=dev)
+        plan = Contraction((p.A.labels, p.A.extents, p.A.strides),
+                           (p.B.labels, p.B.extents, p.B.strides),
+                           (p.C.labels, p.C.extents, p.C.strides), "f64" if f64 else "f32",
+                           form, "auto")
+        ws = plan.workspace(dev)
+        call = lambda: tc.tc_contract(plan.handle, 1.0, A.data_ptr(), B.data_ptr(), 0.0,
+                                      C.data_ptr(), ws.data_ptr() if ws is not None else 0,
+                                      ws.numel() if ws is not None else 0, stream.cuda_stream)
+        nw, ns = (1, 2) if f64 else (warmup, steps)
+        with torch.cuda.stream(stream):
+            for _ in range(nw):
+                call()
+        ms = float(np.median(_event_times(call, stream, flush, ns)))
+        info = plan.info
+        flops = p.flops()
+        bytes_ = p.min_bytes() * (2 if f64 else 1)
+        if f64:
+            cpeak, work, bound_c, src = peaks["fp64"], flops, "alu", peaks["fp64_source"]
+        elif form == "fp8":
+            cpeak, work, bound_c, src = peaks["fp8"], flops, "tensor", peaks["fp8_source"]
+        else:
+            cpeak, work, bound_c = std["bf16"], flops * NPROD[form], "tensor"
+            src = f"bf16_tflops burst {std['bf16']} (MEASURED_PEAKS.json) x {NPROD[form]} products"
+        t_c, t_m = work / (cpeak * 1e12), bytes_ / (std["hbm"] * 1e9)
+        err = sampled_error(p, C.cpu().numpy().astype(np.float64))
+        out.append({"form": form, "kernel": tc.KERNEL_NAME[info.kernel], "tile": int(info.tile),
+                    "ms": ms, "tflops_effective": flops / (ms / 1e3) / 1e12,
+                    "bound": bound_c if t_c >= t_m else "hbm",
+                    "roofline_ms": 1e3 * max(t_c, t_m), "frac": 1e3 * max(t_c, t_m) / ms,
+                    "peak_source": src if t_c >= t_m else f"hbm_gbs {std['hbm']} GB/s",
+                    "rel_err_vs_fp64_oracle_sampled": err, "samples": 64,
+                    "gpu_launches": launches_of(info)})
+        del C, ws, plan, A, B
+        torch.cuda.empty_cache()
+    base = out[0]["ms"]
+    for q in out:
+        q["speedup_vs_plain_fp64"] = base / q["ms"]
+    fp32c = [q for q in out[1:] if q["rel_err_vs_fp64_oracle_sampled"] <= 1e-6]
+    best = min(fp32c, key=lambda q: q["ms"]) if fp32c else None
+    return {"workload": f"precision: C[a,b,i,j] = sum_ef A[a,b,e,f] B[e,f,i,j], a=b=e=f={v}, "
+                        "i=j=32; A = N(0,1)/(1+|a-e|), B = N(0,1); FP32 values (FP64 storage "
+                        "for the plain path)",
+            "l2": "flushed before each timed run", "forms": out,
+            "fastest_fp32_class": None if best is None else {
+                "form": best["form"], "ms": best["ms"],
+                "speedup_vs_plain_fp64": best["speedup_vs_plain_fp64"],
+                "rel_err": best["rel_err_vs_fp64_oracle_sampled"], "bound": 1e-6}}
+
+
+def config1_part(peaks, steps):
+    """Config 1, C[a,b,c] = sum_i A[a,i,c] B[i,b] with every extent 48 (case
+    (iii) of Eq. tenscases), FP64: 1.8 MB of operands, launch-latency bound.
+    Timed by CUDA-graph replay of one tc_contract: back to back with the
+    operands in L2, and one replay at a time with the L2 flushed; also as a
+    plain launch.  The oracle on the host: one thread and every core."""
+    import torch
+    import oracle
+    from paper_1307_2100_gb300 import Contraction, tc
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    p = ts.slice_gemm_48()
+    plan = Contraction((p.A.labels, p.A.extents, p.A.strides),
+                       (p.B.labels, p.B.extents, p.B.strides),
+                       (p.C.labels, p.C.extents, p.C.strides), "f64", "fp64", "auto")
+    A = torch.from_numpy(p.A.data).to(dev)
+    B = torch.from_numpy(p.B.data).to(dev)
+    C = torch.empty(p.C.data.size, dtype=torch.float64, device=dev)
+    ws = plan.workspace(dev)
+    call = lambda: tc.tc_contract(plan.handle, 1.0, A.data_ptr(), B.data_ptr(), 0.0,
+                                  C.data_ptr(), ws.data_ptr() if ws is not None else 0,
+                                  ws.numel() if ws is not None else 0, stream.cuda_stream)
+    with torch.cuda.stream(stream):
+        for _ in range(5):
+            call()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        call()
+    for _ in range(10):
+        g.replay()
+    torch.cuda.synchronize()
+    nrep = 200
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(nrep):
+            g.replay()
+        e1.record(stream)
+    e1.synchronize()
+    warm_ms = e0.elapsed_time(e1) / nrep
+    cold_ms = float(np.median(_event_times(g.replay, stream, flush, max(steps, 10))))
+    plain_ms = float(np.median(_event_times(call, stream, flush, max(steps, 10))))
+    torch.cuda.synchronize()
+    ref = oracle.contract_problem(p)
+    err = oracle.rel_fro(C.cpu().numpy(), ref)
+    info = plan.info
+    flops = p.flops()
+    t_c = flops / (peaks["fp64"] * 1e12)
+    t_m = p.min_bytes() / (peaks_std()["hbm"] * 1e9)
+    t1 = time.perf_counter()
+    oracle.contract_problem(p, nthreads=1)
+    cpu1 = time.perf_counter() - t1
+    nth = cores()
+    t1 = time.perf_counter()
+    oracle.contract_problem(p, nthreads=nth)
+    cpun = time.perf_counter() - t1
+    del g
+    return {"workload": "config 1: C[a,b,c] = sum_i A[a,i,c] B[i,b], all extents 48, FP64, "
+                        "uniform[-1,1)",
+            "class": int(info.cls), "mapping": tc.MAPPING_NAME[info.mapping],
+            "kernel": tc.KERNEL_NAME[info.kernel],
+            "graph_replay_l2_warm_us": 1e3 * warm_ms, "graph_replay_l2_flushed_us": 1e3 * cold_ms,
+            "plain_launch_l2_flushed_us": 1e3 * plain_ms,
+            "tflops_graph_l2_warm": flops / (warm_ms / 1e3) / 1e12,
+            "tflops_graph_l2_flushed": flops / (cold_ms / 1e3) / 1e12,
+            "roofline": {"bound": "alu" if t_c >= t_m else "hbm",
+                         "roofline_us": 1e6 * max(t_c, t_m),
+                         "frac_graph_l2_flushed": 1e3 * max(t_c, t_m) / cold_ms,
+                         "peak_source": peaks["fp64_source"]},
+            "rel_err_vs_fp64_oracle": err,
+            "cpu_oracle": {"one_thread_s": cpu1, "all_cores_s": cpun, "cores": nth,
+                           "one_thread_tflops": flops / cpu1 / 1e12,
+                           "all_cores_tflops": flops / cpun / 1e12, "kind": "oracle",
+                           "sample": "the whole config"}}
+
+
+def selector_part(n_desc=160, budget_s=75.0, reps=3):
+    """The learned selector re-timed on this GPU: held-out descriptors of the
+    selector workload (orders 2-6, extents log-uniform [4, 256], random label
+    placement and strides; the network never saw them), each timed under every
+    candidate mapping (exhaustive timing, median of `reps` runs), and the
+    regret t(choice) / t(best) - 1 of the network's choice (tc_plan with
+    TC_MAP_AUTO, packaged weights) and of the paper's recipe.  Stops at
+    `budget_s` seconds."""
+    import torch
+    from paper_1307_2100_gb300 import selector as sel
+    from paper_1307_2100_gb300 import tc
+    data = os.path.join(ROOT, "paper_1307_2100_gb300", "data")
+    z = np.load(os.path.join(data, "selector_timings_gb300.npz"))
+    seed, n_all = int(z["seed"]), len(z["F"])
+    descs = ts.selector_descriptors(n_all, seed=seed)
+    _, te = sel.split(n_all, 2000)
+    spans = []
+    for i in te[:n_desc]:
+        spans.append(max(sel._span(t) for t in descs[i]))
+    ensure, time_plan, s = sel._timer(1 << 31)
+    ensure(max(spans))
+    spec = {(tc.MAPPING[m], t): j for j, (_, m, t) in enumerate(sel.CANDIDATE_SPECS)}
+
+    def planned(A, B, C, mapping):
+        h = tc.tc_plan(sel._desc(A), sel._desc(B), sel._desc(C), tc.TC_F32,
+                       tc.MATH[sel.MATH], tc.MAPPING[mapping])
+        try:
+            info = tc.tc_plan_get_info(h)
+        finally:
+            tc.tc_plan_destroy(h)
+        m, t = int(info.mapping), int(info.tile)
+        return spec.get((m, t), spec.get((m, -1), 0))
+
+    tc.tc_selector_load(os.path.join(data, "selector_gb300.bin"))
+    rn, rr, rows = [], [], 0
+    t0 = time.perf_counter()
+    try:
+        for i in te[:n_desc]:
+            if time.perf_counter() - t0 > budget_s:
+                break
+            A, B, C = descs[i]
+            T = [sel._time_candidates(descs[i], j, time_plan, reps)
+                 for j in range(len(sel.CANDIDATE_SPECS))]
+            ok = [t for t in T if t is not None]
+            if not ok:
+                continue
+            best = min(ok)
+            cn, cr = planned(A, B, C, "auto"), planned(A, B, C, "recipe")
+            if T[cn] is None or T[cr] is None:
+                continue
+            rn.append(T[cn] / best - 1.0)
+            rr.append(T[cr] / best - 1.0)
+            rows += 1
+    finally:
+        tc.tc_selector_unload()
+    torch.cuda.synchronize()
+    stat = lambda r: {"mean": float(np.mean(r)), "median": float(np.median(r)),
+                      "p90": float(np.percentile(r, 90))} if r else None
+    return {"workload": "selector: held-out descriptors (orders 2-6, extents log-uniform "
+                        "[4,256], random placement and strides), FP32 storage, BF16x6",
+            "descriptors_timed": rows, "candidates": len(sel.CANDIDATE_SPECS),
+            "timing": f"median of {reps} event-timed runs per candidate, live on this GPU",
+            "regret_network": stat(rn), "regret_recipe": stat(rr),
+            "seconds": time.perf_counter() - t0}
+
+
+def peaks_std():
+    """Measured copy bandwidth and cuBLAS BF16 rate (MEASURED_PEAKS.json)."""
+    pk = read_peaks()
+    return {"hbm": pk.get("hbm_gbs", 6784.5), "bf16": pk.get("bf16_tflops", 1884.0),
+            "sm_max_mhz": pk.get("sm_max_mhz", 2070.0)}
+
+
+def roofline_peaks(measured, clk):
+    """Peaks the roofline fractions use.  FP64: the larger of the in-run DFMA
+    probe and the nominal rate at the maximum SM clock (152 SMs x 4 FP64
+    flop/clk); FP8: the in-run block-scaled probe."""
+    std = peaks_std()
+    smax = (clk or {}).get("sm_max_mhz") or std["sm_max_mhz"]
+    nominal = N_SMS * FP64_FLOP_PER_CLK_SM * smax * 1e6 / 1e12
+    fp64 = max(measured.get("dfma", 0.0), nominal)
+    return {"fp64": fp64, "fp8": measured.get("fp8") or std["bf16"] * FP8_PER_BF16,
+            "fp64_source": (f"max(in-run DFMA probe {measured.get('dfma', 0.0):.4f}, "
+                            f"152 SMs x 4 flop/clk x max SM clock {smax:.0f} MHz = "
+                            f"{nominal:.4f}) TFLOP/s"),
+            "fp8_source": (f"in-run tcgen05 kind::mxf8f6f4 probe {measured['fp8']:.1f} TFLOP/s"
+                           if measured.get("fp8") else "2 x bf16_tflops (nominal ratio)")}
 
 
 # --------------------------------------------------------------- GPU arm
@@ -427,19 +791,20 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
-    peaks = read_peaks()
-    hbm = peaks.get("hbm_gbs", 6784.5)
-    sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    fp64_peak = N_SMS * FP64_FLOP_PER_CLK_SM * sm_mhz * 1e6 / 1e12  # TFLOP/s
-    bf16_peak = peaks.get("bf16_tflops", 1884.0)
+    measured = {} if args.no_peaks else measure_peaks(tc, stream)
+    rp = roofline_peaks(measured, clk)
+    hbm = peaks_std()["hbm"]
+    fp64_peak = rp["fp64"]  # TFLOP/s
+    bf16_peak = peaks_std()["bf16"]
     parts = []
     for j, p in enumerate(probs):
         info = plans[j].info
         kms = float(per[:, j].mean())
         if info.kernel == 5:  # FP8 form: one E4M3 product per multiply-add
-            cpeak, work, cbound = bf16_peak * FP8_PER_BF16, p.flops(), "tensor"
+            cpeak, work, cbound = rp["fp8"], p.flops(), "tensor"
         elif fp64 or info.kernel != 2:
-            cpeak, work, cbound = fp64_peak if fp64 else 77.7, p.flops(), "alu"
+            cpeak, work, cbound = (fp64_peak if fp64 else measured.get("ffma", 77.7),
+                                   p.flops(), "alu")
         else:  # tensor-core forms: NPROD BF16 products per logical multiply-add
             cpeak, work, cbound = bf16_peak, p.flops() * NPROD[math], "tensor"
         t_alu = work / (cpeak * 1e12)
@@ -479,10 +844,8 @@ def run_ours(args):
         "roofline": {"bound": dom["bound"], "kernel": dom["kernel"], "workload": dom["name"],
                      "achieved": dom["achieved"], "peak": dom["peak"], "unit": dom["unit"],
                      "frac": dom["frac"], "traffic": traffic,
-                     "peak_source": (("derived: 152 SMs x 4 FP64 flop/clk x median SM clock "
-                                      f"{sm_mhz:.0f} MHz") if dom["bound"] == "alu"
-                                     else "measured bf16_tflops burst (MEASURED_PEAKS.json) x 2 "
-                                     "(nominal FP8/BF16 dense ratio); achieved = FLOPs over the "
+                     "peak_source": (rp["fp64_source"] if dom["bound"] == "alu" and fp64
+                                     else rp["fp8_source"] + "; achieved = FLOPs over the "
                                      "pack pass and the GEMM"
                                      if dom["bound"] == "tensor" and math == "fp8"
                                      else "measured bf16_tflops burst (MEASURED_PEAKS.json); "
@@ -509,6 +872,43 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": sum(q.flops() for q in sprobs) / t / 1e12,
                                 "unit": "TFLOP/s", "cores": nth, "kind": "oracle",
                                 "sample": sample_desc(sprobs), "seconds": t}
+        rprobs = oracle_sample_problems(3.0, nth, fn=recipe_cpu)
+        t0 = time.perf_counter()
+        for q in rprobs:
+            recipe_cpu(q, nth)
+        t = time.perf_counter() - t0
+        line["cpu_baseline_recipe"] = {
+            "value": sum(q.flops() for q in rprobs) / t / 1e12, "unit": "TFLOP/s", "cores": nth,
+            "kind": "the paper's method: class recipe slicing (Sec. 3.2) over host BLAS "
+                    "(torch CPU FP64 matmul, sliced free indices as batch dimensions)",
+            "sample": sample_desc(rprobs), "seconds": t}
+    if world == 1 and fp64 and not args.headline_only:
+        line["peaks_measured"] = dict(measured, unit="TFLOP/s", how=(
+            "tc_peak_probe kernels in this process: DFMA/FFMA chains, DMMA m8n8k4, tcgen05 "
+            "kind::f16 128x128x16 and 128x256x16, kind::mxf8f6f4 128x128x32 from shared "
+            "memory; best of 3 event-timed launches of ~25 ms"))
+        legs = [("precision", lambda: precision_part(rp, args.steps, args.warmup)),
+                ("config1", lambda: config1_part(rp, args.steps))]
+        items = ts.batching_items(512)
+        refs = {}
+
+        def batch_leg(m):
+            r, refs["r"] = batch_measure(items, m, args.steps, args.warmup, refs=refs.get("r"),
+                                         clock=False)
+            return r
+        legs += [("batching_bf16x6", lambda: batch_leg("bf16x6")),
+                 ("batching_bf16x3", lambda: batch_leg("bf16x3")),
+                 ("selector", lambda: selector_part())]
+        extra = ClockSampler(local_rank)
+        extra.start()
+        for key, fn in legs:
+            t0 = time.perf_counter()
+            try:
+                line[key] = fn()
+            except Exception as e:  # a failing leg is reported, the line still prints
+                line[key] = {"error": repr(e)}
+            line[key]["leg_seconds"] = time.perf_counter() - t0
+        line["clocks_parts"] = extra.stop()
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -516,19 +916,18 @@ def run_ours(args):
     return 0
 
 
-def run_batching(args):
-    """512 independent contractions (orders 2-5, extents log-uniform in
-    [8, 192], 1-3 contracted indices, random storage orders, FP32) in one
-    graph-captured tc_contract_batched, against 512 tc_contract calls."""
+def batch_measure(items, math, steps, warmup, autotune=True, separate=True, refs=None,
+                  clock=True):
+    """The batched workload in one form: a batch of `items` planned with
+    autotuned routes (or the threshold rule), one CUDA graph of
+    tc_contract_batched timed by events (L2 flushed before each replay),
+    against one tc_contract call per item, every item checked against the
+    FP64 oracle (`refs`: the oracle's outputs, computed here if None).
+    Returns (result dict, refs)."""
     import torch
     import oracle
-    from paper_1307_2100_gb300 import build as _b
-    _b.build()
     from paper_1307_2100_gb300 import Contraction, tc
     dev = torch.device("cuda", 0)
-    torch.cuda.set_device(0)
-    items = ts.batching_items(args.items)
-    math = args.math
     plans, bufs = [], []
     for p in items:
         plans.append(Contraction((p.A.labels, p.A.extents, p.A.strides),
@@ -543,11 +942,11 @@ def run_batching(args):
     s = torch.cuda.Stream(device=dev)
     handles = [pl.handle for pl in plans]
     tuned = None
-    if args.no_autotune:
+    if not autotune:
         batch = tc.tc_batch_plan(handles)
     else:  # routes per size bucket, chosen by timing (outside the timed region)
-        from paper_1307_2100_gb300 import autotune
-        routes, tuned = autotune.tune_routes(handles, (pa, pb, pc, al, be), s)
+        from paper_1307_2100_gb300 import autotune as at
+        routes, tuned = at.tune_routes(handles, (pa, pb, pc, al, be), s)
         batch = tc.tc_batch_plan_routes(handles, routes)
     info = tc.tc_batch_get_info(batch)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -557,7 +956,7 @@ def run_batching(args):
         tc.tc_contract_batched(batch, pa.data_ptr(), pb.data_ptr(), pc.data_ptr(), al.data_ptr(),
                                be.data_ptr(), s.cuda_stream)
 
-    def separate():
+    def separate_calls():
         for j, pl in enumerate(plans):
             w = ws[j]
             tc.tc_contract(pl.handle, 1.0, bufs[j][0].data_ptr(), bufs[j][1].data_ptr(), 0.0,
@@ -565,18 +964,18 @@ def run_batching(args):
                            w.numel() if w is not None else 0, s.cuda_stream)
 
     with torch.cuda.stream(s):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             batched()
-            if not args.no_separate:
-                separate()
+        if separate:
+            separate_calls()
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=s):
         batched()
 
-    def timed(fn):
+    def timed(fn, n):
         ts_ = []
-        for _ in range(args.steps):
+        for _ in range(n):
             with torch.cuda.stream(s):
                 flush.zero_()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -585,45 +984,42 @@ def run_batching(args):
                 e1.record(s)
             torch.cuda.synchronize()
             ts_.append(e0.elapsed_time(e1))
-        return float(np.median(ts_)), ts_
+        return float(np.median(ts_))
 
-    clocks = ClockSampler(0)
-    clocks.start()
-    t_graph, all_graph = timed(g.replay)
-    t_sep = None if args.no_separate else timed(separate)[0]
-    clk = clocks.stop()
+    clocks = ClockSampler(0) if clock else None
+    if clocks:
+        clocks.start()
+    for _ in range(warmup):
+        g.replay()
+    t_graph = timed(g.replay, steps)
+    t_sep = timed(separate_calls, max(1, min(steps, 2))) if separate else None
+    clk = clocks.stop() if clocks else None
     status = tc.tc_device_status(s.cuda_stream)
-    # accuracy of every item against the FP64 oracle
     g.replay()
     torch.cuda.synchronize()
+    if refs is None:
+        refs = [oracle.contract_problem(p, nthreads=cores()) for p in items]
     errs = []
-    for p, b in zip(items, bufs):
+    for p, b, ref in zip(items, bufs, refs):
         got = b[2].cpu().numpy().astype(np.float64)[: p.C.data.size]
-        errs.append(oracle.rel_fro(got, oracle.contract_problem(p, nthreads=cores())))
+        errs.append(oracle.rel_fro(got, ref))
+    del g
     tc.tc_batch_destroy(batch)
     peaks = read_peaks()
     hbm = peaks.get("hbm_gbs", 6784.5)
     bf16_peak = peaks.get("bf16_tflops", 1884.0)
     flops = info.flops
-    roof_ms = 1e3 * max(flops * NPROD[math] / (bf16_peak * 1e12), info.min_bytes / (hbm * 1e9))
-    value = flops / (t_graph / 1e3) / 1e12
-    line = {
-        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_graph, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 storage, " + math,
-        "data": "synthetic (seeded uniform[-1,1); shapes of the batched workload)",
-        "config": {"workload": f"batching: {len(items)} contractions, orders 2-5, extents "
-                               "log-uniform [8,192], 1-3 contracted, random storage orders",
-                   "l2": "flushed between steps (256 MiB write, outside timing)",
-                   "launch": "one CUDA graph of tc_contract_batched",
-                   "routes": "threshold rule" if args.no_autotune else
-                   "autotuned per size bucket (paper_1307_2100_gb300/autotune.py)"},
-        "roofline": {"bound": "hbm" if info.min_bytes / (hbm * 1e9) >
-                     flops * NPROD[math] / (bf16_peak * 1e12) else "tensor",
-                     "achieved_ms": t_graph, "roofline_ms": roof_ms, "frac": roof_ms / t_graph,
-                     "traffic": None},
-        "batched_vs_separate": None if t_sep is None else {
-            "batched_ms": t_graph, "separate_ms": t_sep, "speedup": t_sep / t_graph},
+    t_tc = flops * NPROD[math] / (bf16_peak * 1e12)
+    t_mem = info.min_bytes / (hbm * 1e9)
+    roof_ms = 1e3 * max(t_tc, t_mem)
+    res = {
+        "math": math, "items": len(items), "ms": t_graph,
+        "tflops_effective": flops / (t_graph / 1e3) / 1e12,
+        "roofline": {"bound": "hbm" if t_mem > t_tc else "tensor", "roofline_ms": roof_ms,
+                     "frac": roof_ms / t_graph,
+                     "peaks": f"bf16 {bf16_peak} TFLOP/s x {NPROD[math]} products, "
+                              f"HBM {hbm} GB/s (MEASURED_PEAKS.json)"},
+        "separate_calls_ms": t_sep, "speedup_vs_separate": None if t_sep is None else t_sep / t_graph,
         "routes": {"tensor_core_items": info.n_tc_items, "cuda_core_items": info.n_simt_items,
                    "tc_tiles": info.n_tiles, "simt_work": info.n_simt_work,
                    "simt_tiles": info.n_simt_tiles, "tc_split_tiles": info.n_tc_split},
@@ -631,13 +1027,45 @@ def run_batching(args):
             "buckets": tuned["buckets"], "default_ms": tuned["default_ms"],
             "tuned_ms": tuned["tuned_ms"],
             "flipped": [t["bucket"] for t in tuned["trials"] if t["kept"]]},
-        "rel_err_vs_fp64_oracle": {"max": float(np.max(errs)), "median": float(np.median(errs))},
+        "rel_err_vs_fp64_oracle": {"max": float(np.max(errs)), "median": float(np.median(errs)),
+                                   "items_checked": len(errs)},
         "sum_flops": flops, "sum_bytes": info.min_bytes, "clocks": clk,
         "device_status": tc.tc_status_string(status),
-        "gpu_launches": args.steps * (2 * int(info.n_tiles > 0) + int(info.n_tc_split > 0) +
-                                      int(info.n_simt_work > 0) +
-                                      int(info.n_simt_tiles > 0) +
-                                      int(info.n_simt_work + info.n_simt_tiles > 0)),
+        "gpu_launches_per_step": (2 * int(info.n_tiles > 0) + int(info.n_tc_split > 0) +
+                                  int(info.n_simt_work > 0) + int(info.n_simt_tiles > 0) +
+                                  int(info.n_simt_work + info.n_simt_tiles > 0)),
+        "launch": "one CUDA graph of tc_contract_batched; L2 flushed before each replay",
+    }
+    del plans, bufs, ws
+    torch.cuda.empty_cache()
+    return res, refs
+
+
+def run_batching(args):
+    """512 independent contractions (orders 2-5, extents log-uniform in
+    [8, 192], 1-3 contracted indices, random storage orders, FP32) in one
+    graph-captured tc_contract_batched, against 512 tc_contract calls."""
+    import torch
+    from paper_1307_2100_gb300 import build as _b
+    _b.build()
+    torch.cuda.set_device(0)
+    items = ts.batching_items(args.items)
+    r, _ = batch_measure(items, args.math, args.steps, args.warmup, not args.no_autotune,
+                         not args.no_separate)
+    line = {
+        "metric": METRIC, "value": r["tflops_effective"], "unit": "TFLOP/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 storage, " + args.math,
+        "data": "synthetic (seeded uniform[-1,1); shapes of the batched workload)",
+        "config": {"workload": f"batching: {len(items)} contractions, orders 2-5, extents "
+                               "log-uniform [8,192], 1-3 contracted, random storage orders",
+                   "l2": "flushed between steps (256 MiB write, outside timing)",
+                   "launch": "one CUDA graph of tc_contract_batched",
+                   "routes": "threshold rule" if args.no_autotune else
+                   "autotuned per size bucket (paper_1307_2100_gb300/autotune.py)"},
+        "roofline": r["roofline"], "batch": r, "clocks": r["clocks"],
+        "gpu_launches": args.steps * r["gpu_launches_per_step"],
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -748,6 +1176,10 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="default workload: only the FP64 three-class step, without the "
+                    "precision, config-1, batching and selector parts")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the in-run peak probes")
     ap.add_argument("--workload", default="class3_fp64",
                     choices=["class3_fp64", "precision", "batching", "skewed"])
     ap.add_argument("--items", type=int, default=512, help="batching: number of contractions")

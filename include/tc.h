@@ -378,6 +378,27 @@ tc_status tc_contract_dot_noalloc(tc_plan_t plan, double alpha, const void* A, c
  * following tc_device_status() reports TC_ERR_TIMEOUT.  No fault, no hang. */
 tc_status tc_selftest_wait_timeout(int64_t timeout_ns, void* stream);
 
+/* ---- Peak-rate probes (measurement support) -------------------------------
+ * The roofline of each kernel is its arithmetic's peak rate on this GPU,
+ * measured in the same process: one launch of a probe kernel that keeps
+ * every SM busy with one kind of arithmetic and no memory traffic (operands
+ * in registers, or a zero tile in shared memory that each MMA re-reads).
+ * tc_peak_probe enqueues it on `stream` (a cudaStream_t) and stores the
+ * floating-point operations the launch performs in *flops (host pointer);
+ * time the launch with events on the same stream.  `iters` >= 1 sets the
+ * length: per thread (CUDA-core kinds) or per issuing thread (tensor-core
+ * kinds).  The paper has no counterpart (its peaks are the CPUs' nominal
+ * figures, Sec. 4). */
+typedef enum {
+  TC_PEAK_DFMA = 0,       /* FP64 fused multiply-add, CUDA cores */
+  TC_PEAK_DMMA = 1,       /* FP64 mma.sync m8n8k4 */
+  TC_PEAK_FFMA = 2,       /* FP32 fused multiply-add, CUDA cores */
+  TC_PEAK_BF16 = 3,       /* tcgen05.mma kind::f16 BF16, 128 x 128 x 16 */
+  TC_PEAK_BF16_N256 = 4,  /* tcgen05.mma kind::f16 BF16, 128 x 256 x 16 */
+  TC_PEAK_FP8 = 5         /* tcgen05.mma kind::mxf8f6f4 E4M3 block-scaled, 128 x 128 x 32 */
+} tc_peak_kind;
+tc_status tc_peak_probe(int32_t kind, int64_t iters, double* flops, void* stream);
+
 /* Static description of a status code. */
 const char* tc_status_string(tc_status s);
 

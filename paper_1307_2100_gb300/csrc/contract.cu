@@ -81,10 +81,10 @@ extern "C" tc_status tc_selftest_wait_timeout(int64_t timeout_ns, void* stream) 
 
 extern "C" tc_status tc_device_status(void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  int h0 = 0, h1 = 0, h2 = 0, h3 = 0;
+  int h0 = 0, h1 = 0, h2 = 0, h3 = 0, h4 = 0;
   if (read_clear_status(&h0, s) != cudaSuccess || tc_gemm_read_status(&h1, s) != TC_OK ||
       tc_fp8_read_status(&h2, s) != TC_OK || tc_pk_read_status(&h3, s) != TC_OK ||
-      cudaStreamSynchronize(s) != cudaSuccess)
+      peak_read_status(&h4, s) != TC_OK || cudaStreamSynchronize(s) != cudaSuccess)
     return TC_ERR_CUDA;
-  return (h0 || h1 || h2 || h3) ? TC_ERR_TIMEOUT : TC_OK;
+  return (h0 || h1 || h2 || h3 || h4) ? TC_ERR_TIMEOUT : TC_OK;
 }

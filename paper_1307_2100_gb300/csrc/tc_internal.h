@@ -184,6 +184,8 @@ tc_status launch_gemm_tc_packed_batch(const PkBatch& b, const void* const* A,
                                       const void* const* B, void* const* C, const double* alpha,
                                       const double* beta, int math, void* stream);
 int num_tiles_simt(tc_dtype dt);
+// Read and clear the peak probes' timeout flag into *h (k_peak.cu).
+tc_status peak_read_status(int* h, void* stream);
 int num_tiles_gemv();
 
 }  // namespace tc

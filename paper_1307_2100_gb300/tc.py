@@ -138,6 +138,9 @@ def _load():
     lib.tc_device_status.argtypes = [P]
     lib.tc_status_string.restype = ctypes.c_char_p
     lib.tc_status_string.argtypes = [ctypes.c_int]
+    lib.tc_peak_probe.restype = ctypes.c_int
+    lib.tc_peak_probe.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                                  P]
     return lib
 
 
@@ -277,6 +280,18 @@ def tc_contract_dot_noalloc(plan: int, alpha: float, A: int, B: int, beta: float
                                      ctypes.c_void_p(stream))
     if st != TC_OK:
         raise TcError(st, "tc_contract_dot_noalloc")
+
+
+PEAK = {"dfma": 0, "dmma": 1, "ffma": 2, "bf16": 3, "bf16_n256": 4, "fp8": 5}
+
+
+def tc_peak_probe(kind: int, iters: int, stream: int = 0) -> float:
+    """Enqueue one peak-rate probe launch; returns the FLOPs it performs."""
+    f = ctypes.c_double(0.0)
+    st = lib.tc_peak_probe(int(kind), int(iters), ctypes.byref(f), ctypes.c_void_p(stream))
+    if st != TC_OK:
+        raise TcError(st, "tc_peak_probe")
+    return f.value
 
 
 def tc_batch_set_route(tc_min_mn: int) -> None:

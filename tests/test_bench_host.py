@@ -31,3 +31,20 @@ def test_committed_summary_parses():
     assert len(line) == 1
     w = line[0].split()
     assert float(w[1]) > 0 and w[2] == "sources_sha256:" and len(w[3]) == 16
+
+
+def test_cpu_recipe_baseline_matches_the_oracle():
+    """The paper's method on the host (recipe slicing over host BLAS), which
+    bench.py times as a CPU baseline, computes the contraction: random
+    descriptors of every class and storage order, against the oracle."""
+    import numpy as np
+
+    import oracle
+    import tcsynth as ts
+    rng = np.random.Generator(np.random.PCG64(20131))
+    probs = [ts.slice_gemm_48(), ts.direct_gemm_64(n=7), ts.fused_permute_48(n=6)]
+    probs += [ts.random_problem(rng, max_order=4, max_ext=5) for _ in range(60)]
+    for p in probs:
+        ref = oracle.contract_problem(p)
+        got = bench.recipe_cpu(p, 2)
+        assert oracle.rel_fro(got, ref) <= 1e-13, p.name
