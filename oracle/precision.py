@@ -1,9 +1,10 @@
 """Reduced-precision forms of the contraction -- TEST INFRASTRUCTURE ONLY.
 
 Parity: pinned (tests/test_oracle_precision.py: exact reconstruction of FP32
-values by three BF16 terms, hand-made rounding ties, the E4M3 value table; the
-FP8 form exact on small integers, equivariant under power-of-two scaling, and
-its GEMM view reproducing the FP64 contraction).
+values by three BF16 terms, hand-made rounding ties, the E4M3 and binary16
+value tables; binary16 rounding against numpy's float16 cast; the FP8 and
+FP16 forms exact on small integers, the FP8 form equivariant under
+power-of-two scaling and its GEMM view reproducing the FP64 contraction).
 
 The paper computes in FP64 only (Sec. 4); these forms come from the project's
 goal of running the bulk of the multiply on BF16/FP8 tensor cores:
@@ -23,6 +24,10 @@ goal of running the bulk of the multiply on BF16/FP8 tensor cores:
   integer with amax / 2^e <= 448, but not below -126 (so that 2^e and 2^-e
   are normal FP32 numbers; blocks whose largest value is below about 2^-135
   then round to zero).
+* FP16 (IEEE binary16: 1 sign, 5 exponent bits with bias 15, 10 significand
+  bits, subnormals, infinities): round to nearest, ties to the even code;
+  magnitudes from 65520 (the midpoint above 65504) on overflow to infinity.
+  The FP16 form rounds both operands to binary16 and contracts exactly.
 """
 from __future__ import annotations
 
@@ -225,3 +230,55 @@ def contract_fp8(p, block: int = 128):
         val = val + p.beta * out[idx]
     out[idx] = val
     return out
+
+
+# ------------------------------------------------------- FP16 (IEEE binary16)
+
+def f16_values() -> Tuple[np.ndarray, np.ndarray]:
+    """All non-negative finite binary16 values with their 15-bit codes, in
+    increasing order: 1 sign bit, 5 exponent bits with bias 15, 10 significand
+    bits; exponent field 0 holds the subnormals (m / 2^10) 2^-14, field 31 the
+    infinities and NaNs (left out)."""
+    codes = np.arange(0x7C00, dtype=np.int64)
+    e = codes >> 10
+    m = (codes & 0x3FF).astype(np.float64)
+    vals = np.where(e == 0, m / 1024.0 * 2.0 ** (-14),
+                    (1.0 + m / 1024.0) * np.exp2((e - 15).astype(np.float64)))
+    return vals, codes
+
+
+_F16_VALS, _F16_CODES = f16_values()
+F16_MAX = 65504.0
+F16_OVERFLOW = 65520.0   # midpoint of 65504 and 2^16: from here on, infinity
+
+
+def f16_rne(x) -> np.ndarray:
+    """Round to the nearest binary16 value, ties to the even code (IEEE 754
+    round-to-nearest-even).  Magnitudes of F16_OVERFLOW or more become
+    infinite: that midpoint is a tie between the odd code of 65504 and the
+    even code of infinity.  Returns float64 values."""
+    x = np.asarray(x, dtype=np.float64)
+    ax = np.abs(x)
+    vals, codes = _F16_VALS, _F16_CODES
+    hi_i = np.clip(np.searchsorted(vals, ax, side="left"), 0, len(vals) - 1)
+    lo_i = np.clip(hi_i - 1, 0, len(vals) - 1)
+    lo, hi = vals[lo_i], vals[hi_i]
+    d_lo, d_hi = ax - lo, hi - ax
+    even_hi = (codes[hi_i] & 1) == 0
+    take_hi = (d_hi < d_lo) | ((d_hi == d_lo) & even_hi)
+    q = np.where(take_hi, hi, lo)
+    q = np.where(ax == vals[hi_i], vals[hi_i], q)
+    q = np.where(ax > F16_MAX, np.where(ax >= F16_OVERFLOW, np.inf, F16_MAX), q)
+    return np.copysign(q, x)
+
+
+def contract_f16(p, nthreads: int = 0) -> np.ndarray:
+    """FP64 result of the FP16 form: every element of A and B rounded to
+    binary16 (f16_rne), the rounded operands contracted exactly-rounded in
+    FP64.  The tensor cores then only add accumulation error: a product of
+    two binary16 values (11-bit significands) is exact in FP32."""
+    import copy
+    A, B = copy.copy(p.A), copy.copy(p.B)
+    A.data = f16_rne(p.A.data)
+    B.data = f16_rne(p.B.data)
+    return contract(A, B, p.C, p.alpha, p.beta, nthreads=nthreads)

@@ -143,3 +143,59 @@ def test_fp8_form_scale_equivariance_and_error():
     np.testing.assert_array_equal(op.contract_fp8(q), base * 2.0 ** 5)
     err = oracle.rel_fro(base, oracle.contract_problem(p))
     assert 1e-4 < err < 6e-2
+
+
+# ----------------------------------------------------------- binary16 (FP16)
+
+def test_f16_value_table_edges():
+    vals, codes = op.f16_values()
+    assert len(vals) == 0x7C00 == 31744            # every finite non-negative code
+    assert np.all(np.diff(vals) > 0)                # codes increase with value
+    assert vals[1] == 2.0 ** -24                    # smallest subnormal
+    assert vals[0x3FF] == 1023 / 1024 * 2.0 ** -14  # largest subnormal
+    assert vals[0x400] == 2.0 ** -14                # smallest normal
+    assert vals[0x3C00] == 1.0 and vals[0x3C01] == 1.0 + 2.0 ** -10
+    assert vals[-1] == op.F16_MAX == 65504.0
+
+
+def test_f16_rounding_ties_to_even_hand_values():
+    cases = {
+        1.0 + 2.0 ** -11: 1.0,                    # halfway: 1.0 has the even code
+        1.0 + 3 * 2.0 ** -11: 1.0 + 2.0 ** -9,    # halfway: up to the even code
+        1.0 + 2.0 ** -11 + 2.0 ** -20: 1.0 + 2.0 ** -10,
+        2049.0: 2048.0,                           # spacing 2 above 2048
+        2051.0: 2052.0,
+        2.0 ** -25: 0.0,                          # halfway between 0 and 2^-24
+        3 * 2.0 ** -25: 2.0 ** -23,               # halfway between codes 1 and 2
+        65519.0: 65504.0,                         # below the overflow midpoint
+        65520.0: np.inf,                          # the midpoint itself: to infinity
+        -70000.0: -np.inf,
+        -(1.0 + 3 * 2.0 ** -11): -(1.0 + 2.0 ** -9),
+    }
+    for x, want in cases.items():
+        assert float(op.f16_rne([x])[0]) == want, x
+
+
+def test_f16_rounding_matches_numpy_float16_conversion():
+    """numpy's float32 -> float16 cast is IEEE round-to-nearest-even: an
+    independent implementation to compare with, across the subnormal range,
+    the normal range and overflow."""
+    rng = np.random.default_rng(16)
+    x = f32(rng.standard_normal(100000) * np.exp2(rng.uniform(-30, 17.5, 100000)))
+    ref = x.astype(np.float16).astype(np.float64)
+    got = op.f16_rne(x)
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_f16_form_exact_on_f16_integers_and_rounds_otherwise():
+    # integers up to 2048 are binary16 values: the form equals the contraction
+    p = ts.problem("int", "iajb", "jcid", "abcd", dict(i=5, a=7, j=3, b=2, c=6, d=3), 61,
+                   dist="int", lo=-8, hi=8, dtype=np.float32)
+    np.testing.assert_array_equal(op.contract_f16(p), oracle.contract_problem(p))
+    # general FP32 data: the result is the contraction of the rounded values,
+    # within the binary16 input rounding (2^-11 relative per operand) of it
+    q = ts.problem("u", "aik", "kib", "ab", dict(a=9, i=11, k=7, b=8), 62, dtype=np.float32)
+    exact = oracle.contract_problem(q)
+    form = op.contract_f16(q)
+    err = oracle.rel_fro(form, exact)
+    assert 0 < err <= 2 * 2.0 ** -11
