@@ -50,15 +50,26 @@ typedef enum {
   TC_ERR_NO_SELECTOR = 9      /* no selector weights loaded */
 } tc_status;
 
-/* Storage type of A, B and C. */
-typedef enum { TC_F64 = 0, TC_F32 = 1 } tc_dtype;
+/* Storage type of A, B and C (all three share it; Sec. 2.1 stores tensors of
+ * one type).  The paper computes in FP64 (Sec. 4); the other types are for
+ * callers whose tensors are FP32, BF16 or FP16 already.  Math forms each
+ * storage type takes (else TC_ERR_UNSUPPORTED):
+ *   TC_F64   TC_MATH_FP64
+ *   TC_F32   TC_MATH_FP32, _BF16, _BF16X3, _BF16X6, _FP8, _FP16
+ *   TC_BF16  TC_MATH_FP32 (CUDA cores), TC_MATH_BF16 (tensor cores)
+ *   TC_F16   TC_MATH_FP32 (CUDA cores), TC_MATH_FP16 (tensor cores)
+ * BF16 and FP16 elements are read exactly; results are computed in FP32 (FP64
+ * where a kernel sums in FP64) and rounded to the storage type to nearest,
+ * ties to even, when C is written. */
+typedef enum { TC_F64 = 0, TC_F32 = 1, TC_BF16 = 2, TC_F16 = 3 } tc_dtype;
 
 /* Arithmetic of the contraction.
  *   TC_MATH_FP64     FP64 inputs, FP64 multiply-add (the plain path; the paper
  *                    computes in double precision, Sec. 4).
- *   TC_MATH_FP32     FP32 inputs, FP32 multiply-add on the CUDA cores.
- *   TC_MATH_BF16     FP32 inputs rounded to BF16, tensor-core products,
- *                    FP32 accumulation.
+ *   TC_MATH_FP32     FP32 multiply-add on the CUDA cores (FP32, BF16 or FP16
+ *                    storage).
+ *   TC_MATH_BF16     FP32 inputs rounded to BF16 (BF16 inputs as stored),
+ *                    tensor-core products, FP32 accumulation.
  *   TC_MATH_BF16X3   FP32 inputs split into 2 BF16 terms; the 3 products of
  *                    order <= 1 on tensor cores.
  *   TC_MATH_BF16X6   FP32 inputs split into 3 BF16 terms; the 6 products of
@@ -74,14 +85,21 @@ typedef enum { TC_F64 = 0, TC_F32 = 1 } tc_dtype;
  *                    added in FP32.  Class 3 contractions only, mapping AUTO,
  *                    RECIPE or FUSED_GEMM (one GEMM).  The paper has no
  *                    reduced-precision form; this one trades accuracy (about
- *                    2^-5 relative per product) for tensor-core throughput. */
+ *                    2^-5 relative per product) for tensor-core throughput.
+ *   TC_MATH_FP16     FP32 inputs rounded to IEEE binary16 (to nearest, ties to
+ *                    even; magnitudes from 65520 on become infinite), FP16
+ *                    inputs as stored; tensor-core products (exact in FP32),
+ *                    FP32 accumulation.  Class 3 GEMM mappings run one GEMM on
+ *                    packed operands (no batch labels); Class 1 and 2 and the
+ *                    GER mapping compute on the CUDA cores in FP32. */
 typedef enum {
   TC_MATH_FP64 = 0,
   TC_MATH_FP32 = 1,
   TC_MATH_BF16 = 2,
   TC_MATH_BF16X3 = 3,
   TC_MATH_BF16X6 = 4,
-  TC_MATH_FP8 = 5
+  TC_MATH_FP8 = 5,
+  TC_MATH_FP16 = 6
 } tc_math;
 
 /* How the contraction is mapped onto kernels.

@@ -7,12 +7,13 @@ class Contraction:
     """A planned contraction C = alpha * A.B + beta * C over labelled indices.
 
     Each operand is (labels, extents, strides-or-None); strides count
-    elements.  `math` is one of tc.MATH, `mapping` one of tc.MAPPING.
+    elements.  `dtype` is one of tc.DTYPE ("f64", "f32", "bf16", "f16"),
+    `math` one of tc.MATH, `mapping` one of tc.MAPPING.
     """
 
     def __init__(self, A, B, C, dtype: str = "f64", math: str = "fp64",
                  mapping: str = "auto", tile: int = -1):
-        self.dtype = tc.TC_F64 if dtype == "f64" else tc.TC_F32
+        self.dtype = tc.DTYPE[dtype]
         self.handle = tc.tc_plan(A, B, C, self.dtype, tc.MATH[math], tc.MAPPING[mapping], tile)
         self.info = tc.tc_plan_get_info(self.handle)
         self._ws = None

@@ -48,7 +48,7 @@ extern "C" tc_status tc_contract(tc_plan_t plan, double alpha, const void* A, co
   switch (P->kernel) {
     case K_GEMM_SIMT: return launch_gemm_simt(a, P->dtype, P->tile, stream);
     case K_GEMM_TC:
-      return P->tile == kTilePacked ? launch_gemm_tc_packed(a, P->math, ws, stream)
+      return P->tile == kTilePacked ? launch_gemm_tc_packed(a, P->math, P->dtype, ws, stream)
                                     : launch_gemm_tc(a, P->math, stream);
     case K_GEMM_FP8: return launch_gemm_fp8(a, ws, stream);
     case K_GEMV: return launch_gemv(a, P->dtype, P->tile, stream);

@@ -13,12 +13,14 @@
 #include <cstdio>
 
 #include "groups.cuh"
+#include "storage.cuh"
 #include "tc_internal.h"
 
 namespace tc {
 
 // ---------------------------------------------------------------------------
-// GEMM on the CUDA cores.  CTA tile TM x TN, K step TK, each thread a 4x4
+// GEMM on the CUDA cores (storage type S, arithmetic in T: FP64 for FP64
+// data, FP32 otherwise).  CTA tile TM x TN, K step TK, each thread a 4x4
 // register tile (rows ty + i*TM/4, columns tx + j*TN/4).  Tiles are taken in
 // the order (m-tile fastest, n-tile, batch).  The next K block is fetched into
 // registers while the current one is multiplied.  With p.ksplit > 1 (FP64,
@@ -26,9 +28,10 @@ namespace tc {
 // slowest; each writes its partial tile [TM][TN] to the workspace and
 // k_simt_reduce adds the ranges in order.
 // ---------------------------------------------------------------------------
-template <typename T, int TM, int TN, int TK>
+template <typename S, int TM, int TN, int TK>
 __global__ void __launch_bounds__((TM / 4) * (TN / 4))
     k_gemm_simt(const __grid_constant__ GemmArgs p) {
+  using T = typename Cmp<S>::T;
   constexpr int NT = (TM / 4) * (TN / 4);
   constexpr int LA = (TM * TK + NT - 1) / NT;  // A elements loaded per thread
   constexpr int LB = (TN * TK + NT - 1) / NT;
@@ -37,9 +40,9 @@ __global__ void __launch_bounds__((TM / 4) * (TN / 4))
   __shared__ int64_t offAm[TM], offCm[TM], offBn[TN], offCn[TN];
   __shared__ int64_t offAk[2][TK], offBk[2][TK];
 
-  const T* __restrict__ A = static_cast<const T*>(p.A);
-  const T* __restrict__ B = static_cast<const T*>(p.B);
-  T* __restrict__ C = static_cast<T*>(p.C);
+  const S* __restrict__ A = static_cast<const S*>(p.A);
+  const S* __restrict__ B = static_cast<const S*>(p.B);
+  S* __restrict__ C = static_cast<S*>(p.C);
   const int tid = threadIdx.x;
   const int tx = tid % (TN / 4), ty = tid / (TN / 4);
   const uint32_t M = (uint32_t)p.M, N = (uint32_t)p.N, K = (uint32_t)p.K;
@@ -99,7 +102,7 @@ __global__ void __launch_bounds__((TM / 4) * (TN / 4))
         T v = T(0);
         if (kl < TK && ml < TM) {
           int64_t om = offAm[ml], ok = offAk[buf][kl];
-          if (om >= 0 && ok >= 0) v = A[bA + om + ok];
+          if (om >= 0 && ok >= 0) v = ld_c(A[bA + om + ok]);
         }
         ra[r] = v;
       }
@@ -112,7 +115,7 @@ __global__ void __launch_bounds__((TM / 4) * (TN / 4))
         T v = T(0);
         if (kl < TK && nl < TN) {
           int64_t on = offBn[nl], ok = offBk[buf][kl];
-          if (on >= 0 && ok >= 0) v = B[bB + on + ok];
+          if (on >= 0 && ok >= 0) v = ld_c(B[bB + on + ok]);
         }
         rb[r] = v;
       }
@@ -182,10 +185,10 @@ __global__ void __launch_bounds__((TM / 4) * (TN / 4))
       for (int j = 0; j < 4; ++j) {
         const int nl = tx + j * (TN / 4);
         if (offBn[nl] < 0) continue;
-        T* dst = C + bC + offCm[ml] + offCn[nl];
+        S* dst = C + bC + offCm[ml] + offCn[nl];
         T v = alpha * acc[i][j];
-        if (p.beta != 0.0) v = fma(beta, *dst, v);
-        *dst = v;
+        if (p.beta != 0.0) v = fma(beta, ld_c(*dst), v);
+        *dst = st_any<S>(v);
       }
     }
   }
@@ -200,14 +203,15 @@ static int grid_for(uint64_t total) {
 }
 
 // Split-K: C = alpha * (sum of the K ranges' partial tiles, in order) + beta * C.
-template <typename T, int TM, int TN>
+template <typename S, int TM, int TN>
 __global__ void __launch_bounds__(256) k_simt_reduce(const __grid_constant__ GemmArgs p) {
+  using T = typename Cmp<S>::T;
   const uint32_t M = (uint32_t)p.M, N = (uint32_t)p.N;
   const uint32_t tiles_m = (M + TM - 1) / TM, tiles_n = (N + TN - 1) / TN;
   const uint64_t total = (uint64_t)tiles_m * tiles_n * (uint64_t)p.nbatch;
   const uint64_t elems = total * (uint64_t)(TM * TN);
   const T* part = static_cast<const T*>(p.ws);
-  T* C = static_cast<T*>(p.C);
+  S* C = static_cast<S*>(p.C);
   for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < elems;
        e += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t tile = e / (TM * TN);
@@ -221,10 +225,10 @@ __global__ void __launch_bounds__(256) k_simt_reduce(const __grid_constant__ Gem
     for (int sp = 0; sp < p.ksplit; ++sp) t += part[(uint64_t)sp * elems + e];
     int64_t bA, bB, bC;
     goff3(p.gb, b, bA, bB, bC);
-    T* dst = C + bC + goff(p.gm, 2, m) + goff(p.gn, 2, n);
+    S* dst = C + bC + goff(p.gm, 2, m) + goff(p.gn, 2, n);
     T v = (T)p.alpha * t;
-    if (p.beta != 0.0) v = fma((T)p.beta, *dst, v);
-    *dst = v;
+    if (p.beta != 0.0) v = fma((T)p.beta, ld_c(*dst), v);
+    *dst = st_any<S>(v);
   }
 }
 
@@ -247,7 +251,7 @@ size_t simt_part_bytes(const GemmArgs& a, tc_dtype dt, int tile) {
   return (size_t)sp * (size_t)tiles * 64 * 64 * sizeof(double);
 }
 
-template <typename T>
+template <typename T>  // the storage type
 static tc_status gemm_simt_t(const GemmArgs& a, int tile, cudaStream_t s) {
   const SimtTile t = kSimtTiles[tile];
   const uint64_t total = (uint64_t)((a.M + t.tm - 1) / t.tm) * (uint64_t)((a.N + t.tn - 1) / t.tn) *
@@ -274,7 +278,13 @@ static tc_status gemm_simt_t(const GemmArgs& a, int tile, cudaStream_t s) {
 
 tc_status launch_gemm_simt(const GemmArgs& a, tc_dtype dt, int tile, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  return dt == TC_F64 ? gemm_simt_t<double>(a, tile, s) : gemm_simt_t<float>(a, tile, s);
+  switch (dt) {
+    case TC_F64: return gemm_simt_t<double>(a, tile, s);
+    case TC_F32: return gemm_simt_t<float>(a, tile, s);
+    case TC_BF16: return gemm_simt_t<__nv_bfloat16>(a, tile, s);
+    case TC_F16: return gemm_simt_t<__half>(a, tile, s);
+    default: return TC_ERR_UNSUPPORTED;
+  }
 }
 
 // Accumulators of the GEMV/DOT kernels.  FP64 data accumulate in FP64; FP32
@@ -312,12 +322,13 @@ struct Acc<float> {
 constexpr int kGemvThreads = 256;
 constexpr int kGemvChunk = 512;
 
-template <typename T>
+template <typename S>
 __global__ void __launch_bounds__(kGemvThreads) k_gemv_m(const __grid_constant__ GemmArgs p) {
+  using T = typename Cmp<S>::T;
   __shared__ int64_t oX[kGemvChunk], oY[kGemvChunk];
-  const T* __restrict__ X = static_cast<const T*>(p.A);
-  const T* __restrict__ Y = static_cast<const T*>(p.B);
-  T* __restrict__ Cp = static_cast<T*>(p.C);
+  const S* __restrict__ X = static_cast<const S*>(p.A);
+  const S* __restrict__ Y = static_cast<const S*>(p.B);
+  S* __restrict__ Cp = static_cast<S*>(p.C);
   const uint32_t M = (uint32_t)p.M, N = (uint32_t)p.N, K = (uint32_t)p.K;
   const uint64_t mblocks = (M + kGemvThreads - 1) / kGemvThreads;
   const uint64_t total = mblocks * (uint64_t)N * (uint64_t)p.nbatch;
@@ -329,8 +340,8 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv_m(const __grid_constant__
     goff3(p.gb, b, bX, bY, bC);
     goff2(p.gn, 1, 2, n, oYn, oCn);
     if (m < M) goff2(p.gm, 0, 2, m, oXm, oCm);
-    const T* xrow = X + bX + oXm;
-    const T* yv = Y + bY + oYn;
+    const S* xrow = X + bX + oXm;
+    const S* yv = Y + bY + oYn;
     Acc<T> acc;
     for (uint32_t k0 = 0; k0 < K; k0 += kGemvChunk) {
       __syncthreads();
@@ -348,20 +359,20 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv_m(const __grid_constant__
         for (; i + 8 <= kn; i += 8) {
           T xv[8], yy[8];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) xv[u] = xrow[oX[i + u]];
+          for (int u = 0; u < 8; ++u) xv[u] = ld_c(xrow[oX[i + u]]);
 #pragma unroll
-          for (int u = 0; u < 8; ++u) yy[u] = yv[oY[i + u]];
+          for (int u = 0; u < 8; ++u) yy[u] = ld_c(yv[oY[i + u]]);
 #pragma unroll
           for (int u = 0; u < 8; ++u) acc.add(xv[u], yy[u]);
         }
-        for (; i < kn; ++i) acc.add(xrow[oX[i]], yv[oY[i]]);
+        for (; i < kn; ++i) acc.add(ld_c(xrow[oX[i]]), ld_c(yv[oY[i]]));
       }
     }
     if (m < M) {
-      T* dst = Cp + bC + oCm + oCn;
+      S* dst = Cp + bC + oCm + oCn;
       double v = p.alpha * acc.value();
-      if (p.beta != 0.0) v += p.beta * (double)*dst;
-      *dst = (T)v;
+      if (p.beta != 0.0) v += p.beta * (double)ld_c(*dst);
+      *dst = st_c<S>(v);
     }
   }
 }
@@ -375,11 +386,12 @@ __device__ __forceinline__ T warp_sum(T v) {
 
 // One warp per output (m, n, b); lanes stride over k.  Used by the transposed
 // GEMV and by the DOT mapping (Sec. 3.2.1: one inner product per output).
-template <typename T>
+template <typename S>
 __global__ void __launch_bounds__(256) k_dot_rows(const __grid_constant__ GemmArgs p) {
-  const T* __restrict__ X = static_cast<const T*>(p.A);
-  const T* __restrict__ Y = static_cast<const T*>(p.B);
-  T* __restrict__ Cp = static_cast<T*>(p.C);
+  using T = typename Cmp<S>::T;
+  const S* __restrict__ X = static_cast<const S*>(p.A);
+  const S* __restrict__ Y = static_cast<const S*>(p.B);
+  S* __restrict__ Cp = static_cast<S*>(p.C);
   const uint32_t M = (uint32_t)p.M, N = (uint32_t)p.N, K = (uint32_t)p.K;
   const uint64_t total = (uint64_t)M * N * (uint64_t)p.nbatch;
   const int lane = threadIdx.x & 31;
@@ -393,20 +405,20 @@ __global__ void __launch_bounds__(256) k_dot_rows(const __grid_constant__ GemmAr
     goff3(p.gb, b, bX, bY, bC);
     goff2(p.gm, 0, 2, m, oXm, oCm);
     goff2(p.gn, 1, 2, n, oYn, oCn);
-    const T* xr = X + bX + oXm;
-    const T* yr = Y + bY + oYn;
+    const S* xr = X + bX + oXm;
+    const S* yr = Y + bY + oYn;
     Acc<T> acc;
     for (uint32_t k = lane; k < K; k += 32) {
       int64_t ox, oy;
       goff2(p.gk, 0, 1, k, ox, oy);
-      acc.add(xr[ox], yr[oy]);
+      acc.add(ld_c(xr[ox]), ld_c(yr[oy]));
     }
     const double tot = warp_sum(acc.value());
     if (lane == 0) {
-      T* dst = Cp + bC + oCm + oCn;
+      S* dst = Cp + bC + oCm + oCn;
       double v = p.alpha * tot;
-      if (p.beta != 0.0) v += p.beta * (double)*dst;
-      *dst = (T)v;
+      if (p.beta != 0.0) v += p.beta * (double)ld_c(*dst);
+      *dst = st_c<S>(v);
     }
   }
 }
@@ -430,7 +442,13 @@ static tc_status gemv_t(const GemmArgs& a, cudaStream_t s) {
 
 tc_status launch_gemv(const GemmArgs& a, tc_dtype dt, int, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  return dt == TC_F64 ? gemv_t<double>(a, s) : gemv_t<float>(a, s);
+  switch (dt) {
+    case TC_F64: return gemv_t<double>(a, s);
+    case TC_F32: return gemv_t<float>(a, s);
+    case TC_BF16: return gemv_t<__nv_bfloat16>(a, s);
+    case TC_F16: return gemv_t<__half>(a, s);
+    default: return TC_ERR_UNSUPPORTED;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -445,14 +463,15 @@ tc_status launch_gemv(const GemmArgs& a, tc_dtype dt, int, void* stream) {
 // ---------------------------------------------------------------------------
 constexpr int kGerThreads = 256, kGerN = 32;
 
-template <typename T, int KB>
+template <typename S, int KB>
 __global__ void __launch_bounds__(kGerThreads) k_ger(const __grid_constant__ GemmArgs p,
                                                      uint32_t tiles_per_chunk) {
+  using T = typename Cmp<S>::T;
   __shared__ T sB[KB][kGerN];
   __shared__ int64_t sC[kGerN];
-  const T* __restrict__ X = static_cast<const T*>(p.A);
-  const T* __restrict__ Y = static_cast<const T*>(p.B);
-  T* __restrict__ Cp = static_cast<T*>(p.C);
+  const S* __restrict__ X = static_cast<const S*>(p.A);
+  const S* __restrict__ Y = static_cast<const S*>(p.B);
+  S* __restrict__ Cp = static_cast<S*>(p.C);
   const uint32_t M = (uint32_t)p.M, N = (uint32_t)p.N, K = (uint32_t)p.K;
   const uint32_t mb = (M + kGerThreads - 1) / kGerThreads, nt = (N + kGerN - 1) / kGerN;
   const uint32_t nchunks = (nt + tiles_per_chunk - 1) / tiles_per_chunk;
@@ -472,8 +491,8 @@ __global__ void __launch_bounds__(kGerThreads) k_ger(const __grid_constant__ Gem
     T a[KB];
 #pragma unroll
     for (int k = 0; k < KB; ++k)
-      a[k] = (row_ok && k < (int)K) ? X[bX + oxm + goff(p.gk, 0, (uint32_t)k)] : T(0);
-    T* Crow = Cp + bC + ocm;
+      a[k] = (row_ok && k < (int)K) ? ld_c(X[bX + oxm + goff(p.gk, 0, (uint32_t)k)]) : T(0);
+    S* Crow = Cp + bC + ocm;
     const uint32_t t_end = min(nt, (ch + 1) * tiles_per_chunk);
     for (uint32_t bn = ch * tiles_per_chunk; bn < t_end; ++bn) {
       __syncthreads();  // the previous columns' shared values are no longer read
@@ -481,7 +500,7 @@ __global__ void __launch_bounds__(kGerThreads) k_ger(const __grid_constant__ Gem
         const int k = i / kGerN, j = i % kGerN;
         const uint32_t n = bn * kGerN + j;
         T v = T(0);
-        if (k < (int)K && n < N) v = Y[bY + goff(p.gn, 1, n) + goff(p.gk, 1, (uint32_t)k)];
+        if (k < (int)K && n < N) v = ld_c(Y[bY + goff(p.gn, 1, n) + goff(p.gk, 1, (uint32_t)k)]);
         sB[k][j] = v;
       }
       if (tid < kGerN) {
@@ -500,14 +519,14 @@ __global__ void __launch_bounds__(kGerThreads) k_ger(const __grid_constant__ Gem
         // alpha and beta in the storage precision (FP64 is the slow pipe on
         // this GPU: FP32 outputs stay in FP32)
         T v = alpha * acc;
-        if (beta != T(0)) v = fma(beta, Crow[cj], v);
-        Crow[cj] = v;
+        if (beta != T(0)) v = fma(beta, ld_c(Crow[cj]), v);
+        Crow[cj] = st_any<S>(v);
       }
     }
   }
 }
 
-template <typename T>
+template <typename T>  // the storage type
 static tc_status ger_t(const GemmArgs& a, cudaStream_t s) {
   const uint64_t mb = (uint64_t)((a.M + kGerThreads - 1) / kGerThreads) * (uint64_t)a.nbatch;
   const uint64_t nt = (uint64_t)((a.N + kGerN - 1) / kGerN);
@@ -527,7 +546,13 @@ static tc_status ger_t(const GemmArgs& a, cudaStream_t s) {
 
 tc_status launch_ger(const GemmArgs& a, tc_dtype dt, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  return dt == TC_F64 ? ger_t<double>(a, s) : ger_t<float>(a, s);
+  switch (dt) {
+    case TC_F64: return ger_t<double>(a, s);
+    case TC_F32: return ger_t<float>(a, s);
+    case TC_BF16: return ger_t<__nv_bfloat16>(a, s);
+    case TC_F16: return ger_t<__half>(a, s);
+    default: return TC_ERR_UNSUPPORTED;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -543,19 +568,19 @@ int dot_partials(const GemmArgs&, int) { return kDotBlocks; }
 
 // `part` receives one FP64 partial per CTA: the plan's workspace, or the
 // library's built-in scratch array for tc_contract_dot_noalloc.
-template <typename T>
+template <typename S>
 __global__ void __launch_bounds__(kDotThreads) k_dot_partial(const __grid_constant__ GemmArgs p,
                                                              double* __restrict__ part) {
   __shared__ double red[kDotThreads / 32];
-  const T* __restrict__ X = static_cast<const T*>(p.A);
-  const T* __restrict__ Y = static_cast<const T*>(p.B);
+  const S* __restrict__ X = static_cast<const S*>(p.A);
+  const S* __restrict__ Y = static_cast<const S*>(p.B);
   const uint32_t K = (uint32_t)p.K;
   double acc = 0.0;
   const uint32_t stride = gridDim.x * kDotThreads;
   for (uint32_t k = blockIdx.x * kDotThreads + threadIdx.x; k < K; k += stride) {
     int64_t ox, oy;
     goff2(p.gk, 0, 1, k, ox, oy);
-    acc = fma((double)X[ox], (double)Y[oy], acc);
+    acc = fma((double)ld_c(X[ox]), (double)ld_c(Y[oy]), acc);
   }
   acc = warp_sum(acc);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -567,7 +592,7 @@ __global__ void __launch_bounds__(kDotThreads) k_dot_partial(const __grid_consta
   }
 }
 
-template <typename T>
+template <typename S>
 __global__ void k_dot_final(const __grid_constant__ GemmArgs p, const double* __restrict__ part,
                             int nparts) {
   __shared__ double red[32];
@@ -579,10 +604,10 @@ __global__ void k_dot_final(const __grid_constant__ GemmArgs p, const double* __
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    T* dst = static_cast<T*>(p.C);
+    S* dst = static_cast<S*>(p.C);
     double v = p.alpha * t;
-    if (p.beta != 0.0) v += p.beta * (double)*dst;
-    *dst = (T)v;
+    if (p.beta != 0.0) v += p.beta * (double)ld_c(*dst);
+    *dst = st_c<S>(v);
   }
 }
 
@@ -594,8 +619,13 @@ static void dot_scalar_t(const GemmArgs& a, double* part, cudaStream_t s) {
 
 tc_status launch_dot_scalar(const GemmArgs& a, tc_dtype dt, double* part, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (dt == TC_F64) dot_scalar_t<double>(a, part, s);
-  else dot_scalar_t<float>(a, part, s);
+  switch (dt) {
+    case TC_F64: dot_scalar_t<double>(a, part, s); break;
+    case TC_F32: dot_scalar_t<float>(a, part, s); break;
+    case TC_BF16: dot_scalar_t<__nv_bfloat16>(a, part, s); break;
+    case TC_F16: dot_scalar_t<__half>(a, part, s); break;
+    default: return TC_ERR_UNSUPPORTED;
+  }
   return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
 }
 
@@ -614,7 +644,13 @@ static tc_status dot_t(const GemmArgs& a, cudaStream_t s) {
 
 tc_status launch_dot(const GemmArgs& a, tc_dtype dt, int, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  return dt == TC_F64 ? dot_t<double>(a, s) : dot_t<float>(a, s);
+  switch (dt) {
+    case TC_F64: return dot_t<double>(a, s);
+    case TC_F32: return dot_t<float>(a, s);
+    case TC_BF16: return dot_t<__nv_bfloat16>(a, s);
+    case TC_F16: return dot_t<__half>(a, s);
+    default: return TC_ERR_UNSUPPORTED;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -709,18 +745,31 @@ static tc_status perm_t(const PermArgs& a, cudaStream_t s) {
 
 tc_status launch_perm(const PermArgs& a, tc_dtype dt, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  return dt == TC_F64 ? perm_t<double>(a, s) : perm_t<float>(a, s);
+  switch (elem_size(dt)) {  // a permute moves bits: one instantiation per size
+    case 8: return perm_t<uint64_t>(a, s);
+    case 4: return perm_t<uint32_t>(a, s);
+    case 2: return perm_t<uint16_t>(a, s);
+    default: return TC_ERR_UNSUPPORTED;
+  }
 }
 
 // C = beta * C over C's own labels (empty contraction or alpha == 0).
 // Wide: C has 2^31 or more elements (index split in 64 bits, as in k_perm_direct).
-template <typename T, bool Wide>
-__global__ void k_scale(const __grid_constant__ Group g, T* C, double beta, uint64_t total) {
+template <typename S, bool Wide>
+__global__ void k_scale(const __grid_constant__ Group g, S* C, double beta, uint64_t total) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < total; q += stride) {
-    T* dst = C + (Wide ? goff_wide(g, 2, q) : goff(g, 2, (uint32_t)q));
-    *dst = beta == 0.0 ? T(0) : (T)(beta * (double)*dst);
+    S* dst = C + (Wide ? goff_wide(g, 2, q) : goff(g, 2, (uint32_t)q));
+    *dst = st_c<S>(beta == 0.0 ? 0.0 : beta * (double)ld_c(*dst));
   }
+}
+
+template <typename S>
+static void scale_t(const Group& gc, void* C, double beta, int64_t total, bool wide, int grid,
+                    cudaStream_t s) {
+  S* c = static_cast<S*>(C);
+  if (wide) k_scale<S, true><<<grid, 256, 0, s>>>(gc, c, beta, (uint64_t)total);
+  else k_scale<S, false><<<grid, 256, 0, s>>>(gc, c, beta, (uint64_t)total);
 }
 
 tc_status launch_scale(const Group& gc, void* C, double beta, tc_dtype dt, int64_t total,
@@ -729,14 +778,12 @@ tc_status launch_scale(const Group& gc, void* C, double beta, tc_dtype dt, int64
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int grid = grid_for(std::min<uint64_t>((total + 255) / 256, 152 * 32));
   const bool wide = total >= ((int64_t)1 << 31);
-  if (dt == TC_F64) {
-    double* c = static_cast<double*>(C);
-    if (wide) k_scale<double, true><<<grid, 256, 0, s>>>(gc, c, beta, (uint64_t)total);
-    else k_scale<double, false><<<grid, 256, 0, s>>>(gc, c, beta, (uint64_t)total);
-  } else {
-    float* c = static_cast<float*>(C);
-    if (wide) k_scale<float, true><<<grid, 256, 0, s>>>(gc, c, beta, (uint64_t)total);
-    else k_scale<float, false><<<grid, 256, 0, s>>>(gc, c, beta, (uint64_t)total);
+  switch (dt) {
+    case TC_F64: scale_t<double>(gc, C, beta, total, wide, grid, s); break;
+    case TC_F32: scale_t<float>(gc, C, beta, total, wide, grid, s); break;
+    case TC_BF16: scale_t<__nv_bfloat16>(gc, C, beta, total, wide, grid, s); break;
+    case TC_F16: scale_t<__half>(gc, C, beta, total, wide, grid, s); break;
+    default: return TC_ERR_UNSUPPORTED;
   }
   return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
 }

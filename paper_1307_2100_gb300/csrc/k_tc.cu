@@ -593,7 +593,7 @@ int num_tiles_tc() { return 4; }
 int tc_chunk_kb(int math, int tile) {
   if (tile == 1) return 2;
   if (tile == 2) return 32;
-  return math == TC_MATH_BF16 ? (1 << 30) : 8;
+  return (math == TC_MATH_BF16 || math == TC_MATH_FP16) ? (1 << 30) : 8;
 }
 
 tc_status tc_gemm_read_status(int* h, void* stream) {

@@ -34,6 +34,7 @@
 
 #include "groups.cuh"
 #include "sm100.cuh"
+#include "storage.cuh"
 #include "tc_internal.h"
 
 namespace tc {
@@ -75,7 +76,7 @@ struct Cfg {
 struct PackArgs {
   Group gr[2];          // rows of operand o (the M and N groups); strides in slot o
   Group gk;             // K group; operand o's strides in slot o
-  const float* in[2];
+  const void* in[2];    // elements of the pack kernel's input type
   uint8_t* q[2];        // [tile][block][term][TERM]
   int64_t rows[2];
   int64_t K;
@@ -102,11 +103,12 @@ __device__ __forceinline__ PackSmem pack_smem(float4* raw) {
 }
 
 // Rows [128 t, 128 t + 128) x K [128 kc, 128 kc + 128) of operand o (strides
-// in slot o of gr and gk), split into NT BF16 terms and stored in the
-// operand's packed blocks Q (block kb of tile t at (t * nkb + kb) * NT * TERM).
-template <int NT>
+// in slot o of gr and gk), split into NT BF16 terms (F16T: rounded to one
+// FP16 term) and stored in the operand's packed blocks Q (block kb of tile t
+// at (t * nkb + kb) * NT * TERM).  In: FP32, BF16 or FP16 elements.
+template <int NT, typename In, bool F16T>
 __device__ __forceinline__ void pack_body(const Group& gr, const Group& gk, int o,
-                                          const float* __restrict__ X, int64_t rows, int64_t K,
+                                          const In* __restrict__ X, int64_t rows, int64_t K,
                                           int t, int kc, int nkb, bool rows_fast,
                                           uint8_t* __restrict__ Qop, const PackSmem& sm) {
   float* tile = sm.tile;
@@ -131,7 +133,7 @@ __device__ __forceinline__ void pack_body(const Group& gr, const Group& gk, int 
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
       const int64_t ko = koff[k0 + kRowThreads * j];
-      v[j] = (ro >= 0 && ko >= 0) ? __ldg(X + ro + ko) : 0.0f;
+      v[j] = (ro >= 0 && ko >= 0) ? ld_c(__ldg(X + ro + ko)) : 0.0f;
     }
 #pragma unroll
     for (int j = 0; j < NJ; ++j) tile[r * kLd + k0 + kRowThreads * j] = v[j];
@@ -142,7 +144,7 @@ __device__ __forceinline__ void pack_body(const Group& gr, const Group& gk, int 
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
       const int64_t ro = roff[r0 + kRowThreads * j];
-      v[j] = (ro >= 0 && ko >= 0) ? __ldg(X + ro + ko) : 0.0f;
+      v[j] = (ro >= 0 && ko >= 0) ? ld_c(__ldg(X + ro + ko)) : 0.0f;
     }
 #pragma unroll
     for (int j = 0; j < NJ; ++j) tile[(r0 + kRowThreads * j) * kLd + k] = v[j];
@@ -162,12 +164,13 @@ __device__ __forceinline__ void pack_body(const Group& gr, const Group& gk, int 
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = src[i];
     uint8_t* dst = Q + (size_t)blk * NT * TERM + (size_t)w * 16;
+    static_assert(!F16T || NT == 1, "the FP16 form has one term");
 #pragma unroll
     for (int tt = 0; tt < NT; ++tt) {
       uint32_t wd[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        wd[i] = pack_bf16x2(v[2 * i], v[2 * i + 1]);
+        wd[i] = F16T ? pack_f16x2(v[2 * i], v[2 * i + 1]) : pack_bf16x2(v[2 * i], v[2 * i + 1]);
         if (tt + 1 < NT) {  // exact FP32 residuals
           v[2 * i] = __fsub_rn(v[2 * i], bf16_lo(wd[i]));
           v[2 * i + 1] = __fsub_rn(v[2 * i + 1], bf16_hi(wd[i]));
@@ -178,15 +181,15 @@ __device__ __forceinline__ void pack_body(const Group& gr, const Group& gk, int 
   }
 }
 
-template <int NT>
+template <int NT, typename In, bool F16T>
 __global__ void __launch_bounds__(kPackThreads) k_bf16_pack(const __grid_constant__ PackArgs P) {
   extern __shared__ float4 pk_smem[];
   int64_t bid = blockIdx.x;
   const int o = bid < P.nblocks0 ? 0 : 1;
   if (o) bid -= P.nblocks0;
   const int t = (int)(bid / P.npk), kc = (int)(bid % P.npk);
-  pack_body<NT>(P.gr[o], P.gk, o, P.in[o], P.rows[o], P.K, t, kc, P.nkb, P.rows_fast[o] != 0,
-                P.q[o], pack_smem(pk_smem));
+  pack_body<NT, In, F16T>(P.gr[o], P.gk, o, static_cast<const In*>(P.in[o]), P.rows[o], P.K, t,
+                          kc, P.nkb, P.rows_fast[o] != 0, P.q[o], pack_smem(pk_smem));
 }
 
 // Batched pack pass: one CTA per entry (item, operand, row tile, 128-K
@@ -218,7 +221,7 @@ __global__ void __launch_bounds__(kPackThreads) k_bf16_pack_batch(
   const float* X = static_cast<const float*>(
       wk.o == 0 ? (sw ? Bp[wk.item] : Ap[wk.item]) : (sw ? Ap[wk.item] : Bp[wk.item]));
   const PkItem& it = pk[wk.item];
-  pack_body<NT>(sg[0], sg[1], wk.o, X, wk.o ? a.N : a.M, a.K, wk.t, wk.kc, it.nkb,
+  pack_body<NT, float, false>(sg[0], sg[1], wk.o, X, wk.o ? a.N : a.M, a.K, wk.t, wk.kc, it.nkb,
                 (wk.o ? a.b_contig : a.a_contig) == CONTIG_MN,
                 const_cast<uint8_t*>(wk.o ? it.qb : it.qa), pack_smem(pk_smem));
 }
@@ -227,8 +230,10 @@ __global__ void __launch_bounds__(kPackThreads) k_bf16_pack_batch(
 // The launch holds it in kernel parameters, a batch in device memory.
 struct PkLaunch {
   PkItem single;             // items == nullptr: tiles 0 .. nwork - 1 of this GEMM
-  float* C;
+  void* C;                   // elements of out_type
   float alpha, beta;
+  uint32_t idesc;            // MMA instruction descriptor (BF16 or FP16 operands)
+  int32_t out_type;          // C's storage: 0 FP32, 1 BF16, 2 FP16 (batches: FP32)
   const PkItem* items;       // batch: per-item GEMMs and (item, tile, K range) work entries
   const int32_t* work;
   void* const* Cp;
@@ -244,7 +249,7 @@ struct Job {
   int tm, tn;
   int64_t tile;
   int split, k0, k1;  // K blocks [k0, k1)
-  float* C;
+  void* C;
   float alpha, beta;
 };
 
@@ -257,7 +262,7 @@ __device__ __forceinline__ Job job_of(const PkLaunch& L, int64_t w) {
     tile = L.work[3 * w + 1];
     j.split = L.work[3 * w + 2];
     j.it = L.items + item;
-    j.C = static_cast<float*>(L.Cp[item]);
+    j.C = L.Cp[item];
     j.alpha = (float)L.alpha_p[item];
     j.beta = (float)L.beta_p[item];
   } else {
@@ -293,12 +298,33 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volati
   return __all_sync(0xffffffffu, ok);
 }
 
-// s + e == a + b exactly (Knuth's TwoSum).
+// C[off] = x (+ beta * C[off]) in C's storage type, rounded to nearest even.
+__device__ __forceinline__ void store_out(void* C, int64_t off, int out_type, float x,
+                                          float beta) {
+  if (out_type == 0) {
+    float* d = static_cast<float*>(C) + off;
+    if (beta != 0.0f) x = fmaf(beta, *d, x);
+    *d = x;
+  } else if (out_type == 1) {
+    __nv_bfloat16* d = static_cast<__nv_bfloat16*>(C) + off;
+    if (beta != 0.0f) x = fmaf(beta, __bfloat162float(*d), x);
+    *d = __float2bfloat16_rn(x);
+  } else {
+    __half* d = static_cast<__half*>(C) + off;
+    if (beta != 0.0f) x = fmaf(beta, __half2float(*d), x);
+    *d = __float2half_rn(x);
+  }
+}
+
+// s + e == a + b exactly (Knuth's TwoSum).  When s is infinite or NaN (an
+// FP16 operand overflowed, or the data hold infinities) e is 0, so that the
+// compensation keeps the infinity instead of turning it into a NaN.
 __device__ __forceinline__ float two_sum(float a, float b, float& e) {
   const float s = __fadd_rn(a, b);
   const float bp = __fsub_rn(s, a);
   const float ap = __fsub_rn(s, bp);
   e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+  if (!(fabsf(s) <= 3.402823466e38f)) e = 0.0f;
   return s;
 }
 
@@ -372,7 +398,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_pk(const __grid_constant__
   } else if (warp == 1) {
     if (lane == 0) {
       // ----------------------------------------------------------- MMA issue
-      constexpr uint32_t idesc = idesc_bf16(TILE, TILE);
+      const uint32_t idesc = L.idesc;
       constexpr uint32_t LBO = (TILE / 8) * 128;
       uint32_t g = 0, gc = 0;
       bool ok = true;
@@ -536,14 +562,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_pk(const __grid_constant__
           tc_fence_before();
           mbar_arrive(&acce[buf]);  // main, correction and high word are free
           if (!partial && rc >= 0) {
-            float* Cr = J.C + rc;
+            const int ot = L.out_type;
 #pragma unroll
             for (int i = 0; i < 64; ++i) {
               const int64_t ci = cc[h * 64 + i];
               if (ci < 0) continue;
-              float x = J.alpha * lo[i];
-              if (J.beta != 0.0f) x = fmaf(J.beta, Cr[ci], x);
-              Cr[ci] = x;
+              store_out(J.C, rc + ci, ot, J.alpha * lo[i], J.beta);
             }
           }
         }
@@ -585,10 +609,8 @@ __global__ void __launch_bounds__(256) k_pk_reduce(const __grid_constant__ PkLau
       const float2 v = P.part[(size_t)sp * total + e];
       t += (double)v.x + (double)v.y;
     }
-    float* dst = L.C + goff(P.gm, 2, (uint32_t)m) + goff(P.gn, 2, (uint32_t)n);
-    float x = (float)(L.alpha * t);
-    if (L.beta != 0.0f) x = fmaf(L.beta, *dst, x);
-    *dst = x;
+    store_out(L.C, goff(P.gm, 2, (uint32_t)m) + goff(P.gn, 2, (uint32_t)n), L.out_type,
+              (float)(L.alpha * t), L.beta);
   }
 }
 
@@ -651,9 +673,7 @@ int set_smem() {
             cudaSuccess)
       return -1;
     if (optin < (int)Cfg<NT>::BYTES) return -2;
-    if (cudaFuncSetAttribute(k_bf16_pack<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kPackSmem) != cudaSuccess ||
-        cudaFuncSetAttribute(k_bf16_pack_batch<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_bf16_pack_batch<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kPackSmem) != cudaSuccess ||
         cudaFuncSetAttribute(k_gemm_pk<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Cfg<NT>::BYTES) != cudaSuccess)
@@ -663,10 +683,24 @@ int set_smem() {
   return bytes;
 }
 
-template <int NT>
-tc_status launch(const GemmArgs& a, const PkLayout& L, void* ws, cudaStream_t s) {
+// Shared memory of one pack kernel instantiation (set once).
+template <int NT, typename In, bool F16T>
+bool set_pack_smem() {
+  static bool done = false;
+  if (!done)
+    done = cudaFuncSetAttribute(k_bf16_pack<NT, In, F16T>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kPackSmem) == cudaSuccess;
+  return done;
+}
+
+// One GEMM: operands of type In packed into NT BF16 terms (F16T: one FP16
+// term), C stored as out_type (0 FP32, 1 BF16, 2 FP16).
+template <int NT, typename In, bool F16T>
+tc_status launch(const GemmArgs& a, const PkLayout& L, void* ws, cudaStream_t s, int out_type) {
   const int sm = set_smem<NT>();
   if (sm == -2) return TC_ERR_UNSUPPORTED;
+  if (!set_pack_smem<NT, In, F16T>()) return TC_ERR_CUDA;
   const int sms = num_sms();
   if (sm < 0 || sms <= 0) return TC_ERR_CUDA;
   uint8_t* w = static_cast<uint8_t*>(ws);
@@ -675,8 +709,8 @@ tc_status launch(const GemmArgs& a, const PkLayout& L, void* ws, cudaStream_t s)
   pa.gr[0] = a.gm;
   pa.gr[1] = a.gn;
   pa.gk = a.gk;
-  pa.in[0] = static_cast<const float*>(a.A);
-  pa.in[1] = static_cast<const float*>(a.B);
+  pa.in[0] = a.A;
+  pa.in[1] = a.B;
   pa.q[0] = w + L.off_qa;
   pa.q[1] = w + L.off_qb;
   pa.rows[0] = a.M;
@@ -691,7 +725,7 @@ tc_status launch(const GemmArgs& a, const PkLayout& L, void* ws, cudaStream_t s)
   pa.rows_fast[1] = a.b_contig == CONTIG_MN;
   const int64_t nblocks = (L.tiles_m + L.tiles_n) * pa.npk;
   if (nblocks > 0x7fffffffll) return TC_ERR_UNSUPPORTED;
-  k_bf16_pack<NT><<<(unsigned)nblocks, kPackThreads, kPackSmem, s>>>(pa);
+  k_bf16_pack<NT, In, F16T><<<(unsigned)nblocks, kPackThreads, kPackSmem, s>>>(pa);
   if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;
 
   PkLaunch g;
@@ -711,9 +745,11 @@ tc_status launch(const GemmArgs& a, const PkLayout& L, void* ws, cudaStream_t s)
   it.raster = a.raster;
   it.ksplit = pk_ksplit(a);
   it.part = it.ksplit > 1 ? reinterpret_cast<float2*>(w + L.bytes) : nullptr;
-  g.C = static_cast<float*>(a.C);
+  g.C = a.C;
   g.alpha = (float)a.alpha;
   g.beta = (float)a.beta;
+  g.idesc = F16T ? idesc_f16(TILE, TILE) : idesc_bf16(TILE, TILE);
+  g.out_type = out_type;
   g.nwork = L.tiles_m * L.tiles_n * it.ksplit;
   const int grid = (int)std::min<int64_t>(g.nwork, sms);
   k_gemm_pk<NT><<<grid, kThreads, sm, s>>>(g);
@@ -744,6 +780,8 @@ tc_status launch_batch(const PkBatch& b, const void* const* A, const void* const
   PkLaunch g;
   std::memset(&g, 0, sizeof(g));
   g.items = b.pk;
+  g.idesc = idesc_bf16(TILE, TILE);
+  g.out_type = 0;
   g.work = b.work;
   g.Cp = C;
   g.alpha_p = alpha;
@@ -765,7 +803,8 @@ tc_status launch_batch(const PkBatch& b, const void* const* A, const void* const
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static int terms_of(int math) {
-  return math == TC_MATH_BF16 ? 1 : math == TC_MATH_BF16X3 ? 2 : math == TC_MATH_BF16X6 ? 3 : 0;
+  return (math == TC_MATH_BF16 || math == TC_MATH_FP16) ? 1
+         : math == TC_MATH_BF16X3 ? 2 : math == TC_MATH_BF16X6 ? 3 : 0;
 }
 
 // Split-K: tiles fewer than the SMs share out their K blocks, so that about
@@ -799,18 +838,24 @@ PkLayout pk_layout(const GemmArgs& a, int math) {
 }
 
 int pk_stage_blocks(int math) {
-  return math == TC_MATH_BF16 ? pk::Cfg<1>::BPS
+  return (math == TC_MATH_BF16 || math == TC_MATH_FP16) ? pk::Cfg<1>::BPS
          : math == TC_MATH_BF16X3 ? pk::Cfg<2>::BPS : pk::Cfg<3>::BPS;
 }
 
-tc_status launch_gemm_tc_packed(const GemmArgs& a, int math, void* ws, void* stream) {
+tc_status launch_gemm_tc_packed(const GemmArgs& a, int math, tc_dtype dt, void* ws,
+                                void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const PkLayout L = pk_layout(a, math);
   if (L.tiles_m == 0 || L.tiles_n == 0 || L.nkb == 0) return TC_OK;
+  if (dt == TC_BF16 && math == TC_MATH_BF16)
+    return pk::launch<1, __nv_bfloat16, false>(a, L, ws, s, 1);
+  if (dt == TC_F16 && math == TC_MATH_FP16) return pk::launch<1, __half, true>(a, L, ws, s, 2);
+  if (dt != TC_F32) return TC_ERR_UNSUPPORTED;
   switch (math) {
-    case TC_MATH_BF16: return pk::launch<1>(a, L, ws, s);
-    case TC_MATH_BF16X3: return pk::launch<2>(a, L, ws, s);
-    case TC_MATH_BF16X6: return pk::launch<3>(a, L, ws, s);
+    case TC_MATH_BF16: return pk::launch<1, float, false>(a, L, ws, s, 0);
+    case TC_MATH_FP16: return pk::launch<1, float, true>(a, L, ws, s, 0);
+    case TC_MATH_BF16X3: return pk::launch<2, float, false>(a, L, ws, s, 0);
+    case TC_MATH_BF16X6: return pk::launch<3, float, false>(a, L, ws, s, 0);
     default: return TC_ERR_UNSUPPORTED;
   }
 }

@@ -26,7 +26,7 @@
 
 namespace tc {
 
-size_t elem_size(tc_dtype dt) { return dt == TC_F64 ? 8 : 4; }
+size_t elem_size(tc_dtype dt) { return dt == TC_F64 ? 8 : dt == TC_F32 ? 4 : 2; }
 
 namespace {
 
@@ -298,10 +298,14 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
                              tc_mapping mapping, int32_t tile) {
   if (!out) return TC_ERR_INVALID_ARG;
   *out = nullptr;
-  if (dtype != TC_F64 && dtype != TC_F32) return TC_ERR_INVALID_ARG;
-  if (math < TC_MATH_FP64 || math > TC_MATH_FP8) return TC_ERR_INVALID_ARG;
+  if (dtype < TC_F64 || dtype > TC_F16) return TC_ERR_INVALID_ARG;
+  if (math < TC_MATH_FP64 || math > TC_MATH_FP16) return TC_ERR_INVALID_ARG;
   if (mapping < TC_MAP_AUTO || mapping > TC_MAP_GER) return TC_ERR_INVALID_ARG;
   if ((math == TC_MATH_FP64) != (dtype == TC_F64)) return TC_ERR_UNSUPPORTED;
+  // BF16 / FP16 storage: FP32 arithmetic on the CUDA cores, or the tensor
+  // cores' products of the stored values (exact)
+  if (dtype == TC_BF16 && math != TC_MATH_FP32 && math != TC_MATH_BF16) return TC_ERR_UNSUPPORTED;
+  if (dtype == TC_F16 && math != TC_MATH_FP32 && math != TC_MATH_FP16) return TC_ERR_UNSUPPORTED;
 
   Tens A, B, C;
   tc_status st;
@@ -506,7 +510,8 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   }
   const bool gemm_family =
       map == TC_MAP_SLICE_GEMM || map == TC_MAP_FUSED_GEMM || map == TC_MAP_COPY_GEMM;
-  const bool tensor_core = math == TC_MATH_BF16 || math == TC_MATH_BF16X3 || math == TC_MATH_BF16X6;
+  const bool tensor_core = math == TC_MATH_BF16 || math == TC_MATH_BF16X3 ||
+                           math == TC_MATH_BF16X6 || math == TC_MATH_FP16;
   int32_t kernel = fp8 ? K_GEMM_FP8
                  : gemm_family ? (tensor_core ? K_GEMM_TC : K_GEMM_SIMT)
                  : map == TC_MAP_GER ? K_GER
@@ -643,7 +648,8 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   // packed size (beyond 64 MB of slack)
   bool packed_ok = false;
   if (kernel == K_GEMM_TC && Bt == 1) {
-    const double terms = math == TC_MATH_BF16 ? 1 : math == TC_MATH_BF16X3 ? 2 : 3;
+    const double terms = (math == TC_MATH_BF16 || math == TC_MATH_FP16) ? 1
+                         : math == TC_MATH_BF16X3 ? 2 : 3;
     const double dense = 2.0 * terms * 2.0 * (double)(M + N) * (double)Kt;
     packed_ok = (double)pk_layout(g, math).bytes <= 2.0 * dense + 64.0 * (1 << 20);
   }
@@ -652,6 +658,21 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   if (kernel == K_GEMM_TC && tile == kTilePacked && Bt > 1) {
     delete P;  // packed operands: one GEMM, no batch group
     return TC_ERR_UNSUPPORTED;
+  }
+  // BF16 / FP16 storage and the FP16 form run only on packed operands (the
+  // gathering kernel stages 4-byte elements); a batch of GEMMs of BF16 or FP16
+  // data computes on the CUDA cores instead, in FP32 (the products of the
+  // stored values are exact there too)
+  if (kernel == K_GEMM_TC && (dtype == TC_BF16 || dtype == TC_F16 || math == TC_MATH_FP16)) {
+    if (Bt > 1 && dtype != TC_F32 && tile < 0) {
+      kernel = K_GEMM_SIMT;
+      P->kernel = kernel;
+    } else if (Bt > 1 || (tile >= 0 && tile != kTilePacked)) {
+      delete P;
+      return TC_ERR_UNSUPPORTED;
+    } else {
+      tile = kTilePacked;
+    }
   }
   if (tile < 0) {
     if (kernel == K_GEMM_SIMT) {

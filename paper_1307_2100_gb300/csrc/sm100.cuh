@@ -202,6 +202,14 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
          | ((uint32_t)(M >> 4) << 24);  // M / 16
 }
 
+// Instruction descriptor of kind::f16 with FP16 A and B (format 0), FP32 D,
+// both K-major.  A and B always share the format.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4)                      // D format: F32
+         | ((uint32_t)(N >> 3) << 17)   // N / 8
+         | ((uint32_t)(M >> 4) << 24);  // M / 16
+}
+
 // Instruction descriptor of kind::mxf8f6f4: E4M3 A and B, FP32 D, K-major,
 // UE8M0 scales (bit 23), scale bytes sfa_id / sfb_id of the scale cells.
 __host__ __device__ constexpr uint32_t idesc_mx_e4m3(int M, int N, uint32_t sfa_id,
@@ -225,6 +233,13 @@ __device__ __forceinline__ uint16_t pack_e4m3x2(float lo, float hi) {
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   uint32_t r;
   asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+// Two FP32 values rounded to nearest-even IEEE binary16, packed (lo in bits
+// 0..15); magnitudes beyond the binary16 range become infinite.
+__device__ __forceinline__ uint32_t pack_f16x2(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
   return r;
 }
 __device__ __forceinline__ float bf16_lo(uint32_t p) { return __uint_as_float(p << 16); }

@@ -154,7 +154,8 @@ size_t pk_part_bytes(const GemmArgs& a);
 // 32-K blocks per ring stage of the packed GEMM for a math form: every
 // accumulation chunk must hold a multiple of them.
 int pk_stage_blocks(int math);
-tc_status launch_gemm_tc_packed(const GemmArgs& a, int math, void* ws, void* stream);
+tc_status launch_gemm_tc_packed(const GemmArgs& a, int math, tc_dtype dt, void* ws,
+                                void* stream);
 tc_status tc_pk_read_status(int* h, void* stream);
 
 // One GEMM on packed operands as the packed kernel sees it.

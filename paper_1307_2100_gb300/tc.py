@@ -19,8 +19,9 @@ TC_ERR_TIMEOUT = 8
 STATUS = {0: "TC_OK", 1: "TC_ERR_INVALID_ARG", 2: "TC_ERR_LABEL", 3: "TC_ERR_EXTENT_MISMATCH",
           4: "TC_ERR_STRIDE", 5: "TC_ERR_UNSUPPORTED", 6: "TC_ERR_WORKSPACE", 7: "TC_ERR_CUDA",
           8: "TC_ERR_TIMEOUT", 9: "TC_ERR_NO_SELECTOR"}
-TC_F64, TC_F32 = 0, 1
-MATH = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16x3": 3, "bf16x6": 4, "fp8": 5}
+TC_F64, TC_F32, TC_BF16, TC_F16 = 0, 1, 2, 3
+DTYPE = {"f64": TC_F64, "f32": TC_F32, "bf16": TC_BF16, "f16": TC_F16}
+MATH = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16x3": 3, "bf16x6": 4, "fp8": 5, "fp16": 6}
 MAPPING = {"auto": 0, "recipe": 1, "slice_gemm": 2, "fused_gemm": 3, "copy_gemm": 4, "gemv": 5,
            "dot": 6, "ger": 7}
 MAPPING_NAME = {v: k for k, v in MAPPING.items()}

@@ -383,3 +383,18 @@ def test_autotune_passes_repeat_while_flips_are_kept(monkeypatch):
     assert kept == [(0, autotune.bucket_of(8, 8, 4)), (1, autotune.bucket_of(32, 32, 4))]
     routes1, rep1 = autotune.tune_routes(list(range(6)), None, None, passes=1)
     assert list(routes1) == [1, 1, 1, 1, 0, 0] and rep1["tuned_ms"] == 8.0
+
+
+def test_storage_and_math_combinations_planned_or_refused():
+    """BF16 storage takes the FP32 and BF16 forms, FP16 storage the FP32 and
+    FP16 forms; FP32 storage also takes the FP16 form."""
+    p = ts.fused_permute_48(n=5)
+    d = ((p.A.labels, p.A.extents, p.A.strides), (p.B.labels, p.B.extents, p.B.strides),
+         (p.C.labels, p.C.extents, p.C.strides))
+    ok = {("bf16", "fp32"), ("bf16", "bf16"), ("f16", "fp32"), ("f16", "fp16")}
+    for dt in ("bf16", "f16"):
+        for m in tc.MATH:
+            st = tc.tc_plan_status(*d, tc.DTYPE[dt], tc.MATH[m])
+            assert (st == 0) == ((dt, m) in ok), (dt, m, st)
+    assert tc.tc_plan_status(*d, tc.TC_F32, tc.MATH["fp16"]) == 0
+    assert tc.tc_plan_status(*d, 4, tc.MATH["fp32"]) == 1          # no such storage type
