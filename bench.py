@@ -70,7 +70,7 @@ def workloads(alloc=None, only=None, kind="class3_fp64", precision_v=128, gemv_b
     return [makers[n]() for n in names]
 
 
-NPROD = {"bf16": 1, "bf16x3": 3, "bf16x6": 6}
+NPROD = {"bf16": 1, "bf16x3": 3, "bf16x6": 6, "fp16": 1}
 FP8_PER_BF16 = 2.0   # nominal dense tensor rate of E4M3 over BF16 (4.5 / 2.25 PFLOP/s)
 
 
@@ -1188,7 +1188,7 @@ def main(argv=None):
     ap.add_argument("--no-autotune", action="store_true",
                     help="batching: the threshold route rule instead of tuned routes")
     ap.add_argument("--math", default="bf16x6",
-                    choices=["bf16", "bf16x3", "bf16x6", "fp8", "fp32"],
+                    choices=["bf16", "bf16x3", "bf16x6", "fp8", "fp16", "fp32"],
                     help="math of the precision workload")
     ap.add_argument("--tile", type=int, default=-1)
     ap.add_argument("--mapping", default="auto",

@@ -16,7 +16,8 @@ extern "C" tc_status tc_contract(tc_plan_t plan, double alpha, const void* A, co
   if (P->empty_out) return TC_OK;
   if (!C) return TC_ERR_INVALID_ARG;
   if (P->workspace > 0 && (!workspace || ws_bytes < P->workspace)) return TC_ERR_WORKSPACE;
-  const bool packed = P->kernel == K_GEMM_FP8 || (P->kernel == K_GEMM_TC && P->tile == kTilePacked);
+  const bool packed = P->kernel == K_GEMM_FP8 ||
+                      (P->kernel == K_GEMM_TC && (P->tile == kTilePacked || P->tile == kTilePackedWide));
   if (packed && (reinterpret_cast<uintptr_t>(workspace) & 15) != 0)
     return TC_ERR_INVALID_ARG;  // the packed operands are moved by 16-byte bulk copies
   if (P->empty_k || alpha == 0.0)
@@ -48,7 +49,8 @@ extern "C" tc_status tc_contract(tc_plan_t plan, double alpha, const void* A, co
   switch (P->kernel) {
     case K_GEMM_SIMT: return launch_gemm_simt(a, P->dtype, P->tile, stream);
     case K_GEMM_TC:
-      return P->tile == kTilePacked ? launch_gemm_tc_packed(a, P->math, P->dtype, ws, stream)
+      return (P->tile == kTilePacked || P->tile == kTilePackedWide)
+                 ? launch_gemm_tc_packed(a, P->math, P->dtype, P->tile, ws, stream)
                                     : launch_gemm_tc(a, P->math, stream);
     case K_GEMM_FP8: return launch_gemm_fp8(a, ws, stream);
     case K_GEMV: return launch_gemv(a, P->dtype, P->tile, stream);

@@ -316,6 +316,23 @@ __device__ __forceinline__ void store_out(void* C, int64_t off, int out_type, fl
   }
 }
 
+// C[rc + ch[i]] = alpha * v[i] (+ beta * C[...]) for NC columns of one row,
+// in C's storage type O (columns with ch[i] < 0 lie outside C).  One unrolled
+// loop per storage type keeps the epilogue's registers for its sums.
+template <typename O, int NC>
+__device__ __forceinline__ void store_row(void* C, int64_t rc, const int64_t* ch,
+                                          const float (&v)[NC], float alpha, float beta) {
+  O* Cr = static_cast<O*>(C) + rc;
+#pragma unroll
+  for (int i = 0; i < NC; ++i) {
+    const int64_t ci = ch[i];
+    if (ci < 0) continue;
+    float x = alpha * v[i];
+    if (beta != 0.0f) x = fmaf(beta, ld_c(Cr[ci]), x);
+    Cr[ci] = st_cf<O>(x);
+  }
+}
+
 // s + e == a + b exactly (Knuth's TwoSum).  When s is infinite or NaN (an
 // FP16 operand overflowed, or the data hold infinities) e is 0, so that the
 // compensation keeps the infinity instead of turning it into a NaN.
@@ -562,17 +579,311 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_pk(const __grid_constant__
           tc_fence_before();
           mbar_arrive(&acce[buf]);  // main, correction and high word are free
           if (!partial && rc >= 0) {
-            const int ot = L.out_type;
-#pragma unroll
-            for (int i = 0; i < 64; ++i) {
-              const int64_t ci = cc[h * 64 + i];
-              if (ci < 0) continue;
-              store_out(J.C, rc + ci, ot, J.alpha * lo[i], J.beta);
-            }
+            const int64_t* ch = cc + h * 64;
+            if (L.out_type == 0) store_row<float, 64>(J.C, rc, ch, lo, J.alpha, J.beta);
+            else if (L.out_type == 1)
+              store_row<__nv_bfloat16, 64>(J.C, rc, ch, lo, J.alpha, J.beta);
+            else store_row<__half, 64>(J.C, rc, ch, lo, J.alpha, J.beta);
           }
         }
       }
       named_bar_sync(1, kEpiThreads);  // this tile's columns read; the next tile's written
+    }
+  }
+
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Wide tiles (tile configuration 4): 128 x 256 outputs per CTA for the BF16,
+// FP16 and BF16x3 forms.  Every product of a K chunk goes into one FP32
+// accumulator of 256 columns; tensor memory double-buffers it ([0,256) and
+// [256,512), each two N = 128 halves), and sixteen epilogue warps (64
+// columns each) add every drained chunk into a running FP32 sum held in
+// registers.  The tensor cores' FP32 accumulation is not round-to-nearest, so
+// its error grows with the number of blocks it adds: BF16x3 drains every
+// 256 K (as the 128 x 128 kernel does), BF16 and FP16 (whose error is their
+// operands' rounding) once per tile.  A 32-K block moves NT x 8 KB of A for
+// NT x 16 KB of B: 27 % fewer operand bytes per multiply-add than the
+// 128 x 128 tile; each stage's A block is shared by the two N = 128 MMAs of
+// the two halves.  BF16x6 keeps the 128 x 128 kernel: its FP32-class sum
+// needs the separate correction accumulator, for which there is no room.
+// ---------------------------------------------------------------------------
+constexpr int TILE_W = 256;
+
+template <int NT>
+struct CfgW {
+  static constexpr int BPS = NT == 1 ? 2 : 1;                 // 32-K blocks per stage
+  static constexpr uint32_t OPA = NT * TERM;                   // one block of A (NT terms)
+  static constexpr uint32_t OPH = NT * TERM;                   // one block of one B half
+  static constexpr uint32_t STAGE = BPS * (OPA + 2 * OPH);     // A blocks, B half 0, B half 1
+  static constexpr int S = (int)(kRing / STAGE);               // 4 stages of 48 KB
+  static constexpr uint32_t OFF_COLC = S * STAGE;              // int64 colC[2][256]
+  static constexpr uint32_t OFF_BAR = OFF_COLC + 2 * TILE_W * 8;
+  static constexpr uint32_t NBAR = 2 * S + 4 + 1;
+  static constexpr uint32_t OFF_MISC = OFF_BAR + NBAR * 8;
+  static constexpr uint32_t BYTES = OFF_MISC + 16 + 1024;
+};
+
+// Work entry w of a wide launch: split-major over the 128 x 256 tiles of one
+// GEMM (n-pairs fastest when raster, else m-tiles fastest).
+struct JobW {
+  int tm, tn0;       // 128-row tile of A; first of the two 128-column tiles of B
+  bool h1;           // the second half exists (tn0 + 1 < tiles_n)
+  int split, k0, k1;
+};
+
+__device__ __forceinline__ JobW jobw_of(const PkItem& P, int64_t w) {
+  JobW j;
+  const int tn2 = (P.tiles_n + 1) / 2;
+  const int64_t ntiles = (int64_t)P.tiles_m * tn2;
+  j.split = (int)(w / ntiles);
+  const int64_t t = w % ntiles;
+  int tp;
+  if (P.raster) {
+    tp = (int)(t % tn2);
+    j.tm = (int)(t / tn2);
+  } else {
+    j.tm = (int)(t % P.tiles_m);
+    tp = (int)(t / P.tiles_m);
+  }
+  j.tn0 = 2 * tp;
+  j.h1 = j.tn0 + 1 < P.tiles_n;
+  j.k0 = (int)((int64_t)j.split * P.nkb / P.ksplit);
+  j.k1 = (int)((int64_t)(j.split + 1) * P.nkb / P.ksplit);
+  return j;
+}
+
+// Index of 128 x 128 tile (tm, tn) in the split-K partial buffer, in the
+// order k_pk_reduce reads it.
+__device__ __forceinline__ int64_t tile128_index(const PkItem& P, int tm, int tn) {
+  return P.raster ? (int64_t)tm * P.tiles_n + tn : (int64_t)tn * P.tiles_m + tm;
+}
+
+constexpr int kEpiThreadsW = 256;
+constexpr int kThreadsW = 64 + kEpiThreadsW;
+
+template <int NT>
+__global__ void __launch_bounds__(kThreadsW, 1) k_gemm_pkw(const __grid_constant__ PkLaunch L) {
+  using G = CfgW<NT>;
+  constexpr int S = G::S;
+  extern __shared__ uint8_t pkw_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(pkw_raw) + 1023) & ~(uintptr_t)1023);
+  int64_t* colC = reinterpret_cast<int64_t*>(smem + G::OFF_COLC);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + G::OFF_BAR);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + S;
+  uint64_t* accf = bars + 2 * S;
+  uint64_t* acce = accf + 2;
+  uint64_t* done = acce + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + G::OFF_MISC);
+  volatile int* abort = reinterpret_cast<volatile int*>(smem + G::OFF_MISC + 4);
+  const PkItem& P = L.single;
+  const int ckb = max(P.chunk_kb, 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&accf[i], 1);
+      mbar_init(&acce[i], kEpiThreadsW);
+    }
+    mbar_init(done, 1);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t sbase = smem_u32(smem);
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------------------ producer
+      uint32_t g = 0;
+      bool ok = true;
+      for (int64_t w = blockIdx.x; ok && w < L.nwork; w += gridDim.x) {
+        const JobW J = jobw_of(P, w);
+        const uint8_t* a = P.qa + (size_t)J.tm * P.nkb * G::OPA;
+        const uint8_t* b0 = P.qb + (size_t)J.tn0 * P.nkb * G::OPH;
+        const uint8_t* b1 = b0 + (size_t)P.nkb * G::OPH;
+        for (int kb = J.k0; kb < J.k1; kb += G::BPS, ++g) {
+          const int s = (int)(g % S);
+          if (g >= (uint32_t)S && !mbar_wait(&empty[s], ((g / S) - 1) & 1, abort, kTimeoutNs)) {
+            ok = false;
+            break;
+          }
+          const uint32_t nb = (uint32_t)min(G::BPS, J.k1 - kb);
+          const uint32_t dst = sbase + (uint32_t)s * G::STAGE;
+          mbar_arrive_expect_tx(&full[s], nb * (G::OPA + (J.h1 ? 2 : 1) * G::OPH));
+          bulk_g2s(dst, a + (size_t)kb * G::OPA, nb * G::OPA, &full[s]);
+          bulk_g2s(dst + G::BPS * G::OPA, b0 + (size_t)kb * G::OPH, nb * G::OPH, &full[s]);
+          if (J.h1)
+            bulk_g2s(dst + G::BPS * (G::OPA + G::OPH), b1 + (size_t)kb * G::OPH, nb * G::OPH,
+                     &full[s]);
+        }
+      }
+      volatile int never = 0;
+      for (uint32_t i = g > (uint32_t)S ? g - S : 0; i < g; ++i)
+        mbar_wait(&full[i % S], (i / S) & 1, &never, kTimeoutNs);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ----------------------------------------------------------- MMA issue
+      // chunk gc (counted over the launch) goes to accumulator buffer gc % 2,
+      // free once the epilogue drained chunk gc - 2
+      const uint32_t idesc = L.idesc;
+      constexpr uint32_t LBO = (TILE / 8) * 128;
+      uint32_t g = 0, gc = 0;
+      bool ok = true;
+      for (int64_t w = blockIdx.x; ok && w < L.nwork; w += gridDim.x) {
+        const JobW J = jobw_of(P, w);
+        const int nchunks = (J.k1 - J.k0 + ckb - 1) / ckb;
+        int kb = J.k0;
+        for (int j = 0; ok && j < nchunks; ++j, ++gc) {
+          const uint32_t buf = gc & 1;
+          if (gc >= 2 && !mbar_wait(&acce[buf], ((gc >> 1) - 1) & 1, abort, kTimeoutNs)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t dacc = tmem + buf * TILE_W;
+          const int kend = min(J.k1, J.k0 + (j + 1) * ckb), kstart = kb;
+          for (; kb < kend; kb += G::BPS, ++g) {
+            const int s = (int)(g % S);
+            if (!mbar_wait(&full[s], (g / S) & 1, abort, kTimeoutNs)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const int nb = min(G::BPS, kend - kb);
+            const uint32_t st = sbase + (uint32_t)s * G::STAGE;
+            for (int bi = 0; bi < nb; ++bi) {
+              const uint32_t sa = st + bi * G::OPA;
+              const uint32_t sb0 = st + G::BPS * G::OPA + bi * G::OPH;
+              const uint32_t sb1 = sb0 + G::BPS * G::OPH;
+#pragma unroll
+              for (int kk = 0; kk < BK / 16; ++kk) {
+#pragma unroll
+                for (int pi = 0; pi < nprod(NT); ++pi) {
+                  const uint32_t acc = (kb > kstart || bi > 0 || kk > 0 || pi > 0) ? 1u : 0u;
+                  const uint64_t da = smem_desc(sa + kProdA[pi] * TERM + kk * 2 * LBO, LBO, 128);
+                  mma_bf16(dacc, da,
+                           smem_desc(sb0 + kProdB[pi] * TERM + kk * 2 * LBO, LBO, 128), idesc,
+                           acc);
+                  if (J.h1)
+                    mma_bf16(dacc + TILE, da,
+                             smem_desc(sb1 + kProdB[pi] * TERM + kk * 2 * LBO, LBO, 128), idesc,
+                             acc);
+                }
+              }
+            }
+            mma_commit(&empty[s]);
+          }
+          if (!ok) break;
+          mma_commit(&accf[buf]);
+        }
+      }
+      mma_commit(done);
+      volatile int never = 0;
+      mbar_wait(done, 0, &never, kTimeoutNs);
+    }
+  } else {
+    // ------------------------------------------------------------- epilogue
+    // warps 2-9: lane quadrant q = warp % 4 and N-half hh = (warp - 2) / 4;
+    // each thread owns one row and the 128 columns of its half, whose running
+    // sums stay in registers
+    const int ew = warp - 2;
+    const int q = warp & 3;
+    const int hh = ew >> 2;
+    const int row = q * 32 + lane;
+    const int etid = ew * 32 + lane;
+    uint32_t gc = 0, it = 0;
+    bool live = true;
+    auto setup = [&](int64_t w, int64_t* cc, JobW& J, int64_t& rc) {
+      J = jobw_of(P, w);
+      if (etid < TILE_W) {
+        const int64_t n = (int64_t)J.tn0 * TILE + etid;
+        cc[etid] = n < P.N ? goff(P.gn, 2, (uint32_t)n) : -1;
+      }
+      const int64_t m = (int64_t)J.tm * TILE + row;
+      rc = m < P.M ? goff(P.gm, 2, (uint32_t)m) : -1;
+    };
+    JobW Jn;
+    int64_t rcn = -1;
+    if (blockIdx.x < L.nwork) setup(blockIdx.x, colC, Jn, rcn);
+    named_bar_sync(1, kEpiThreadsW);
+    for (int64_t w = blockIdx.x; w < L.nwork; w += gridDim.x, ++it) {
+      const JobW J = Jn;
+      const int64_t rc = rcn;
+      int64_t* cc = colC + (it & 1) * TILE_W;
+      if (w + gridDim.x < L.nwork)
+        setup(w + gridDim.x, colC + ((it + 1) & 1) * TILE_W, Jn, rcn);
+      if (!live) {
+        named_bar_sync(1, kEpiThreadsW);
+        continue;
+      }
+      const int nchunks = (J.k1 - J.k0 + ckb - 1) / ckb;
+      float hi[128];
+      for (int j = 0; j < nchunks; ++j, ++gc) {
+        const uint32_t buf = gc & 1;
+        if (!warp_wait(&accf[buf], (gc >> 1) & 1, abort)) {
+          live = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + buf * TILE_W + hh * TILE;
+        if (j == 0) {
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            uint32_t r[16];
+            tmem_ld16(tl + c * 16, r);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) hi[c * 16 + i] = __uint_as_float(r[i]);
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            uint32_t r[16];
+            tmem_ld16(tl + c * 16, r);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) hi[c * 16 + i] = __fadd_rn(hi[c * 16 + i],
+                                                                    __uint_as_float(r[i]));
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&acce[buf]);  // this buffer may take the chunk after next
+      }
+      if (live && (hh == 0 || J.h1)) {
+        if (P.ksplit > 1) {
+          float2* pp = P.part + ((size_t)J.split * P.tiles_m * P.tiles_n +
+                                 tile128_index(P, J.tm, J.tn0 + hh)) * (size_t)(TILE * TILE) +
+                       row;
+#pragma unroll
+          for (int i = 0; i < 128; ++i) pp[(size_t)i * TILE] = make_float2(hi[i], 0.0f);
+        } else if (rc >= 0) {
+          const int64_t* ch = cc + hh * TILE;
+          if (L.out_type == 0) store_row<float, 128>(L.C, rc, ch, hi, L.alpha, L.beta);
+          else if (L.out_type == 1)
+            store_row<__nv_bfloat16, 128>(L.C, rc, ch, hi, L.alpha, L.beta);
+          else store_row<__half, 128>(L.C, rc, ch, hi, L.alpha, L.beta);
+        }
+      }
+      named_bar_sync(1, kEpiThreadsW);  // this tile's columns read; the next tile's written
     }
   }
 
@@ -763,6 +1074,84 @@ tc_status launch(const GemmArgs& a, const PkLayout& L, void* ws, cudaStream_t s,
   return TC_OK;
 }
 
+// One GEMM on wide tiles (tile configuration 4), same arguments as launch.
+template <int NT, typename In, bool F16T>
+tc_status launch_w(const GemmArgs& a, const PkLayout& L, void* ws, cudaStream_t s, int out_type) {
+  static int sm = 0;
+  if (sm == 0) {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess)
+      return TC_ERR_CUDA;
+    if (optin < (int)CfgW<NT>::BYTES) return TC_ERR_UNSUPPORTED;
+    if (cudaFuncSetAttribute(k_gemm_pkw<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)CfgW<NT>::BYTES) != cudaSuccess)
+      return TC_ERR_CUDA;
+    sm = (int)CfgW<NT>::BYTES;
+  }
+  if (!set_pack_smem<NT, In, F16T>()) return TC_ERR_CUDA;
+  const int sms = num_sms();
+  if (sms <= 0) return TC_ERR_CUDA;
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  PackArgs pa;
+  std::memset(&pa, 0, sizeof(pa));
+  pa.gr[0] = a.gm;
+  pa.gr[1] = a.gn;
+  pa.gk = a.gk;
+  pa.in[0] = a.A;
+  pa.in[1] = a.B;
+  pa.q[0] = w + L.off_qa;
+  pa.q[1] = w + L.off_qb;
+  pa.rows[0] = a.M;
+  pa.rows[1] = a.N;
+  pa.K = a.K;
+  pa.tiles[0] = (int32_t)L.tiles_m;
+  pa.tiles[1] = (int32_t)L.tiles_n;
+  pa.nkb = (int32_t)L.nkb;
+  pa.npk = (int32_t)((L.nkb + PK / BK - 1) / (PK / BK));
+  pa.nblocks0 = L.tiles_m * pa.npk;
+  pa.rows_fast[0] = a.a_contig == CONTIG_MN;
+  pa.rows_fast[1] = a.b_contig == CONTIG_MN;
+  const int64_t nblocks = (L.tiles_m + L.tiles_n) * pa.npk;
+  if (nblocks > 0x7fffffffll) return TC_ERR_UNSUPPORTED;
+  k_bf16_pack<NT, In, F16T><<<(unsigned)nblocks, kPackThreads, kPackSmem, s>>>(pa);
+  if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;
+
+  PkLaunch g;
+  std::memset(&g, 0, sizeof(g));
+  PkItem& it = g.single;
+  it.gm = a.gm;
+  it.gn = a.gn;
+  it.qa = pa.q[0];
+  it.qb = pa.q[1];
+  it.M = a.M;
+  it.N = a.N;
+  it.tiles_m = (int32_t)L.tiles_m;
+  it.tiles_n = (int32_t)L.tiles_n;
+  it.nkb = (int32_t)L.nkb;
+  it.chunk_kb = a.chunk_kb;
+  it.raster = a.raster;
+  it.ksplit = pk_ksplit_w(a);
+  it.part = it.ksplit > 1 ? reinterpret_cast<float2*>(w + L.bytes) : nullptr;
+  g.C = a.C;
+  g.alpha = (float)a.alpha;
+  g.beta = (float)a.beta;
+  g.idesc = F16T ? idesc_f16(TILE, TILE) : idesc_bf16(TILE, TILE);
+  g.out_type = out_type;
+  g.nwork = L.tiles_m * ((L.tiles_n + 1) / 2) * it.ksplit;
+  const int grid = (int)std::min<int64_t>(g.nwork, sms);
+  k_gemm_pkw<NT><<<grid, kThreadsW, sm, s>>>(g);
+  if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;
+  if (it.ksplit > 1) {
+    const int64_t total = L.tiles_m * L.tiles_n * TILE * TILE;
+    const int rgrid = (int)std::min<int64_t>((total + 255) / 256, (int64_t)sms * 8);
+    k_pk_reduce<<<rgrid, 256, 0, s>>>(g);
+    if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;
+  }
+  return TC_OK;
+}
+
 template <int NT>
 tc_status launch_batch(const PkBatch& b, const void* const* A, const void* const* B,
                        void* const* C, const double* alpha, const double* beta, cudaStream_t s) {
@@ -817,8 +1206,18 @@ int pk_ksplit(const GemmArgs& a) {
   return (int)std::max<int64_t>(1, std::min<int64_t>({want, nkb / 16, 64}));
 }
 
-size_t pk_part_bytes(const GemmArgs& a) {
-  const int sp = pk_ksplit(a);
+// Split-K of the wide tiles: the same rule over 128 x 256 tiles.
+int pk_ksplit_w(const GemmArgs& a) {
+  const int64_t tiles =
+      ((a.M + pk::TILE - 1) / pk::TILE) * (((a.N + pk::TILE - 1) / pk::TILE + 1) / 2);
+  const int64_t nkb = (a.K + pk::BK - 1) / pk::BK;
+  if (tiles <= 0 || tiles >= 152) return 1;
+  const int64_t want = (2 * 152 + tiles - 1) / tiles;
+  return (int)std::max<int64_t>(1, std::min<int64_t>({want, nkb / 16, 64}));
+}
+
+size_t pk_part_bytes(const GemmArgs& a, int tile) {
+  const int sp = tile == kTilePackedWide ? pk_ksplit_w(a) : pk_ksplit(a);
   if (sp <= 1) return 0;
   const int64_t tiles = ((a.M + pk::TILE - 1) / pk::TILE) * ((a.N + pk::TILE - 1) / pk::TILE);
   return (size_t)sp * (size_t)tiles * pk::TILE * pk::TILE * sizeof(float2);
@@ -842,11 +1241,24 @@ int pk_stage_blocks(int math) {
          : math == TC_MATH_BF16X3 ? pk::Cfg<2>::BPS : pk::Cfg<3>::BPS;
 }
 
-tc_status launch_gemm_tc_packed(const GemmArgs& a, int math, tc_dtype dt, void* ws,
+tc_status launch_gemm_tc_packed(const GemmArgs& a, int math, tc_dtype dt, int tile, void* ws,
                                 void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const PkLayout L = pk_layout(a, math);
   if (L.tiles_m == 0 || L.tiles_n == 0 || L.nkb == 0) return TC_OK;
+  if (tile == kTilePackedWide) {
+    if (dt == TC_BF16 && math == TC_MATH_BF16)
+      return pk::launch_w<1, __nv_bfloat16, false>(a, L, ws, s, 1);
+    if (dt == TC_F16 && math == TC_MATH_FP16)
+      return pk::launch_w<1, __half, true>(a, L, ws, s, 2);
+    if (dt != TC_F32) return TC_ERR_UNSUPPORTED;
+    switch (math) {
+      case TC_MATH_BF16: return pk::launch_w<1, float, false>(a, L, ws, s, 0);
+      case TC_MATH_FP16: return pk::launch_w<1, float, true>(a, L, ws, s, 0);
+      case TC_MATH_BF16X3: return pk::launch_w<2, float, false>(a, L, ws, s, 0);
+      default: return TC_ERR_UNSUPPORTED;
+    }
+  }
   if (dt == TC_BF16 && math == TC_MATH_BF16)
     return pk::launch<1, __nv_bfloat16, false>(a, L, ws, s, 1);
   if (dt == TC_F16 && math == TC_MATH_FP16) return pk::launch<1, __half, true>(a, L, ws, s, 2);

@@ -655,8 +655,12 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   }
   if (tile < 0 && sel_tile >= 0 && kernel == K_GEMM_TC && (sel_tile != kTilePacked || packed_ok))
     tile = sel_tile;  // the selector's tile configuration, where it applies
-  if (kernel == K_GEMM_TC && tile == kTilePacked && Bt > 1) {
+  if (kernel == K_GEMM_TC && (tile == kTilePacked || tile == kTilePackedWide) && Bt > 1) {
     delete P;  // packed operands: one GEMM, no batch group
+    return TC_ERR_UNSUPPORTED;
+  }
+  if (kernel == K_GEMM_TC && tile == kTilePackedWide && math == TC_MATH_BF16X6) {
+    delete P;  // wide tiles keep one accumulator: not the FP32-class form
     return TC_ERR_UNSUPPORTED;
   }
   // BF16 / FP16 storage and the FP16 form run only on packed operands (the
@@ -667,10 +671,10 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
     if (Bt > 1 && dtype != TC_F32 && tile < 0) {
       kernel = K_GEMM_SIMT;
       P->kernel = kernel;
-    } else if (Bt > 1 || (tile >= 0 && tile != kTilePacked)) {
+    } else if (Bt > 1 || (tile >= 0 && tile != kTilePacked && tile != kTilePackedWide)) {
       delete P;
       return TC_ERR_UNSUPPORTED;
-    } else {
+    } else if (tile < 0) {
       tile = kTilePacked;
     }
   }
@@ -685,7 +689,9 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
     } else if (kernel == K_GEMM_TC) {
       // the gathering kernel for a batch of GEMMs (the slicing mapping) and
       // for skinny operands
-      tile = packed_ok ? kTilePacked : 0;
+      // BF16x3 moves fewer operand bytes per multiply-add on 128 x 256 tiles
+      tile = !packed_ok ? 0
+             : (math == TC_MATH_BF16X3 && N > 128) ? kTilePackedWide : kTilePacked;
     } else {
       tile = 0;
     }
@@ -702,8 +708,8 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   ws = (ws + 255) & ~(size_t)255;
   if (P->copy_which) ws += ((size_t)P->copy_elems * es + 255) & ~(size_t)255;
   if (kernel == K_GEMM_FP8) ws += fp8_layout(g).bytes;
-  if (kernel == K_GEMM_TC && tile == kTilePacked)
-    ws += pk_layout(g, math).bytes + pk_part_bytes(g);  // packed terms, split-K partials
+  if (kernel == K_GEMM_TC && (tile == kTilePacked || tile == kTilePackedWide))
+    ws += pk_layout(g, math).bytes + pk_part_bytes(g, tile);  // packed terms, split-K partials
   if (kernel == K_GEMM_SIMT) {
     g.ksplit = simt_ksplit(g, dtype, tile);
     ws += simt_part_bytes(g, dtype, tile);               // FP64 split-K partial tiles

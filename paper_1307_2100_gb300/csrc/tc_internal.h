@@ -142,6 +142,9 @@ tc_status tc_fp8_read_status(int* h, void* stream);
 // Split-BF16 forms with packed operands (tile configuration kTilePacked of
 // the tensor-core GEMM): workspace layout and launcher.
 constexpr int kTilePacked = 3;
+// Packed operands on 128 x 256 tiles with one FP32 accumulator per tile (the
+// BF16, FP16 and BF16x3 forms).
+constexpr int kTilePackedWide = 4;
 struct PkLayout {
   int64_t tiles_m, tiles_n, nkb;
   size_t off_qa, off_qb, bytes;
@@ -150,11 +153,12 @@ PkLayout pk_layout(const GemmArgs& a, int math);
 // K ranges of a packed GEMM (split-K when there are fewer tiles than SMs),
 // and the bytes of its partial sums (part of the plan's workspace).
 int pk_ksplit(const GemmArgs& a);
-size_t pk_part_bytes(const GemmArgs& a);
+int pk_ksplit_w(const GemmArgs& a);
+size_t pk_part_bytes(const GemmArgs& a, int tile);
 // 32-K blocks per ring stage of the packed GEMM for a math form: every
 // accumulation chunk must hold a multiple of them.
 int pk_stage_blocks(int math);
-tc_status launch_gemm_tc_packed(const GemmArgs& a, int math, tc_dtype dt, void* ws,
+tc_status launch_gemm_tc_packed(const GemmArgs& a, int math, tc_dtype dt, int tile, void* ws,
                                 void* stream);
 tc_status tc_pk_read_status(int* h, void* stream);
 

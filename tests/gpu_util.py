@@ -148,7 +148,7 @@ def magnitude(p):
     return oracle.contract(A, B, C, abs(p.alpha), 0.0)
 
 
-def tc_bounds(p, form, chunk_k=256):
+def tc_bounds(p, form, chunk_k=256, single=False):
     """(accumulation bound, total bound) as multiples of sum |a||b| for the
     tensor-core forms.  The tensor cores add each 16-product block into FP32
     with an error of at most one unit of the running sum (2^-23 relative):
@@ -156,13 +156,16 @@ def tc_bounds(p, form, chunk_k=256):
     (2^-8 smaller) over all of K; BF16 keeps one accumulator over all of K.
     The split error of the form adds to that: 2^-8 (BF16), 3*2^-18 (the
     missing a1*b1 and the 2-term residuals, BF16x3), 4*2^-26 (products of
-    order >= 3, BF16x6)."""
+    order >= 3, BF16x6).  single: every product of every block goes into one
+    accumulator over all of K (the wide-tile kernel), (K/16) NPROD + 1 units."""
     K = 1
     for l, e in zip(p.A.labels, p.A.extents):
         if l in p.B.labels:
             K *= int(e)
     u = 2.0 ** -23
-    if form == "bf16":
+    if single:
+        acc = (K / 16 * NPROD[form] + 1) * u
+    elif form == "bf16":
         acc = (K / 16 + 1) * u
     else:
         acc = (min(K, chunk_k) / 16 + 1) * u + (K / 16 + 1) * (NPROD[form] - 1) * u * 2.0 ** -8

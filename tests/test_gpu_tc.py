@@ -16,8 +16,8 @@ import pytest
 import oracle
 from oracle import precision as op
 import tcsynth as ts
-from gpu_util import (compare, gather, magnitude, random_output_indices, run, sample_outputs,
-                      sample_outputs_form, tc_bounds, within)
+from gpu_util import (SPLIT_ERR, compare, gather, magnitude, random_output_indices, run,
+                      sample_outputs, sample_outputs_form, tc_bounds, within)
 
 pytestmark = pytest.mark.gpu
 
@@ -166,3 +166,77 @@ def test_packed_split_k():
     info = plans[-1]
     tiles = -(-info["M"] // 128) * -(-info["N"] // 128)
     assert tiles < 152 and info["workspace"] > 0
+
+
+# tile 4: packed operands on 128 x 256 tiles, one FP32 accumulator per tile
+WIDE_FORMS = ["bf16", "bf16x3"]
+
+
+@pytest.mark.parametrize("form", WIDE_FORMS)
+def test_wide_tiles_integer_inputs_exact(form):
+    p = ts.problem("int", "iajb", "jcid", "abcd", dict(i=9, a=70, j=11, b=3, c=65, d=5), 61,
+                   dist="int", dtype=np.float32, lo=-4, hi=4)
+    got = run(p, form, "fused_gemm", 4)
+    np.testing.assert_array_equal(got, oracle.contract_problem(p))
+
+
+@pytest.mark.parametrize("form", WIDE_FORMS)
+def test_wide_tiles_against_method_and_fp64_oracles(form):
+    """Shapes of every kind, an odd number of 128-column tiles (the second
+    half of the last wide tile missing), ragged K, a long K and a split-K
+    shape (few tiles): within the one-accumulator bound of the form's oracle."""
+    cases = shapes() + [
+        f32(ts.problem("odd_n", "ai", "ib", "ab", dict(a=129, i=45, b=260), 84)),
+        f32(ts.problem("one_n", "ai", "ib", "ab", dict(a=300, i=70, b=60), 85)),
+        f32(ts.problem("longk", "ai", "ib", "ab", dict(a=200, i=3000, b=150), 83)),
+        f32(ts.problem("splitk", "iajb", "icjd", "abcd",
+                       dict(i=60, j=55, a=30, b=8, c=30, d=9), 121)),
+    ]
+    for p in cases:
+        plans = []
+        got = run(p, form, "fused_gemm", 4, plan_out=plans)
+        assert plans[-1]["tile"] == 4
+        mag = magnitude(p)
+        acc, _ = tc_bounds(p, form, single=True)
+        ok, d = within(got, op.contract_form(p, form), mag, p.C, acc)
+        assert ok, (p.name, form, "method", d)
+        ok, d = within(got, oracle.contract_problem(p), mag, p.C, acc + SPLIT_ERR[form])
+        assert ok, (p.name, form, "fp64", d)
+
+
+def test_wide_tiles_alpha_beta():
+    p = f32(ts.direct_gemm_64(n=21))
+    p.C.data = np.linspace(-2, 2, p.C.data.size).astype(np.float32)
+    p.alpha, p.beta = -1.5, 0.25
+    got = run(p, "bf16x3", "fused_gemm", 4)
+    acc, _ = tc_bounds(p, "bf16x3", single=True)
+    mag = magnitude(p) + abs(p.beta) * np.abs(p.C.data.astype(np.float64))
+    assert within(got, op.contract_form(p, "bf16x3"), mag, p.C, acc)[0]
+
+
+def test_wide_tiles_refuse_the_fp32_class_form():
+    from paper_1307_2100_gb300 import tc
+    p = f32(ts.direct_gemm_64(n=9))
+    d = ((p.A.labels, p.A.extents, p.A.strides), (p.B.labels, p.B.extents, p.B.strides),
+         (p.C.labels, p.C.extents, p.C.strides))
+    assert tc.tc_plan_status(*d, tc.TC_F32, tc.MATH["bf16x6"], tc.MAPPING["fused_gemm"], 4) == 5
+
+
+@pytest.mark.parametrize("form", WIDE_FORMS)
+def test_wide_tiles_precision_workload_full_size_sampled(form):
+    p = ts.precision_ccd()
+    s = random_output_indices(p, 96, seed=3)
+    ref64 = sample_outputs(p, s)
+    import copy
+    pm = copy.copy(p)
+    pm.A = copy.copy(p.A)
+    pm.B = copy.copy(p.B)
+    pm.A.data = np.abs(p.A.data)
+    pm.B.data = np.abs(p.B.data)
+    mag = sample_outputs(pm, s)
+    got = run(p, form, "fused_gemm", 4)
+    g = gather(got, p.C, s)
+    acc, _ = tc_bounds(p, form, single=True)
+    assert np.linalg.norm(g - sample_outputs_form(p, s, form)) <= acc * np.linalg.norm(mag)
+    assert np.linalg.norm(g - ref64) <= (acc + SPLIT_ERR[form]) * np.linalg.norm(mag)
+
