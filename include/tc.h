@@ -207,6 +207,32 @@ typedef struct {
 
 tc_status tc_plan_layout_advice(tc_plan_t plan, tc_layout_advice* out);
 
+/* ---- Free-index sharding -------------------------------------------------
+ * Slicing a free index of C splits a contraction into independent ones (Sec.
+ * 2.4), which can run on different devices with no data exchanged.  For n
+ * shards, tc_shard_free_index picks C's largest free index (ties: the larger
+ * stride in C) and gives shard `shard` the balanced index range
+ * [begin, end) = [shard * E / n, (shard + 1) * E / n) of it.  The shard's slab
+ * is the same contraction with that label's extent end - begin in every
+ * tensor holding it, the tensors' strides unchanged (pass them explicitly),
+ * and its buffers starting offset_a, offset_b, offset_c elements into A, B
+ * and C; plan it with tc_plan and run it with tc_contract.  A shard whose
+ * range is empty has nothing to do.  An order-0 C has no free index: label
+ * -1, shard 0 computes the whole contraction (end = 1), the others nothing
+ * (end = 0).  Host only; the descriptors are read, not kept.  Errors as
+ * tc_plan's descriptor checks; TC_ERR_INVALID_ARG for n_shards < 1 or shard
+ * outside [0, n_shards). */
+typedef struct {
+  int32_t label;                          /* the split label of C, -1 for an order-0 C */
+  int32_t pos_a, pos_b, pos_c;            /* its index position in A, B, C; -1 where absent */
+  int64_t begin, end;                     /* this shard's index range of that label */
+  int64_t offset_a, offset_b, offset_c;   /* element offsets of the slab in A, B, C */
+} tc_shard;
+
+tc_status tc_shard_free_index(const tc_tensor_desc* A, const tc_tensor_desc* B,
+                              const tc_tensor_desc* C, int32_t n_shards, int32_t shard,
+                              tc_shard* out);
+
 /* Run the contraction asynchronously on `stream` (a cudaStream_t; NULL = the
  * legacy default stream).  A, B, C are device pointers to elements of the
  * plan's dtype laid out as described at tc_plan time; C is read only when
@@ -319,14 +345,18 @@ tc_status tc_device_status(void* stream);
 #define TC_SELECTOR_CANDIDATE(mapping, tile) ((int32_t)(mapping) | (((int32_t)(tile) + 1) << 8))
 
 tc_status tc_plan_features(tc_plan_t plan, float* out, int32_t n);
-/* Load (replacing any loaded one) or unload the process-wide selector.
- * tc_selector_load returns TC_ERR_INVALID_ARG for a malformed file. */
+/* Load a selector file or unload every selector.  A file holds the network of
+ * one storage type and math form; loading replaces the selector loaded for
+ * that form, if any, and keeps those of other forms (up to eight forms, else
+ * TC_ERR_UNSUPPORTED).  tc_plan(AUTO) consults the selector of the plan's own
+ * storage type and math form.  tc_selector_load returns TC_ERR_INVALID_ARG
+ * for a malformed file. */
 tc_status tc_selector_load(const char* path);
 tc_status tc_selector_unload(void);
-/* Host prediction for n feature vectors (n x TC_SELECTOR_FEATURES floats):
- * out is n x n_cand log2 runtimes, cand receives the candidates
- * (TC_SELECTOR_CANDIDATE values, array of at least 16).  TC_ERR_NO_SELECTOR if
- * none is loaded. */
+/* Host prediction, with the most recently loaded selector, for n feature
+ * vectors (n x TC_SELECTOR_FEATURES floats): out is n x n_cand log2 runtimes,
+ * cand receives the candidates (TC_SELECTOR_CANDIDATE values, array of at
+ * least 16).  TC_ERR_NO_SELECTOR if none is loaded. */
 tc_status tc_selector_predict(const float* features, int32_t n, float* out, int32_t* cand,
                               int32_t* n_cand);
 

@@ -653,7 +653,9 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
     const double dense = 2.0 * terms * 2.0 * (double)(M + N) * (double)Kt;
     packed_ok = (double)pk_layout(g, math).bytes <= 2.0 * dense + 64.0 * (1 << 20);
   }
-  if (tile < 0 && sel_tile >= 0 && kernel == K_GEMM_TC && (sel_tile != kTilePacked || packed_ok))
+  if (tile < 0 && sel_tile >= 0 &&
+      ((kernel == K_GEMM_TC && (sel_tile != kTilePacked || packed_ok)) ||
+       (kernel == K_GEMM_SIMT && sel_tile < num_tiles_simt(dtype))))
     tile = sel_tile;  // the selector's tile configuration, where it applies
   if (kernel == K_GEMM_TC && (tile == kTilePacked || tile == kTilePackedWide) && Bt > 1) {
     delete P;  // packed operands: one GEMM, no batch group
@@ -767,4 +769,57 @@ extern "C" const char* tc_status_string(tc_status s) {
     case TC_ERR_NO_SELECTOR: return "no selector loaded";
   }
   return "unknown status";
+}
+
+// ---------------------------------------------------------------------------
+// Free-index sharding (Sec. 2.4: slicing a free index of C gives independent
+// contractions, one per slice).  C's largest free index is split into n
+// balanced ranges; shard r contracts the slab of A, B and C where that index
+// lies in its range.  No data crosses shards.
+// ---------------------------------------------------------------------------
+extern "C" tc_status tc_shard_free_index(const tc_tensor_desc* Ad, const tc_tensor_desc* Bd,
+                                         const tc_tensor_desc* Cd, int32_t n_shards,
+                                         int32_t shard, tc_shard* out) {
+  if (!out || n_shards < 1 || shard < 0 || shard >= n_shards) return TC_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  Tens A, B, C;
+  tc_status st;
+  if ((st = read_desc(Ad, A)) != TC_OK) return st;
+  if ((st = read_desc(Bd, B)) != TC_OK) return st;
+  if ((st = read_desc(Cd, C)) != TC_OK) return st;
+  for (size_t i = 0; i < A.lab.size(); ++i) {  // contracted labels agree too
+    const int pb = B.find(A.lab[i]);
+    if (pb >= 0 && A.ext[i] != B.ext[pb]) return TC_ERR_EXTENT_MISMATCH;
+  }
+  int pick = -1;
+  for (size_t i = 0; i < C.lab.size(); ++i) {
+    const int32_t l = C.lab[i];
+    const int pa = A.find(l), pb = B.find(l);
+    if (pa < 0 && pb < 0) return TC_ERR_LABEL;
+    if ((pa >= 0 && A.ext[pa] != C.ext[i]) || (pb >= 0 && B.ext[pb] != C.ext[i]))
+      return TC_ERR_EXTENT_MISMATCH;
+    // the largest extent; ties go to the larger stride in C, so that a
+    // column-major C is cut into contiguous slabs
+    if (pick < 0 || C.ext[i] > C.ext[pick] || (C.ext[i] == C.ext[pick] && C.st[i] > C.st[pick]))
+      pick = (int)i;
+  }
+  if (pick < 0) {  // an order-0 C has no free index: shard 0 computes it
+    out->label = -1;
+    out->pos_a = out->pos_b = out->pos_c = -1;
+    out->begin = 0;
+    out->end = shard == 0 ? 1 : 0;
+    return TC_OK;
+  }
+  const int32_t l = C.lab[pick];
+  const int64_t E = C.ext[pick];
+  out->label = l;
+  out->pos_a = A.find(l);
+  out->pos_b = B.find(l);
+  out->pos_c = pick;
+  out->begin = (int64_t)((__int128)shard * E / n_shards);
+  out->end = (int64_t)((__int128)(shard + 1) * E / n_shards);
+  out->offset_a = out->pos_a >= 0 ? out->begin * A.st[out->pos_a] : 0;
+  out->offset_b = out->pos_b >= 0 ? out->begin * B.st[out->pos_b] : 0;
+  out->offset_c = out->begin * C.st[pick];
+  return TC_OK;
 }

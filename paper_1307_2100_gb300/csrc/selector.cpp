@@ -30,8 +30,18 @@ struct Selector {
   std::vector<float> W1, b1, W2, b2, W3, b3;
 };
 
+// One selector per (storage type, math form); the most recently loaded one
+// answers tc_selector_predict.
 std::mutex g_mu;
-Selector* g_sel = nullptr;
+constexpr int kMaxSelectors = 8;
+Selector* g_sels[kMaxSelectors] = {};
+Selector* g_last = nullptr;
+
+Selector* find(int32_t dtype, int32_t math) {
+  for (Selector* s : g_sels)
+    if (s && s->dtype == dtype && s->math == math) return s;
+  return nullptr;
+}
 
 float half_to_float(uint16_t h) {
   const uint32_t sign = (uint32_t)(h & 0x8000u) << 16;
@@ -83,8 +93,9 @@ void forward(const Selector& S, const float* x, float* y) {
 bool selector_predict(const float* features, tc_dtype dtype, tc_math math, int32_t* cand,
                       float* pred, int32_t* n_cand) {
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_sel || g_sel->dtype != dtype || g_sel->math != math) return false;
-  const Selector& S = *g_sel;
+  const Selector* sp = find(dtype, math);
+  if (!sp) return false;
+  const Selector& S = *sp;
   if (S.n_in != TC_SELECTOR_FEATURES || S.n_out > 16) return false;
   for (int i = 0; i < S.n_in; ++i) {
     const float margin = 0.05f * (S.hi[i] - S.lo[i]) + 1e-6f;
@@ -143,15 +154,28 @@ extern "C" tc_status tc_selector_load(const char* path) {
     return TC_ERR_INVALID_ARG;
   }
   std::lock_guard<std::mutex> lock(g_mu);
-  delete g_sel;
-  g_sel = S;
+  int slot = -1;
+  for (int i = 0; i < kMaxSelectors; ++i)
+    if (g_sels[i] && g_sels[i]->dtype == S->dtype && g_sels[i]->math == S->math) slot = i;
+  for (int i = 0; i < kMaxSelectors && slot < 0; ++i)
+    if (!g_sels[i]) slot = i;
+  if (slot < 0) {
+    delete S;
+    return TC_ERR_UNSUPPORTED;  // selectors for kMaxSelectors forms are loaded already
+  }
+  delete g_sels[slot];
+  g_sels[slot] = S;
+  g_last = S;
   return TC_OK;
 }
 
 extern "C" tc_status tc_selector_unload(void) {
   std::lock_guard<std::mutex> lock(g_mu);
-  delete g_sel;
-  g_sel = nullptr;
+  for (Selector*& s : g_sels) {
+    delete s;
+    s = nullptr;
+  }
+  g_last = nullptr;
   return TC_OK;
 }
 
@@ -159,8 +183,8 @@ extern "C" tc_status tc_selector_predict(const float* features, int32_t n, float
                                          int32_t* cand, int32_t* n_cand) {
   if (!features || !out || !cand || !n_cand || n < 0) return TC_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_sel) return TC_ERR_NO_SELECTOR;
-  const Selector& S = *g_sel;
+  if (!g_last) return TC_ERR_NO_SELECTOR;
+  const Selector& S = *g_last;
   for (int32_t i = 0; i < n; ++i) forward(S, features + (size_t)i * S.n_in, out + (size_t)i * S.n_out);
   for (int i = 0; i < S.n_out; ++i) cand[i] = S.cand[i];
   *n_cand = S.n_out;

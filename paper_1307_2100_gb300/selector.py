@@ -1,14 +1,21 @@
 """The learned mapping selector: timing dataset, training and evaluation.
 
-    python -m paper_1307_2100_gb300.selector generate --n 20000 --out sel_data.npz
+    python -m paper_1307_2100_gb300.selector generate --n 20000 --out sel_data.npz [--kind fp64]
     python -m paper_1307_2100_gb300.selector fill --data sel_data.npz --out sel_data.npz
     python -m paper_1307_2100_gb300.selector train --data sel_data.npz --out selector.bin
     python -m paper_1307_2100_gb300.selector evaluate --data sel_data.npz --weights selector.bin
 
-Every descriptor is planned under each candidate -- a mapping and, for the
-fused and COPY+GEMM mappings, the packed-operand or the gathering tensor-core
-kernel -- (FP32 storage, BF16x6 math, the FP32-class form) and timed by CUDA
-events (median of a few runs after a warm-up).  The network (libtc's tc_mlp_* kernels: forward,
+A selector serves one storage type and math form (a "kind"):
+  bf16x6  FP32 storage, BF16x6 math (the FP32-class form); candidates are a
+          mapping and, for the fused and COPY+GEMM mappings, the
+          packed-operand or the gathering tensor-core kernel;
+  fp64    FP64 storage and math (the paper's own arithmetic); candidates are
+          the CUDA-core GEMM's three tile shapes (64x64, 32x32, 128x64) for
+          the fused mapping, the slicing and COPY+GEMM mappings, GEMV, DOT and
+          GER.  Its descriptors are those of the bf16x6 kind with at most
+          2^34 flops (a second at the FP64 rate), so that timing stays bounded.
+Every descriptor is planned under each candidate and timed by CUDA events
+(median of a few runs after a warm-up).  The network (libtc's tc_mlp_* kernels: forward,
 masked-MSE backward, Adam; FP16 working weights) learns the log2 runtime of
 every candidate from the plan's features (tc_plan_features).  Regret of a
 choice is t(choice) / t(best) - 1 against the same exhaustive timing table;
@@ -33,20 +40,69 @@ from . import tc
 # tensor-core kernel (tile 0); the slicing mapping's batches on the latter;
 # GER (K <= 32) on the CUDA cores in FP32.  New candidates go at the end (the
 # timing tables keep their columns).
-CANDIDATE_SPECS = [
-    ("fused_gemm", "fused_gemm", 3),
-    ("fused_gemm_gather", "fused_gemm", 0),
-    ("slice_gemm", "slice_gemm", -1),
-    ("copy_gemm", "copy_gemm", 3),
-    ("copy_gemm_gather", "copy_gemm", 0),
-    ("gemv", "gemv", -1),
-    ("dot", "dot", -1),
-    ("ger", "ger", -1),
-]
+KINDS = {
+    "bf16x6": {"dtype": tc.TC_F32, "math": "bf16x6", "max_flops": None, "candidates": [
+        ("fused_gemm", "fused_gemm", 3),
+        ("fused_gemm_gather", "fused_gemm", 0),
+        ("slice_gemm", "slice_gemm", -1),
+        ("copy_gemm", "copy_gemm", 3),
+        ("copy_gemm_gather", "copy_gemm", 0),
+        ("gemv", "gemv", -1),
+        ("dot", "dot", -1),
+        ("ger", "ger", -1),
+    ]},
+    "fp64": {"dtype": tc.TC_F64, "math": "fp64", "max_flops": 2.0 ** 34, "candidates": [
+        ("fused_gemm_64x64", "fused_gemm", 0),
+        ("fused_gemm_32x32", "fused_gemm", 1),
+        ("fused_gemm_128x64", "fused_gemm", 2),
+        ("slice_gemm", "slice_gemm", -1),
+        ("copy_gemm", "copy_gemm", -1),
+        ("gemv", "gemv", -1),
+        ("dot", "dot", -1),
+        ("ger", "ger", -1),
+    ]},
+}
+CANDIDATE_SPECS = KINDS["bf16x6"]["candidates"]
 CANDIDATES = [c[0] for c in CANDIDATE_SPECS]
-CAND_IDS = [tc.MAPPING[m] | ((t + 1) << 8) for _, m, t in CANDIDATE_SPECS]
 MATH = "bf16x6"
 HIDDEN = 128
+
+
+def specs(kind):
+    return KINDS[kind]["candidates"]
+
+
+def cand_ids(kind):
+    return [tc.MAPPING[m] | ((t + 1) << 8) for _, m, t in specs(kind)]
+
+
+CAND_IDS = cand_ids("bf16x6")
+
+
+def _flops(desc):
+    ext = {}
+    for t in desc:
+        for l, e in zip(t.labels, t.extents):
+            ext[l] = int(e)
+    f = 2.0
+    for e in ext.values():
+        f *= e
+    return f
+
+
+def descriptors(kind, n, seed):
+    """The n descriptors of a kind's dataset (seeded): the selector workload's
+    descriptors, for fp64 only those with at most 2^34 flops."""
+    import tcsynth as ts
+    cap = KINDS[kind]["max_flops"]
+    if cap is None:
+        return ts.selector_descriptors(n, seed=seed)
+    m = n + n // 32 + 64
+    while True:   # the generator's first m descriptors do not depend on m
+        d = [x for x in ts.selector_descriptors(m, seed=seed) if _flops(x) <= cap]
+        if len(d) >= n:
+            return d[:n]
+        m *= 2
 
 
 def _desc(t):
@@ -59,11 +115,12 @@ def _span(t):
     return 1 + sum((e - 1) * s for e, s in zip(t.extents, t.strides))
 
 
-def _timer(ws_bytes):
+def _timer(ws_bytes, dtype=None):
     """Device buffers and a function timing one planned candidate (median of
     `reps` runs after a warm-up, ms; None if the workspace does not fit)."""
     import torch
     dev = torch.device("cuda", 0)
+    tdt = torch.float64 if dtype == tc.TC_F64 else torch.float32
     state = {"big": 0, "arena": None, "cbuf": None}
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
     s = torch.cuda.current_stream(dev)
@@ -71,8 +128,8 @@ def _timer(ws_bytes):
 
     def ensure(big):
         if big > state["big"]:
-            state["arena"] = [torch.rand(big, device=dev) * 2 - 1 for _ in range(2)]
-            state["cbuf"] = torch.zeros(big, device=dev)
+            state["arena"] = [torch.rand(big, device=dev, dtype=tdt) * 2 - 1 for _ in range(2)]
+            state["cbuf"] = torch.zeros(big, device=dev, dtype=tdt)
             state["big"] = big
 
     def time_plan(h, reps):
@@ -97,11 +154,12 @@ def _timer(ws_bytes):
     return ensure, time_plan, s
 
 
-def _time_candidates(desc, j, time_plan, reps):
+def _time_candidates(desc, j, time_plan, reps, kind="bf16x6"):
     A, B, C = desc
-    _, mname, tile = CANDIDATE_SPECS[j]
+    _, mname, tile = specs(kind)[j]
+    k = KINDS[kind]
     try:
-        h = tc.tc_plan(_desc(A), _desc(B), _desc(C), tc.TC_F32, tc.MATH[MATH],
+        h = tc.tc_plan(_desc(A), _desc(B), _desc(C), k["dtype"], tc.MATH[k["math"]],
                        tc.MAPPING[mname], tile)
     except tc.TcError:
         return None
@@ -111,16 +169,17 @@ def _time_candidates(desc, j, time_plan, reps):
         tc.tc_plan_destroy(h)
 
 
-def generate(n, seed, out, reps=5, checkpoint=500, ws_bytes=1 << 28, log=sys.stderr):
-    """Time every candidate on n descriptors; save features, times (ms; NaN if
-    the candidate cannot compute it or its workspace exceeds ws_bytes), class
-    and the recipe's choice."""
-    import tcsynth as ts
-    descs = ts.selector_descriptors(n, seed=seed)
-    ensure, time_plan, s = _timer(ws_bytes)
+def generate(n, seed, out, reps=5, checkpoint=500, ws_bytes=1 << 28, log=sys.stderr,
+             kind="bf16x6"):
+    """Time every candidate of a kind on its n descriptors; save features,
+    times (ms; NaN if the candidate cannot compute it or its workspace exceeds
+    ws_bytes), class    and the recipe's choice."""
+    descs = descriptors(kind, n, seed)
+    k = KINDS[kind]
+    ensure, time_plan, s = _timer(ws_bytes, k["dtype"])
     ensure(max(max(_span(a), _span(b), _span(c)) for a, b, c in descs))
     F = np.zeros((n, tc.N_FEATURES), np.float32)
-    T = np.full((n, len(CANDIDATES)), np.nan, np.float64)
+    T = np.full((n, len(specs(kind))), np.nan, np.float64)
     cls = np.zeros(n, np.int32)
     recipe = np.zeros(n, np.int32)
     start = 0
@@ -132,14 +191,15 @@ def generate(n, seed, out, reps=5, checkpoint=500, ws_bytes=1 << 28, log=sys.std
     t0 = time.time()
     for i in range(start, n):
         A, B, C = descs[i]
-        h = tc.tc_plan(_desc(A), _desc(B), _desc(C), tc.TC_F32, tc.MATH[MATH], tc.MAPPING["recipe"])
+        h = tc.tc_plan(_desc(A), _desc(B), _desc(C), k["dtype"], tc.MATH[k["math"]],
+                       tc.MAPPING["recipe"])
         info = tc.tc_plan_get_info(h)
         F[i] = tc.tc_plan_features(h)
         cls[i] = info.cls
         recipe[i] = info.mapping
         tc.tc_plan_destroy(h)
-        for j in range(len(CANDIDATES)):
-            t = _time_candidates(descs[i], j, time_plan, reps)
+        for j in range(len(specs(kind))):
+            t = _time_candidates(descs[i], j, time_plan, reps, kind)
             if t is not None:
                 T[i, j] = t
         if (i + 1) % checkpoint == 0 or i + 1 == n:
@@ -148,8 +208,8 @@ def generate(n, seed, out, reps=5, checkpoint=500, ws_bytes=1 << 28, log=sys.std
                   flush=True)
     if tc.tc_device_status(s.cuda_stream) != tc.TC_OK:
         raise RuntimeError("device status not ok after timing")
-    np.savez(out, F=F, T=T, cls=cls, recipe=recipe, candidates=np.array(CAND_IDS, np.int32),
-             seed=seed)
+    np.savez(out, F=F, T=T, cls=cls, recipe=recipe, candidates=np.array(cand_ids(kind), np.int32),
+             seed=seed, kind=kind)
     if os.path.exists(out + ".partial.npz"):
         os.remove(out + ".partial.npz")
     return out
@@ -158,21 +218,22 @@ def generate(n, seed, out, reps=5, checkpoint=500, ws_bytes=1 << 28, log=sys.std
 def fill(data, out, reps=5, ws_bytes=1 << 31, log=sys.stderr):
     """Time the candidates a dataset lacks (NaN) whose plans exist and whose
     workspace fits ws_bytes; write the completed dataset to out."""
-    import tcsynth as ts
     z = dict(np.load(data))
+    kind = _kind_of(z)
     T = z["T"].copy()
-    if T.shape[1] < len(CANDIDATES):   # candidates added since: untimed columns
-        T = np.concatenate([T, np.full((len(T), len(CANDIDATES) - T.shape[1]), np.nan)], 1)
-        z["candidates"] = np.array(CAND_IDS, np.int32)
-    descs = ts.selector_descriptors(len(T), seed=int(z["seed"]))
-    ensure, time_plan, s = _timer(ws_bytes)
+    nc = len(specs(kind))
+    if T.shape[1] < nc:   # candidates added since: untimed columns
+        T = np.concatenate([T, np.full((len(T), nc - T.shape[1]), np.nan)], 1)
+        z["candidates"] = np.array(cand_ids(kind), np.int32)
+    descs = descriptors(kind, len(T), int(z["seed"]))
+    ensure, time_plan, s = _timer(ws_bytes, KINDS[kind]["dtype"])
     todo = [(i, j) for i, j in zip(*np.where(~np.isfinite(T)))]
     rows = sorted({i for i, _ in todo})
     if rows:
         ensure(max(max(_span(a), _span(b), _span(c)) for a, b, c in (descs[i] for i in rows)))
     filled = 0
     for i, j in todo:
-        t = _time_candidates(descs[i], j, time_plan, reps)
+        t = _time_candidates(descs[i], j, time_plan, reps, kind)
         if t is not None:
             T[i, j] = t
             filled += 1
@@ -182,6 +243,10 @@ def fill(data, out, reps=5, ws_bytes=1 << 31, log=sys.stderr):
     z["T"] = T
     np.savez(out, **z)
     return out
+
+
+def _kind_of(z):
+    return str(z["kind"]) if "kind" in z else "bf16x6"
 
 
 def split(n, holdout, seed=1):
@@ -202,6 +267,7 @@ def train(data, out, holdout=2000, epochs=400, batch=256, lr=2e-3, seed=0, log=s
     selector file read by tc_selector_load."""
     import torch
     z = np.load(data)
+    kind = _kind_of(z)
     F, T = z["F"].astype(np.float32), z["T"]
     tr, _ = split(len(F), holdout)
     Y, M = _targets(T)
@@ -259,14 +325,16 @@ def train(data, out, holdout=2000, epochs=400, batch=256, lr=2e-3, seed=0, log=s
         tc.tc_mlp_get_params(net, work.ctypes.data, n_par, working=True)
     finally:
         tc.tc_mlp_destroy(net)
-    write_weights(out, n_in, HIDDEN, n_out, CAND_IDS, lo, hi, mean, scale, ym, ys, work)
+    write_weights(out, n_in, HIDDEN, n_out, cand_ids(kind), lo, hi, mean, scale, ym, ys, work,
+                  KINDS[kind]["dtype"], KINDS[kind]["math"])
     return out
 
 
-def write_weights(path, n_in, n_hidden, n_out, cand, lo, hi, mean, scale, ym, ys, params):
+def write_weights(path, n_in, n_hidden, n_out, cand, lo, hi, mean, scale, ym, ys, params,
+                  dtype=tc.TC_F32, math=MATH):
     with open(path, "wb") as f:
         f.write(b"TCSEL01\0")
-        f.write(struct.pack("<5i", n_in, n_hidden, n_out, tc.TC_F32, tc.MATH[MATH]))
+        f.write(struct.pack("<5i", n_in, n_hidden, n_out, dtype, tc.MATH[math]))
         f.write(np.asarray(cand, "<i4").tobytes())
         for a in (lo, hi, mean, scale):
             f.write(np.asarray(a, "<f4").tobytes())
@@ -274,30 +342,30 @@ def write_weights(path, n_in, n_hidden, n_out, cand, lo, hi, mean, scale, ym, ys
         f.write(np.asarray(params, np.float32).astype("<f2").tobytes())
 
 
-def feasible(cls):
+def feasible(cls, kind="bf16x6"):
     """Candidates able to compute a contraction of the given class: slicing and
     COPY+GEMM need a free index in each operand (Class 3); GER's limit on K
     shows as a missing timing."""
-    ok = np.ones((len(cls), len(CANDIDATES)), bool)
+    ok = np.ones((len(cls), len(specs(kind))), bool)
     c3 = np.isin(cls, [31, 32])
-    for j, (_, mname, _t) in enumerate(CANDIDATE_SPECS):
+    for j, (_, mname, _t) in enumerate(specs(kind)):
         if mname in ("slice_gemm", "copy_gemm"):
             ok[~c3, j] = False
     return ok
 
 
-def planned_candidates(seed, n, holdout, mapping="recipe"):
+def planned_candidates(seed, n, holdout, mapping="recipe", kind="bf16x6"):
     """Candidate index of what tc_plan decides (mapping and tile) for each
     held-out descriptor, planned again on the host: mapping "recipe" is the
     paper's recipe, "auto" the loaded selector."""
-    import tcsynth as ts
-    descs = ts.selector_descriptors(n, seed=seed)
+    descs = descriptors(kind, n, seed)
     _, te = split(n, holdout)
-    spec = {(tc.MAPPING[m], t): j for j, (_, m, t) in enumerate(CANDIDATE_SPECS)}
+    k = KINDS[kind]
+    spec = {(tc.MAPPING[m], t): j for j, (_, m, t) in enumerate(specs(kind))}
     out = np.zeros(len(te), np.int64)
     for r, i in enumerate(te):
         A, B, C = descs[i]
-        h = tc.tc_plan(_desc(A), _desc(B), _desc(C), tc.TC_F32, tc.MATH[MATH],
+        h = tc.tc_plan(_desc(A), _desc(B), _desc(C), k["dtype"], tc.MATH[k["math"]],
                        tc.MAPPING[mapping])
         try:
             info = tc.tc_plan_get_info(h)
@@ -318,33 +386,34 @@ def evaluate(data, weights, holdout=2000, use_gpu=True):
     """Regret of the network, of the recipe, and of each fixed candidate on the
     held-out descriptors (timings from the dataset)."""
     z = np.load(data)
+    kind = _kind_of(z)
     F, T, cls, recipe = z["F"].astype(np.float32), z["T"], z["cls"], z["recipe"]
     _, te = split(len(F), holdout)
     F, T, cls, recipe = F[te], T[te], cls[te], recipe[te]
     ran = np.isfinite(T)
     keep = ran.any(axis=1)
     F, T, cls, recipe, ran = F[keep], T[keep], cls[keep], recipe[keep], ran[keep]
-    ok = feasible(cls) & ran
+    ok = feasible(cls, kind) & ran
     best = np.where(ok, T, np.inf).min(axis=1)
     seed, n_all = int(z["seed"]), len(z["F"])
     tc.tc_selector_load(weights)
     try:
         pred, cand = tc.tc_selector_predict(F)
         # what tc_plan(AUTO) runs with this network loaded
-        choice = planned_candidates(seed, n_all, holdout, "auto")[keep]
+        choice = planned_candidates(seed, n_all, holdout, "auto", kind)[keep]
     finally:
         tc.tc_selector_unload()
     gpu_pred = None
     if use_gpu:
         gpu_pred = gpu_forward(weights, F)
     t_choice = T[np.arange(len(T)), choice]
-    rec_idx = planned_candidates(seed, n_all, holdout, "recipe")[keep]
+    rec_idx = planned_candidates(seed, n_all, holdout, "recipe", kind)[keep]
     t_recipe = np.where(ok[np.arange(len(T)), rec_idx], T[np.arange(len(T)), rec_idx], np.inf)
-    res = {"n": int(len(T)), "network": regret_stats(t_choice, best),
+    res = {"kind": kind, "n": int(len(T)), "network": regret_stats(t_choice, best),
            "recipe": regret_stats(t_recipe, best),
            "total_time_ms": {"network": float(t_choice.sum()), "recipe": float(t_recipe.sum()),
                              "best": float(best.sum())}}
-    for j, c in enumerate(CANDIDATES):
+    for j, (c, _m, _t) in enumerate(specs(kind)):
         tj = np.where(ok[:, j], T[:, j], np.inf)
         fin = np.isfinite(tj)
         res["always_" + c] = {"coverage": float(fin.mean()),
@@ -390,6 +459,8 @@ def main(argv=None):
     g.add_argument("--seed", type=int, default=20130712)
     g.add_argument("--out", required=True)
     g.add_argument("--reps", type=int, default=5)
+    g.add_argument("--kind", default="bf16x6", choices=sorted(KINDS))
+    g.add_argument("--ws-gb", type=float, default=2.0)
     t = sub.add_parser("train")
     t.add_argument("--data", required=True)
     t.add_argument("--out", required=True)
@@ -405,7 +476,7 @@ def main(argv=None):
     e.add_argument("--holdout", type=int, default=2000)
     a = ap.parse_args(argv)
     if a.cmd == "generate":
-        generate(a.n, a.seed, a.out, a.reps)
+        generate(a.n, a.seed, a.out, a.reps, ws_bytes=int(a.ws_gb * (1 << 30)), kind=a.kind)
     elif a.cmd == "fill":
         fill(a.data, a.out, ws_bytes=int(a.ws_gb * (1 << 30)))
     elif a.cmd == "train":

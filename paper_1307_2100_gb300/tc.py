@@ -75,6 +75,13 @@ class BatchInfo(ctypes.Structure):
                 ("n_simt_tiles", ctypes.c_int64), ("n_tc_split", ctypes.c_int64)]
 
 
+class Shard(ctypes.Structure):
+    _fields_ = [("label", ctypes.c_int32), ("pos_a", ctypes.c_int32), ("pos_b", ctypes.c_int32),
+                ("pos_c", ctypes.c_int32), ("begin", ctypes.c_int64), ("end", ctypes.c_int64),
+                ("offset_a", ctypes.c_int64), ("offset_b", ctypes.c_int64),
+                ("offset_c", ctypes.c_int64)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is not built; run paper_1307_2100_gb300.build.build()")
@@ -139,6 +146,10 @@ def _load():
     lib.tc_device_status.argtypes = [P]
     lib.tc_status_string.restype = ctypes.c_char_p
     lib.tc_status_string.argtypes = [ctypes.c_int]
+    lib.tc_shard_free_index.restype = ctypes.c_int
+    lib.tc_shard_free_index.argtypes = [ctypes.POINTER(TensorDesc), ctypes.POINTER(TensorDesc),
+                                        ctypes.POINTER(TensorDesc), ctypes.c_int32,
+                                        ctypes.c_int32, ctypes.POINTER(Shard)]
     lib.tc_peak_probe.restype = ctypes.c_int
     lib.tc_peak_probe.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
                                   P]
@@ -184,6 +195,18 @@ def tc_plan_status(A, B, C, dtype: int, math: int, mapping: int = 0, tile: int =
         return e.status
     tc_plan_destroy(h)
     return TC_OK
+
+
+def tc_shard_free_index(A, B, C, n_shards: int, shard: int) -> Shard:
+    """A, B, C: (labels, extents, strides-or-None).  Shard `shard` of n."""
+    dA, kA = make_desc(*A)
+    dB, kB = make_desc(*B)
+    dC, kC = make_desc(*C)
+    out = Shard()
+    _check(lib.tc_shard_free_index(ctypes.byref(dA), ctypes.byref(dB), ctypes.byref(dC),
+                                   int(n_shards), int(shard), ctypes.byref(out)),
+           "tc_shard_free_index")
+    return out
 
 
 def tc_plan_layout_advice(plan: int) -> LayoutAdvice:
