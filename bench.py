@@ -558,70 +558,81 @@ def config1_part(peaks, steps):
                            "sample": "the whole config"}}
 
 
-def selector_part(n_desc=160, budget_s=75.0, reps=3):
-    """The learned selector re-timed on this GPU: held-out descriptors of the
-    selector workload (orders 2-6, extents log-uniform [4, 256], random label
-    placement and strides; the network never saw them), each timed under every
-    candidate mapping (exhaustive timing, median of `reps` runs), and the
-    regret t(choice) / t(best) - 1 of the network's choice (tc_plan with
-    TC_MAP_AUTO, packaged weights) and of the paper's recipe.  Stops at
-    `budget_s` seconds."""
+SELECTORS = [  # (kind, weights, timing table, held-out descriptors re-timed)
+    ("bf16x6", "selector_gb300.bin", "selector_timings_gb300.npz", 160),
+    ("fp64", "selector_gb300_fp64.bin", "selector_timings_gb300_fp64.npz", 80),
+]
+
+
+def selector_part(budget_s=90.0, reps=3):
+    """The learned selectors re-timed on this GPU: for each kind (FP32 storage
+    with BF16x6; FP64), held-out descriptors of the selector workload (orders
+    2-6, extents log-uniform [4, 256], random label placement and strides; the
+    network never saw them), each timed under every candidate mapping and tile
+    (exhaustive timing, median of `reps` runs), and the regret t(choice) /
+    t(best) - 1 of the network's choice (tc_plan with TC_MAP_AUTO, packaged
+    weights) and of the paper's recipe.  Stops at `budget_s` seconds."""
     import torch
     from paper_1307_2100_gb300 import selector as sel
     from paper_1307_2100_gb300 import tc
     data = os.path.join(ROOT, "paper_1307_2100_gb300", "data")
-    z = np.load(os.path.join(data, "selector_timings_gb300.npz"))
-    seed, n_all = int(z["seed"]), len(z["F"])
-    descs = ts.selector_descriptors(n_all, seed=seed)
-    _, te = sel.split(n_all, 2000)
-    spans = []
-    for i in te[:n_desc]:
-        spans.append(max(sel._span(t) for t in descs[i]))
-    ensure, time_plan, s = sel._timer(1 << 31)
-    ensure(max(spans))
-    spec = {(tc.MAPPING[m], t): j for j, (_, m, t) in enumerate(sel.CANDIDATE_SPECS)}
-
-    def planned(A, B, C, mapping):
-        h = tc.tc_plan(sel._desc(A), sel._desc(B), sel._desc(C), tc.TC_F32,
-                       tc.MATH[sel.MATH], tc.MAPPING[mapping])
-        try:
-            info = tc.tc_plan_get_info(h)
-        finally:
-            tc.tc_plan_destroy(h)
-        m, t = int(info.mapping), int(info.tile)
-        return spec.get((m, t), spec.get((m, -1), 0))
-
-    tc.tc_selector_load(os.path.join(data, "selector_gb300.bin"))
-    rn, rr, rows = [], [], 0
+    out = {"timing": f"median of {reps} event-timed runs per candidate, live on this GPU"}
     t0 = time.perf_counter()
-    try:
-        for i in te[:n_desc]:
-            if time.perf_counter() - t0 > budget_s:
-                break
-            A, B, C = descs[i]
-            T = [sel._time_candidates(descs[i], j, time_plan, reps)
-                 for j in range(len(sel.CANDIDATE_SPECS))]
-            ok = [t for t in T if t is not None]
-            if not ok:
-                continue
-            best = min(ok)
-            cn, cr = planned(A, B, C, "auto"), planned(A, B, C, "recipe")
-            if T[cn] is None or T[cr] is None:
-                continue
-            rn.append(T[cn] / best - 1.0)
-            rr.append(T[cr] / best - 1.0)
-            rows += 1
-    finally:
-        tc.tc_selector_unload()
-    torch.cuda.synchronize()
-    stat = lambda r: {"mean": float(np.mean(r)), "median": float(np.median(r)),
-                      "p90": float(np.percentile(r, 90))} if r else None
-    return {"workload": "selector: held-out descriptors (orders 2-6, extents log-uniform "
-                        "[4,256], random placement and strides), FP32 storage, BF16x6",
-            "descriptors_timed": rows, "candidates": len(sel.CANDIDATE_SPECS),
-            "timing": f"median of {reps} event-timed runs per candidate, live on this GPU",
-            "regret_network": stat(rn), "regret_recipe": stat(rr),
-            "seconds": time.perf_counter() - t0}
+    for kind, wfile, tfile, n_desc in SELECTORS:
+        if not os.path.exists(os.path.join(data, wfile)):
+            out[kind] = {"error": "no packaged weights"}
+            continue
+        z = np.load(os.path.join(data, tfile))
+        seed, n_all = int(z["seed"]), len(z["F"])
+        descs = sel.descriptors(kind, n_all, seed)
+        _, te = sel.split(n_all, 2000)
+        k = sel.KINDS[kind]
+        ensure, time_plan, s = sel._timer(1 << 31, k["dtype"])
+        ensure(max(max(sel._span(t) for t in descs[i]) for i in te[:n_desc]))
+        spec = {(tc.MAPPING[m], t): j for j, (_, m, t) in enumerate(sel.specs(kind))}
+
+        def planned(A, B, C, mapping):
+            h = tc.tc_plan(sel._desc(A), sel._desc(B), sel._desc(C), k["dtype"],
+                           tc.MATH[k["math"]], tc.MAPPING[mapping])
+            try:
+                info = tc.tc_plan_get_info(h)
+            finally:
+                tc.tc_plan_destroy(h)
+            m, t = int(info.mapping), int(info.tile)
+            return spec.get((m, t), spec.get((m, -1), 0))
+
+        tc.tc_selector_load(os.path.join(data, wfile))
+        rn, rr, rows = [], [], 0
+        tk = time.perf_counter()
+        try:
+            for i in te[:n_desc]:
+                if time.perf_counter() - t0 > budget_s:
+                    break
+                A, B, C = descs[i]
+                T = [sel._time_candidates(descs[i], j, time_plan, reps, kind)
+                     for j in range(len(sel.specs(kind)))]
+                ok = [t for t in T if t is not None]
+                if not ok:
+                    continue
+                best = min(ok)
+                cn, cr = planned(A, B, C, "auto"), planned(A, B, C, "recipe")
+                if T[cn] is None or T[cr] is None:
+                    continue
+                rn.append(T[cn] / best - 1.0)
+                rr.append(T[cr] / best - 1.0)
+                rows += 1
+        finally:
+            tc.tc_selector_unload()
+        torch.cuda.synchronize()
+        stat = lambda r: {"mean": float(np.mean(r)), "median": float(np.median(r)),
+                          "p90": float(np.percentile(r, 90))} if r else None
+        out[kind] = {"workload": "held-out selector descriptors (orders 2-6, extents "
+                                 "log-uniform [4,256], random placement and strides), "
+                                 f"{'FP64' if kind == 'fp64' else 'FP32 storage, BF16x6'}",
+                     "descriptors_timed": rows, "candidates": len(sel.specs(kind)),
+                     "regret_network": stat(rn), "regret_recipe": stat(rr),
+                     "seconds": time.perf_counter() - tk}
+    return out
 
 
 def peaks_std():

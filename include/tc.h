@@ -293,10 +293,15 @@ tc_status tc_batch_plan(tc_batch_t* out, const tc_plan_t* plans, int32_t n);
 
 /* tc_batch_plan with a route per plan (routes may be NULL: all -1):
  *   -1  the threshold rule of tc_batch_set_route,
- *    0  the CUDA-core route,
- *    1  the tensor-core route (TC_ERR_UNSUPPORTED for a plan with a batch
- *       group); any other value is TC_ERR_INVALID_ARG.
- * An autotuner (paper_1307_2100_gb300/autotune.py) picks routes by timing. */
+ *    0  the CUDA-core route, its shape by the rule (32x32 tiles where
+ *       min(M, N) >= 16, else a thread or a warp per output),
+ *    1  the tensor-core route, 128x128 tiles (TC_ERR_UNSUPPORTED for a plan
+ *       with a batch group),
+ *    2  the CUDA-core route on 32x32 output tiles,
+ *    3  the CUDA-core route with a thread (a warp below 256 outputs) per output;
+ * any other value is TC_ERR_INVALID_ARG.  An autotuner
+ * (paper_1307_2100_gb300/autotune.py) picks a route and shape per size
+ * bucket by timing. */
 tc_status tc_batch_plan_routes(tc_batch_t* out, const tc_plan_t* plans, const int32_t* routes,
                                int32_t n);
 

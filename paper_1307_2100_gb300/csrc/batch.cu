@@ -513,7 +513,7 @@ extern "C" tc_status tc_batch_plan_routes(tc_batch_t* out, const tc_plan_t* plan
     flops += P->info.flops;
     bytes += P->info.min_bytes;
     const int32_t route = routes ? routes[i] : -1;
-    if (route < -1 || route > 1) return TC_ERR_INVALID_ARG;
+    if (route < -1 || route > 3) return TC_ERR_INVALID_ARG;
     if (route == 1 && a.nbatch != 1) return TC_ERR_UNSUPPORTED;
     const bool to_tc =
         route == 1 || (route == -1 && a.M >= g_tc_min_mn && a.N >= g_tc_min_mn && a.nbatch == 1);
@@ -552,7 +552,10 @@ extern "C" tc_status tc_batch_plan_routes(tc_batch_t* out, const tc_plan_t* plan
       ++nsimt;
       const int64_t outs = a.M * a.N * a.nbatch;
       const int64_t K = a.K;
-      if (std::min(a.M, a.N) >= kTileMin) {  // 32x32 tiles; split K when there are few
+      // 32x32 tiles (route 2, or the rule for min(M, N) >= kTileMin); split K
+      // when there are few
+      const bool tiled = route == 2 || (route != 3 && std::min(a.M, a.N) >= kTileMin);
+      if (tiled) {
         const int64_t tiles = ((a.M + kTile - 1) / kTile) * ((a.N + kTile - 1) / kTile) * a.nbatch;
         int64_t nseg = std::max<int64_t>(1, std::min<int64_t>((K + 511) / 512, 1216 / tiles));
         const int64_t KS = (K + nseg - 1) / nseg;

@@ -653,10 +653,15 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
     const double dense = 2.0 * terms * 2.0 * (double)(M + N) * (double)Kt;
     packed_ok = (double)pk_layout(g, math).bytes <= 2.0 * dense + 64.0 * (1 << 20);
   }
+  // the selector's tile configuration, where it applies: it was timed with
+  // exactly that tile (packed operands too, whatever their padding costs, up
+  // to the 2 GB of workspace the timing allowed)
+  const bool packed_sel = Bt == 1 && kernel == K_GEMM_TC &&
+                          pk_layout(g, math).bytes <= ((size_t)2 << 30);
   if (tile < 0 && sel_tile >= 0 &&
-      ((kernel == K_GEMM_TC && (sel_tile != kTilePacked || packed_ok)) ||
+      ((kernel == K_GEMM_TC && (sel_tile != kTilePacked || packed_sel)) ||
        (kernel == K_GEMM_SIMT && sel_tile < num_tiles_simt(dtype))))
-    tile = sel_tile;  // the selector's tile configuration, where it applies
+    tile = sel_tile;
   if (kernel == K_GEMM_TC && (tile == kTilePacked || tile == kTilePackedWide) && Bt > 1) {
     delete P;  // packed operands: one GEMM, no batch group
     return TC_ERR_UNSUPPORTED;
@@ -682,12 +687,15 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   }
   if (tile < 0) {
     if (kernel == K_GEMM_SIMT) {
-      // enough 64x64 tiles to fill the GPU twice, else the small tile; FP64
-      // with a long K keeps the 64x64 tile and splits K instead
-      int64_t t64 = ((M + 63) / 64) * ((N + 63) / 64) * std::max<int64_t>(Bt, 1);
-      tile = t64 >= 2 * 152 ? 0 : 1;
+      // the largest tile that still gives every SM two (64x64, then 32x32),
+      // else 16x16 tiles; FP64 with a long K keeps the 64x64 tile and splits
+      // K instead
+      const int64_t bt = std::max<int64_t>(Bt, 1);
+      const int64_t t64 = ((M + 63) / 64) * ((N + 63) / 64) * bt;
+      const int64_t t32 = ((M + 31) / 32) * ((N + 31) / 32) * bt;
+      tile = t64 >= 2 * 152 ? 0 : t32 >= 2 * 152 ? 1 : 3;
       g.ksplit = 1;
-      if (tile == 1 && simt_ksplit(g, dtype, 0) > 1) tile = 0;
+      if (tile != 0 && simt_ksplit(g, dtype, 0) > 1) tile = 0;
     } else if (kernel == K_GEMM_TC) {
       // the gathering kernel for a batch of GEMMs (the slicing mapping) and
       // for skinny operands

@@ -10,7 +10,7 @@ A selector serves one storage type and math form (a "kind"):
           mapping and, for the fused and COPY+GEMM mappings, the
           packed-operand or the gathering tensor-core kernel;
   fp64    FP64 storage and math (the paper's own arithmetic); candidates are
-          the CUDA-core GEMM's three tile shapes (64x64, 32x32, 128x64) for
+          the CUDA-core GEMM's four tile shapes (64x64, 32x32, 128x64, 16x16) for
           the fused mapping, the slicing and COPY+GEMM mappings, GEMV, DOT and
           GER.  Its descriptors are those of the bf16x6 kind with at most
           2^34 flops (a second at the FP64 rate), so that timing stays bounded.
@@ -60,6 +60,7 @@ KINDS = {
         ("gemv", "gemv", -1),
         ("dot", "dot", -1),
         ("ger", "ger", -1),
+        ("fused_gemm_16x16", "fused_gemm", 3),
     ]},
 }
 CANDIDATE_SPECS = KINDS["bf16x6"]["candidates"]

@@ -254,7 +254,7 @@ def test_batch_routes_are_checked_before_any_allocation():
     h1 = tc.tc_plan(_t(p.A), _t(p.B), _t(p.C), tc.TC_F32, bf)
     h2 = tc.tc_plan(_t(s.A), _t(s.B), _t(s.C), tc.TC_F32, bf, tc.MAPPING["slice_gemm"])
     try:
-        for bad in ([2, -1], [-2, 0]):
+        for bad in ([4, -1], [-2, 0]):
             with pytest.raises(tc.TcError) as e:
                 tc.tc_batch_plan_routes([h1, h2], bad)
             assert e.value.status == 1
@@ -358,31 +358,33 @@ def test_batch_labels_form_the_batch_group():
     assert hi.batch == 45 and hi.K == 1
 
 
-def test_autotune_passes_repeat_while_flips_are_kept(monkeypatch):
-    """The route search repeats its visit of the buckets while a pass keeps a
-    flip: a bucket whose flip pays only after another bucket moved is found
-    in the second pass (fake plans and a fake timer, no GPU)."""
+def test_autotune_passes_repeat_while_changes_are_kept(monkeypatch):
+    """The search over route and shape (1 tensor cores, 2 CUDA-core tiles, 3
+    CUDA cores per output) repeats its visit of the buckets while a pass keeps
+    a change: a bucket whose change pays only after another bucket moved is
+    found in the second pass, and each visit keeps the faster of the two
+    shapes tried (fake plans and a fake timer, no GPU)."""
     from types import SimpleNamespace
     from paper_1307_2100_gb300 import autotune
-    # bucket X (4 items) and bucket Y (2 items, most flops: visited first),
-    # all on the CUDA cores
+    # bucket X (4 items, per output by the rule) and bucket Y (2 items, tiles
+    # by the rule; most flops: visited first)
     infos = ([SimpleNamespace(M=8, N=8, K=4, batch=1, flops=10.0)] * 4 +
              [SimpleNamespace(M=32, N=32, K=4, batch=1, flops=100.0)] * 2)
     monkeypatch.setattr(autotune.tc, "tc_plan_get_info", lambda h: infos[h])
+    table = {(3, 2): 10.0, (3, 1): 11.0, (3, 3): 12.0, (1, 2): 8.0, (2, 2): 9.5,
+             (1, 1): 6.0, (1, 3): 9.0, (2, 1): 7.0, (2, 3): 10.5}
 
     def fake_time(plans, routes, ptrs, stream, reps):
-        x, y = routes[0], routes[4]
-        # moving X to the tensor cores pays; moving Y pays only once X moved
-        return {(0, 0): 10.0, (1, 0): 8.0, (0, 1): 11.0, (1, 1): 6.0}[(int(x), int(y))]
+        return table[(int(routes[0]), int(routes[4]))]
 
     monkeypatch.setattr(autotune, "time_routes", fake_time)
     routes, rep = autotune.tune_routes(list(range(6)), None, None, passes=3)
     assert list(routes) == [1, 1, 1, 1, 1, 1]
     assert rep["default_ms"] == 10.0 and rep["tuned_ms"] == 6.0
-    kept = [(t["pass"], tuple(t["bucket"])) for t in rep["trials"] if t["kept"]]
-    assert kept == [(0, autotune.bucket_of(8, 8, 4)), (1, autotune.bucket_of(32, 32, 4))]
+    kept = [(t["pass"], tuple(t["bucket"]), t["route"]) for t in rep["trials"] if t["kept"]]
+    assert kept == [(0, autotune.bucket_of(8, 8, 4), 1), (1, autotune.bucket_of(32, 32, 4), 1)]
     routes1, rep1 = autotune.tune_routes(list(range(6)), None, None, passes=1)
-    assert list(routes1) == [1, 1, 1, 1, 0, 0] and rep1["tuned_ms"] == 8.0
+    assert list(routes1) == [1, 1, 1, 1, 2, 2] and rep1["tuned_ms"] == 8.0
 
 
 def test_storage_and_math_combinations_planned_or_refused():

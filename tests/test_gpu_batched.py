@@ -299,10 +299,11 @@ def test_batching_workload_every_item_against_oracle():
 
 
 def test_autotuned_routes():
-    """The route autotuner over the 512-item batching workload: the tuned
-    batch is no slower than the threshold rule it starts from, every route is
-    one of the two, and the tuned batch is within every item's bound of the
-    FP64 oracle (routes change the arithmetic: BF16x3 or FP32)."""
+    """The route and shape autotuner over the 512-item batching workload: the
+    tuned batch is no slower than the threshold rule it starts from, every
+    item takes one of the three shapes, and the tuned batch is within every
+    item's bound of the FP64 oracle (routes change the arithmetic: BF16x3 or
+    FP32)."""
     import torch
     from paper_1307_2100_gb300 import autotune, tc
     items = ts.batching_items(512)
@@ -311,7 +312,7 @@ def test_autotuned_routes():
     s = torch.cuda.Stream()
     routes, rep = autotune.tune_routes([pl.handle for pl in plans], (pa, pb, pc, al, be), s,
                                        reps=3)
-    assert set(np.unique(routes)) <= {0, 1}
+    assert set(np.unique(routes)) <= {1, 2, 3}
     assert rep["tuned_ms"] <= rep["default_ms"]
     batch = tc.tc_batch_plan_routes([pl.handle for pl in plans], routes)
     try:
@@ -327,3 +328,36 @@ def test_autotuned_routes():
         _, tot = tc_bounds(p, "bf16x3")
         ok, d = within(got, oracle.contract_problem(p), magnitude(p), p.C, tot)
         assert ok, (p.name, d)
+
+
+@pytest.mark.parametrize("shape", [2, 3])
+def test_cuda_core_shapes_forced_on_every_item(shape):
+    """Routes 2 (32 x 32 tiles) and 3 (a thread or warp per output) forced on
+    every item, whatever its GEMM view: each within the CUDA-core route's FP32
+    bound (40 * 2^-24 of sum |a||b|) of the FP64 oracle."""
+    import torch
+    from paper_1307_2100_gb300 import tc
+    items = small_items()
+    plans, bufs = _plans_and_buffers(items, "bf16x6")
+    batch = tc.tc_batch_plan_routes([pl.handle for pl in plans], [shape] * len(items))
+    try:
+        pa, pb, pc, al, be = _pointer_arrays(bufs, items)
+        for _, _, C in bufs:
+            C.fill_(float("nan"))
+        s = torch.cuda.current_stream().cuda_stream
+        tc.tc_contract_batched(batch, pa.data_ptr(), pb.data_ptr(), pc.data_ptr(), al.data_ptr(),
+                               be.data_ptr(), s)
+        torch.cuda.synchronize()
+        info = tc.tc_batch_get_info(batch)
+    finally:
+        tc.tc_batch_destroy(batch)
+    assert info.n_tc_items == 0
+    assert (info.n_simt_work == 0) if shape == 2 else (info.n_simt_tiles == 0)
+    for p, (_, _, C) in zip(items, bufs):
+        got = C.cpu().numpy().astype(np.float64)[: p.C.data.size]
+        mag = magnitude(p)
+        if p.beta != 0.0:
+            mag = mag + abs(p.beta) * np.abs(p.C.data.astype(np.float64))
+        ok, d = within(got, oracle.contract_problem(p), mag, p.C, 40 * 2.0 ** -24)
+        assert ok, (p.name, shape, d)
+

@@ -38,7 +38,7 @@ def test_fp64_small_workloads_all_mappings(mapping):
         assert err <= TOL_FP64, (p.name, mapping, err)
 
 
-@pytest.mark.parametrize("tile", [0, 1, 2])
+@pytest.mark.parametrize("tile", [0, 1, 2, 3])
 def test_fp64_gemm_tiles(tile):
     p = ts.fused_permute_48(n=17)
     ref = oracle.contract_problem(p)
@@ -174,3 +174,14 @@ def test_fp64_split_k_integer_bitwise():
     p = ts.problem("sk_int", "ai", "ib", "ab", dict(a=65, i=4099, b=64), 64,
                    dist="int", lo=-4, hi=4)
     np.testing.assert_array_equal(run(p, "fp64", "fused_gemm"), oracle.contract_problem(p))
+
+
+def test_small_gemms_take_16x16_tiles():
+    """48 GEMMs of 48^3 (config 1) give 192 tiles of 32 x 32, fewer than two
+    per SM: the planner takes 16 x 16 tiles (432), bitwise exact on integers."""
+    p = ts.slice_gemm_48(dist="int")
+    plans = []
+    got = run(p, "fp64", "auto", plan_out=plans)
+    assert plans[-1]["kernel"] == 1 and plans[-1]["tile"] == 3
+    np.testing.assert_array_equal(got, oracle.contract_problem(p))
+
