@@ -17,7 +17,8 @@ extern "C" tc_status tc_contract(tc_plan_t plan, double alpha, const void* A, co
   if (!C) return TC_ERR_INVALID_ARG;
   if (P->workspace > 0 && (!workspace || ws_bytes < P->workspace)) return TC_ERR_WORKSPACE;
   const bool packed = P->kernel == K_GEMM_FP8 ||
-                      (P->kernel == K_GEMM_TC && (P->tile == kTilePacked || P->tile == kTilePackedWide));
+                      (P->kernel == K_GEMM_TC && (P->tile == kTilePacked || P->tile == kTilePackedWide ||
+                                                  P->tile == kTilePackedPair));
   if (packed && (reinterpret_cast<uintptr_t>(workspace) & 15) != 0)
     return TC_ERR_INVALID_ARG;  // the packed operands are moved by 16-byte bulk copies
   if (P->empty_k || alpha == 0.0)
@@ -49,7 +50,8 @@ extern "C" tc_status tc_contract(tc_plan_t plan, double alpha, const void* A, co
   switch (P->kernel) {
     case K_GEMM_SIMT: return launch_gemm_simt(a, P->dtype, P->tile, stream);
     case K_GEMM_TC:
-      return (P->tile == kTilePacked || P->tile == kTilePackedWide)
+      return (P->tile == kTilePacked || P->tile == kTilePackedWide ||
+              P->tile == kTilePackedPair)
                  ? launch_gemm_tc_packed(a, P->math, P->dtype, P->tile, ws, stream)
                                     : launch_gemm_tc(a, P->math, stream);
     case K_GEMM_FP8: return launch_gemm_fp8(a, ws, stream);

@@ -195,9 +195,9 @@ __global__ void __launch_bounds__((TM / 4) * (TN / 4))
 }
 
 struct SimtTile { int tm, tn; };
-// Tile configurations 0-3.  16 x 16 tiles (16 threads) serve GEMMs too small
-// to give every SM two 32 x 32 tiles: their finer grain evens out the SMs'
-// FP64 work (48 GEMMs of 48^3: 432 tiles instead of 192).
+// Tile configurations 0-3.  16 x 16 tiles (16 threads: half-filled warps)
+// are a candidate of the FP64 selector for small GEMMs; the planner's default
+// is 64 x 64 or 32 x 32.
 static const SimtTile kSimtTiles[] = {{64, 64}, {32, 32}, {128, 64}, {16, 16}};
 int num_tiles_simt(tc_dtype) { return 4; }
 

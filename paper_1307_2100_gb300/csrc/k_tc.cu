@@ -590,12 +590,13 @@ uint64_t tiles_of(const GemmArgs& a) {
 // (k_tcpk.cu: a pack pass splits the operands once, the GEMM moves the terms
 // with bulk copies); tile 4: packed operands on 128 x 256 tiles with one
 // accumulator per tile (BF16, FP16 and BF16x3 only).
-int num_tiles_tc() { return 5; }
+int num_tiles_tc() { return 6; }
 int tc_chunk_kb(int math, int tile) {
   if (tile == 1) return 2;
   if (tile == 2) return 32;
   // wide tiles: chunks of 256 K for BF16x3, one chunk per tile otherwise
-  if (tile == kTilePackedWide) return math == TC_MATH_BF16X3 ? 8 : (1 << 30);
+  if (tile == kTilePackedWide || tile == kTilePackedPair)
+    return math == TC_MATH_BF16X3 ? 8 : (1 << 30);
   return (math == TC_MATH_BF16 || math == TC_MATH_FP16) ? (1 << 30) : 8;
 }
 

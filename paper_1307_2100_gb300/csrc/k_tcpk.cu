@@ -896,6 +896,309 @@ __global__ void __launch_bounds__(kThreadsW, 1) k_gemm_pkw(const __grid_constant
   }
 }
 
+// ---------------------------------------------------------------------------
+// CTA pairs on 256 x 256 tiles (tile configuration 5): the arithmetic of the
+// wide tiles (BF16, FP16, BF16x3: every product of a chunk into one FP32
+// accumulator, chunks added in registers), with two SMs on one tile.  Each
+// CTA of the pair holds its own 128 rows of A and its own 128-row half of B;
+// one thread of the first CTA issues tcgen05.mma.cta_group::2 (M = 256,
+// N = 256), which reads both CTAs' shared memory and leaves each CTA's 128
+// rows of D in that CTA's tensor memory.  A 32-K block thus moves NT x 16 KB
+// per SM for a 128 x 256 share of the outputs, against NT x 24 KB on the
+// wide tiles: a third fewer operand bytes per SM per multiply-add.
+// Hand-offs: each CTA's producer fills its own ring (full barrier of its own);
+// the second CTA's relay thread forwards each completed stage to the first
+// CTA's pfull barrier; the MMA thread's commits arrive on both CTAs' empty and
+// accf barriers; both CTAs' epilogues arrive on the first CTA's acce barrier.
+// ---------------------------------------------------------------------------
+template <int NT>
+struct CfgP {
+  static constexpr int BPS = NT == 1 ? 2 : 1;                 // 32-K blocks per stage
+  static constexpr uint32_t OPA = NT * TERM;                   // own A block (128 rows)
+  static constexpr uint32_t OPB = NT * TERM;                   // own B half block (128 rows)
+  static constexpr uint32_t STAGE = BPS * (OPA + OPB);         // A blocks, then B blocks
+  static constexpr int S = (int)(kRing / STAGE);               // 6 stages of 32 KB
+  static constexpr uint32_t OFF_COLC = S * STAGE;              // int64 colC[2][256]
+  static constexpr uint32_t OFF_BAR = OFF_COLC + 2 * TILE_W * 8;
+  static constexpr uint32_t NBAR = 3 * S + 4 + 1;              // full, pfull, empty, acc*, done
+  static constexpr uint32_t OFF_MISC = OFF_BAR + NBAR * 8;
+  static constexpr uint32_t BYTES = OFF_MISC + 16 + 1024;
+};
+
+// Work entry w of a pair launch: split-major over 256 x 256 pair tiles.
+struct JobP {
+  int tmp, tnp;       // pair tile: A tiles 2 tmp, 2 tmp + 1; B tiles 2 tnp, 2 tnp + 1
+  int split, k0, k1;
+};
+
+__device__ __forceinline__ JobP jobp_of(const PkItem& P, int64_t w) {
+  JobP j;
+  const int mp = (P.tiles_m + 1) / 2, np = (P.tiles_n + 1) / 2;
+  const int64_t ntiles = (int64_t)mp * np;
+  j.split = (int)(w / ntiles);
+  const int64_t t = w % ntiles;
+  if (P.raster) {
+    j.tnp = (int)(t % np);
+    j.tmp = (int)(t / np);
+  } else {
+    j.tmp = (int)(t % mp);
+    j.tnp = (int)(t / mp);
+  }
+  j.k0 = (int)((int64_t)j.split * P.nkb / P.ksplit);
+  j.k1 = (int)((int64_t)(j.split + 1) * P.nkb / P.ksplit);
+  return j;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(kThreadsW, 1) k_gemm_pkp(const __grid_constant__ PkLaunch L) {
+  using G = CfgP<NT>;
+  constexpr int S = G::S;
+  extern __shared__ uint8_t pkp_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(pkp_raw) + 1023) & ~(uintptr_t)1023);
+  int64_t* colC = reinterpret_cast<int64_t*>(smem + G::OFF_COLC);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + G::OFF_BAR);
+  uint64_t* full = bars;
+  uint64_t* pfull = bars + S;
+  uint64_t* empty = bars + 2 * S;
+  uint64_t* accf = bars + 3 * S;
+  uint64_t* acce = accf + 2;
+  uint64_t* done = acce + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + G::OFF_MISC);
+  volatile int* abort = reinterpret_cast<volatile int*>(smem + G::OFF_MISC + 4);
+  const PkItem& P = L.single;
+  const int ckb = max(P.chunk_kb, 1);
+  const uint32_t rank = cluster_ctarank();
+  const bool lead = rank == 0;
+  const int64_t pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&pfull[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&accf[i], 1);
+      mbar_init(&acce[i], 2 * kEpiThreadsW);  // both CTAs' epilogue threads
+    }
+    mbar_init(done, 1);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  cluster_sync();  // both CTAs' barriers exist before any remote arrival
+  if (warp == 1) tmem_alloc2(tmem_slot, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t sbase = smem_u32(smem);
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------------------ producer
+      // this CTA's 128 rows of A and its 128-row half of B, into its own ring
+      uint32_t g = 0;
+      bool ok = true;
+      for (int64_t w = pair; ok && w < L.nwork; w += npairs) {
+        const JobP J = jobp_of(P, w);
+        const int tm = 2 * J.tmp + (int)rank, tn = 2 * J.tnp + (int)rank;
+        const bool va = tm < P.tiles_m, vb = tn < P.tiles_n;   // else: rows the pair discards
+        const uint8_t* a = P.qa + (size_t)(va ? tm : 0) * P.nkb * G::OPA;
+        const uint8_t* b = P.qb + (size_t)(vb ? tn : 0) * P.nkb * G::OPB;
+        for (int kb = J.k0; kb < J.k1; kb += G::BPS, ++g) {
+          const int s = (int)(g % S);
+          if (g >= (uint32_t)S && !mbar_wait(&empty[s], ((g / S) - 1) & 1, abort, kTimeoutNs)) {
+            ok = false;
+            break;
+          }
+          const uint32_t nb = (uint32_t)min(G::BPS, J.k1 - kb);
+          const uint32_t dst = sbase + (uint32_t)s * G::STAGE;
+          mbar_arrive_expect_tx(&full[s], nb * ((va ? G::OPA : 0u) + (vb ? G::OPB : 0u)));
+          if (va) bulk_g2s(dst, a + (size_t)kb * G::OPA, nb * G::OPA, &full[s]);
+          if (vb) bulk_g2s(dst + G::BPS * G::OPA, b + (size_t)kb * G::OPB, nb * G::OPB, &full[s]);
+        }
+      }
+      // before exit: this CTA's copies have landed and the pair's last
+      // commits have arrived on its empty barriers
+      volatile int never = 0;
+      for (uint32_t i = g > (uint32_t)S ? g - S : 0; i < g; ++i)
+        mbar_wait(&full[i % S], (i / S) & 1, &never, kTimeoutNs);
+      for (uint32_t i = g > (uint32_t)S ? g - S : 0; i < g; ++i)
+        mbar_wait(&empty[i % S], (i / S) & 1, &never, kTimeoutNs);
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && !lead) {
+      // ------------------------------------------------ relay (second CTA)
+      // each stage of this CTA's ring, once complete, to the first CTA's pfull
+      uint32_t g = 0;
+      bool ok = true;
+      for (int64_t w = pair; ok && w < L.nwork; w += npairs) {
+        const JobP J = jobp_of(P, w);
+        for (int kb = J.k0; kb < J.k1; kb += G::BPS, ++g) {
+          const int s = (int)(g % S);
+          if (!mbar_wait(&full[s], (g / S) & 1, abort, kTimeoutNs)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_remote(&pfull[s], 0, 1);
+        }
+      }
+    } else if (lane == 0) {
+      // ------------------------------------------- MMA issue (first CTA)
+      const uint32_t idesc = L.idesc;
+      constexpr uint32_t LBO = (TILE / 8) * 128;
+      uint32_t g = 0, gc = 0;
+      bool ok = true;
+      for (int64_t w = pair; ok && w < L.nwork; w += npairs) {
+        const JobP J = jobp_of(P, w);
+        const int nchunks = (J.k1 - J.k0 + ckb - 1) / ckb;
+        int kb = J.k0;
+        for (int j = 0; ok && j < nchunks; ++j, ++gc) {
+          const uint32_t buf = gc & 1;
+          // both CTAs' epilogues drained chunk gc - 2 of this buffer
+          if (gc >= 2 && !mbar_wait(&acce[buf], ((gc >> 1) - 1) & 1, abort, kTimeoutNs)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t dacc = tmem + buf * TILE_W;
+          const int kend = min(J.k1, J.k0 + (j + 1) * ckb), kstart = kb;
+          for (; kb < kend; kb += G::BPS, ++g) {
+            const int s = (int)(g % S);
+            if (!mbar_wait(&full[s], (g / S) & 1, abort, kTimeoutNs) ||
+                !mbar_wait(&pfull[s], (g / S) & 1, abort, kTimeoutNs)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const int nb = min(G::BPS, kend - kb);
+            const uint32_t st = sbase + (uint32_t)s * G::STAGE;
+            for (int bi = 0; bi < nb; ++bi) {
+              const uint32_t sa = st + bi * G::OPA;
+              const uint32_t sb = st + G::BPS * G::OPA + bi * G::OPB;
+#pragma unroll
+              for (int kk = 0; kk < BK / 16; ++kk) {
+#pragma unroll
+                for (int pi = 0; pi < nprod(NT); ++pi) {
+                  const uint32_t acc = (kb > kstart || bi > 0 || kk > 0 || pi > 0) ? 1u : 0u;
+                  mma_bf16_pair(dacc, smem_desc(sa + kProdA[pi] * TERM + kk * 2 * LBO, LBO, 128),
+                                smem_desc(sb + kProdB[pi] * TERM + kk * 2 * LBO, LBO, 128),
+                                idesc, acc);
+                }
+              }
+            }
+            mma_commit_pair(&empty[s], 3);  // both CTAs may refill this stage
+          }
+          if (!ok) break;
+          mma_commit_pair(&accf[buf], 3);   // both CTAs' epilogues may drain it
+        }
+      }
+      mma_commit_pair(done, 1);
+      volatile int never = 0;
+      mbar_wait(done, 0, &never, kTimeoutNs);
+    }
+  } else {
+    // ------------------------------------------------------------- epilogue
+    // warps 2-9 of each CTA: lane quadrant q = warp % 4 and N-half hh =
+    // (warp - 2) / 4 of this CTA's 128 rows x 256 columns
+    const int ew = warp - 2;
+    const int q = warp & 3;
+    const int hh = ew >> 2;
+    const int row = q * 32 + lane;
+    const int etid = ew * 32 + lane;
+    uint32_t gc = 0, it = 0;
+    bool live = true;
+    auto setup = [&](int64_t w, int64_t* cc, JobP& J, int64_t& rc) {
+      J = jobp_of(P, w);
+      if (etid < TILE_W) {
+        const int64_t n = (int64_t)J.tnp * TILE_W + etid;
+        cc[etid] = n < P.N ? goff(P.gn, 2, (uint32_t)n) : -1;
+      }
+      const int64_t m = (int64_t)(2 * J.tmp + (int)rank) * TILE + row;
+      rc = m < P.M ? goff(P.gm, 2, (uint32_t)m) : -1;
+    };
+    JobP Jn;
+    int64_t rcn = -1;
+    if (pair < L.nwork) setup(pair, colC, Jn, rcn);
+    named_bar_sync(1, kEpiThreadsW);
+    for (int64_t w = pair; w < L.nwork; w += npairs, ++it) {
+      const JobP J = Jn;
+      const int64_t rc = rcn;
+      int64_t* cc = colC + (it & 1) * TILE_W;
+      if (w + npairs < L.nwork) setup(w + npairs, colC + ((it + 1) & 1) * TILE_W, Jn, rcn);
+      if (!live) {
+        named_bar_sync(1, kEpiThreadsW);
+        continue;
+      }
+      const int nchunks = (J.k1 - J.k0 + ckb - 1) / ckb;
+      float hi[128];
+      for (int j = 0; j < nchunks; ++j, ++gc) {
+        const uint32_t buf = gc & 1;
+        if (!warp_wait(&accf[buf], (gc >> 1) & 1, abort)) {
+          live = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + buf * TILE_W + hh * TILE;
+        if (j == 0) {
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            uint32_t r[16];
+            tmem_ld16(tl + c * 16, r);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) hi[c * 16 + i] = __uint_as_float(r[i]);
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            uint32_t r[16];
+            tmem_ld16(tl + c * 16, r);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) hi[c * 16 + i] = __fadd_rn(hi[c * 16 + i],
+                                                                    __uint_as_float(r[i]));
+          }
+        }
+        tc_fence_before();
+        if (lead) {
+          mbar_arrive(&acce[buf]);
+        } else {  // one arrival of 32 per warp on the first CTA's barrier
+          __syncwarp();
+          if (lane == 0) mbar_arrive_remote(&acce[buf], 0, 32);
+        }
+      }
+      const int tm = 2 * J.tmp + (int)rank, tn = 2 * J.tnp + hh;
+      if (live && tm < P.tiles_m && tn < P.tiles_n) {
+        if (P.ksplit > 1) {
+          float2* pp = P.part + ((size_t)J.split * P.tiles_m * P.tiles_n +
+                                 tile128_index(P, tm, tn)) * (size_t)(TILE * TILE) + row;
+#pragma unroll
+          for (int i = 0; i < 128; ++i) pp[(size_t)i * TILE] = make_float2(hi[i], 0.0f);
+        } else if (rc >= 0) {
+          const int64_t* ch = cc + hh * TILE;
+          if (L.out_type == 0) store_row<float, 128>(L.C, rc, ch, hi, L.alpha, L.beta);
+          else if (L.out_type == 1)
+            store_row<__nv_bfloat16, 128>(L.C, rc, ch, hi, L.alpha, L.beta);
+          else store_row<__half, 128>(L.C, rc, ch, hi, L.alpha, L.beta);
+        }
+      }
+      named_bar_sync(1, kEpiThreadsW);  // this tile's columns read; the next tile's written
+    }
+  }
+
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();  // the pair's MMAs and both epilogues are done with both CTAs' memory
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc2(tmem, kTmemCols);
+  }
+}
+
 // Split-K: C = alpha * (sum of the K ranges' partial sums, in order) + beta * C.
 __global__ void __launch_bounds__(256) k_pk_reduce(const __grid_constant__ PkLaunch L) {
   const PkItem& P = L.single;
@@ -1152,6 +1455,110 @@ tc_status launch_w(const GemmArgs& a, const PkLayout& L, void* ws, cudaStream_t 
   return TC_OK;
 }
 
+// One GEMM on CTA pairs (tile configuration 5), same arguments as launch.
+// The grid is two CTAs per pair, as many pairs as fit at once (persistent).
+template <int NT, typename In, bool F16T>
+tc_status launch_p(const GemmArgs& a, const PkLayout& L, void* ws, cudaStream_t s, int out_type) {
+  static int max_pairs = 0;
+  if (max_pairs == 0) {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess)
+      return TC_ERR_CUDA;
+    if (optin < (int)CfgP<NT>::BYTES) return TC_ERR_UNSUPPORTED;
+    if (cudaFuncSetAttribute(k_gemm_pkp<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)CfgP<NT>::BYTES) != cudaSuccess ||
+        cudaFuncSetAttribute(k_gemm_pkp<NT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 0) !=
+            cudaSuccess)
+      return TC_ERR_CUDA;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * 152, 1, 1);
+    cfg.blockDim = dim3(kThreadsW, 1, 1);
+    cfg.dynamicSmemBytes = CfgP<NT>::BYTES;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_gemm_pkp<NT>, &cfg) != cudaSuccess || n <= 0)
+      return TC_ERR_UNSUPPORTED;
+    max_pairs = n;
+  }
+  if (!set_pack_smem<NT, In, F16T>()) return TC_ERR_CUDA;
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  PackArgs pa;
+  std::memset(&pa, 0, sizeof(pa));
+  pa.gr[0] = a.gm;
+  pa.gr[1] = a.gn;
+  pa.gk = a.gk;
+  pa.in[0] = a.A;
+  pa.in[1] = a.B;
+  pa.q[0] = w + L.off_qa;
+  pa.q[1] = w + L.off_qb;
+  pa.rows[0] = a.M;
+  pa.rows[1] = a.N;
+  pa.K = a.K;
+  pa.tiles[0] = (int32_t)L.tiles_m;
+  pa.tiles[1] = (int32_t)L.tiles_n;
+  pa.nkb = (int32_t)L.nkb;
+  pa.npk = (int32_t)((L.nkb + PK / BK - 1) / (PK / BK));
+  pa.nblocks0 = L.tiles_m * pa.npk;
+  pa.rows_fast[0] = a.a_contig == CONTIG_MN;
+  pa.rows_fast[1] = a.b_contig == CONTIG_MN;
+  const int64_t nblocks = (L.tiles_m + L.tiles_n) * pa.npk;
+  if (nblocks > 0x7fffffffll) return TC_ERR_UNSUPPORTED;
+  k_bf16_pack<NT, In, F16T><<<(unsigned)nblocks, kPackThreads, kPackSmem, s>>>(pa);
+  if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;
+
+  PkLaunch g;
+  std::memset(&g, 0, sizeof(g));
+  PkItem& it = g.single;
+  it.gm = a.gm;
+  it.gn = a.gn;
+  it.qa = pa.q[0];
+  it.qb = pa.q[1];
+  it.M = a.M;
+  it.N = a.N;
+  it.tiles_m = (int32_t)L.tiles_m;
+  it.tiles_n = (int32_t)L.tiles_n;
+  it.nkb = (int32_t)L.nkb;
+  it.chunk_kb = a.chunk_kb;
+  it.raster = a.raster;
+  it.ksplit = pk_ksplit_p(a);
+  it.part = it.ksplit > 1 ? reinterpret_cast<float2*>(w + L.bytes) : nullptr;
+  g.C = a.C;
+  g.alpha = (float)a.alpha;
+  g.beta = (float)a.beta;
+  g.idesc = F16T ? idesc_f16(2 * TILE, TILE_W) : idesc_bf16(2 * TILE, TILE_W);
+  g.out_type = out_type;
+  g.nwork = ((L.tiles_m + 1) / 2) * ((L.tiles_n + 1) / 2) * it.ksplit;
+  const int pairs = (int)std::min<int64_t>(g.nwork, max_pairs);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(2 * pairs, 1, 1);
+  cfg.blockDim = dim3(kThreadsW, 1, 1);
+  cfg.dynamicSmemBytes = CfgP<NT>::BYTES;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, k_gemm_pkp<NT>, g) != cudaSuccess) return TC_ERR_CUDA;
+  if (it.ksplit > 1) {
+    const int64_t total = L.tiles_m * L.tiles_n * TILE * TILE;
+    const int rgrid = (int)std::min<int64_t>((total + 255) / 256, (int64_t)152 * 8);
+    k_pk_reduce<<<rgrid, 256, 0, s>>>(g);
+    if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;
+  }
+  return TC_OK;
+}
+
 template <int NT>
 tc_status launch_batch(const PkBatch& b, const void* const* A, const void* const* B,
                        void* const* C, const double* alpha, const double* beta, cudaStream_t s) {
@@ -1216,8 +1623,20 @@ int pk_ksplit_w(const GemmArgs& a) {
   return (int)std::max<int64_t>(1, std::min<int64_t>({want, nkb / 16, 64}));
 }
 
+// Split-K of the CTA pairs: pair tiles fewer than the pairs that fit share
+// out their K blocks, about one work entry per pair, each >= 512 K.
+int pk_ksplit_p(const GemmArgs& a) {
+  const int64_t tiles = (((a.M + pk::TILE - 1) / pk::TILE + 1) / 2) *
+                        (((a.N + pk::TILE - 1) / pk::TILE + 1) / 2);
+  const int64_t nkb = (a.K + pk::BK - 1) / pk::BK;
+  if (tiles <= 0 || tiles >= 76) return 1;
+  const int64_t want = (76 + tiles - 1) / tiles;
+  return (int)std::max<int64_t>(1, std::min<int64_t>({want, nkb / 16, 64}));
+}
+
 size_t pk_part_bytes(const GemmArgs& a, int tile) {
-  const int sp = tile == kTilePackedWide ? pk_ksplit_w(a) : pk_ksplit(a);
+  const int sp = tile == kTilePackedWide ? pk_ksplit_w(a)
+                 : tile == kTilePackedPair ? pk_ksplit_p(a) : pk_ksplit(a);
   if (sp <= 1) return 0;
   const int64_t tiles = ((a.M + pk::TILE - 1) / pk::TILE) * ((a.N + pk::TILE - 1) / pk::TILE);
   return (size_t)sp * (size_t)tiles * pk::TILE * pk::TILE * sizeof(float2);
@@ -1246,6 +1665,19 @@ tc_status launch_gemm_tc_packed(const GemmArgs& a, int math, tc_dtype dt, int ti
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const PkLayout L = pk_layout(a, math);
   if (L.tiles_m == 0 || L.tiles_n == 0 || L.nkb == 0) return TC_OK;
+  if (tile == kTilePackedPair) {
+    if (dt == TC_BF16 && math == TC_MATH_BF16)
+      return pk::launch_p<1, __nv_bfloat16, false>(a, L, ws, s, 1);
+    if (dt == TC_F16 && math == TC_MATH_FP16)
+      return pk::launch_p<1, __half, true>(a, L, ws, s, 2);
+    if (dt != TC_F32) return TC_ERR_UNSUPPORTED;
+    switch (math) {
+      case TC_MATH_BF16: return pk::launch_p<1, float, false>(a, L, ws, s, 0);
+      case TC_MATH_FP16: return pk::launch_p<1, float, true>(a, L, ws, s, 0);
+      case TC_MATH_BF16X3: return pk::launch_p<2, float, false>(a, L, ws, s, 0);
+      default: return TC_ERR_UNSUPPORTED;
+    }
+  }
   if (tile == kTilePackedWide) {
     if (dt == TC_BF16 && math == TC_MATH_BF16)
       return pk::launch_w<1, __nv_bfloat16, false>(a, L, ws, s, 1);

@@ -662,11 +662,14 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
       ((kernel == K_GEMM_TC && (sel_tile != kTilePacked || packed_sel)) ||
        (kernel == K_GEMM_SIMT && sel_tile < num_tiles_simt(dtype))))
     tile = sel_tile;
-  if (kernel == K_GEMM_TC && (tile == kTilePacked || tile == kTilePackedWide) && Bt > 1) {
+  const bool packed_tile =
+      tile == kTilePacked || tile == kTilePackedWide || tile == kTilePackedPair;
+  if (kernel == K_GEMM_TC && packed_tile && Bt > 1) {
     delete P;  // packed operands: one GEMM, no batch group
     return TC_ERR_UNSUPPORTED;
   }
-  if (kernel == K_GEMM_TC && tile == kTilePackedWide && math == TC_MATH_BF16X6) {
+  if (kernel == K_GEMM_TC && (tile == kTilePackedWide || tile == kTilePackedPair) &&
+      math == TC_MATH_BF16X6) {
     delete P;  // wide tiles keep one accumulator: not the FP32-class form
     return TC_ERR_UNSUPPORTED;
   }
@@ -678,7 +681,8 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
     if (Bt > 1 && dtype != TC_F32 && tile < 0) {
       kernel = K_GEMM_SIMT;
       P->kernel = kernel;
-    } else if (Bt > 1 || (tile >= 0 && tile != kTilePacked && tile != kTilePackedWide)) {
+    } else if (Bt > 1 || (tile >= 0 && tile != kTilePacked && tile != kTilePackedWide &&
+                          tile != kTilePackedPair)) {
       delete P;
       return TC_ERR_UNSUPPORTED;
     } else if (tile < 0) {
@@ -687,15 +691,13 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   }
   if (tile < 0) {
     if (kernel == K_GEMM_SIMT) {
-      // the largest tile that still gives every SM two (64x64, then 32x32),
-      // else 16x16 tiles; FP64 with a long K keeps the 64x64 tile and splits
-      // K instead
-      const int64_t bt = std::max<int64_t>(Bt, 1);
-      const int64_t t64 = ((M + 63) / 64) * ((N + 63) / 64) * bt;
-      const int64_t t32 = ((M + 31) / 32) * ((N + 31) / 32) * bt;
-      tile = t64 >= 2 * 152 ? 0 : t32 >= 2 * 152 ? 1 : 3;
+      // enough 64x64 tiles to fill the GPU twice, else 32x32 tiles; FP64
+      // with a long K keeps the 64x64 tile and splits K instead (the 16x16
+      // tile, half-filled warps, is left to the selector, which times it)
+      int64_t t64 = ((M + 63) / 64) * ((N + 63) / 64) * std::max<int64_t>(Bt, 1);
+      tile = t64 >= 2 * 152 ? 0 : 1;
       g.ksplit = 1;
-      if (tile != 0 && simt_ksplit(g, dtype, 0) > 1) tile = 0;
+      if (tile == 1 && simt_ksplit(g, dtype, 0) > 1) tile = 0;
     } else if (kernel == K_GEMM_TC) {
       // the gathering kernel for a batch of GEMMs (the slicing mapping) and
       // for skinny operands
@@ -718,7 +720,8 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   ws = (ws + 255) & ~(size_t)255;
   if (P->copy_which) ws += ((size_t)P->copy_elems * es + 255) & ~(size_t)255;
   if (kernel == K_GEMM_FP8) ws += fp8_layout(g).bytes;
-  if (kernel == K_GEMM_TC && (tile == kTilePacked || tile == kTilePackedWide))
+  if (kernel == K_GEMM_TC &&
+      (tile == kTilePacked || tile == kTilePackedWide || tile == kTilePackedPair))
     ws += pk_layout(g, math).bytes + pk_part_bytes(g, tile);  // packed terms, split-K partials
   if (kernel == K_GEMM_SIMT) {
     g.ksplit = simt_ksplit(g, dtype, tile);

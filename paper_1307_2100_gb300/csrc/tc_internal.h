@@ -145,6 +145,9 @@ constexpr int kTilePacked = 3;
 // Packed operands on 128 x 256 tiles with one FP32 accumulator per tile (the
 // BF16, FP16 and BF16x3 forms).
 constexpr int kTilePackedWide = 4;
+// Packed operands on 256 x 256 tiles shared by a pair of SMs (a cluster of
+// two CTAs on tcgen05.mma.cta_group::2), same arithmetic as tile 4.
+constexpr int kTilePackedPair = 5;
 struct PkLayout {
   int64_t tiles_m, tiles_n, nkb;
   size_t off_qa, off_qb, bytes;
@@ -154,6 +157,7 @@ PkLayout pk_layout(const GemmArgs& a, int math);
 // and the bytes of its partial sums (part of the plan's workspace).
 int pk_ksplit(const GemmArgs& a);
 int pk_ksplit_w(const GemmArgs& a);
+int pk_ksplit_p(const GemmArgs& a);
 size_t pk_part_bytes(const GemmArgs& a, int tile);
 // 32-K blocks per ring stage of the packed GEMM for a math form: every
 // accumulation chunk must hold a multiple of them.

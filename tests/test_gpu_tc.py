@@ -168,34 +168,39 @@ def test_packed_split_k():
     assert tiles < 152 and info["workspace"] > 0
 
 
-# tile 4: packed operands on 128 x 256 tiles, one FP32 accumulator per tile
+# tile 4: packed operands on 128 x 256 tiles, one FP32 accumulator per chunk;
+# tile 5: the same arithmetic on 256 x 256 tiles shared by a pair of SMs
 WIDE_FORMS = ["bf16", "bf16x3"]
+WIDE_TILES = [4, 5]
 
 
+@pytest.mark.parametrize("tile", WIDE_TILES)
 @pytest.mark.parametrize("form", WIDE_FORMS)
-def test_wide_tiles_integer_inputs_exact(form):
+def test_wide_tiles_integer_inputs_exact(form, tile):
     p = ts.problem("int", "iajb", "jcid", "abcd", dict(i=9, a=70, j=11, b=3, c=65, d=5), 61,
                    dist="int", dtype=np.float32, lo=-4, hi=4)
-    got = run(p, form, "fused_gemm", 4)
+    got = run(p, form, "fused_gemm", tile)
     np.testing.assert_array_equal(got, oracle.contract_problem(p))
 
 
+@pytest.mark.parametrize("tile", WIDE_TILES)
 @pytest.mark.parametrize("form", WIDE_FORMS)
-def test_wide_tiles_against_method_and_fp64_oracles(form):
+def test_wide_tiles_against_method_and_fp64_oracles(form, tile):
     """Shapes of every kind, an odd number of 128-column tiles (the second
     half of the last wide tile missing), ragged K, a long K and a split-K
     shape (few tiles): within the one-accumulator bound of the form's oracle."""
     cases = shapes() + [
         f32(ts.problem("odd_n", "ai", "ib", "ab", dict(a=129, i=45, b=260), 84)),
         f32(ts.problem("one_n", "ai", "ib", "ab", dict(a=300, i=70, b=60), 85)),
+        f32(ts.problem("one_m", "ai", "ib", "ab", dict(a=100, i=70, b=390), 86)),
         f32(ts.problem("longk", "ai", "ib", "ab", dict(a=200, i=3000, b=150), 83)),
         f32(ts.problem("splitk", "iajb", "icjd", "abcd",
                        dict(i=60, j=55, a=30, b=8, c=30, d=9), 121)),
     ]
     for p in cases:
         plans = []
-        got = run(p, form, "fused_gemm", 4, plan_out=plans)
-        assert plans[-1]["tile"] == 4
+        got = run(p, form, "fused_gemm", tile, plan_out=plans)
+        assert plans[-1]["tile"] == tile
         mag = magnitude(p)
         acc, _ = tc_bounds(p, form, single=True)
         ok, d = within(got, op.contract_form(p, form), mag, p.C, acc)
@@ -204,11 +209,12 @@ def test_wide_tiles_against_method_and_fp64_oracles(form):
         assert ok, (p.name, form, "fp64", d)
 
 
-def test_wide_tiles_alpha_beta():
+@pytest.mark.parametrize("tile", WIDE_TILES)
+def test_wide_tiles_alpha_beta(tile):
     p = f32(ts.direct_gemm_64(n=21))
     p.C.data = np.linspace(-2, 2, p.C.data.size).astype(np.float32)
     p.alpha, p.beta = -1.5, 0.25
-    got = run(p, "bf16x3", "fused_gemm", 4)
+    got = run(p, "bf16x3", "fused_gemm", tile)
     acc, _ = tc_bounds(p, "bf16x3", single=True)
     mag = magnitude(p) + abs(p.beta) * np.abs(p.C.data.astype(np.float64))
     assert within(got, op.contract_form(p, "bf16x3"), mag, p.C, acc)[0]
@@ -219,11 +225,14 @@ def test_wide_tiles_refuse_the_fp32_class_form():
     p = f32(ts.direct_gemm_64(n=9))
     d = ((p.A.labels, p.A.extents, p.A.strides), (p.B.labels, p.B.extents, p.B.strides),
          (p.C.labels, p.C.extents, p.C.strides))
-    assert tc.tc_plan_status(*d, tc.TC_F32, tc.MATH["bf16x6"], tc.MAPPING["fused_gemm"], 4) == 5
+    for tile in WIDE_TILES:
+        assert tc.tc_plan_status(*d, tc.TC_F32, tc.MATH["bf16x6"], tc.MAPPING["fused_gemm"],
+                                 tile) == 5
 
 
+@pytest.mark.parametrize("tile", WIDE_TILES)
 @pytest.mark.parametrize("form", WIDE_FORMS)
-def test_wide_tiles_precision_workload_full_size_sampled(form):
+def test_wide_tiles_precision_workload_full_size_sampled(form, tile):
     p = ts.precision_ccd()
     s = random_output_indices(p, 96, seed=3)
     ref64 = sample_outputs(p, s)
@@ -234,7 +243,7 @@ def test_wide_tiles_precision_workload_full_size_sampled(form):
     pm.A.data = np.abs(p.A.data)
     pm.B.data = np.abs(p.B.data)
     mag = sample_outputs(pm, s)
-    got = run(p, form, "fused_gemm", 4)
+    got = run(p, form, "fused_gemm", tile)
     g = gather(got, p.C, s)
     acc, _ = tc_bounds(p, form, single=True)
     assert np.linalg.norm(g - sample_outputs_form(p, s, form)) <= acc * np.linalg.norm(mag)
