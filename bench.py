@@ -984,15 +984,17 @@ def batch_measure(items, math, steps, warmup, autotune=True, separate=True, refs
     with torch.cuda.graph(g, stream=s):
         batched()
 
-    def timed(fn, n):
+    def timed(fn, n, label):
         ts_ = []
         for _ in range(n):
             with torch.cuda.stream(s):
                 flush.zero_()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.nvtx.range_push(label)   # marks the timed launches for profilers
                 e0.record(s)
                 fn()
                 e1.record(s)
+                torch.cuda.nvtx.range_pop()
             torch.cuda.synchronize()
             ts_.append(e0.elapsed_time(e1))
         return float(np.median(ts_))
@@ -1002,8 +1004,8 @@ def batch_measure(items, math, steps, warmup, autotune=True, separate=True, refs
         clocks.start()
     for _ in range(warmup):
         g.replay()
-    t_graph = timed(g.replay, steps)
-    t_sep = timed(separate_calls, max(1, min(steps, 2))) if separate else None
+    t_graph = timed(g.replay, steps, "batched")
+    t_sep = timed(separate_calls, max(1, min(steps, 2)), "separate") if separate else None
     clk = clocks.stop() if clocks else None
     status = tc.tc_device_status(s.cuda_stream)
     g.replay()
