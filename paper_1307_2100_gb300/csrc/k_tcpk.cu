@@ -27,6 +27,7 @@
 //                               strided store.
 // Tensor memory (512 columns): [0,256) main accumulators, [256,384) the
 // correction accumulator, [384,512) the high word of the chunk sum.
+#include <cuda.h>  // CUtensorMap and cuTensorMapEncodeTiled's types (entry point via the runtime)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -229,6 +230,7 @@ __global__ void __launch_bounds__(kPackThreads) k_bf16_pack_batch(
 // One GEMM on packed operands (a single contraction, or one item of a batch).
 // The launch holds it in kernel parameters, a batch in device memory.
 struct PkLaunch {
+  CUtensorMap tma_a, tma_b;  // CTA pairs: the packed operands as rows of 2 KB
   PkItem single;             // items == nullptr: tiles 0 .. nwork - 1 of this GEMM
   void* C;                   // elements of out_type
   float alpha, beta;
@@ -906,10 +908,12 @@ __global__ void __launch_bounds__(kThreadsW, 1) k_gemm_pkw(const __grid_constant
 // rows of D in that CTA's tensor memory.  A 32-K block thus moves NT x 16 KB
 // per SM for a 128 x 256 share of the outputs, against NT x 24 KB on the
 // wide tiles: a third fewer operand bytes per SM per multiply-add.
-// Hand-offs: each CTA's producer fills its own ring (full barrier of its own);
-// the second CTA's relay thread forwards each completed stage to the first
-// CTA's pfull barrier; the MMA thread's commits arrive on both CTAs' empty and
-// accf barriers; both CTAs' epilogues arrive on the first CTA's acce barrier.
+// Hand-offs: each CTA's producer fills its own ring with tiled TMA loads
+// (tensor maps viewing the packed operands as rows of 2 KB) that complete on
+// the first CTA's full barrier (cta_group::2), whose expected byte count
+// covers both CTAs' loads; the MMA thread's commits arrive on both CTAs'
+// empty and accf barriers; both CTAs' epilogues arrive on the first CTA's
+// acce barrier.
 // ---------------------------------------------------------------------------
 template <int NT>
 struct CfgP {
@@ -920,7 +924,7 @@ struct CfgP {
   static constexpr int S = (int)(kRing / STAGE);               // 6 stages of 32 KB
   static constexpr uint32_t OFF_COLC = S * STAGE;              // int64 colC[2][256]
   static constexpr uint32_t OFF_BAR = OFF_COLC + 2 * TILE_W * 8;
-  static constexpr uint32_t NBAR = 3 * S + 4 + 1;              // full, pfull, empty, acc*, done
+  static constexpr uint32_t NBAR = 2 * S + 4 + 1;              // full, empty, acc*, done
   static constexpr uint32_t OFF_MISC = OFF_BAR + NBAR * 8;
   static constexpr uint32_t BYTES = OFF_MISC + 16 + 1024;
 };
@@ -959,9 +963,8 @@ __global__ void __launch_bounds__(kThreadsW, 1) k_gemm_pkp(const __grid_constant
   int64_t* colC = reinterpret_cast<int64_t*>(smem + G::OFF_COLC);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + G::OFF_BAR);
   uint64_t* full = bars;
-  uint64_t* pfull = bars + S;
-  uint64_t* empty = bars + 2 * S;
-  uint64_t* accf = bars + 3 * S;
+  uint64_t* empty = bars + S;
+  uint64_t* accf = bars + 2 * S;
   uint64_t* acce = accf + 2;
   uint64_t* done = acce + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + G::OFF_MISC);
@@ -976,7 +979,6 @@ __global__ void __launch_bounds__(kThreadsW, 1) k_gemm_pkp(const __grid_constant
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&pfull[s], 1);
       mbar_init(&empty[s], 1);
     }
     for (int i = 0; i < 2; ++i) {
@@ -998,54 +1000,47 @@ __global__ void __launch_bounds__(kThreadsW, 1) k_gemm_pkp(const __grid_constant
   if (warp == 0) {
     if (lane == 0) {
       // ------------------------------------------------------------ producer
-      // this CTA's 128 rows of A and its 128-row half of B, into its own ring
+      // this CTA's 128 rows of A and its 128-row half of B, into its own ring;
+      // the loads of both CTAs complete on the first CTA's full barrier
       uint32_t g = 0;
       bool ok = true;
       for (int64_t w = pair; ok && w < L.nwork; w += npairs) {
         const JobP J = jobp_of(P, w);
-        const int tm = 2 * J.tmp + (int)rank, tn = 2 * J.tnp + (int)rank;
+        const int tm0 = 2 * J.tmp, tn0 = 2 * J.tnp;
+        const int tm = tm0 + (int)rank, tn = tn0 + (int)rank;
         const bool va = tm < P.tiles_m, vb = tn < P.tiles_n;   // else: rows the pair discards
-        const uint8_t* a = P.qa + (size_t)(va ? tm : 0) * P.nkb * G::OPA;
-        const uint8_t* b = P.qb + (size_t)(vb ? tn : 0) * P.nkb * G::OPB;
+        const uint32_t pair_block = (tm0 < P.tiles_m ? G::OPA : 0u) +
+                                    (tm0 + 1 < P.tiles_m ? G::OPA : 0u) +
+                                    (tn0 < P.tiles_n ? G::OPB : 0u) +
+                                    (tn0 + 1 < P.tiles_n ? G::OPB : 0u);
         for (int kb = J.k0; kb < J.k1; kb += G::BPS, ++g) {
           const int s = (int)(g % S);
           if (g >= (uint32_t)S && !mbar_wait(&empty[s], ((g / S) - 1) & 1, abort, kTimeoutNs)) {
             ok = false;
             break;
           }
-          const uint32_t nb = (uint32_t)min(G::BPS, J.k1 - kb);
+          const int nb = min(G::BPS, J.k1 - kb);
           const uint32_t dst = sbase + (uint32_t)s * G::STAGE;
-          mbar_arrive_expect_tx(&full[s], nb * ((va ? G::OPA : 0u) + (vb ? G::OPB : 0u)));
-          if (va) bulk_g2s(dst, a + (size_t)kb * G::OPA, nb * G::OPA, &full[s]);
-          if (vb) bulk_g2s(dst + G::BPS * G::OPA, b + (size_t)kb * G::OPB, nb * G::OPB, &full[s]);
+          if (lead) mbar_arrive_expect_tx(&full[s], (uint32_t)nb * pair_block);
+          const uint32_t mb = mapa_shared(smem_u32(&full[s]), 0);
+          for (int bi = 0; bi < nb; ++bi) {
+            if (va)
+              tma_load_2d_pair(dst + bi * G::OPA, &L.tma_a, 0,
+                               (int32_t)(((int64_t)tm * P.nkb + kb + bi) * (G::OPA / 2048)), mb);
+            if (vb)
+              tma_load_2d_pair(dst + G::BPS * G::OPA + bi * G::OPB, &L.tma_b, 0,
+                               (int32_t)(((int64_t)tn * P.nkb + kb + bi) * (G::OPB / 2048)), mb);
+          }
         }
       }
-      // before exit: this CTA's copies have landed and the pair's last
-      // commits have arrived on its empty barriers
+      // before exit: the pair's last commits have arrived on this CTA's empty
+      // barriers (so its MMAs, and the loads they read, are done)
       volatile int never = 0;
-      for (uint32_t i = g > (uint32_t)S ? g - S : 0; i < g; ++i)
-        mbar_wait(&full[i % S], (i / S) & 1, &never, kTimeoutNs);
       for (uint32_t i = g > (uint32_t)S ? g - S : 0; i < g; ++i)
         mbar_wait(&empty[i % S], (i / S) & 1, &never, kTimeoutNs);
     }
   } else if (warp == 1) {
-    if (lane == 0 && !lead) {
-      // ------------------------------------------------ relay (second CTA)
-      // each stage of this CTA's ring, once complete, to the first CTA's pfull
-      uint32_t g = 0;
-      bool ok = true;
-      for (int64_t w = pair; ok && w < L.nwork; w += npairs) {
-        const JobP J = jobp_of(P, w);
-        for (int kb = J.k0; kb < J.k1; kb += G::BPS, ++g) {
-          const int s = (int)(g % S);
-          if (!mbar_wait(&full[s], (g / S) & 1, abort, kTimeoutNs)) {
-            ok = false;
-            break;
-          }
-          mbar_arrive_remote(&pfull[s], 0, 1);
-        }
-      }
-    } else if (lane == 0) {
+    if (lane == 0 && lead) {
       // ------------------------------------------- MMA issue (first CTA)
       const uint32_t idesc = L.idesc;
       constexpr uint32_t LBO = (TILE / 8) * 128;
@@ -1067,8 +1062,7 @@ __global__ void __launch_bounds__(kThreadsW, 1) k_gemm_pkp(const __grid_constant
           const int kend = min(J.k1, J.k0 + (j + 1) * ckb), kstart = kb;
           for (; kb < kend; kb += G::BPS, ++g) {
             const int s = (int)(g % S);
-            if (!mbar_wait(&full[s], (g / S) & 1, abort, kTimeoutNs) ||
-                !mbar_wait(&pfull[s], (g / S) & 1, abort, kTimeoutNs)) {
+            if (!mbar_wait(&full[s], (g / S) & 1, abort, kTimeoutNs)) {
               ok = false;
               break;
             }
@@ -1455,6 +1449,45 @@ tc_status launch_w(const GemmArgs& a, const PkLayout& L, void* ws, cudaStream_t 
   return TC_OK;
 }
 
+// cuTensorMapEncodeTiled, looked up once through the runtime (the library
+// links no driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// The packed blocks of one operand as a 2-D tensor of 8-byte elements in rows
+// of 2 KB (256 elements); a box is box_bytes (one block, NT x 8 KB).  Loads
+// always start at x = 0, so every copy starts on a 2 KB boundary.
+bool rows_map(CUtensorMap* m, const void* base, size_t bytes, uint32_t box_bytes) {
+  EncodeTiledFn f = encode_tiled();
+  if (!f || bytes == 0 || bytes % 2048 || box_bytes % 2048 || box_bytes / 2048 > 256 ||
+      (reinterpret_cast<uintptr_t>(base) & 15))
+    return false;
+  cuuint64_t dims[2] = {256, (cuuint64_t)(bytes / 2048)};
+  cuuint64_t strides[1] = {2048};
+  cuuint32_t box[2] = {256, box_bytes / 2048};
+  cuuint32_t es[2] = {1, 1};
+  return f(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void*>(base), dims, strides, box, es,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // One GEMM on CTA pairs (tile configuration 5), same arguments as launch.
 // The grid is two CTAs per pair, as many pairs as fit at once (persistent).
 template <int NT, typename In, bool F16T>
@@ -1536,6 +1569,9 @@ tc_status launch_p(const GemmArgs& a, const PkLayout& L, void* ws, cudaStream_t 
   g.idesc = F16T ? idesc_f16(2 * TILE, TILE_W) : idesc_bf16(2 * TILE, TILE_W);
   g.out_type = out_type;
   g.nwork = ((L.tiles_m + 1) / 2) * ((L.tiles_n + 1) / 2) * it.ksplit;
+  if (!rows_map(&g.tma_a, it.qa, (size_t)L.tiles_m * L.nkb * CfgP<NT>::OPA, CfgP<NT>::OPA) ||
+      !rows_map(&g.tma_b, it.qb, (size_t)L.tiles_n * L.nkb * CfgP<NT>::OPB, CfgP<NT>::OPB))
+    return TC_ERR_CUDA;
   const int pairs = (int)std::min<int64_t>(g.nwork, max_pairs);
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];

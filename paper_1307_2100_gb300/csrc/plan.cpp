@@ -686,7 +686,7 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
       delete P;
       return TC_ERR_UNSUPPORTED;
     } else if (tile < 0) {
-      tile = kTilePacked;
+      tile = (M > 128 && N > 128) ? kTilePackedPair : kTilePacked;
     }
   }
   if (tile < 0) {
@@ -701,8 +701,12 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
     } else if (kernel == K_GEMM_TC) {
       // the gathering kernel for a batch of GEMMs (the slicing mapping) and
       // for skinny operands
-      // BF16x3 moves fewer operand bytes per multiply-add on 128 x 256 tiles
+      // the one-accumulator forms (BF16, FP16, BF16x3) on CTA pairs when both
+      // M and N span two tiles or more (a third fewer operand bytes per SM),
+      // BF16x3 on 128 x 256 tiles when only N does
+      const bool one_acc = math == TC_MATH_BF16 || math == TC_MATH_FP16 || math == TC_MATH_BF16X3;
       tile = !packed_ok ? 0
+             : (one_acc && M > 128 && N > 128) ? kTilePackedPair
              : (math == TC_MATH_BF16X3 && N > 128) ? kTilePackedWide : kTilePacked;
     } else {
       tile = 0;

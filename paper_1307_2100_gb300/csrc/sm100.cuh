@@ -167,6 +167,28 @@ __device__ __forceinline__ void mbar_arrive_remote(uint64_t* bar, uint32_t rank,
                : "memory");
 }
 
+// Shared::cluster address of the object at local shared address `addr` in CTA
+// `rank` of the cluster.
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+
+// Tiled TMA load of the 2-D box at (x, y) of tensor map `tmap` (a
+// __grid_constant__ kernel parameter) into this CTA's shared memory at `dst`,
+// completing its bytes on the mbarrier at shared::cluster address `mbar`,
+// which may lie in either CTA of the pair (cta_group::2).  x must be a
+// multiple of 16 bytes' worth of elements; this library always passes 0.
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const void* tmap, int32_t x,
+                                                 int32_t y, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2 "
+      "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+
 // Tensor memory of a CTA pair: one warp of each CTA allocates (and frees)
 // together.
 __device__ __forceinline__ void tmem_alloc2(uint32_t* dst_smem, uint32_t ncols) {
