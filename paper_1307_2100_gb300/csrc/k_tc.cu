@@ -595,8 +595,10 @@ int tc_chunk_kb(int math, int tile) {
   if (tile == 1) return 2;
   if (tile == 2) return 32;
   // wide tiles: chunks of 256 K for BF16x3, one chunk per tile otherwise
+  // one chunk per tile for BF16 and FP16 (their error is the operands'
+  // rounding); 256-K chunks for the split forms
   if (tile == kTilePackedWide || tile == kTilePackedPair)
-    return math == TC_MATH_BF16X3 ? 8 : (1 << 30);
+    return (math == TC_MATH_BF16X3 || math == TC_MATH_BF16X6) ? 8 : (1 << 30);
   return (math == TC_MATH_BF16 || math == TC_MATH_FP16) ? (1 << 30) : 8;
 }
 

@@ -1193,6 +1193,331 @@ __global__ void __launch_bounds__(kThreadsW, 1) k_gemm_pkp(const __grid_constant
   }
 }
 
+// ---------------------------------------------------------------------------
+// CTA pairs for the split forms with compensated sums (tile configuration 5
+// with BF16x6): the arithmetic of the 128 x 128 kernel -- the main product in
+// a double-buffered accumulator emptied every chunk into a compensated sum,
+// the correction products in an accumulator of their own -- on 256 x 128
+// tiles shared by two SMs (tcgen05.mma.cta_group::2, M = 256, N = 128).  Each
+// CTA holds its own 128 rows of A and a 64-row half of the tile's B (the rows
+// of its rank, taken by TMA at an x offset of 1 KB from the packed 128-row
+// blocks): 25 % fewer operand bytes per SM per multiply-add, while each CTA's
+// tensor memory keeps the 128 x 128 kernel's layout for its own rows.  The
+// loads of both CTAs complete on the first CTA's full barrier; the MMA
+// thread's commits arrive on both CTAs' barriers; both epilogues arrive on the
+// first CTA's acce barrier.
+// ---------------------------------------------------------------------------
+template <int NT>
+struct CfgP6 {
+  static constexpr int BPS = 2;                                // 32-K blocks per stage
+  static constexpr uint32_t OPA = NT * TERM;                   // own A block (128 rows)
+  static constexpr uint32_t HTERM = TERM / 2;                  // one term of a 64-row B half
+  static constexpr uint32_t OPB = NT * HTERM;                  // own B half block
+  static constexpr uint32_t STAGE = BPS * (OPA + OPB);         // 72 KB for BF16x6
+  static constexpr uint32_t RING = 216 * 1024;
+  static constexpr int S = (int)(RING / STAGE);                // 3 stages
+  static constexpr uint32_t OFF_COLC = S * STAGE;              // int64 colC[2][128]
+  static constexpr uint32_t OFF_BAR = OFF_COLC + 2 * TILE * 8;
+  static constexpr uint32_t NBAR = 2 * S + 4 + 1;
+  static constexpr uint32_t OFF_MISC = OFF_BAR + NBAR * 8;
+  static constexpr uint32_t BYTES = OFF_MISC + 16 + 1024;
+};
+
+// Work entry w: split-major over the 256 x 128 pair tiles (A tiles 2 tmp and
+// 2 tmp + 1, B tile tn).
+struct JobP6 {
+  int tmp, tn, split, k0, k1;
+};
+
+__device__ __forceinline__ JobP6 jobp6_of(const PkItem& P, int64_t w) {
+  JobP6 j;
+  const int mp = (P.tiles_m + 1) / 2;
+  const int64_t ntiles = (int64_t)mp * P.tiles_n;
+  j.split = (int)(w / ntiles);
+  const int64_t t = w % ntiles;
+  if (P.raster) {
+    j.tn = (int)(t % P.tiles_n);
+    j.tmp = (int)(t / P.tiles_n);
+  } else {
+    j.tmp = (int)(t % mp);
+    j.tn = (int)(t / mp);
+  }
+  j.k0 = (int)((int64_t)j.split * P.nkb / P.ksplit);
+  j.k1 = (int)((int64_t)(j.split + 1) * P.nkb / P.ksplit);
+  return j;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(kThreads, 1) k_gemm_pkp6(const __grid_constant__ PkLaunch L) {
+  using G = CfgP6<NT>;
+  constexpr int S = G::S;
+  extern __shared__ uint8_t pkp6_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(pkp6_raw) + 1023) & ~(uintptr_t)1023);
+  int64_t* colC = reinterpret_cast<int64_t*>(smem + G::OFF_COLC);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + G::OFF_BAR);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + S;
+  uint64_t* accf = bars + 2 * S;
+  uint64_t* acce = accf + 2;
+  uint64_t* done = acce + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + G::OFF_MISC);
+  volatile int* abort = reinterpret_cast<volatile int*>(smem + G::OFF_MISC + 4);
+  const PkItem& P = L.single;
+  const int ckb = max(P.chunk_kb, 1);
+  const uint32_t rank = cluster_ctarank();
+  const bool lead = rank == 0;
+  const int64_t pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&accf[i], 1);
+      mbar_init(&acce[i], 2 * kEpiThreads);  // both CTAs' epilogue threads
+    }
+    mbar_init(done, 1);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  cluster_sync();  // both CTAs' barriers exist before any remote arrival
+  if (warp == 1) tmem_alloc2(tmem_slot, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t sbase = smem_u32(smem);
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------------------ producer
+      // this CTA's 128 rows of A and the 64 rows of B of its rank
+      uint32_t g = 0;
+      bool ok = true;
+      for (int64_t w = pair; ok && w < L.nwork; w += npairs) {
+        const JobP6 J = jobp6_of(P, w);
+        const int tm0 = 2 * J.tmp, tm = tm0 + (int)rank;
+        const bool va = tm < P.tiles_m;   // else: rows the pair discards
+        const uint32_t pair_block = (tm0 < P.tiles_m ? G::OPA : 0u) +
+                                    (tm0 + 1 < P.tiles_m ? G::OPA : 0u) + 2 * G::OPB;
+        for (int kb = J.k0; kb < J.k1; kb += G::BPS, ++g) {
+          const int s = (int)(g % S);
+          if (g >= (uint32_t)S && !mbar_wait(&empty[s], ((g / S) - 1) & 1, abort, kTimeoutNs)) {
+            ok = false;
+            break;
+          }
+          const int nb = min(G::BPS, J.k1 - kb);
+          const uint32_t dst = sbase + (uint32_t)s * G::STAGE;
+          if (lead) mbar_arrive_expect_tx(&full[s], (uint32_t)nb * pair_block);
+          const uint32_t mb = mapa_shared(smem_u32(&full[s]), 0);
+          for (int bi = 0; bi < nb; ++bi) {
+            if (va)
+              tma_load_2d_pair(dst + bi * G::OPA, &L.tma_a, 0,
+                               (int32_t)(((int64_t)tm * P.nkb + kb + bi) * (G::OPA / 2048)), mb);
+            const int64_t brow = ((int64_t)J.tn * P.nkb + kb + bi) * (NT * TERM / 2048);
+#pragma unroll
+            for (int t = 0; t < NT; ++t)
+              tma_load_2d_pair(dst + G::BPS * G::OPA + bi * G::OPB + t * G::HTERM, &L.tma_b,
+                               (int32_t)(rank * 128), (int32_t)(brow + t * (TERM / 2048)), mb);
+          }
+        }
+      }
+      volatile int never = 0;
+      for (uint32_t i = g > (uint32_t)S ? g - S : 0; i < g; ++i)
+        mbar_wait(&empty[i % S], (i / S) & 1, &never, kTimeoutNs);
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && lead) {
+      // ------------------------------------------- MMA issue (first CTA)
+      const uint32_t idesc = L.idesc;
+      constexpr uint32_t LBOA = (TILE / 8) * 128;        // 128-row A blocks
+      constexpr uint32_t LBOB = (TILE / 2 / 8) * 128;    // 64-row B halves
+      uint32_t g = 0, gc = 0;
+      bool ok = true;
+      for (int64_t w = pair; ok && w < L.nwork; w += npairs) {
+        const JobP6 J = jobp6_of(P, w);
+        const int nchunks = (J.k1 - J.k0 + ckb - 1) / ckb;
+        // the correction accumulator, both main buffers and the high words are
+        // free once both CTAs drained the previous tile's last chunk
+        if (gc >= 1 && !mbar_wait(&acce[(gc - 1) & 1], ((gc - 1) >> 1) & 1, abort, kTimeoutNs)) {
+          ok = false;
+          break;
+        }
+        int kb = J.k0;
+        for (int j = 0; ok && j < nchunks; ++j, ++gc) {
+          const uint32_t buf = gc & 1;
+          if (gc >= 2 && !mbar_wait(&acce[buf], ((gc >> 1) - 1) & 1, abort, kTimeoutNs)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t dmain = tmem + buf * TILE;
+          const int kend = min(J.k1, J.k0 + (j + 1) * ckb), kstart = kb;
+          for (; kb < kend; kb += G::BPS, ++g) {
+            const int s = (int)(g % S);
+            if (!mbar_wait(&full[s], (g / S) & 1, abort, kTimeoutNs)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const int nb = min(G::BPS, kend - kb);
+            const uint32_t st = sbase + (uint32_t)s * G::STAGE;
+            for (int bi = 0; bi < nb; ++bi) {
+              const uint32_t sa = st + bi * G::OPA;
+              const uint32_t sb = st + G::BPS * G::OPA + bi * G::OPB;
+#pragma unroll
+              for (int kk = 0; kk < BK / 16; ++kk) {
+                const bool first = bi == 0 && kk == 0;
+                mma_bf16_pair(dmain, smem_desc(sa + kk * 2 * LBOA, LBOA, 128),
+                              smem_desc(sb + kk * 2 * LBOB, LBOB, 128), idesc,
+                              (kb > kstart || !first) ? 1u : 0u);
+#pragma unroll
+                for (int pi = 1; pi < nprod(NT); ++pi)
+                  mma_bf16_pair(tmem + COL_CORR,
+                                smem_desc(sa + kProdA[pi] * TERM + kk * 2 * LBOA, LBOA, 128),
+                                smem_desc(sb + kProdB[pi] * G::HTERM + kk * 2 * LBOB, LBOB, 128),
+                                idesc, (kb > J.k0 || !first || pi > 1) ? 1u : 0u);
+              }
+            }
+            mma_commit_pair(&empty[s], 3);  // both CTAs may refill this stage
+          }
+          if (!ok) break;
+          mma_commit_pair(&accf[buf], 3);   // both CTAs' epilogues may drain it
+        }
+      }
+      mma_commit_pair(done, 1);
+      volatile int never = 0;
+      mbar_wait(done, 0, &never, kTimeoutNs);
+    }
+  } else {
+    // ------------------------------------------------------------- epilogue
+    // each CTA drains its own 128 rows: two warps per lane quadrant, 64
+    // columns each, as in the 128 x 128 kernel
+    const int ew = warp - 2;
+    const int q = warp & 3;
+    const int h = ew >> 2;
+    const int row = q * 32 + lane;
+    const int etid = ew * 32 + lane;
+    const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)h * 64;
+    uint32_t gc = 0;
+    int64_t it = 0;
+    bool live = true;
+    auto release = [&](uint32_t buf) {  // this CTA's epilogue is done with buffer buf
+      if (lead) {
+        mbar_arrive(&acce[buf]);
+      } else {
+        __syncwarp();
+        if (lane == 0) mbar_arrive_remote(&acce[buf], 0, 32);
+      }
+    };
+    auto setup = [&](int64_t w, int64_t* cc, JobP6& J, int64_t& rc) {
+      J = jobp6_of(P, w);
+      if (etid < TILE) {
+        const int64_t n = (int64_t)J.tn * TILE + etid;
+        cc[etid] = n < P.N ? goff(P.gn, 2, (uint32_t)n) : -1;
+      }
+      const int64_t m = (int64_t)(2 * J.tmp + (int)rank) * TILE + row;
+      rc = m < P.M ? goff(P.gm, 2, (uint32_t)m) : -1;
+    };
+    JobP6 Jn;
+    int64_t rcn = -1;
+    if (pair < L.nwork) setup(pair, colC, Jn, rcn);
+    named_bar_sync(1, kEpiThreads);
+    for (int64_t w = pair; w < L.nwork; w += npairs, ++it) {
+      const JobP6 J = Jn;
+      const int64_t rc = rcn;
+      int64_t* cc = colC + (it & 1) * TILE;
+      if (w + npairs < L.nwork) setup(w + npairs, colC + ((it + 1) & 1) * TILE, Jn, rcn);
+      if (!live) {
+        named_bar_sync(1, kEpiThreads);
+        continue;
+      }
+      const int nchunks = (J.k1 - J.k0 + ckb - 1) / ckb;
+      const int tm = 2 * J.tmp + (int)rank;
+      const bool partial = P.ksplit > 1;
+      float2* pp = (partial && tm < P.tiles_m)
+                       ? P.part + ((size_t)J.split * P.tiles_m * P.tiles_n +
+                                   tile128_index(P, tm, J.tn)) * (size_t)(TILE * TILE) +
+                             (size_t)h * 64 * TILE + row
+                       : nullptr;
+      float lo[64];
+#pragma unroll
+      for (int i = 0; i < 64; ++i) lo[i] = 0.0f;
+      for (int j = 0; j < nchunks; ++j, ++gc) {
+        const uint32_t buf = gc & 1;
+        if (!warp_wait(&accf[buf], (gc >> 1) & 1, abort)) {
+          live = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t tmain = tl + buf * TILE;
+        if (j + 1 < nchunks) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            uint32_t mv[16], hv[16];
+            tmem_ld16(tmain + c * 16, mv);
+            if (j > 0) tmem_ld16(tl + COL_HI + c * 16, hv);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const float hi0 = j > 0 ? __uint_as_float(hv[i]) : 0.0f;
+              float e;
+              const float s = two_sum(hi0, __uint_as_float(mv[i]), e);
+              lo[c * 16 + i] = __fadd_rn(lo[c * 16 + i], e);
+              hv[i] = __float_as_uint(s);
+            }
+            tmem_st16(tl + COL_HI + c * 16, hv);
+          }
+          tmem_wait_st();
+          tc_fence_before();
+          release(buf);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            uint32_t mv[16], hv[16], cv[16];
+            tmem_ld16(tmain + c * 16, mv);
+            if (j > 0) tmem_ld16(tl + COL_HI + c * 16, hv);
+            if (NT > 1) tmem_ld16(tl + COL_CORR + c * 16, cv);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const float hi0 = j > 0 ? __uint_as_float(hv[i]) : 0.0f;
+              float e;
+              const float s = two_sum(hi0, __uint_as_float(mv[i]), e);
+              float r = __fadd_rn(lo[c * 16 + i], e);
+              if (NT > 1) r = __fadd_rn(r, __uint_as_float(cv[i]));
+              if (pp) pp[(size_t)(c * 16 + i) * TILE] = make_float2(s, r);
+              else lo[c * 16 + i] = __fadd_rn(s, r);
+            }
+          }
+          tc_fence_before();
+          release(buf);  // main, correction and high word are free
+          if (!partial && rc >= 0) {
+            const int64_t* ch = cc + h * 64;
+            if (L.out_type == 0) store_row<float, 64>(L.C, rc, ch, lo, L.alpha, L.beta);
+            else if (L.out_type == 1)
+              store_row<__nv_bfloat16, 64>(L.C, rc, ch, lo, L.alpha, L.beta);
+            else store_row<__half, 64>(L.C, rc, ch, lo, L.alpha, L.beta);
+          }
+        }
+      }
+      named_bar_sync(1, kEpiThreads);  // this tile's columns read; the next tile's written
+    }
+  }
+
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();  // the pair's MMAs and both epilogues are done with both CTAs' memory
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc2(tmem, kTmemCols);
+  }
+}
+
 // Split-K: C = alpha * (sum of the K ranges' partial sums, in order) + beta * C.
 __global__ void __launch_bounds__(256) k_pk_reduce(const __grid_constant__ PkLaunch L) {
   const PkItem& P = L.single;
@@ -1472,16 +1797,18 @@ EncodeTiledFn encode_tiled() {
 }
 
 // The packed blocks of one operand as a 2-D tensor of 8-byte elements in rows
-// of 2 KB (256 elements); a box is box_bytes (one block, NT x 8 KB).  Loads
-// always start at x = 0, so every copy starts on a 2 KB boundary.
-bool rows_map(CUtensorMap* m, const void* base, size_t bytes, uint32_t box_bytes) {
+// of 2 KB (256 elements); a box is box_x elements (box_x x 8 bytes) of
+// box_bytes / 2048 rows.  Loads start at x = 0, or at x = 128 for the second
+// half of a row (1 KB: a 16-byte multiple, as tiled TMA copies need).
+bool rows_map(CUtensorMap* m, const void* base, size_t bytes, uint32_t box_bytes,
+              uint32_t box_x = 256) {
   EncodeTiledFn f = encode_tiled();
   if (!f || bytes == 0 || bytes % 2048 || box_bytes % 2048 || box_bytes / 2048 > 256 ||
-      (reinterpret_cast<uintptr_t>(base) & 15))
+      box_x == 0 || box_x > 256 || (reinterpret_cast<uintptr_t>(base) & 15))
     return false;
   cuuint64_t dims[2] = {256, (cuuint64_t)(bytes / 2048)};
   cuuint64_t strides[1] = {2048};
-  cuuint32_t box[2] = {256, box_bytes / 2048};
+  cuuint32_t box[2] = {box_x, box_bytes / 2048};
   cuuint32_t es[2] = {1, 1};
   return f(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void*>(base), dims, strides, box, es,
            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -1595,6 +1922,106 @@ tc_status launch_p(const GemmArgs& a, const PkLayout& L, void* ws, cudaStream_t 
   return TC_OK;
 }
 
+// BF16x6 on CTA pairs (tile configuration 5): FP32 storage.
+template <int NT>
+tc_status launch_p6(const GemmArgs& a, const PkLayout& L, void* ws, cudaStream_t s) {
+  static int max_pairs = 0;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  if (max_pairs == 0) {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess)
+      return TC_ERR_CUDA;
+    if (optin < (int)CfgP6<NT>::BYTES) return TC_ERR_UNSUPPORTED;
+    if (cudaFuncSetAttribute(k_gemm_pkp6<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)CfgP6<NT>::BYTES) != cudaSuccess)
+      return TC_ERR_CUDA;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * 152, 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = CfgP6<NT>::BYTES;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_gemm_pkp6<NT>, &cfg) != cudaSuccess || n <= 0)
+      return TC_ERR_UNSUPPORTED;
+    max_pairs = n;
+  }
+  if (!set_pack_smem<NT, float, false>()) return TC_ERR_CUDA;
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  PackArgs pa;
+  std::memset(&pa, 0, sizeof(pa));
+  pa.gr[0] = a.gm;
+  pa.gr[1] = a.gn;
+  pa.gk = a.gk;
+  pa.in[0] = a.A;
+  pa.in[1] = a.B;
+  pa.q[0] = w + L.off_qa;
+  pa.q[1] = w + L.off_qb;
+  pa.rows[0] = a.M;
+  pa.rows[1] = a.N;
+  pa.K = a.K;
+  pa.tiles[0] = (int32_t)L.tiles_m;
+  pa.tiles[1] = (int32_t)L.tiles_n;
+  pa.nkb = (int32_t)L.nkb;
+  pa.npk = (int32_t)((L.nkb + PK / BK - 1) / (PK / BK));
+  pa.nblocks0 = L.tiles_m * pa.npk;
+  pa.rows_fast[0] = a.a_contig == CONTIG_MN;
+  pa.rows_fast[1] = a.b_contig == CONTIG_MN;
+  const int64_t nblocks = (L.tiles_m + L.tiles_n) * pa.npk;
+  if (nblocks > 0x7fffffffll) return TC_ERR_UNSUPPORTED;
+  k_bf16_pack<NT, float, false><<<(unsigned)nblocks, kPackThreads, kPackSmem, s>>>(pa);
+  if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;
+
+  PkLaunch g;
+  std::memset(&g, 0, sizeof(g));
+  PkItem& it = g.single;
+  it.gm = a.gm;
+  it.gn = a.gn;
+  it.qa = pa.q[0];
+  it.qb = pa.q[1];
+  it.M = a.M;
+  it.N = a.N;
+  it.tiles_m = (int32_t)L.tiles_m;
+  it.tiles_n = (int32_t)L.tiles_n;
+  it.nkb = (int32_t)L.nkb;
+  it.chunk_kb = a.chunk_kb;
+  if (max(a.chunk_kb, 1) % CfgP6<NT>::BPS != 0) return TC_ERR_UNSUPPORTED;
+  it.raster = a.raster;
+  it.ksplit = pk_ksplit_p6(a);
+  it.part = it.ksplit > 1 ? reinterpret_cast<float2*>(w + L.bytes) : nullptr;
+  g.C = a.C;
+  g.alpha = (float)a.alpha;
+  g.beta = (float)a.beta;
+  g.idesc = idesc_bf16(2 * TILE, TILE);
+  g.out_type = 0;
+  g.nwork = ((L.tiles_m + 1) / 2) * L.tiles_n * it.ksplit;
+  if (!rows_map(&g.tma_a, it.qa, (size_t)L.tiles_m * L.nkb * CfgP6<NT>::OPA, CfgP6<NT>::OPA) ||
+      !rows_map(&g.tma_b, it.qb, (size_t)L.tiles_n * L.nkb * NT * TERM, 4 * 2048, 128))
+    return TC_ERR_CUDA;
+  const int pairs = (int)std::min<int64_t>(g.nwork, max_pairs);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * pairs, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = CfgP6<NT>::BYTES;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, k_gemm_pkp6<NT>, g) != cudaSuccess) return TC_ERR_CUDA;
+  if (it.ksplit > 1) {
+    const int64_t total = L.tiles_m * L.tiles_n * TILE * TILE;
+    const int rgrid = (int)std::min<int64_t>((total + 255) / 256, (int64_t)152 * 8);
+    k_pk_reduce<<<rgrid, 256, 0, s>>>(g);
+    if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;
+  }
+  return TC_OK;
+}
+
 template <int NT>
 tc_status launch_batch(const PkBatch& b, const void* const* A, const void* const* B,
                        void* const* C, const double* alpha, const double* beta, cudaStream_t s) {
@@ -1670,9 +2097,21 @@ int pk_ksplit_p(const GemmArgs& a) {
   return (int)std::max<int64_t>(1, std::min<int64_t>({want, nkb / 16, 64}));
 }
 
+// Split-K of the BF16x6 CTA pairs (256 x 128 pair tiles): the same rule.
+int pk_ksplit_p6(const GemmArgs& a) {
+  const int64_t tiles = (((a.M + pk::TILE - 1) / pk::TILE + 1) / 2) *
+                        ((a.N + pk::TILE - 1) / pk::TILE);
+  const int64_t nkb = (a.K + pk::BK - 1) / pk::BK;
+  if (tiles <= 0 || tiles >= 76) return 1;
+  const int64_t want = (76 + tiles - 1) / tiles;
+  return (int)std::max<int64_t>(1, std::min<int64_t>({want, nkb / 16, 64}));
+}
+
 size_t pk_part_bytes(const GemmArgs& a, int tile) {
   const int sp = tile == kTilePackedWide ? pk_ksplit_w(a)
-                 : tile == kTilePackedPair ? pk_ksplit_p(a) : pk_ksplit(a);
+                 : tile == kTilePackedPair ? (a.math == TC_MATH_BF16X6 ? pk_ksplit_p6(a)
+                                                                       : pk_ksplit_p(a))
+                 : pk_ksplit(a);
   if (sp <= 1) return 0;
   const int64_t tiles = ((a.M + pk::TILE - 1) / pk::TILE) * ((a.N + pk::TILE - 1) / pk::TILE);
   return (size_t)sp * (size_t)tiles * pk::TILE * pk::TILE * sizeof(float2);
@@ -1701,6 +2140,8 @@ tc_status launch_gemm_tc_packed(const GemmArgs& a, int math, tc_dtype dt, int ti
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const PkLayout L = pk_layout(a, math);
   if (L.tiles_m == 0 || L.tiles_n == 0 || L.nkb == 0) return TC_OK;
+  if (tile == kTilePackedPair && math == TC_MATH_BF16X6)
+    return dt == TC_F32 ? pk::launch_p6<3>(a, L, ws, s) : TC_ERR_UNSUPPORTED;
   if (tile == kTilePackedPair) {
     if (dt == TC_BF16 && math == TC_MATH_BF16)
       return pk::launch_p<1, __nv_bfloat16, false>(a, L, ws, s, 1);

@@ -668,8 +668,7 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
     delete P;  // packed operands: one GEMM, no batch group
     return TC_ERR_UNSUPPORTED;
   }
-  if (kernel == K_GEMM_TC && (tile == kTilePackedWide || tile == kTilePackedPair) &&
-      math == TC_MATH_BF16X6) {
+  if (kernel == K_GEMM_TC && tile == kTilePackedWide && math == TC_MATH_BF16X6) {
     delete P;  // wide tiles keep one accumulator: not the FP32-class form
     return TC_ERR_UNSUPPORTED;
   }
@@ -707,6 +706,7 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
       const bool one_acc = math == TC_MATH_BF16 || math == TC_MATH_FP16 || math == TC_MATH_BF16X3;
       tile = !packed_ok ? 0
              : (one_acc && M > 128 && N > 128) ? kTilePackedPair
+             : (math == TC_MATH_BF16X6 && M > 128) ? kTilePackedPair
              : (math == TC_MATH_BF16X3 && N > 128) ? kTilePackedWide : kTilePacked;
     } else {
       tile = 0;

@@ -158,6 +158,7 @@ PkLayout pk_layout(const GemmArgs& a, int math);
 int pk_ksplit(const GemmArgs& a);
 int pk_ksplit_w(const GemmArgs& a);
 int pk_ksplit_p(const GemmArgs& a);
+int pk_ksplit_p6(const GemmArgs& a);
 size_t pk_part_bytes(const GemmArgs& a, int tile);
 // 32-K blocks per ring stage of the packed GEMM for a math form: every
 // accumulation chunk must hold a multiple of them.

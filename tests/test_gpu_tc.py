@@ -249,3 +249,54 @@ def test_wide_tiles_precision_workload_full_size_sampled(form, tile):
     assert np.linalg.norm(g - sample_outputs_form(p, s, form)) <= acc * np.linalg.norm(mag)
     assert np.linalg.norm(g - ref64) <= (acc + SPLIT_ERR[form]) * np.linalg.norm(mag)
 
+
+
+# BF16x6 on CTA pairs (tile 5): 256 x 128 tiles, the 128 x 128 kernel's
+# compensated chunk sums and separate correction accumulator
+def test_bf16x6_pairs_integer_inputs_exact():
+    p = ts.problem("int", "iajb", "jcid", "abcd", dict(i=9, a=70, j=11, b=3, c=65, d=5), 61,
+                   dist="int", dtype=np.float32, lo=-4, hi=4)
+    plans = []
+    got = run(p, "bf16x6", "fused_gemm", 5, plan_out=plans)
+    assert plans[-1]["tile"] == 5
+    np.testing.assert_array_equal(got, oracle.contract_problem(p))
+
+
+def test_bf16x6_pairs_against_method_and_fp64_oracles():
+    """Every shape kind, an odd number of 128-row tiles (the second CTA of the
+    last pair holding no rows of C), one row tile, long K and split-K."""
+    cases = shapes() + [
+        f32(ts.problem("odd_m", "ai", "ib", "ab", dict(a=390, i=45, b=260), 87)),
+        f32(ts.problem("one_m", "ai", "ib", "ab", dict(a=100, i=70, b=390), 86)),
+        f32(ts.problem("longk", "ai", "ib", "ab", dict(a=200, i=3000, b=150), 83)),
+        f32(ts.problem("splitk", "iajb", "icjd", "abcd",
+                       dict(i=60, j=55, a=30, b=8, c=30, d=9), 121)),
+    ]
+    for p in cases:
+        got = run(p, "bf16x6", "fused_gemm", 5)
+        mag = magnitude(p)
+        acc, tot = tc_bounds(p, "bf16x6")
+        ok, d = within(got, op.contract_form(p, "bf16x6"), mag, p.C, acc)
+        assert ok, (p.name, "method", d)
+        ok, d = within(got, oracle.contract_problem(p), mag, p.C, tot)
+        assert ok, (p.name, "fp64", d)
+
+
+def test_bf16x6_pairs_alpha_beta():
+    p = f32(ts.direct_gemm_64(n=21))
+    p.C.data = np.linspace(-2, 2, p.C.data.size).astype(np.float32)
+    p.alpha, p.beta = -1.5, 0.25
+    got = run(p, "bf16x6", "fused_gemm", 5)
+    acc, _ = tc_bounds(p, "bf16x6")
+    mag = magnitude(p) + abs(p.beta) * np.abs(p.C.data.astype(np.float64))
+    assert within(got, op.contract_form(p, "bf16x6"), mag, p.C, acc)[0]
+
+
+def test_bf16x6_pairs_precision_workload_full_size_fp32_class():
+    p = ts.precision_ccd()
+    s = random_output_indices(p, 96, seed=3)
+    ref64 = sample_outputs(p, s)
+    got = run(p, "bf16x6", "fused_gemm", 5)
+    g = gather(got, p.C, s)
+    assert np.all(np.isfinite(got))
+    assert oracle.rel_fro(g, ref64) <= FP32_CLASS
