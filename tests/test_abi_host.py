@@ -210,12 +210,13 @@ def test_fp8_k_order_follows_a_whichever_operand_is_first():
 
 
 def test_tensor_core_tile_defaults():
-    # one GEMM: packed operands (tile 3) with a workspace; a batch of GEMMs
-    # (the slicing mapping): the gathering kernel, no workspace
+    # one GEMM: packed operands on CTA pairs (tile 5: M spans two row tiles)
+    # with a workspace; a batch of GEMMs (the slicing mapping): the gathering
+    # kernel, no workspace
     p = ts.fused_permute_48(n=40)
     bf = tc.MATH["bf16x6"]
     info = plan_info(p, bf, dtype=tc.TC_F32)
-    assert info.tile == 3 and info.batch == 1
+    assert info.tile == 5 and info.batch == 1 and info.M > 128
     tm, tn, nkb = -(-info.M // 128), -(-info.N // 128), -(-info.K // 32)
     r = lambda x: -(-x // 256) * 256
     assert info.workspace == r(tm * nkb * 3 * 8192) + r(tn * nkb * 3 * 8192)
@@ -400,3 +401,20 @@ def test_storage_and_math_combinations_planned_or_refused():
             assert (st == 0) == ((dt, m) in ok), (dt, m, st)
     assert tc.tc_plan_status(*d, tc.TC_F32, tc.MATH["fp16"]) == 0
     assert tc.tc_plan_status(*d, 4, tc.MATH["fp32"]) == 1          # no such storage type
+
+
+def test_packed_tile_defaults_by_form_and_shape():
+    """Packed one-GEMM plans: CTA pairs (tile 5) for BF16 / FP16 / BF16x3 when
+    M and N span two 128-row tiles and for BF16x6 when M does; 128 x 256
+    tiles (4) for BF16x3 when only N does; 128 x 128 tiles (3) otherwise."""
+    big = ts.problem("big", "ai", "ib", "ab", dict(a=300, i=64, b=300), 1)
+    skinny_m = ts.problem("sm", "ai", "ib", "ab", dict(a=100, i=64, b=300), 2)
+    skinny_n = ts.problem("sn", "ai", "ib", "ab", dict(a=300, i=64, b=100), 3)
+    want = {("bf16", "big"): 5, ("bf16x3", "big"): 5, ("bf16x6", "big"): 5, ("fp16", "big"): 5,
+            ("bf16", "sm"): 3, ("bf16x3", "sm"): 4, ("bf16x6", "sm"): 3,
+            ("bf16", "sn"): 3, ("bf16x3", "sn"): 3, ("bf16x6", "sn"): 5}
+    for (m, name), tile in want.items():
+        p = {"big": big, "sm": skinny_m, "sn": skinny_n}[name]
+        info = plan_info(p, tc.MATH[m], dtype=tc.TC_F32)
+        assert info.tile == tile, (m, name, info.tile, info.M, info.N)
+
