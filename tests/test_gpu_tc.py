@@ -220,14 +220,15 @@ def test_wide_tiles_alpha_beta(tile):
     assert within(got, op.contract_form(p, "bf16x3"), mag, p.C, acc)[0]
 
 
-def test_wide_tiles_refuse_the_fp32_class_form():
+def test_wide_tiles_refuse_the_fp32_class_form_pairs_take_it():
     from paper_1307_2100_gb300 import tc
     p = f32(ts.direct_gemm_64(n=9))
     d = ((p.A.labels, p.A.extents, p.A.strides), (p.B.labels, p.B.extents, p.B.strides),
          (p.C.labels, p.C.extents, p.C.strides))
-    for tile in WIDE_TILES:
-        assert tc.tc_plan_status(*d, tc.TC_F32, tc.MATH["bf16x6"], tc.MAPPING["fused_gemm"],
-                                 tile) == 5
+    # tile 4 keeps one accumulator per chunk; the pairs (tile 5) run BF16x6
+    # with the compensated sums of the 128 x 128 kernel
+    assert tc.tc_plan_status(*d, tc.TC_F32, tc.MATH["bf16x6"], tc.MAPPING["fused_gemm"], 4) == 5
+    assert tc.tc_plan_status(*d, tc.TC_F32, tc.MATH["bf16x6"], tc.MAPPING["fused_gemm"], 5) == 0
 
 
 @pytest.mark.parametrize("tile", WIDE_TILES)
