@@ -2087,13 +2087,14 @@ int pk_ksplit_w(const GemmArgs& a) {
 }
 
 // Split-K of the CTA pairs: pair tiles fewer than the pairs that fit share
-// out their K blocks, about one work entry per pair, each >= 512 K.
+// out their K blocks, at most one work entry per pair (a second, partial
+// round of entries would double the time), each >= 512 K.
 int pk_ksplit_p(const GemmArgs& a) {
   const int64_t tiles = (((a.M + pk::TILE - 1) / pk::TILE + 1) / 2) *
                         (((a.N + pk::TILE - 1) / pk::TILE + 1) / 2);
   const int64_t nkb = (a.K + pk::BK - 1) / pk::BK;
   if (tiles <= 0 || tiles >= 76) return 1;
-  const int64_t want = (76 + tiles - 1) / tiles;
+  const int64_t want = 76 / tiles;
   return (int)std::max<int64_t>(1, std::min<int64_t>({want, nkb / 16, 64}));
 }
 
@@ -2103,7 +2104,7 @@ int pk_ksplit_p6(const GemmArgs& a) {
                         ((a.N + pk::TILE - 1) / pk::TILE);
   const int64_t nkb = (a.K + pk::BK - 1) / pk::BK;
   if (tiles <= 0 || tiles >= 76) return 1;
-  const int64_t want = (76 + tiles - 1) / tiles;
+  const int64_t want = 76 / tiles;
   return (int)std::max<int64_t>(1, std::min<int64_t>({want, nkb / 16, 64}));
 }
 
