@@ -606,16 +606,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_pk(const __grid_constant__
 // Wide tiles (tile configuration 4): 128 x 256 outputs per CTA for the BF16,
 // FP16 and BF16x3 forms.  Every product of a K chunk goes into one FP32
 // accumulator of 256 columns; tensor memory double-buffers it ([0,256) and
-// [256,512), each two N = 128 halves), and sixteen epilogue warps (64
-// columns each) add every drained chunk into a running FP32 sum held in
-// registers.  The tensor cores' FP32 accumulation is not round-to-nearest, so
+// [256,512), each two N = 128 halves), and eight epilogue warps (one lane
+// quadrant and 128 columns each) add every drained chunk into a running FP32
+// sum held in registers.  The tensor cores' FP32 accumulation is not round-to-nearest, so
 // its error grows with the number of blocks it adds: BF16x3 drains every
 // 256 K (as the 128 x 128 kernel does), BF16 and FP16 (whose error is their
 // operands' rounding) once per tile.  A 32-K block moves NT x 8 KB of A for
 // NT x 16 KB of B: 27 % fewer operand bytes per multiply-add than the
 // 128 x 128 tile; each stage's A block is shared by the two N = 128 MMAs of
-// the two halves.  BF16x6 keeps the 128 x 128 kernel: its FP32-class sum
-// needs the separate correction accumulator, for which there is no room.
+// the two halves.  BF16x6 is not taken here: its FP32-class sum needs the
+// separate correction accumulator, for which there is no room (it runs on the
+// 128 x 128 tiles, or on CTA pairs over 256 x 128 tiles).
 // ---------------------------------------------------------------------------
 constexpr int TILE_W = 256;
 
