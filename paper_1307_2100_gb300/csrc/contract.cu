@@ -54,7 +54,7 @@ extern "C" tc_status tc_contract(tc_plan_t plan, double alpha, const void* A, co
               P->tile == kTilePackedPair)
                  ? launch_gemm_tc_packed(a, P->math, P->dtype, P->tile, ws, stream)
                                     : launch_gemm_tc(a, P->math, stream);
-    case K_GEMM_FP8: return launch_gemm_fp8(a, ws, stream);
+    case K_GEMM_FP8: return launch_gemm_fp8(a, P->tile, ws, stream);
     case K_GEMV: return launch_gemv(a, P->dtype, P->tile, stream);
     case K_DOT: return launch_dot(a, P->dtype, P->tile, stream);
     case K_GER: return launch_ger(a, P->dtype, stream);

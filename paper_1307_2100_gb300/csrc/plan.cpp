@@ -636,7 +636,7 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
   // ---- tiles and workspace
   int ntiles = kernel == K_GEMM_SIMT ? num_tiles_simt(dtype)
                : kernel == K_GEMM_TC ? num_tiles_tc()
-               : kernel == K_GEMM_FP8 ? 1
+               : kernel == K_GEMM_FP8 ? kFp8Tiles
                : kernel == K_GEMV    ? num_tiles_gemv()
                                      : 1;
   if (tile >= ntiles) {
@@ -711,6 +711,10 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
     } else {
       tile = 0;
     }
+  }
+  if (kernel == K_GEMM_FP8 && tile == 1 && !fp8_fusable(g)) {
+    delete P;  // in-kernel packing needs a plain first operand, M contiguous
+    return TC_ERR_UNSUPPORTED;
   }
   P->tile = tile;
   if (kernel == K_GEMM_TC || kernel == K_GEMM_FP8) {

@@ -132,11 +132,20 @@ int tc_chunk_kb(int math, int tile);
 // FP8 form: workspace layout of the packed operands (byte offsets).
 struct Fp8Layout {
   int64_t tiles_m, tiles_n, nkb, ngroups;
-  size_t off_qa, off_qb, off_sa, off_sb, bytes;
+  size_t off_qa, off_qb, off_sa, off_sb;
+  size_t off_ready, ready_bytes;  // in-kernel packing: claim counter, per-block counts
+  size_t bytes;
 };
 Fp8Layout fp8_layout(const GemmArgs& a);
-// Pack both operands into `ws` (16-byte aligned) and run the FP8 GEMM.
-tc_status launch_gemm_fp8(const GemmArgs& a, void* ws, void* stream);
+// Tile configurations of the FP8 GEMM: 0 (the default) packs both operands in
+// a pass of their own first; 1 packs the second operand first and the first
+// operand inside the GEMM launch, overlapped with the multiplications (needs
+// fp8_fusable; slower on GB300 for the shapes measured: the pack warps' loads
+// and the GEMM's operand copies share each SM's bandwidth).
+constexpr int kFp8Tiles = 2;
+bool fp8_fusable(const GemmArgs& a);
+// Pack the operands into `ws` (16-byte aligned) and run the FP8 GEMM.
+tc_status launch_gemm_fp8(const GemmArgs& a, int tile, void* ws, void* stream);
 tc_status tc_fp8_read_status(int* h, void* stream);
 
 // Split-BF16 forms with packed operands (tile configuration kTilePacked of

@@ -177,6 +177,7 @@ def test_fp8_plans():
     ng = -(-nkb // 4)                                   # scale bytes: 512 per 4 blocks
     r = lambda x: -(-x // 256) * 256
     want = r(tm * nkb * 16384) + r(tn * nkb * 16384) + r(tm * ng * 512) + r(tn * ng * 512)
+    want += r(16 + tm * nkb * 4)                        # in-kernel packing: claim counter, counts
     assert info.workspace == want
     f8 = tc.MATH["fp8"]
     x = (ts.lab("i"), [5], None)
@@ -418,3 +419,22 @@ def test_packed_tile_defaults_by_form_and_shape():
         info = plan_info(p, tc.MATH[m], dtype=tc.TC_F32)
         assert info.tile == tile, (m, name, info.tile, info.M, info.N)
 
+
+
+def test_fp8_tile_defaults():
+    """FP8: both operands packed in a pass of their own (tile 0) by default;
+    the first operand packed inside the GEMM launch (tile 1) on request when
+    it is a plain matrix with M contiguous and a K stride of a multiple of 16
+    bytes, and tile 1 refused otherwise."""
+    fp8 = tc.MATH["fp8"]
+    for p in (ts.problem("f", "ai", "ib", "ab", dict(a=300, i=200, b=130), 1),
+              ts.precision_ccd(v=24, o=20)):
+        assert plan_info(p, fp8, dtype=tc.TC_F32).tile == 0, p.name
+        assert plan_info(p, fp8, tile=1, dtype=tc.TC_F32).tile == 1, p.name
+    for p in (ts.problem("odd", "ai", "ib", "ab", dict(a=130, i=200, b=140), 2),   # stride 130
+              ts.direct_gemm_64(n=9),                                             # two M labels
+              ts.problem("kfast", "ia", "ib", "ab", dict(a=300, i=200, b=130), 3)):  # K fastest
+        assert plan_info(p, fp8, dtype=tc.TC_F32).tile == 0, p.name
+        with pytest.raises(tc.TcError) as e:
+            plan_info(p, fp8, tile=1, dtype=tc.TC_F32)
+        assert e.value.status == 5

@@ -160,3 +160,46 @@ def test_fp8_precision_workload_full_size_sampled():
     g = gather(got, p.C, s)
     assert np.linalg.norm(g - sample_outputs_fp8(p, s)) <= fp8_bound(p) * np.linalg.norm(mag)
     assert np.linalg.norm(g - ref64) <= QUANT * np.linalg.norm(mag)
+
+
+# Tile configuration 1: the first operand packed inside the GEMM launch.  Its
+# pack warps produce the same E4M3 codes and scale bytes as the packing pass
+# and the MMAs run in the same order, so C must equal tile 0's bit for bit.
+def fusable(k):
+    return [
+        lambda: f32(ts.problem("m1", "ai", "ib", "ab", dict(a=300, i=200, b=130), 51)),
+        lambda: f32(ts.precision_ccd(v=24, o=20)),                     # merged M and K labels
+        lambda: f32(ts.problem("longk", "ai", "ib", "ab", dict(a=132, i=3000, b=140), 56)),
+        lambda: f32(ts.problem("wide_n", "ai", "ib", "ab", dict(a=260, i=130, b=2100), 57)),
+    ][k]()
+
+
+@pytest.mark.parametrize("k", range(4))
+def test_fp8_in_kernel_packing_matches_the_packing_pass(k):
+    p = fusable(k)
+    info = []
+    got1 = run(p, "fp8", "fused_gemm", tile=1, plan_out=info)
+    assert info[0]["tile"] == 1
+    np.testing.assert_array_equal(got1, run(p, "fp8", "fused_gemm", tile=0))
+    ok, d = within(got1, op.contract_fp8(p), magnitude(p), p.C, fp8_bound(p))
+    assert ok, (p.name, d)
+
+
+def test_fp8_in_kernel_packing_alpha_beta_and_integers():
+    p = fusable(0)
+    p.C.data = np.linspace(-2, 2, p.C.data.size).astype(np.float32)
+    p.alpha, p.beta = -1.5, 0.25
+    np.testing.assert_array_equal(run(p, "fp8", "fused_gemm", tile=1),
+                                  run(p, "fp8", "fused_gemm", tile=0))
+    q = ts.problem("int", "ai", "ib", "ab", dict(a=300, i=200, b=130), 62, dist="int",
+                   dtype=np.float32, lo=-4, hi=4)
+    np.testing.assert_array_equal(run(q, "fp8", "fused_gemm", tile=1), oracle.contract_problem(q))
+
+
+def test_fp8_in_kernel_packing_over_several_groups():
+    """200 row tiles of A and one pair of column tiles: 200 GEMM tiles on at
+    most 152 CTAs, so the pack units come in two groups and the second wave
+    of tiles waits on the second group."""
+    p = f32(ts.problem("groups", "ai", "ib", "ab", dict(a=25600, i=264, b=200), 58))
+    np.testing.assert_array_equal(run(p, "fp8", "fused_gemm", tile=1),
+                                  run(p, "fp8", "fused_gemm", tile=0))
