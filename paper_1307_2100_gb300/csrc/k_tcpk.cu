@@ -1444,9 +1444,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_pkp6(const __grid_constant
                                    tile128_index(P, tm, J.tn)) * (size_t)(TILE * TILE) +
                              (size_t)h * 64 * TILE + row
                        : nullptr;
-      float lo[64];
+      float lo[64], hi[64];  // the compensated sum of the drained chunks
 #pragma unroll
-      for (int i = 0; i < 64; ++i) lo[i] = 0.0f;
+      for (int i = 0; i < 64; ++i) lo[i] = hi[i] = 0.0f;
       for (int j = 0; j < nchunks; ++j, ++gc) {
         const uint32_t buf = gc & 1;
         if (!warp_wait(&accf[buf], (gc >> 1) & 1, abort)) {
@@ -1458,40 +1458,35 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_pkp6(const __grid_constant
         if (j + 1 < nchunks) {
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
-            uint32_t mv[16], hv[16];
+            uint32_t mv[16];
             tmem_ld16(tmain + c * 16, mv);
-            if (j > 0) tmem_ld16(tl + COL_HI + c * 16, hv);
             tmem_wait_ld();
+            if (c == 3) {
+              tc_fence_before();
+              release(buf);  // the chunk is in registers
+            }
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-              const float hi0 = j > 0 ? __uint_as_float(hv[i]) : 0.0f;
               float e;
-              const float s = two_sum(hi0, __uint_as_float(mv[i]), e);
+              hi[c * 16 + i] = two_sum(hi[c * 16 + i], __uint_as_float(mv[i]), e);
               lo[c * 16 + i] = __fadd_rn(lo[c * 16 + i], e);
-              hv[i] = __float_as_uint(s);
             }
-            tmem_st16(tl + COL_HI + c * 16, hv);
           }
-          tmem_wait_st();
-          tc_fence_before();
-          release(buf);
         } else {
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            uint32_t mv[16], hv[16], cv[16];
-            tmem_ld16(tmain + c * 16, mv);
-            if (j > 0) tmem_ld16(tl + COL_HI + c * 16, hv);
-            if (NT > 1) tmem_ld16(tl + COL_CORR + c * 16, cv);
+          for (int c = 0; c < 8; ++c) {  // eight columns at a time: few registers live
+            uint32_t mv[8], cv[8];
+            tmem_ld8(tmain + c * 8, mv);
+            if (NT > 1) tmem_ld8(tl + COL_CORR + c * 8, cv);
             tmem_wait_ld();
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              const float hi0 = j > 0 ? __uint_as_float(hv[i]) : 0.0f;
+            for (int i = 0; i < 8; ++i) {
               float e;
-              const float s = two_sum(hi0, __uint_as_float(mv[i]), e);
-              float r = __fadd_rn(lo[c * 16 + i], e);
+              const float s = two_sum(hi[c * 8 + i], __uint_as_float(mv[i]), e);
+              float r = __fadd_rn(lo[c * 8 + i], e);
               if (NT > 1) r = __fadd_rn(r, __uint_as_float(cv[i]));
-              if (pp) pp[(size_t)(c * 16 + i) * TILE] = make_float2(s, r);
-              else lo[c * 16 + i] = __fadd_rn(s, r);
+              if (pp) pp[(size_t)(c * 8 + i) * TILE] = make_float2(s, r);
+              else lo[c * 8 + i] = __fadd_rn(s, r);
             }
           }
           tc_fence_before();
