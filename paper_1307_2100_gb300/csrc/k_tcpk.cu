@@ -918,11 +918,11 @@ __global__ void __launch_bounds__(kThreadsW, 1) k_gemm_pkw(const __grid_constant
 // ---------------------------------------------------------------------------
 template <int NT>
 struct CfgP {
-  static constexpr int BPS = NT == 1 ? 2 : 1;                 // 32-K blocks per stage
+  static constexpr int BPS = NT == 1 ? 4 : 1;                 // 32-K blocks per stage
   static constexpr uint32_t OPA = NT * TERM;                   // own A block (128 rows)
   static constexpr uint32_t OPB = NT * TERM;                   // own B half block (128 rows)
   static constexpr uint32_t STAGE = BPS * (OPA + OPB);         // A blocks, then B blocks
-  static constexpr int S = (int)(kRing / STAGE);               // 6 stages of 32 KB
+  static constexpr int S = (int)(kRing / STAGE);               // 3 x 64 KB, 6 x 32 KB, 4 x 48 KB
   static constexpr uint32_t OFF_COLC = S * STAGE;              // int64 colC[2][256]
   static constexpr uint32_t OFF_BAR = OFF_COLC + 2 * TILE_W * 8;
   static constexpr uint32_t NBAR = 2 * S + 4 + 1;              // full, empty, acc*, done
@@ -1815,6 +1815,7 @@ bool rows_map(CUtensorMap* m, const void* base, size_t bytes, uint32_t box_bytes
 // The grid is two CTAs per pair, as many pairs as fit at once (persistent).
 template <int NT, typename In, bool F16T>
 tc_status launch_p(const GemmArgs& a, const PkLayout& L, void* ws, cudaStream_t s, int out_type) {
+  if (max(a.chunk_kb, 1) % CfgP<NT>::BPS != 0) return TC_ERR_UNSUPPORTED;  // chunks end on stages
   static int max_pairs = 0;
   if (max_pairs == 0) {
     int dev = 0, optin = 0;
