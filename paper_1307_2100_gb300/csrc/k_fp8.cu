@@ -271,6 +271,8 @@ __global__ void __launch_bounds__(kPackThreads) k_fp8_pack(const __grid_constant
 
 struct GemmFp8 {
   CUtensorMap tma_a;     // in-kernel packing: A's FP32 elements as [K][M], M contiguous
+  CUtensorMap tma_qa;    // CTA pairs: the packed blocks of A and B as rows of 2 KB
+  CUtensorMap tma_qb;
   Group gm, gn;          // C offsets in slot 2
   uint8_t* qa;           // packed blocks (written by the pack warps when they pack A)
   const uint8_t* qb;
@@ -829,6 +831,310 @@ __global__ void __launch_bounds__(Cfg<FUSE>::THREADS, 1) k_gemm_fp8(const __grid
   }
 }
 
+// ---------------------------------------------------------------------------
+// CTA pairs (tile configuration 2): 256 x 256 output tiles shared by two SMs
+// (cluster of two, tcgen05.mma.cta_group::2, M = 256, N = 256, K = 32).  Each
+// CTA holds its own 128-row tile of A and its own 128-column tile of B: per
+// SM and K block 32 KB of operands for 128 x 256 outputs, against 48 KB on
+// the one-CTA 128 x 256 tile.  Each CTA's half of the MMA reads the scale
+// cells in its own tensor memory (A's for its own rows, B's for all 256
+// columns, in the layout above), so both CTAs' scale writers fill the same
+// 12-column groups from their own tiles and arrive on the first CTA's sff
+// barrier.  The loads of both CTAs (tiled TMA, the packed blocks viewed as
+// rows of 2 KB) complete on the first CTA's full barrier; the MMA thread's
+// commits arrive on both CTAs' barriers; both epilogues arrive on the first
+// CTA's acce barrier.  A stage holds two K blocks (64 KB), three stages.
+// ---------------------------------------------------------------------------
+constexpr int BPS_P = 2;  // K blocks per stage
+struct CfgP8 {
+  static constexpr uint32_t STAGE = BPS_P * 2 * CHUNK;     // A blocks, then B blocks
+  static constexpr int S = 3;
+  static constexpr uint32_t OFF_COLC = S * STAGE;          // int64 colC[2][256]
+  static constexpr uint32_t OFF_BAR = OFF_COLC + 2 * 2 * TILE * 8;
+  static constexpr uint32_t NBAR = 2 * S + 2 + 2 * NG + 1;
+  static constexpr uint32_t OFF_MISC = OFF_BAR + NBAR * 8;
+  static constexpr uint32_t BYTES = OFF_MISC + 16 + 1024;  // + alignment slack
+};
+
+// Pair tile w: 128-row tiles 2 tmp, 2 tmp + 1 of A; 128-column tiles 2 tp,
+// 2 tp + 1 of B.
+__device__ __forceinline__ void pair_coords(const GemmFp8& P, int64_t w, int& tmp, int& tp) {
+  const int mp = (P.tiles_m + 1) / 2;
+  if (P.raster) {
+    tp = (int)(w % P.tiles_p);
+    tmp = (int)(w / P.tiles_p);
+  } else {
+    tmp = (int)(w % mp);
+    tp = (int)(w / mp);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_gemm_fp8p(const __grid_constant__ GemmFp8 P) {
+  using Cf = CfgP8;
+  constexpr int S = Cf::S;
+  extern __shared__ uint8_t fp8p_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(fp8p_raw) + 1023) & ~(uintptr_t)1023);
+  int64_t* colC = reinterpret_cast<int64_t*>(smem + Cf::OFF_COLC);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cf::OFF_BAR);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + S;
+  uint64_t* accf = bars + 2 * S;
+  uint64_t* acce = accf + 1;
+  uint64_t* sff = acce + 1;
+  uint64_t* sfe = sff + NG;
+  uint64_t* done = sfe + NG;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + Cf::OFF_MISC);
+  volatile int* abort = reinterpret_cast<volatile int*>(smem + Cf::OFF_MISC + 4);
+  const uint32_t rank = cluster_ctarank();
+  const bool lead = rank == 0;
+  const int64_t pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accf, 1);
+    mbar_init(acce, 2 * kEpiThreads);  // both CTAs' epilogue threads
+    for (int i = 0; i < NG; ++i) {
+      mbar_init(&sff[i], 2 * 128);     // both CTAs' scale writers
+      mbar_init(&sfe[i], 1);
+    }
+    mbar_init(done, 1);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  cluster_sync();  // both CTAs' barriers exist before any remote arrival
+  if (warp == 1) tmem_alloc2(tmem_slot, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t sbase = smem_u32(smem);
+  const int nkb = P.nkb, ngroups = P.ngroups;
+  // arrive on the first CTA's barrier: every thread of a warp (count 1 each)
+  auto arrive_lead = [&](uint64_t* bar) {
+    if (lead) {
+      mbar_arrive(bar);
+    } else {
+      __syncwarp();
+      if (lane == 0) mbar_arrive_remote(bar, 0, 32);
+    }
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------------------ producer
+      uint32_t g = 0;
+      bool ok = true;
+      for (int64_t w = pair; ok && w < P.ntiles; w += npairs) {
+        int tmp, tp;
+        pair_coords(P, w, tmp, tp);
+        const int tm0 = 2 * tmp, tn0 = 2 * tp;
+        const int tm = tm0 + (int)rank, tn = tn0 + (int)rank;
+        const bool va = tm < P.tiles_m, vb = tn < P.tiles_n;  // else: outputs the pair discards
+        const uint32_t pair_block = (tm0 < P.tiles_m ? CHUNK : 0u) +
+                                    (tm0 + 1 < P.tiles_m ? CHUNK : 0u) +
+                                    (tn0 < P.tiles_n ? CHUNK : 0u) +
+                                    (tn0 + 1 < P.tiles_n ? CHUNK : 0u);
+        for (int kb = 0; kb < nkb; kb += BPS_P, ++g) {
+          const int s = (int)(g % S);
+          if (g >= (uint32_t)S && !mbar_wait(&empty[s], ((g / S) - 1) & 1, abort, kTimeoutNs)) {
+            ok = false;
+            break;
+          }
+          const int nb = min(BPS_P, nkb - kb);
+          const uint32_t dst = sbase + (uint32_t)s * Cf::STAGE;
+          if (lead) mbar_arrive_expect_tx(&full[s], (uint32_t)nb * pair_block);
+          const uint32_t mb = mapa_shared(smem_u32(&full[s]), 0);
+          for (int bi = 0; bi < nb; ++bi) {
+            if (va)
+              tma_load_2d_pair(dst + bi * CHUNK, &P.tma_qa, 0,
+                               (int32_t)(((int64_t)tm * nkb + kb + bi) * (CHUNK / 2048)), mb);
+            if (vb)
+              tma_load_2d_pair(dst + (BPS_P + bi) * CHUNK, &P.tma_qb, 0,
+                               (int32_t)(((int64_t)tn * nkb + kb + bi) * (CHUNK / 2048)), mb);
+          }
+        }
+      }
+      // the copies still in flight (at most the last S stages) land before exit
+      volatile int never = 0;
+      for (uint32_t i = g > (uint32_t)S ? g - S : 0; i < g; ++i)
+        mbar_wait(&empty[i % S], (i / S) & 1, &never, kTimeoutNs);
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && lead) {
+      // ------------------------------------------- MMA issue (first CTA)
+      constexpr uint32_t LBO = (TILE / 8) * 128;  // next 16-byte K chunk
+      uint32_t g = 0, G = 0, t = 0;
+      bool ok = true;
+      for (int64_t w = pair; ok && w < P.ntiles; w += npairs, ++t) {
+        // the accumulator is free once both epilogues have read the previous tile
+        if (t >= 1 && !mbar_wait(acce, (t - 1) & 1, abort, kTimeoutNs)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        for (int kb = 0; ok && kb < nkb; kb += BPS_P, ++g) {
+          const int s = (int)(g % S);
+          if (!mbar_wait(&full[s], (g / S) & 1, abort, kTimeoutNs)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const int nb = min(BPS_P, nkb - kb);
+          for (int bi = 0; bi < nb; ++bi) {
+            const int k = kb + bi;
+            const uint32_t slot = G % NG;
+            if ((k & 3) == 0) {  // both CTAs wrote the group's scale columns
+              if (!mbar_wait(&sff[slot], (G / NG) & 1, abort, kTimeoutNs)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+            }
+            const uint32_t sa = sbase + (uint32_t)s * Cf::STAGE + bi * CHUNK;
+            const uint32_t sb = sbase + (uint32_t)s * Cf::STAGE + (BPS_P + bi) * CHUNK;
+            const uint32_t id = (uint32_t)(k & 3);
+            const uint32_t idesc = idesc_mx_e4m3(2 * TILE, 2 * TILE, id, id);
+            const uint32_t tsf = tmem + COL_SF + slot * 12;
+#pragma unroll
+            for (int kk = 0; kk < KB / 32; ++kk)
+              mma_mx_e4m3_pair(tmem, smem_desc(sa + kk * 2 * LBO, LBO, 128),
+                               smem_desc(sb + kk * 2 * LBO, LBO, 128), idesc, tsf, tsf + 4,
+                               (k > 0 || kk > 0) ? 1u : 0u);
+            if ((k & 3) == 3 || k == nkb - 1) {
+              mma_commit_pair(&sfe[slot], 3);  // both CTAs may rewrite the group's columns
+              ++G;
+            }
+          }
+          if (!ok) break;
+          mma_commit_pair(&empty[s], 3);  // both CTAs may refill this stage
+        }
+        if (!ok) break;
+        mma_commit_pair(accf, 3);  // both CTAs' epilogues may read the accumulator
+      }
+      mma_commit_pair(done, 1);  // arrives once every MMA issued above has completed
+      volatile int never = 0;
+      mbar_wait(done, 0, &never, kTimeoutNs);
+    }
+  } else if (warp < 6) {
+    // --------------------------------------------------- scale-byte writers
+    // A's cells for this CTA's own 128 rows, B's for both column tiles
+    const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    uint32_t G = 0;
+    int64_t w = pair;
+    int gi = 0;
+    auto load = [&](int64_t ww, int gg, uint4& va, uint4& vb0, uint4& vb1) {
+      int tmp, tp;
+      pair_coords(P, ww, tmp, tp);
+      const int tm = min(2 * tmp + (int)rank, P.tiles_m - 1);  // a missing tile: rows discarded
+      va = __ldg(reinterpret_cast<const uint4*>(P.sfa + sf_index(tm, ngroups, 4 * gg, 0)) + lane);
+      vb0 = __ldg(reinterpret_cast<const uint4*>(P.sfb + sf_index(2 * tp, ngroups, 4 * gg, 0)) +
+                  lane);
+      if (2 * tp + 1 < P.tiles_n)
+        vb1 = __ldg(
+            reinterpret_cast<const uint4*>(P.sfb + sf_index(2 * tp + 1, ngroups, 4 * gg, 0)) +
+            lane);
+      else
+        vb1 = vb0;  // no second column tile: its columns are discarded
+    };
+    uint4 va, vb0, vb1;
+    if (w < P.ntiles) load(w, 0, va, vb0, vb1);
+    while (w < P.ntiles) {
+      int64_t w2 = w;
+      int g2 = gi + 1;
+      if (g2 == ngroups) {
+        g2 = 0;
+        w2 += npairs;
+      }
+      uint4 na = va, nb0 = vb0, nb1 = vb1;
+      if (w2 < P.ntiles) load(w2, g2, na, nb0, nb1);
+      const uint32_t slot = G % NG;
+      if (G >= (uint32_t)NG && !warp_wait(&sfe[slot], ((G / NG) - 1) & 1, abort)) break;
+      tc_fence_after();
+      const uint32_t ra[4] = {va.x, va.y, va.z, va.w};
+      const uint32_t r0[4] = {vb0.x, vb0.y, vb0.z, vb0.w};
+      const uint32_t r1[4] = {vb1.x, vb1.y, vb1.z, vb1.w};
+      tmem_st4(tl + COL_SF + slot * 12, ra);
+      tmem_st4(tl + COL_SF + slot * 12 + 4, r0);
+      tmem_st4(tl + COL_SF + slot * 12 + 8, r1);
+      tmem_wait_st();
+      tc_fence_before();
+      arrive_lead(&sff[slot]);
+      ++G;
+      w = w2;
+      gi = g2;
+      va = na;
+      vb0 = nb0;
+      vb1 = nb1;
+    }
+  } else {
+    // ------------------------------------------------------------- epilogue
+    const int ew = warp - 6;
+    const int q = warp & 3;                 // tensor-memory lane quadrant of this warp
+    const int h = ew >> 2;                  // 128-column half of the tile
+    const int row = q * 32 + lane;
+    const int etid = ew * 32 + lane;
+    const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)h * TILE;
+    uint32_t t = 0;
+    bool live = true;  // after a wait gave up, tiles are walked without work so
+                       // that every epilogue warp still meets each named barrier
+    for (int64_t w = pair; w < P.ntiles; w += npairs, ++t) {
+      int tmp, tp;
+      pair_coords(P, w, tmp, tp);
+      int64_t* cc = colC + (t & 1) * 2 * TILE;
+      {
+        const int64_t n = (int64_t)tp * 2 * TILE + etid;  // 256 columns, one per thread
+        cc[etid] = n < P.N ? goff(P.gn, 2, (uint32_t)n) : -1;
+      }
+      named_bar_sync(1, kEpiThreads);
+      if (!live) continue;
+      const int64_t m = (int64_t)(2 * tmp + (int)rank) * TILE + row;
+      const int64_t rc = m < P.M ? goff(P.gm, 2, (uint32_t)m) : -1;
+      if (!warp_wait(accf, t & 1, abort)) {
+        live = false;
+        continue;
+      }
+      tc_fence_after();
+      // two passes of 64 columns; the accumulator is released after the last load
+#pragma unroll
+      for (int pass = 0; pass < 2; ++pass) {
+        uint32_t v[4][16];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) tmem_ld16(tl + pass * 64 + c * 16, v[c]);
+        tmem_wait_ld();
+        if (pass == 1) {
+          tc_fence_before();
+          arrive_lead(acce);  // the accumulator may take the next tile
+        }
+        if (rc >= 0) {
+          float* Cr = P.C + rc;
+#pragma unroll
+          for (int i = 0; i < 64; ++i) {
+            const int64_t ci = cc[h * TILE + pass * 64 + i];
+            if (ci < 0) continue;
+            float x = P.alpha * __uint_as_float(v[i / 16][i % 16]);
+            if (P.beta != 0.0f) x = fmaf(P.beta, Cr[ci], x);
+            Cr[ci] = x;
+          }
+        }
+      }
+    }
+  }
+
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();  // the pair's MMAs and both epilogues are done with both CTAs' memory
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc2(tmem, kTmemCols);
+  }
+}
+
 int num_sms() {
   static int n = 0;
   if (n == 0) {
@@ -849,7 +1155,9 @@ int set_smem() {
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
             cudaSuccess)
       return -1;
-    if (optin < (int)Cfg<false>::BYTES || optin < (int)Cfg<true>::BYTES) return -2;
+    if (optin < (int)Cfg<false>::BYTES || optin < (int)Cfg<true>::BYTES ||
+        optin < (int)CfgP8::BYTES)
+      return -2;
     if (cudaFuncSetAttribute(k_fp8_pack, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kPackSmem) != cudaSuccess ||
         cudaFuncSetAttribute(k_gemm_fp8<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -868,9 +1176,7 @@ using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t
                                    const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// A's FP32 elements as the 2-D tensor [K][M] (M contiguous, K rows `ldk`
-// elements apart); boxes of 64 rows of A by 128 K, zero outside A.
-bool first_operand_map(CUtensorMap* m, const GemmArgs& a) {
+EncodeTiledFn encoder() {
   static EncodeTiledFn fn = nullptr;
   static bool tried = false;
   if (!tried) {
@@ -882,6 +1188,52 @@ bool first_operand_map(CUtensorMap* m, const GemmArgs& a) {
         q == cudaDriverEntryPointSuccess)
       fn = reinterpret_cast<EncodeTiledFn>(p);
   }
+  return fn;
+}
+
+// Packed blocks as a 2-D tensor of 8-byte elements in rows of 2 KB; a box is
+// one 16 KB block (8 rows).
+bool packed_map(CUtensorMap* m, const void* base, size_t bytes) {
+  EncodeTiledFn fn = encoder();
+  if (!fn || bytes == 0 || bytes % 2048 || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
+  cuuint64_t dims[2] = {256, (cuuint64_t)(bytes / 2048)};
+  cuuint64_t strides[1] = {2048};
+  cuuint32_t box[2] = {256, CHUNK / 2048};
+  cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Pairs that run at once (cluster occupancy of k_gemm_fp8p), looked up once.
+int max_pairs() {
+  static int n = -1;
+  if (n < 0) {
+    n = 0;
+    if (cudaFuncSetAttribute(k_gemm_fp8p, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)CfgP8::BYTES) != cudaSuccess)
+      return 0;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2, 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = CfgP8::BYTES;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int c = 0;
+    if (cudaOccupancyMaxActiveClusters(&c, k_gemm_fp8p, &cfg) == cudaSuccess && c > 0) n = c;
+  }
+  return n;
+}
+
+// A's FP32 elements as the 2-D tensor [K][M] (M contiguous, K rows `ldk`
+// elements apart); boxes of 64 rows of A by 128 K, zero outside A.
+bool first_operand_map(CUtensorMap* m, const GemmArgs& a) {
+  EncodeTiledFn fn = encoder();
   if (!fn || (reinterpret_cast<uintptr_t>(a.A) & 15)) return false;
   cuuint64_t dims[2] = {(cuuint64_t)a.M, (cuuint64_t)a.K};
   cuuint64_t strides[1] = {(cuuint64_t)a.gk.st[0][0] * 4};
@@ -986,6 +1338,29 @@ tc_status launch_gemm_fp8(const GemmArgs& a, int tile, void* ws, void* stream) {
   g.nkb = (int32_t)L.nkb;
   g.ngroups = (int32_t)L.ngroups;
   g.raster = a.raster;
+  if (tile == 2) {
+    // CTA pairs over 256 x 256 tiles, as many pairs as run at once
+    const int pairs_max = fp8::max_pairs();
+    if (pairs_max <= 0) return TC_ERR_CUDA;
+    g.ntiles = ((L.tiles_m + 1) / 2) * g.tiles_p;
+    if (!fp8::packed_map(&g.tma_qa, g.qa, (size_t)L.tiles_m * L.nkb * fp8::CHUNK) ||
+        !fp8::packed_map(&g.tma_qb, g.qb, (size_t)L.tiles_n * L.nkb * fp8::CHUNK))
+      return TC_ERR_CUDA;
+    const int pairs = (int)std::min<int64_t>(g.ntiles, pairs_max);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * pairs, 1, 1);
+    cfg.blockDim = dim3(fp8::kThreads, 1, 1);
+    cfg.dynamicSmemBytes = fp8::CfgP8::BYTES;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fp8::k_gemm_fp8p, g) == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+  }
   const int grid = (int)std::min<int64_t>(g.ntiles, sms);
   if (!fuse) {
     fp8::k_gemm_fp8<false><<<grid, fp8::Cfg<false>::THREADS, fp8::Cfg<false>::BYTES, s>>>(g);

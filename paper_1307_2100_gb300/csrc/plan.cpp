@@ -708,6 +708,8 @@ extern "C" tc_status tc_plan(tc_plan_t* out, const tc_tensor_desc* Ad, const tc_
              : (one_acc && M > 128 && N > 128) ? kTilePackedPair
              : (math == TC_MATH_BF16X6 && M > 128) ? kTilePackedPair
              : (math == TC_MATH_BF16X3 && N > 128) ? kTilePackedWide : kTilePacked;
+    } else if (kernel == K_GEMM_FP8) {
+      tile = (M > 128 && N > 128) ? 2 : 0;  // CTA pairs when both span two tiles
     } else {
       tile = 0;
     }

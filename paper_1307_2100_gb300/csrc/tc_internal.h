@@ -137,12 +137,14 @@ struct Fp8Layout {
   size_t bytes;
 };
 Fp8Layout fp8_layout(const GemmArgs& a);
-// Tile configurations of the FP8 GEMM: 0 (the default) packs both operands in
-// a pass of their own first; 1 packs the second operand first and the first
-// operand inside the GEMM launch, overlapped with the multiplications (needs
-// fp8_fusable; slower on GB300 for the shapes measured: the pack warps' loads
-// and the GEMM's operand copies share each SM's bandwidth).
-constexpr int kFp8Tiles = 2;
+// Tile configurations of the FP8 GEMM: 0 packs both operands in a pass of
+// their own first, then multiplies on 128 x 256 tiles; 1 packs the second
+// operand first and the first operand inside the GEMM launch, overlapped with
+// the multiplications (needs fp8_fusable; slower on GB300 for the shapes
+// measured: the pack warps' loads and the GEMM's operand copies share each
+// SM's bandwidth); 2 (the default when M and N both span two 128-row tiles)
+// packs as 0 and multiplies on CTA pairs over 256 x 256 tiles.
+constexpr int kFp8Tiles = 3;
 bool fp8_fusable(const GemmArgs& a);
 // Pack the operands into `ws` (16-byte aligned) and run the FP8 GEMM.
 tc_status launch_gemm_fp8(const GemmArgs& a, int tile, void* ws, void* stream);

@@ -422,19 +422,23 @@ def test_packed_tile_defaults_by_form_and_shape():
 
 
 def test_fp8_tile_defaults():
-    """FP8: both operands packed in a pass of their own (tile 0) by default;
-    the first operand packed inside the GEMM launch (tile 1) on request when
-    it is a plain matrix with M contiguous and a K stride of a multiple of 16
-    bytes, and tile 1 refused otherwise."""
+    """FP8: CTA pairs over 256 x 256 tiles (tile 2) by default when M and N
+    both span two 128-row tiles, else the 128 x 256 tiles (tile 0); the first
+    operand packed inside the GEMM launch (tile 1) on request when it is a
+    plain matrix with M contiguous and a K stride of a multiple of 16 bytes,
+    and tile 1 refused otherwise."""
     fp8 = tc.MATH["fp8"]
     for p in (ts.problem("f", "ai", "ib", "ab", dict(a=300, i=200, b=130), 1),
               ts.precision_ccd(v=24, o=20)):
-        assert plan_info(p, fp8, dtype=tc.TC_F32).tile == 0, p.name
+        assert plan_info(p, fp8, dtype=tc.TC_F32).tile == 2, p.name
         assert plan_info(p, fp8, tile=1, dtype=tc.TC_F32).tile == 1, p.name
+    for d, want in ((dict(a=128, i=64, b=300), 0), (dict(a=300, i=64, b=128), 0),
+                    (dict(a=129, i=64, b=129), 2)):
+        p = ts.problem("edge", "ai", "ib", "ab", d, 4)
+        assert plan_info(p, fp8, dtype=tc.TC_F32).tile == want, d
     for p in (ts.problem("odd", "ai", "ib", "ab", dict(a=130, i=200, b=140), 2),   # stride 130
               ts.direct_gemm_64(n=9),                                             # two M labels
               ts.problem("kfast", "ia", "ib", "ab", dict(a=300, i=200, b=130), 3)):  # K fastest
-        assert plan_info(p, fp8, dtype=tc.TC_F32).tile == 0, p.name
         with pytest.raises(tc.TcError) as e:
             plan_info(p, fp8, tile=1, dtype=tc.TC_F32)
         assert e.value.status == 5

@@ -203,3 +203,38 @@ def test_fp8_in_kernel_packing_over_several_groups():
     p = f32(ts.problem("groups", "ai", "ib", "ab", dict(a=25600, i=264, b=200), 58))
     np.testing.assert_array_equal(run(p, "fp8", "fused_gemm", tile=1),
                                   run(p, "fp8", "fused_gemm", tile=0))
+
+
+# Tile configuration 2: CTA pairs over 256 x 256 tiles.  The same E4M3 codes
+# and scale bytes, and for each output the same block-scaled MMAs in the same
+# K order, so C must equal the 128 x 256 tiles' (tile 0) bit for bit.
+def pair_shapes(k):
+    return [
+        lambda: f32(ts.problem("m1", "ai", "ib", "ab", dict(a=300, i=200, b=130), 51)),  # odd pair row
+        lambda: f32(ts.problem("wide_n", "ai", "ib", "ab", dict(a=260, i=130, b=2100), 57)),  # 17 col tiles
+        lambda: f32(ts.direct_gemm_64(n=23)),                                # gathered groups
+        lambda: f32(ts.problem("cfromb", "ai", "ib", "ba", dict(a=140, i=77, b=260), 52)),
+        lambda: f32(ts.problem("longk", "aijb", "ijc", "abc", dict(a=130, i=40, j=60, b=2, c=129), 53)),
+    ][k]()
+
+
+@pytest.mark.parametrize("k", range(5))
+def test_fp8_pairs_match_the_one_cta_tiles(k):
+    p = pair_shapes(k)
+    info = []
+    got2 = run(p, "fp8", "fused_gemm", tile=2, plan_out=info)
+    assert info[0]["tile"] == 2
+    np.testing.assert_array_equal(got2, run(p, "fp8", "fused_gemm", tile=0))
+    ok, d = within(got2, op.contract_fp8(p), magnitude(p), p.C, fp8_bound(p))
+    assert ok, (p.name, d)
+
+
+def test_fp8_pairs_alpha_beta_and_integers():
+    p = pair_shapes(0)
+    p.C.data = np.linspace(-2, 2, p.C.data.size).astype(np.float32)
+    p.alpha, p.beta = -1.5, 0.25
+    np.testing.assert_array_equal(run(p, "fp8", "fused_gemm", tile=2),
+                                  run(p, "fp8", "fused_gemm", tile=0))
+    q = ts.problem("int", "iajb", "jcid", "abcd", dict(i=29, a=70, j=11, b=3, c=65, d=2), 61,
+                   dist="int", dtype=np.float32, lo=-4, hi=4)
+    np.testing.assert_array_equal(run(q, "fp8", "fused_gemm", tile=2), oracle.contract_problem(q))
