@@ -845,10 +845,10 @@ __global__ void __launch_bounds__(Cfg<FUSE>::THREADS, 1) k_gemm_fp8(const __grid
 // commits arrive on both CTAs' barriers; both epilogues arrive on the first
 // CTA's acce barrier.  A stage holds two K blocks (64 KB), three stages.
 // ---------------------------------------------------------------------------
-constexpr int BPS_P = 2;  // K blocks per stage
+constexpr int BPS_P = 1;  // K blocks per stage
 struct CfgP8 {
   static constexpr uint32_t STAGE = BPS_P * 2 * CHUNK;     // A blocks, then B blocks
-  static constexpr int S = 3;
+  static constexpr int S = (int)((192u * 1024u) / STAGE);
   static constexpr uint32_t OFF_COLC = S * STAGE;          // int64 colC[2][256]
   static constexpr uint32_t OFF_BAR = OFF_COLC + 2 * 2 * TILE * 8;
   static constexpr uint32_t NBAR = 2 * S + 2 + 2 * NG + 1;

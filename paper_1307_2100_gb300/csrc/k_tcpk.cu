@@ -930,18 +930,45 @@ struct CfgP {
   static constexpr uint32_t BYTES = OFF_MISC + 16 + 1024;
 };
 
-// Work entry w of a pair launch: split-major over 256 x 256 pair tiles.
+// Work entry w of a pair launch: split-major over 256 x 256 pair tiles; with
+// a tail split, whole tiles first, then the tail tiles' K ranges.
 struct JobP {
   int tmp, tnp;       // pair tile: A tiles 2 tmp, 2 tmp + 1; B tiles 2 tnp, 2 tnp + 1
   int split, k0, k1;
+  int tail;           // tail split: the tail tile's index (-1: a whole tile)
 };
 
 __device__ __forceinline__ JobP jobp_of(const PkItem& P, int64_t w) {
   JobP j;
   const int mp = (P.tiles_m + 1) / 2, np = (P.tiles_n + 1) / 2;
   const int64_t ntiles = (int64_t)mp * np;
+  j.tail = -1;
+  int64_t t;
+  if (P.tsplit > 1) {
+    if (w < P.nfull) {
+      t = w;
+      j.split = 0;
+      j.k0 = 0;
+      j.k1 = P.nkb;
+    } else {
+      const int64_t r = w - P.nfull;
+      j.tail = (int)(r / P.tsplit);
+      t = P.nfull + j.tail;
+      j.split = (int)(r % P.tsplit);
+      j.k0 = (int)((int64_t)j.split * P.nkb / P.tsplit);
+      j.k1 = (int)((int64_t)(j.split + 1) * P.nkb / P.tsplit);
+    }
+    if (P.raster) {
+      j.tnp = (int)(t % np);
+      j.tmp = (int)(t / np);
+    } else {
+      j.tmp = (int)(t % mp);
+      j.tnp = (int)(t / mp);
+    }
+    return j;
+  }
   j.split = (int)(w / ntiles);
-  const int64_t t = w % ntiles;
+  t = w % ntiles;
   if (P.raster) {
     j.tnp = (int)(t % np);
     j.tmp = (int)(t / np);
@@ -1167,7 +1194,13 @@ __global__ void __launch_bounds__(kThreadsW, 1) k_gemm_pkp(const __grid_constant
       }
       const int tm = 2 * J.tmp + (int)rank, tn = 2 * J.tnp + hh;
       if (live && tm < P.tiles_m && tn < P.tiles_n) {
-        if (P.ksplit > 1) {
+        if (J.tail >= 0) {  // a tail tile's K range: partial sums of this quarter
+          const int64_t ntail = (((int64_t)(P.tiles_m + 1) / 2) * ((P.tiles_n + 1) / 2)) - P.nfull;
+          float2* pp = P.part + (((size_t)J.split * ntail + J.tail) * 4 + rank * 2 + hh) *
+                                    (size_t)(TILE * TILE) + row;
+#pragma unroll
+          for (int i = 0; i < 128; ++i) pp[(size_t)i * TILE] = make_float2(hi[i], 0.0f);
+        } else if (P.ksplit > 1) {
           float2* pp = P.part + ((size_t)J.split * P.tiles_m * P.tiles_n +
                                  tile128_index(P, tm, tn)) * (size_t)(TILE * TILE) + row;
 #pragma unroll
@@ -1543,6 +1576,41 @@ __global__ void __launch_bounds__(256) k_pk_reduce(const __grid_constant__ PkLau
   }
 }
 
+// Tail split of CTA pairs: C of the tail tiles = alpha * (sum of their K
+// ranges' partial sums, in order) + beta * C.
+__global__ void __launch_bounds__(256) k_pkp_reduce_tail(const __grid_constant__ PkLaunch L) {
+  const PkItem& P = L.single;
+  const int mp = (P.tiles_m + 1) / 2, np = (P.tiles_n + 1) / 2;
+  const int64_t ntail = (int64_t)mp * np - P.nfull;
+  const int64_t total = ntail * 4 * TILE * TILE;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sub = e / (TILE * TILE);
+    const int64_t tail = sub / 4;
+    const int quarter = (int)(sub % 4);
+    const int col = (int)((e / TILE) % TILE), row = (int)(e % TILE);
+    const int64_t t = P.nfull + tail;
+    int tmp, tnp;
+    if (P.raster) {
+      tnp = (int)(t % np);
+      tmp = (int)(t / np);
+    } else {
+      tmp = (int)(t % mp);
+      tnp = (int)(t / mp);
+    }
+    const int tm = 2 * tmp + (quarter >> 1), tn = 2 * tnp + (quarter & 1);
+    const int64_t m = (int64_t)tm * TILE + row, n = (int64_t)tn * TILE + col;
+    if (tm >= P.tiles_m || tn >= P.tiles_n || m >= P.M || n >= P.N) continue;
+    double s = 0.0;
+    for (int sp = 0; sp < P.tsplit; ++sp) {
+      const float2 v = P.part[(size_t)sp * total + e];
+      s += (double)v.x + (double)v.y;
+    }
+    store_out(L.C, goff(P.gm, 2, (uint32_t)m) + goff(P.gn, 2, (uint32_t)n), L.out_type,
+              (float)(L.alpha * s), L.beta);
+  }
+}
+
 // Batched split-K: a block adds the K ranges of 1/kRedParts of one
 // (item, tile), in order, applies the item's alpha and beta and stores
 // through its groups.
@@ -1886,13 +1954,17 @@ tc_status launch_p(const GemmArgs& a, const PkLayout& L, void* ws, cudaStream_t 
   it.chunk_kb = a.chunk_kb;
   it.raster = a.raster;
   it.ksplit = pk_ksplit_p(a);
-  it.part = it.ksplit > 1 ? reinterpret_cast<float2*>(w + L.bytes) : nullptr;
+  int64_t nfull = 0;
+  it.tsplit = pk_tail_split_p(a, &nfull);
+  it.nfull = nfull;
+  it.part = (it.ksplit > 1 || it.tsplit > 1) ? reinterpret_cast<float2*>(w + L.bytes) : nullptr;
   g.C = a.C;
   g.alpha = (float)a.alpha;
   g.beta = (float)a.beta;
   g.idesc = F16T ? idesc_f16(2 * TILE, TILE_W) : idesc_bf16(2 * TILE, TILE_W);
   g.out_type = out_type;
-  g.nwork = ((L.tiles_m + 1) / 2) * ((L.tiles_n + 1) / 2) * it.ksplit;
+  const int64_t ptiles = ((L.tiles_m + 1) / 2) * ((L.tiles_n + 1) / 2);
+  g.nwork = it.tsplit > 1 ? nfull + (ptiles - nfull) * it.tsplit : ptiles * it.ksplit;
   if (!rows_map(&g.tma_a, it.qa, (size_t)L.tiles_m * L.nkb * CfgP<NT>::OPA, CfgP<NT>::OPA) ||
       !rows_map(&g.tma_b, it.qb, (size_t)L.tiles_n * L.nkb * CfgP<NT>::OPB, CfgP<NT>::OPB))
     return TC_ERR_CUDA;
@@ -1910,6 +1982,12 @@ tc_status launch_p(const GemmArgs& a, const PkLayout& L, void* ws, cudaStream_t 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   if (cudaLaunchKernelEx(&cfg, k_gemm_pkp<NT>, g) != cudaSuccess) return TC_ERR_CUDA;
+  if (it.tsplit > 1) {
+    const int64_t total = (ptiles - nfull) * 4 * TILE * TILE;
+    const int rgrid = (int)std::min<int64_t>((total + 255) / 256, (int64_t)152 * 8);
+    k_pkp_reduce_tail<<<rgrid, 256, 0, s>>>(g);
+    if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;
+  }
   if (it.ksplit > 1) {
     const int64_t total = L.tiles_m * L.tiles_n * TILE * TILE;
     const int rgrid = (int)std::min<int64_t>((total + 255) / 256, (int64_t)152 * 8);
@@ -2095,6 +2173,24 @@ int pk_ksplit_p(const GemmArgs& a) {
   return (int)std::max<int64_t>(1, std::min<int64_t>({want, nkb / 16, 64}));
 }
 
+// Tail split of the CTA pairs: with more pair tiles than pairs (76) and a
+// last round of entries that would leave pairs idle, the tiles of that round
+// share out their K blocks (each part >= 512 K), at most one entry per pair;
+// the other tiles are whole entries.  Returns the parts per tail tile (1: no
+// tail split) and sets *nfull, the whole entries.
+int pk_tail_split_p(const GemmArgs& a, int64_t* nfull) {
+  const int64_t tiles = (((a.M + pk::TILE - 1) / pk::TILE + 1) / 2) *
+                        (((a.N + pk::TILE - 1) / pk::TILE + 1) / 2);
+  const int64_t nkb = (a.K + pk::BK - 1) / pk::BK;
+  *nfull = tiles;
+  if (tiles <= 76 || tiles % 76 == 0) return 1;
+  const int64_t rem = tiles % 76;
+  const int64_t parts = std::min<int64_t>(76 / rem, nkb / 16);
+  if (parts < 2) return 1;
+  *nfull = tiles - rem;
+  return (int)parts;
+}
+
 // Split-K of the BF16x6 CTA pairs (256 x 128 pair tiles): the same rule.
 int pk_ksplit_p6(const GemmArgs& a) {
   const int64_t tiles = (((a.M + pk::TILE - 1) / pk::TILE + 1) / 2) *
@@ -2110,6 +2206,15 @@ size_t pk_part_bytes(const GemmArgs& a, int tile) {
                  : tile == kTilePackedPair ? (a.math == TC_MATH_BF16X6 ? pk_ksplit_p6(a)
                                                                        : pk_ksplit_p(a))
                  : pk_ksplit(a);
+  if (tile == kTilePackedPair && a.math != TC_MATH_BF16X6) {
+    int64_t nfull = 0;
+    const int ts = pk_tail_split_p(a, &nfull);
+    if (ts > 1) {
+      const int64_t ptiles = (((a.M + pk::TILE - 1) / pk::TILE + 1) / 2) *
+                             (((a.N + pk::TILE - 1) / pk::TILE + 1) / 2);
+      return (size_t)ts * (size_t)(ptiles - nfull) * 4 * pk::TILE * pk::TILE * sizeof(float2);
+    }
+  }
   if (sp <= 1) return 0;
   const int64_t tiles = ((a.M + pk::TILE - 1) / pk::TILE) * ((a.N + pk::TILE - 1) / pk::TILE);
   return (size_t)sp * (size_t)tiles * pk::TILE * pk::TILE * sizeof(float2);

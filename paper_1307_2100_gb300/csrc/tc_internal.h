@@ -169,6 +169,7 @@ PkLayout pk_layout(const GemmArgs& a, int math);
 int pk_ksplit(const GemmArgs& a);
 int pk_ksplit_w(const GemmArgs& a);
 int pk_ksplit_p(const GemmArgs& a);
+int pk_tail_split_p(const GemmArgs& a, int64_t* nfull);
 int pk_ksplit_p6(const GemmArgs& a);
 size_t pk_part_bytes(const GemmArgs& a, int tile);
 // 32-K blocks per ring stage of the packed GEMM for a math form: every
@@ -187,6 +188,12 @@ struct PkItem {
   int32_t tiles_m, tiles_n, nkb, chunk_kb, raster;
   int32_t ksplit;        // K ranges per tile (1: the tile writes C)
   float2* part;          // ksplit > 1: compensated partial sums [split][tile][col][row]
+  // CTA pairs: the tiles of a last, partial round of work entries split K
+  // (tsplit > 1): entries [0, nfull) are whole tiles, then each tail tile
+  // t >= nfull is tsplit entries whose partial sums are
+  // part[split][t - nfull][quarter][col][row]
+  int64_t nfull;
+  int32_t tsplit;
 };
 // Tensor-core route of a batch on packed operands (device tables owned by
 // the batch): the pack entries (item, operand, row tile, 128-K chunk; int32

@@ -301,3 +301,21 @@ def test_bf16x6_pairs_precision_workload_full_size_fp32_class():
     g = gather(got, p.C, s)
     assert np.all(np.isfinite(got))
     assert oracle.rel_fro(g, ref64) <= FP32_CLASS
+
+
+@pytest.mark.parametrize("form", ["bf16", "bf16x3"])
+def test_pairs_tail_split(form):
+    """80 pair tiles of 256 x 256 on 76 pairs: 76 whole tiles write C, the 4
+    tiles of the last round split K in two and a reduction adds their partial
+    sums (aligned and ragged shapes); integer inputs stay exact."""
+    for dims in (dict(a=2560, i=1024, b=2048), dict(a=2500, i=1100, b=2000)):
+        p = f32(ts.problem("tail", "ai", "ib", "ab", dims, 71))
+        plans = []
+        got = run(p, form, "fused_gemm", 5, plan_out=plans)
+        assert plans[0]["tile"] == 5
+        acc, _ = tc_bounds(p, form, single=True)
+        ok, d = within(got, op.contract_form(p, form), magnitude(p), p.C, acc)
+        assert ok, (dims, form, d)
+    q = ts.problem("int", "ai", "ib", "ab", dict(a=2500, i=1100, b=2000), 72, dist="int",
+                   dtype=np.float32, lo=-2, hi=2)
+    np.testing.assert_array_equal(run(q, form, "fused_gemm", 5), oracle.contract_problem(q))
