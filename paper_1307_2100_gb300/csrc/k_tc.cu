@@ -86,8 +86,15 @@ struct Cfg {
 };
 
 // Products (term of A, term of B) of each form; product 0 is the main one.
-__constant__ int8_t kProdA[6] = {0, 0, 1, 0, 1, 2};
-__constant__ int8_t kProdB[6] = {0, 1, 0, 2, 1, 0};
+// Terms of product pi: a_{prod_a(pi)} * b_{prod_b(pi)} (a0 b0; a0 b1, a1 b0;
+// a0 b2, a1 b1, a2 b0).  Compile-time functions, so that the unrolled MMA
+// loops fold them into their descriptor offsets.
+__host__ __device__ constexpr int prod_a(int pi) {
+  return pi == 2 || pi == 4 ? 1 : pi == 5 ? 2 : 0;
+}
+__host__ __device__ constexpr int prod_b(int pi) {
+  return pi == 1 || pi == 4 ? 1 : pi == 3 ? 2 : 0;
+}
 __host__ __device__ constexpr int nprod(int nt) { return nt == 1 ? 1 : nt == 2 ? 3 : 6; }
 
 // Copy one operand's FP32 block (ROWS x BK) into a staging slot.  Operands
@@ -490,8 +497,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
 #pragma unroll
             for (int pi = 1; pi < nprod(NT); ++pi) {
               mma_bf16(tmem + COL_CORR,
-                       smem_desc(sa + kProdA[pi] * G::A_TERM + kk * 2 * LBO_A, LBO_A, 128),
-                       smem_desc(sb + kProdB[pi] * G::B_TERM + kk * 2 * LBO_B, LBO_B, 128),
+                       smem_desc(sa + prod_a(pi) * G::A_TERM + kk * 2 * LBO_A, LBO_A, 128),
+                       smem_desc(sb + prod_b(pi) * G::B_TERM + kk * 2 * LBO_B, LBO_B, 128),
                        idesc, (kb > 0 || kk > 0 || pi > 1) ? 1u : 0u);
             }
           }

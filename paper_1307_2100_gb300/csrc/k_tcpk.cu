@@ -291,8 +291,15 @@ __device__ __forceinline__ Job job_of(const PkLaunch& L, int64_t w) {
   return j;
 }
 
-__constant__ int8_t kProdA[6] = {0, 0, 1, 0, 1, 2};
-__constant__ int8_t kProdB[6] = {0, 1, 0, 2, 1, 0};
+// Terms of product pi: a_{prod_a(pi)} * b_{prod_b(pi)} (a0 b0; a0 b1, a1 b0;
+// a0 b2, a1 b1, a2 b0).  Compile-time functions, so that the unrolled MMA
+// loops fold them into their descriptor offsets.
+__host__ __device__ constexpr int prod_a(int pi) {
+  return pi == 2 || pi == 4 ? 1 : pi == 5 ? 2 : 0;
+}
+__host__ __device__ constexpr int prod_b(int pi) {
+  return pi == 1 || pi == 4 ? 1 : pi == 3 ? 2 : 0;
+}
 __host__ __device__ constexpr int nprod(int nt) { return nt == 1 ? 1 : nt == 2 ? 3 : 6; }
 
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
@@ -463,8 +470,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_pk(const __grid_constant__
 #pragma unroll
                 for (int pi = 1; pi < nprod(NT); ++pi)
                   mma_bf16(tmem + COL_CORR,
-                           smem_desc(sa + kProdA[pi] * TERM + kk * 2 * LBO, LBO, 128),
-                           smem_desc(sb + kProdB[pi] * TERM + kk * 2 * LBO, LBO, 128), idesc,
+                           smem_desc(sa + prod_a(pi) * TERM + kk * 2 * LBO, LBO, 128),
+                           smem_desc(sb + prod_b(pi) * TERM + kk * 2 * LBO, LBO, 128), idesc,
                            (kb > J.k0 || !first || pi > 1) ? 1u : 0u);
               }
             }
@@ -782,13 +789,13 @@ __global__ void __launch_bounds__(kThreadsW, 1) k_gemm_pkw(const __grid_constant
 #pragma unroll
                 for (int pi = 0; pi < nprod(NT); ++pi) {
                   const uint32_t acc = (kb > kstart || bi > 0 || kk > 0 || pi > 0) ? 1u : 0u;
-                  const uint64_t da = smem_desc(sa + kProdA[pi] * TERM + kk * 2 * LBO, LBO, 128);
+                  const uint64_t da = smem_desc(sa + prod_a(pi) * TERM + kk * 2 * LBO, LBO, 128);
                   mma_bf16(dacc, da,
-                           smem_desc(sb0 + kProdB[pi] * TERM + kk * 2 * LBO, LBO, 128), idesc,
+                           smem_desc(sb0 + prod_b(pi) * TERM + kk * 2 * LBO, LBO, 128), idesc,
                            acc);
                   if (J.h1)
                     mma_bf16(dacc + TILE, da,
-                             smem_desc(sb1 + kProdB[pi] * TERM + kk * 2 * LBO, LBO, 128), idesc,
+                             smem_desc(sb1 + prod_b(pi) * TERM + kk * 2 * LBO, LBO, 128), idesc,
                              acc);
                 }
               }
@@ -1105,8 +1112,8 @@ __global__ void __launch_bounds__(kThreadsW, 1) k_gemm_pkp(const __grid_constant
 #pragma unroll
                 for (int pi = 0; pi < nprod(NT); ++pi) {
                   const uint32_t acc = (kb > kstart || bi > 0 || kk > 0 || pi > 0) ? 1u : 0u;
-                  mma_bf16_pair(dacc, smem_desc(sa + kProdA[pi] * TERM + kk * 2 * LBO, LBO, 128),
-                                smem_desc(sb + kProdB[pi] * TERM + kk * 2 * LBO, LBO, 128),
+                  mma_bf16_pair(dacc, smem_desc(sa + prod_a(pi) * TERM + kk * 2 * LBO, LBO, 128),
+                                smem_desc(sb + prod_b(pi) * TERM + kk * 2 * LBO, LBO, 128),
                                 idesc, acc);
                 }
               }
@@ -1399,20 +1406,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_pkp6(const __grid_constant
             tc_fence_after();
             const int nb = min(G::BPS, kend - kb);
             const uint32_t st = sbase + (uint32_t)s * G::STAGE;
-            for (int bi = 0; bi < nb; ++bi) {
-              const uint32_t sa = st + bi * G::OPA;
-              const uint32_t sb = st + G::BPS * G::OPA + bi * G::OPB;
+            // descriptors of the stage's first blocks; every operand of the
+            // stage is a compile-time offset from them (the address field is
+            // the byte address / 16, and shared memory stays below 256 KB)
+            const uint64_t da0 = smem_desc(st, LBOA, 128);
+            const uint64_t db0 = smem_desc(st + G::BPS * G::OPA, LBOB, 128);
+#pragma unroll
+            for (int bi = 0; bi < G::BPS; ++bi) {
+              if (bi >= nb) break;
 #pragma unroll
               for (int kk = 0; kk < BK / 16; ++kk) {
                 const bool first = bi == 0 && kk == 0;
-                mma_bf16_pair(dmain, smem_desc(sa + kk * 2 * LBOA, LBOA, 128),
-                              smem_desc(sb + kk * 2 * LBOB, LBOB, 128), idesc,
+                mma_bf16_pair(dmain, da0 + ((bi * G::OPA + kk * 2 * LBOA) >> 4),
+                              db0 + ((bi * G::OPB + kk * 2 * LBOB) >> 4), idesc,
                               (kb > kstart || !first) ? 1u : 0u);
 #pragma unroll
                 for (int pi = 1; pi < nprod(NT); ++pi)
                   mma_bf16_pair(tmem + COL_CORR,
-                                smem_desc(sa + kProdA[pi] * TERM + kk * 2 * LBOA, LBOA, 128),
-                                smem_desc(sb + kProdB[pi] * G::HTERM + kk * 2 * LBOB, LBOB, 128),
+                                da0 + ((bi * G::OPA + prod_a(pi) * TERM + kk * 2 * LBOA) >> 4),
+                                db0 + ((bi * G::OPB + prod_b(pi) * G::HTERM + kk * 2 * LBOB) >> 4),
                                 idesc, (kb > J.k0 || !first || pi > 1) ? 1u : 0u);
               }
             }
