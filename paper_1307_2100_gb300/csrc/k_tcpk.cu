@@ -1358,11 +1358,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_pkp6(const __grid_constant
             if (va)
               tma_load_2d_pair(dst + bi * G::OPA, &L.tma_a, 0,
                                (int32_t)(((int64_t)tm * P.nkb + kb + bi) * (G::OPA / 2048)), mb);
+            // the NT terms of this CTA's 64-row half of B: 4 NT rows of 2 KB from
+            // x = 1 KB * rank, landing term after term (HTERM apart)
             const int64_t brow = ((int64_t)J.tn * P.nkb + kb + bi) * (NT * TERM / 2048);
-#pragma unroll
-            for (int t = 0; t < NT; ++t)
-              tma_load_2d_pair(dst + G::BPS * G::OPA + bi * G::OPB + t * G::HTERM, &L.tma_b,
-                               (int32_t)(rank * 128), (int32_t)(brow + t * (TERM / 2048)), mb);
+            tma_load_2d_pair(dst + G::BPS * G::OPA + bi * G::OPB, &L.tma_b, (int32_t)(rank * 128),
+                             (int32_t)brow, mb);
           }
         }
       }
@@ -2089,7 +2089,7 @@ tc_status launch_p6(const GemmArgs& a, const PkLayout& L, void* ws, cudaStream_t
   g.out_type = 0;
   g.nwork = ((L.tiles_m + 1) / 2) * L.tiles_n * it.ksplit;
   if (!rows_map(&g.tma_a, it.qa, (size_t)L.tiles_m * L.nkb * CfgP6<NT>::OPA, CfgP6<NT>::OPA) ||
-      !rows_map(&g.tma_b, it.qb, (size_t)L.tiles_n * L.nkb * NT * TERM, 4 * 2048, 128))
+      !rows_map(&g.tma_b, it.qb, (size_t)L.tiles_n * L.nkb * NT * TERM, NT * 4 * 2048, 128))
     return TC_ERR_CUDA;
   const int pairs = (int)std::min<int64_t>(g.nwork, max_pairs);
   cudaLaunchConfig_t cfg = {};
