@@ -442,3 +442,23 @@ def test_fp8_tile_defaults():
         with pytest.raises(tc.TcError) as e:
             plan_info(p, fp8, tile=1, dtype=tc.TC_F32)
         assert e.value.status == 5
+
+
+def test_pair_tail_split_workspace():
+    """CTA pairs (tile 5) split K over the tiles of a last, partial round:
+    the plan's workspace then holds their partial sums on top of the packed
+    operands (which tile 4 needs alone): parts x tail tiles x 4 quarters x
+    128^2 (s, r) pairs of FP32.  80 pair tiles on 76 pairs: 4 tail tiles in
+    2 parts; 76 tiles (a whole number of rounds) and K < 1024 (parts shorter
+    than 512 K) split nothing."""
+    bf16x3 = tc.MATH["bf16x3"]
+
+    def extra(a, i, b):
+        p = ts.problem("tail", "ai", "ib", "ab", dict(a=a, i=i, b=b), 5)
+        w5 = plan_info(p, bf16x3, tile=5, dtype=tc.TC_F32).workspace
+        w4 = plan_info(p, bf16x3, tile=4, dtype=tc.TC_F32).workspace
+        return w5 - w4
+
+    assert extra(2560, 1024, 2048) == 2 * 4 * 4 * 128 * 128 * 8   # 10 x 8 pair tiles
+    assert extra(4864, 1024, 1024) == 0                            # 19 x 4 = 76 pair tiles
+    assert extra(2560, 992, 2048) == 0                             # 31 K blocks: no 2 parts
